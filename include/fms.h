@@ -1,0 +1,178 @@
+/*
+ * fms.h -- C ABI of the GB300 (sm_103a) Faster Mean-shift library.
+ *
+ * Gaussian-kernel mean-shift clustering with the Euclidean metric, after
+ * "GPU-accelerated Faster Mean Shift with euclidean distance metrics"
+ * (arXiv 2112.13891):
+ *   - the update of every seed y is the Gaussian-weighted mean over ALL n
+ *     points, m(y) = sum_j w_j x_j / sum_j w_j, w_j = exp(-||y - x_j||^2/(2h^2))
+ *     (Sec. II-A Eq. 6 and Eq. 9-10 read with the Gaussian profile; Sec. II-B,
+ *     Alg. 2 line 6 and the prose after Eq. 11: no window search);
+ *   - Seed Selection: N = 128 seeds drawn from the points, doubled while
+ *     N < L*M with L = 8 (Alg. 2 line 2, Sec. II-C Eq. 15, Sec. II-D);
+ *   - Early Stopping: iteration ends once ceil(gamma*N) seeds have converged;
+ *     seeds not converged by then are discarded (Sec. II-C);
+ *   - modes are pruned (Alg. 2 line 10) and every point is labelled by its
+ *     nearest mode (Alg. 2 lines 11-13).
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are DEVICE pointers unless marked "host".  Points are
+ *     row-major float32 [n x d], contiguous.  The caller owns every buffer.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is issued on it, in order.
+ *   - Nothing throws across the ABI.  Every call returns an fms_status; device
+ *     detected errors (non-finite input, exhausted capacity, a wait that timed
+ *     out) come back through a status word the call reads before returning.
+ *   - Calls that return host-visible results (counts, stats) synchronise the
+ *     stream once before returning; this is stated per call.
+ *   - Calls on the same device and stream are serialised by the stream; calls
+ *     that share one workspace must not overlap.
+ */
+#ifndef FMS_H
+#define FMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fms_status {
+  FMS_OK = 0,
+  FMS_ERR_INVALID_ARG = 1,  /* a size, pointer or option is out of range          */
+  FMS_ERR_NONFINITE = 2,    /* a point coordinate is NaN or +-inf                  */
+  FMS_ERR_CAPACITY = 3,     /* more modes than max_modes (count still reported)    */
+  FMS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up                       */
+  FMS_ERR_CUDA = 5,         /* a CUDA runtime call failed                          */
+  FMS_ERR_WORKSPACE = 6,    /* workspace too small or misaligned                   */
+  FMS_ERR_UNSUPPORTED = 7   /* dimension or mode not built into this library       */
+} fms_status;
+
+/* Largest point dimension the library accepts. */
+#define FMS_MAX_DIM 64
+
+/*
+ * Options.  A zero-initialised struct selects the defaults shown.
+ */
+typedef struct fms_options {
+  int32_t all_seeds;        /* 0: Seed Selection + Early Stopping (Alg. 2).
+                               1: every point is a seed, gamma = 1, no doubling
+                                  (plain mean shift, Alg. 1).                    */
+  int32_t n_initial;        /* initial seed count N; 0 -> 128 (Sec. II-D)        */
+  float L;                  /* doubling factor: double N while N < L*M; 0 -> 8   */
+  float gamma;              /* Early Stopping fraction in (0, 1]; 0 -> 0.95.
+                               The paper gives no value (Sec. II-C).             */
+  float merge_radius;       /* prune radius in point units; 0 -> h               */
+  int32_t skip_refine;      /* 0: refine every merged mode with FP64-accumulated
+                               updates until the step is <= 1e-5*h (at most 50
+                               updates) and merge again; 1: report the merged
+                               seeds as they are.                                */
+  uint64_t rng_seed;        /* key of the seed permutation (see fms_select_seeds) */
+  const int32_t* seed_indices; /* optional DEVICE list of seed point indices; when
+                               non-NULL it replaces Seed Selection and doubling   */
+  int32_t n_seed_indices;   /* its length                                         */
+  int32_t reserved[7];      /* must be zero                                       */
+} fms_options;
+
+/* Statistics of one clustering call (host struct, filled when non-NULL). */
+typedef struct fms_stats {
+  int32_t iterations;       /* global mean-shift iterations over all rounds       */
+  int32_t rounds;           /* 1 + number of seed doublings                       */
+  int32_t n_seeds_final;    /* N at the end                                       */
+  int32_t n_converged;      /* seeds converged by the final stop iteration        */
+  int32_t n_discarded;      /* seeds dropped by Early Stopping or failed (sum w=0) */
+  int32_t n_kept;           /* seeds that entered the final prune                 */
+  int32_t n_modes;          /* M                                                  */
+  int32_t refine_iterations;/* FP64-accumulated refinement updates                */
+  int32_t t_star_last;      /* stop iteration of the last round                   */
+  int32_t reserved0;
+  int64_t evals;            /* seed-point kernel evaluations in mean-shift updates */
+  int64_t score_evals;      /* evaluations spent on prune scores and refinement   */
+  uint64_t workspace_bytes; /* bytes of workspace the call used                   */
+} fms_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char* fms_strerror(fms_status status);
+
+/* Fill *opt with the explicit default values listed in fms_options. */
+void fms_options_default(fms_options* opt);
+
+/*
+ * Workspace bytes fms_cluster needs for n points of dimension d with the
+ * given options (NULL = defaults).  Returns 0 for invalid sizes.
+ */
+size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt);
+
+/*
+ * Faster Mean-shift clustering (Alg. 2, Sec. II-C/D) or plain mean shift
+ * (Alg. 1, opt->all_seeds = 1) of n points in R^d.
+ *
+ *   points       [n x d] float32, device.  1 <= d <= FMS_MAX_DIM, n >= 1.
+ *   h            Gaussian bandwidth, > 0.
+ *   tol          convergence radius: a seed has converged when one update
+ *                moves it by at most tol (in point units); 0 -> 1e-3*h.
+ *   max_iter     cap on updates per seed (> 0).
+ *   out_modes    [max_modes x d] float32, device: the modes, in canonical
+ *                order (KDE value at the mode descending, ties by coordinates).
+ *   out_n_modes  host int32: M.  If M > max_modes, FMS_ERR_CAPACITY is
+ *                returned, *out_n_modes = M and out_modes holds the first
+ *                max_modes modes; labels are still written.
+ *   out_labels   [n] int32, device: index of the nearest mode (ties -> lowest).
+ *   out_margins  [n] float32, device, nullable: distance to the second-nearest
+ *                mode minus distance to the nearest (+inf when M = 1).
+ *   workspace    device buffer of >= fms_workspace_size(n, d, opt) bytes,
+ *                256-byte aligned; NULL -> the call allocates one with
+ *                cudaMallocAsync on `stream` and frees it before returning.
+ *   stats        host, nullable.
+ * Synchronises `stream` once per seed round and once at the end.
+ */
+fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
+                       int32_t max_iter, const fms_options* opt, float* out_modes,
+                       int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                       float* out_margins, void* workspace, size_t workspace_bytes,
+                       fms_stats* stats, void* stream);
+
+/*
+ * Seed Selection (Alg. 2 line 2): writes entries [start, start+count) of a
+ * keyed pseudo-random permutation pi of [0, n) to out_indices (device int32).
+ * pi(i) applies a balanced 6-round Feistel network on 2*hb bits (4^hb the
+ * smallest power of four >= n, hb >= 1) whose round r XORs the left half with
+ * the low hb bits of mix64(k_r ^ right), and repeats it while the result is
+ * >= n (cycle walking).  mix64 is the SplitMix64 output function and k_r
+ * (r = 0..5) are the first six SplitMix64 outputs of the stream seeded with
+ * rng_seed.  Requires 1 <= n < 2^31, 0 <= start, start+count <= n.
+ * Asynchronous.
+ */
+fms_status fms_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
+                            int32_t* out_indices, void* stream);
+
+/*
+ * One Gaussian mean-shift update of m seeds against all n points (Eq. 6 with
+ * the Gaussian weight; Alg. 2 line 6):
+ *   out_seeds[i] = sum_j w_ij x_j / sum_j w_ij,  w_ij = exp(-||seeds_i - x_j||^2/(2h^2)).
+ *   seeds, out_seeds  [m x d] float32, device (may alias).
+ *   out_wsum     [m] float32, device, nullable: sum_j w_ij.
+ *   workspace    >= fms_step_workspace_size(n, d, m) bytes or NULL (allocated).
+ * Asynchronous unless workspace is NULL.
+ */
+size_t fms_step_workspace_size(int64_t n, int32_t d, int64_t m);
+fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float h,
+                               const float* seeds, int64_t m, float* out_seeds,
+                               float* out_wsum, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
+/*
+ * Nearest-mode labelling (Alg. 2 lines 11-13): labels[j] = argmin_k
+ * ||x_j - modes_k|| (ties -> lowest k) and, if margins is non-NULL,
+ * margins[j] = second-nearest minus nearest distance (+inf when M = 1).
+ * points [n x d], modes [M x d] float32, device; M >= 1.  Asynchronous.
+ */
+fms_status fms_label_points(const float* points, int64_t n, int32_t d, const float* modes,
+                            int32_t M, int32_t* labels, float* margins, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMS_H */

@@ -72,7 +72,9 @@ typedef struct fms_options {
   const int32_t* seed_indices; /* optional DEVICE list of seed point indices; when
                                non-NULL it replaces Seed Selection and doubling   */
   int32_t n_seed_indices;   /* its length                                         */
-  int32_t reserved[7];      /* must be zero                                       */
+  int32_t profile;          /* 1: time every ms_step launch with CUDA events and
+                               report it in fms_stats (adds event records)        */
+  int32_t reserved[6];      /* must be zero                                       */
 } fms_options;
 
 /* Statistics of one clustering call (host struct, filled when non-NULL). */
@@ -90,6 +92,11 @@ typedef struct fms_stats {
   int64_t evals;            /* seed-point kernel evaluations in mean-shift updates */
   int64_t score_evals;      /* evaluations spent on prune scores and refinement   */
   uint64_t workspace_bytes; /* bytes of workspace the call used                   */
+  /* filled when opt->profile = 1 (else zero): */
+  double step_kernel_ms;    /* summed device time of ms_step launches that had work */
+  int32_t step_launches;    /* ms_step launches that had work                     */
+  int32_t reserved1;
+  int64_t step_evals;       /* seed-point evaluations of those launches           */
 } fms_stats;
 
 /* Human-readable name of a status code (static storage). */

@@ -1,0 +1,224 @@
+"""Python binding of the GB300 Faster Mean-shift library (libfms_gb300.so).
+
+Argument marshalling only: every step of the clustering runs in the library's
+CUDA kernels.  Tensors must be CUDA tensors; work is issued on the current
+torch stream.  The library is required -- there is no fallback: importing
+this package raises if ``libfms_gb300.so`` has not been built (run
+``python -m paper_2112_13891_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfms_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python -m paper_2112_13891_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FMS_OK, FMS_ERR_INVALID_ARG, FMS_ERR_NONFINITE, FMS_ERR_CAPACITY = 0, 1, 2, 3
+FMS_ERR_TIMEOUT, FMS_ERR_CUDA, FMS_ERR_WORKSPACE, FMS_ERR_UNSUPPORTED = 4, 5, 6, 7
+MAX_DIM = 64
+
+
+class FmsOptions(ctypes.Structure):
+    _fields_ = [("all_seeds", ctypes.c_int32), ("n_initial", ctypes.c_int32),
+                ("L", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("merge_radius", ctypes.c_float), ("skip_refine", ctypes.c_int32),
+                ("rng_seed", ctypes.c_uint64), ("seed_indices", ctypes.c_void_p),
+                ("n_seed_indices", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class FmsStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("n_seeds_final", ctypes.c_int32), ("n_converged", ctypes.c_int32),
+                ("n_discarded", ctypes.c_int32), ("n_kept", ctypes.c_int32),
+                ("n_modes", ctypes.c_int32), ("refine_iterations", ctypes.c_int32),
+                ("t_star_last", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("evals", ctypes.c_int64), ("score_evals", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_uint64), ("step_kernel_ms", ctypes.c_double),
+                ("step_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("step_evals", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+_P, _I32, _I64, _F32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+
+_lib.fms_strerror.restype = ctypes.c_char_p
+_lib.fms_strerror.argtypes = [ctypes.c_int]
+_lib.fms_options_default.restype = None
+_lib.fms_options_default.argtypes = [ctypes.POINTER(FmsOptions)]
+_lib.fms_workspace_size.restype = _SZ
+_lib.fms_workspace_size.argtypes = [_I64, _I32, ctypes.POINTER(FmsOptions)]
+_lib.fms_cluster.restype = ctypes.c_int
+_lib.fms_cluster.argtypes = [_P, _I64, _I32, _F32, _F32, _I32, ctypes.POINTER(FmsOptions), _P,
+                             _I32, ctypes.POINTER(_I32), _P, _P, _P, _SZ,
+                             ctypes.POINTER(FmsStats), _P]
+_lib.fms_select_seeds.restype = ctypes.c_int
+_lib.fms_select_seeds.argtypes = [_I64, ctypes.c_uint64, _I64, _I64, _P, _P]
+_lib.fms_step_workspace_size.restype = _SZ
+_lib.fms_step_workspace_size.argtypes = [_I64, _I32, _I64]
+_lib.fms_mean_shift_step.restype = ctypes.c_int
+_lib.fms_mean_shift_step.argtypes = [_P, _I64, _I32, _F32, _P, _I64, _P, _P, _P, _SZ, _P]
+_lib.fms_label_points.restype = ctypes.c_int
+_lib.fms_label_points.argtypes = [_P, _I64, _I32, _P, _I32, _P, _P, _P]
+
+
+class FmsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (status {code})")
+
+
+def strerror(code: int) -> str:
+    return _lib.fms_strerror(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != FMS_OK:
+        raise FmsError(code, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _points(x: torch.Tensor) -> torch.Tensor:
+    if not x.is_cuda:
+        raise ValueError("points must be a CUDA tensor")
+    if x.dim() != 2:
+        raise ValueError("points must be [n, d]")
+    return x.to(torch.float32).contiguous()
+
+
+def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
+                 skip_refine=False, rng_seed=0, seed_indices=None, profile=False) -> FmsOptions:
+    o = FmsOptions()
+    _lib.fms_options_default(ctypes.byref(o))
+    o.all_seeds = int(bool(all_seeds))
+    o.n_initial = int(n_initial)
+    o.L = float(L)
+    o.gamma = float(gamma)
+    o.merge_radius = float(merge_radius)
+    o.skip_refine = int(bool(skip_refine))
+    o.rng_seed = int(rng_seed) & ((1 << 64) - 1)
+    if seed_indices is not None:
+        o.seed_indices = seed_indices.data_ptr()
+        o.n_seed_indices = int(seed_indices.numel())
+    o.profile = int(bool(profile))
+    return o
+
+
+def workspace_size(n: int, d: int, **opts) -> int:
+    o = make_options(**opts)
+    return int(_lib.fms_workspace_size(int(n), int(d), ctypes.byref(o)))
+
+
+@dataclass
+class ClusterResult:
+    modes: torch.Tensor        # [M, d] float32, canonical order
+    labels: torch.Tensor       # [n] int32
+    margins: torch.Tensor      # [n] float32 or None
+    stats: dict
+    status: int
+
+
+class Workspace:
+    """A reusable device workspace for repeated calls of the same shape."""
+
+    def __init__(self, nbytes: int, device=None):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+
+    @property
+    def nbytes(self):
+        return self.buf.numel()
+
+
+def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 300, *,
+            all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
+            skip_refine=False, rng_seed=0, seed_indices=None, max_modes=None, margins=True,
+            workspace: Workspace = None, profile=False, out=None) -> ClusterResult:
+    """Faster Mean-shift clustering of the rows of `points` (fms_cluster).
+
+    `out` may pass preallocated (modes [max_modes, d], labels [n], margins [n]).
+    """
+    X = _points(points)
+    n, d = X.shape
+    if seed_indices is not None:
+        seed_indices = seed_indices.to(device=X.device, dtype=torch.int32).contiguous()
+    o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
+                     merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
+                     seed_indices=seed_indices, profile=profile)
+    if out is not None:
+        modes, labels, mar = out
+        cap = modes.shape[0]
+    else:
+        cap = int(max_modes) if max_modes is not None else n
+        modes = torch.empty((max(cap, 1), d), dtype=torch.float32, device=X.device)
+        labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        mar = torch.empty(n, dtype=torch.float32, device=X.device) if margins else None
+    need = int(_lib.fms_workspace_size(n, d, ctypes.byref(o)))
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, X.device)
+    nm = _I32(0)
+    st = FmsStats()
+    code = _lib.fms_cluster(_ptr(X), n, d, float(h), float(tol), int(max_iter), ctypes.byref(o),
+                            _ptr(modes), cap, ctypes.byref(nm), _ptr(labels), _ptr(mar),
+                            _ptr(workspace.buf), workspace.nbytes, ctypes.byref(st), _stream())
+    if code not in (FMS_OK, FMS_ERR_CAPACITY):
+        raise FmsError(code, "fms_cluster")
+    M = nm.value
+    return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar,
+                         stats=st.as_dict(), status=code)
+
+
+def select_seeds(n: int, rng_seed: int, start: int, count: int, device="cuda") -> torch.Tensor:
+    """Entries [start, start+count) of the keyed seed permutation (fms_select_seeds)."""
+    out = torch.empty(max(int(count), 0), dtype=torch.int32, device=device)
+    _check(_lib.fms_select_seeds(int(n), int(rng_seed) & ((1 << 64) - 1), int(start), int(count),
+                                 _ptr(out), _stream()), "fms_select_seeds")
+    return out
+
+
+def mean_shift_step(points: torch.Tensor, seeds: torch.Tensor, h: float, with_wsum=False,
+                    workspace: Workspace = None):
+    """One Gaussian mean-shift update of each row of `seeds` (fms_mean_shift_step)."""
+    X = _points(points)
+    Y = _points(seeds)
+    n, d = X.shape
+    m = Y.shape[0]
+    out = torch.empty_like(Y)
+    wsum = torch.empty(m, dtype=torch.float32, device=X.device) if with_wsum else None
+    need = int(_lib.fms_step_workspace_size(n, d, m))
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, X.device)
+    _check(_lib.fms_mean_shift_step(_ptr(X), n, d, float(h), _ptr(Y), m, _ptr(out), _ptr(wsum),
+                                    _ptr(workspace.buf), workspace.nbytes, _stream()),
+           "fms_mean_shift_step")
+    return (out, wsum) if with_wsum else out
+
+
+def label_points(points: torch.Tensor, modes: torch.Tensor, with_margins=True):
+    """Nearest-mode labels and margins (fms_label_points)."""
+    X = _points(points)
+    Mo = _points(modes)
+    n, d = X.shape
+    labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    mar = torch.empty(n, dtype=torch.float32, device=X.device) if with_margins else None
+    _check(_lib.fms_label_points(_ptr(X), n, d, _ptr(Mo), Mo.shape[0], _ptr(labels), _ptr(mar),
+                                 _stream()), "fms_label_points")
+    return (labels, mar) if with_margins else labels

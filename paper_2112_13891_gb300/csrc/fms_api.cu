@@ -1,0 +1,519 @@
+// C ABI entry points (include/fms.h) and the host-side control of one
+// clustering call.  Every arithmetic step runs in the kernels of k_*.cu; the
+// host only carves the workspace, launches, and reads the small control
+// blocks the device writes (one synchronisation per batch of updates).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/fms.h"
+#include "fms_internal.cuh"
+
+using namespace fms;
+
+namespace {
+
+constexpr int kUpdatesPerBatch = 8;   // updates issued between host checks
+constexpr int kRefineMaxIter = 50;    // refinement cap (updates per mode)
+constexpr double kRefineTolFactor = 1e-5;
+constexpr int kCtasPerSm = 3;         // resident ms_step CTAs per SM (<= 80 registers)
+
+struct Dev {
+  int sms = 0;
+};
+
+Dev device_info() {
+  Dev d;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return d;
+  if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) d.sms = 0;
+  return d;
+}
+
+int padded_dim(int d) {
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  return (d + 3) / 4 * 4;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Workspace carving.  All sizes in bytes, every region 256-byte aligned.
+struct Layout {
+  size_t off_Xs, off_y, off_seed_idx, off_it, off_conv, off_state, off_active, off_kept,
+      off_alive, off_acc1, off_acc2, off_score, off_ym, off_mdone, off_mscore, off_modes_full,
+      off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, total;
+  int DP, DA, R, grid_ctas;
+  int64_t Ncap;
+  Tiling tl;
+};
+
+constexpr int kSlogCap = 4096;
+
+Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
+  Layout L{};
+  L.DP = padded_dim(d);
+  L.DA = step_accumulators(d);
+  L.R = step_seeds_per_warp(d);
+  L.grid_ctas = (sms > 0 ? sms : 1) * kCtasPerSm;
+  L.tl.target_warps = L.grid_ctas * 8;
+  L.tl.min_chunk = 256;
+  L.Ncap = Ncap;
+  const int64_t TW8 = 8LL * L.tl.target_warps;
+  const int64_t Gmax = (Ncap + L.R - 1) / L.R;
+  const size_t part_floats = (size_t)(TW8 + Gmax + 1) * L.R * L.DA;
+  const size_t part64_doubles = (size_t)(TW8 + Ncap + 1) * (d + 1);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes > 0 ? bytes : 1);
+    return at;
+  };
+  L.off_Xs = take((size_t)n * L.DP * 4);
+  L.off_y = take((size_t)Ncap * L.DP * 4);
+  L.off_seed_idx = take((size_t)Ncap * 4);
+  L.off_it = take((size_t)Ncap * 4);
+  L.off_conv = take((size_t)Ncap * 4);
+  L.off_state = take((size_t)Ncap * 4);
+  L.off_active = take((size_t)Ncap * 4);
+  L.off_kept = take((size_t)Ncap * 4);
+  L.off_alive = take((size_t)Ncap * 4);
+  L.off_acc1 = take((size_t)Ncap * 4);
+  L.off_acc2 = take((size_t)Ncap * 4);
+  L.off_score = take((size_t)Ncap * 4);
+  L.off_ym = take((size_t)Ncap * L.DP * 8);
+  L.off_mdone = take((size_t)Ncap * 4);
+  L.off_mscore = take((size_t)Ncap * 8);
+  L.off_modes_full = take((size_t)Ncap * d * 4);
+  L.off_part = take(part_floats * 4);
+  L.off_part64 = take(part64_doubles * 8);
+  L.off_ctl = take(sizeof(IterCtl));
+  L.off_mctl = take(sizeof(MergeCtl));
+  L.off_status = take(64);
+  L.off_slog = take((size_t)kSlogCap * 4);
+  L.total = o;
+  return L;
+}
+
+void fill_defaults(const fms_options* in, fms_options* o) {
+  fms_options_default(o);
+  if (!in) return;
+  o->all_seeds = in->all_seeds;
+  if (in->n_initial > 0) o->n_initial = in->n_initial;
+  if (in->L > 0.0f) o->L = in->L;
+  if (in->gamma > 0.0f) o->gamma = in->gamma;
+  if (in->merge_radius > 0.0f) o->merge_radius = in->merge_radius;
+  o->skip_refine = in->skip_refine;
+  o->rng_seed = in->rng_seed;
+  o->seed_indices = in->seed_indices;
+  o->n_seed_indices = in->n_seed_indices;
+  o->profile = in->profile;
+}
+
+int64_t seed_capacity(int64_t n, const fms_options& o) {
+  if (o.seed_indices) return o.n_seed_indices;
+  return n;
+}
+
+#define FMS_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) {                    \
+      rc = FMS_ERR_CUDA;                        \
+      goto done;                                \
+    }                                           \
+  } while (0)
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fms_strerror(fms_status s) {
+  switch (s) {
+    case FMS_OK: return "ok";
+    case FMS_ERR_INVALID_ARG: return "invalid argument";
+    case FMS_ERR_NONFINITE: return "non-finite point coordinate";
+    case FMS_ERR_CAPACITY: return "more modes than max_modes";
+    case FMS_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case FMS_ERR_CUDA: return "CUDA runtime error";
+    case FMS_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case FMS_ERR_UNSUPPORTED: return "unsupported dimension or mode";
+  }
+  return "unknown status";
+}
+
+void fms_options_default(fms_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->n_initial = 128;
+  o->L = 8.0f;
+  o->gamma = 0.95f;
+  o->merge_radius = 0.0f;
+}
+
+size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt) {
+  if (n < 1 || n > INT32_MAX || d < 1 || d > FMS_MAX_DIM) return 0;
+  fms_options o;
+  fill_defaults(opt, &o);
+  const int64_t Ncap = seed_capacity(n, o);
+  if (Ncap < 1) return 0;
+  return make_layout(n, d, Ncap, device_info().sms).total;
+}
+
+fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
+                       int32_t max_iter, const fms_options* opt_in, float* out_modes,
+                       int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                       float* out_margins, void* workspace, size_t workspace_bytes,
+                       fms_stats* stats, void* stream_) {
+  fms_status rc = FMS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  fms_options o;
+  fill_defaults(opt_in, &o);
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!points || !out_labels || !out_n_modes || n < 1 || n > INT32_MAX || d < 1 ||
+      d > FMS_MAX_DIM || !(h > 0.0f) || !isfinite(h) || !(tol >= 0.0f) || !isfinite(tol) ||
+      max_iter < 1 || max_modes < 0 || (max_modes > 0 && !out_modes) ||
+      !(o.gamma > 0.0f && o.gamma <= 1.0f) || !(o.L > 0.0f) || !isfinite(o.merge_radius) ||
+      o.merge_radius < 0.0f || (o.seed_indices && o.n_seed_indices < 1))
+    return FMS_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i)
+    if (o.reserved[i] != 0) return FMS_ERR_INVALID_ARG;
+  if (tol == 0.0f) tol = 1e-3f * h;
+  if (o.all_seeds) o.gamma = 1.0f;
+
+  const Dev dv = device_info();
+  if (dv.sms <= 0) return FMS_ERR_CUDA;
+  const int64_t Ncap = seed_capacity(n, o);
+  const Layout Lo = make_layout(n, d, Ncap, dv.sms);
+  const int DP = Lo.DP, DA = Lo.DA, R = Lo.R;
+  bool owns_ws = false;
+  void* ws = workspace;
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_slot;
+  IterCtl hctl{};
+  MergeCtl hm{};
+  uint32_t hstatus = 0;
+  int32_t N = 0, rounds = 0, Mfinal = 0, K_last = 0;
+
+  if (ws) {
+    if (workspace_bytes < Lo.total || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+      return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, Lo.total, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns_ws = true;
+  }
+  {
+    float* Xs = at<float>(ws, Lo.off_Xs);
+    float* y = at<float>(ws, Lo.off_y);
+    int32_t* seed_idx = at<int32_t>(ws, Lo.off_seed_idx);
+    int32_t* it = at<int32_t>(ws, Lo.off_it);
+    int32_t* conv = at<int32_t>(ws, Lo.off_conv);
+    int32_t* state = at<int32_t>(ws, Lo.off_state);
+    int32_t* active = at<int32_t>(ws, Lo.off_active);
+    int32_t* kept = at<int32_t>(ws, Lo.off_kept);
+    int32_t* alive = at<int32_t>(ws, Lo.off_alive);
+    int32_t* acc1 = at<int32_t>(ws, Lo.off_acc1);
+    int32_t* acc2 = at<int32_t>(ws, Lo.off_acc2);
+    float* score = at<float>(ws, Lo.off_score);
+    double* ym = at<double>(ws, Lo.off_ym);
+    int32_t* mdone = at<int32_t>(ws, Lo.off_mdone);
+    double* mscore = at<double>(ws, Lo.off_mscore);
+    float* modes_full = at<float>(ws, Lo.off_modes_full);
+    float* part = at<float>(ws, Lo.off_part);
+    double* part64 = at<double>(ws, Lo.off_part64);
+    IterCtl* ctl = at<IterCtl>(ws, Lo.off_ctl);
+    MergeCtl* mctl = at<MergeCtl>(ws, Lo.off_mctl);
+    uint32_t* status = at<uint32_t>(ws, Lo.off_status);
+    int32_t* slog = at<int32_t>(ws, Lo.off_slog);
+
+    const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    const double tol_s = (double)tol * scale;
+    const float tol2_s = (float)(tol_s * tol_s);
+    const double r_merge = o.merge_radius > 0.0f ? (double)o.merge_radius : (double)h;
+    const double r2_s = (r_merge * scale) * (r_merge * scale);
+    const bool allow_doubling = !o.all_seeds && !o.seed_indices;
+    const int update_grid = dv.sms * 8;
+    int n_slog = 0;
+
+    auto step_launch = [&](const int32_t* list, const int32_t* s_ptr, const int32_t* C_ptr,
+                           const int32_t* Lc_ptr) -> cudaError_t {
+      int32_t* lg = nullptr;
+      if (o.profile && n_slog < kSlogCap) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+          return cudaErrorUnknown;
+        cudaEventRecord(a, st);
+        lg = slog + n_slog;
+        cudaError_t e = launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part,
+                                       Lo.grid_ctas, st, lg);
+        cudaEventRecord(b, st);
+        evs.push_back(a);
+        evs.push_back(b);
+        ev_slot.push_back(n_slog++);
+        return e;
+      }
+      return launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part, Lo.grid_ctas, st,
+                            nullptr);
+    };
+
+    FMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IterCtl), st));
+    FMS_CUDA(cudaMemsetAsync(mctl, 0, sizeof(MergeCtl), st));
+    FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
+    FMS_CUDA(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
+
+    // --- Seed Selection (Alg. 2 line 2) ---
+    if (o.all_seeds) N = (int32_t)n;
+    else if (o.seed_indices) N = o.n_seed_indices;
+    else N = (int32_t)(o.n_initial < n ? o.n_initial : n);
+    FMS_CUDA(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y, it,
+                              conv, state, status, st));
+
+    for (;;) {
+      ++rounds;
+      int target = (int)ceil((double)o.gamma * (double)N);
+      if (target < 1) target = 1;
+      if (target > N) target = N;
+      // --- mean-shift iterations under Early Stopping (Sec. II-C) ---
+      FMS_CUDA(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
+                                 st));
+      for (;;) {
+        for (int b = 0; b < kUpdatesPerBatch; ++b) {
+          FMS_CUDA(step_launch(active, &ctl->s, &ctl->C, &ctl->Lc));
+          FMS_CUDA(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
+                                 max_iter, st, update_grid));
+          FMS_CUDA(launch_compact(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
+                                  st));
+        }
+        FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+        FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+        FMS_CUDA(cudaStreamSynchronize(st));
+        if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
+        if (hctl.done) break;
+      }
+      // --- prune (Alg. 2 line 10) ---
+      FMS_CUDA(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
+                                Lo.tl, st));
+      FMS_CUDA(step_launch(kept, &mctl->K, &mctl->C, &mctl->Lc));
+      FMS_CUDA(launch_score_reduce(part, mctl, DA, score, N, st));
+      FMS_CUDA(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
+                                     &mctl->M, st));
+      // --- seed-count control (Sec. II-D) ---
+      FMS_CUDA(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
+      FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
+      FMS_CUDA(cudaStreamSynchronize(st));
+      K_last = hm.K;
+      if (hm.next_N > N) {
+        FMS_CUDA(launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, N, N, hm.next_N - N, seed_idx,
+                                  y, it, conv, state, status, st));
+        N = hm.next_N;
+        continue;
+      }
+      break;
+    }
+
+    // --- refinement and second prune ---
+    if (!o.skip_refine && hm.M > 0) {
+      FMS_CUDA(launch_refine_init(y, kept, acc1, mctl, DP, ym, mdone, n, Lo.tl, hm.M, st));
+      const double rtol_s = kRefineTolFactor * (double)h * scale;
+      int iters = 0;
+      while (iters < kRefineMaxIter) {
+        const int b = kRefineMaxIter - iters < kUpdatesPerBatch ? kRefineMaxIter - iters
+                                                                 : kUpdatesPerBatch;
+        for (int i = 0; i < b; ++i) {
+          FMS_CUDA(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
+          FMS_CUDA(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, rtol_s * rtol_s,
+                                        0, hm.M, st));
+        }
+        iters += b;
+        FMS_CUDA(launch_refine_count(mctl, mdone, st));
+        FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
+        FMS_CUDA(cudaStreamSynchronize(st));
+        if (hm.refine_active == 0) break;
+      }
+      // density at the refined modes (FP64-accumulated), for the second prune
+      FMS_CUDA(cudaMemsetAsync(mdone, 0, (size_t)hm.M * 4, st));
+      FMS_CUDA(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
+      FMS_CUDA(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, 0.0, 1, hm.M, st));
+      FMS_CUDA(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
+                                     st));
+      FMS_CUDA(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale, out_modes,
+                                      max_modes, modes_full, nullptr, hm.M, st));
+    } else {
+      FMS_CUDA(launch_unrefined_modes(y, kept, acc1, score, mctl, DP, ym, mscore, hm.M, st));
+      FMS_CUDA(cudaMemcpyAsync(&mctl->Mr, &mctl->M, 4, cudaMemcpyDeviceToDevice, st));
+      FMS_CUDA(launch_canonical_order(ym, mscore, nullptr, &mctl->Mr, d, DP, 1.0 / scale,
+                                      out_modes, max_modes, modes_full, nullptr, hm.M, st));
+    }
+    // --- labels (Alg. 2 lines 11-13) ---
+    FMS_CUDA(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
+    FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
+    FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+    FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> hslog(n_slog);
+    if (n_slog > 0)
+      FMS_CUDA(cudaMemcpyAsync(hslog.data(), slog, (size_t)n_slog * 4, cudaMemcpyDeviceToHost, st));
+    FMS_CUDA(cudaStreamSynchronize(st));
+    Mfinal = hm.Mr;
+    *out_n_modes = Mfinal;
+    if (hstatus & kStNonFinite) goto device_error;
+    if (hstatus & kStBadArg) goto device_error;
+    if (Mfinal > max_modes) rc = FMS_ERR_CAPACITY;
+    if (stats) {
+      stats->iterations = hctl.steps;
+      stats->rounds = rounds;
+      stats->n_seeds_final = N;
+      stats->n_converged = hctl.n_converged;
+      stats->n_kept = K_last;
+      stats->n_discarded = N - K_last;
+      stats->n_modes = Mfinal;
+      stats->refine_iterations = hm.refine_iters;
+      stats->t_star_last = hm.t_star;
+      stats->evals = hctl.evals;
+      stats->score_evals = hm.evals;
+      stats->workspace_bytes = Lo.total;
+      if (o.profile) {
+        double ms = 0.0;
+        int launches = 0;
+        int64_t ev = 0;
+        for (size_t i = 0; i < ev_slot.size(); ++i) {
+          const int s_i = hslog[ev_slot[i]];
+          if (s_i <= 0) continue;
+          float t = 0.0f;
+          cudaEventElapsedTime(&t, evs[2 * i], evs[2 * i + 1]);
+          ms += t;
+          ++launches;
+          ev += (int64_t)s_i * n;
+        }
+        stats->step_kernel_ms = ms;
+        stats->step_launches = launches;
+        stats->step_evals = ev;
+      }
+    }
+    goto done;
+  }
+device_error:
+  if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+  else rc = FMS_ERR_INVALID_ARG;
+done:
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  if (owns_ws) {
+    cudaFreeAsync(ws, st);
+    if (rc == FMS_OK || rc == FMS_ERR_CAPACITY) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) rc = FMS_ERR_CUDA;
+    }
+  }
+  return rc;
+}
+
+fms_status fms_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
+                            int32_t* out_indices, void* stream) {
+  if (n < 1 || n > INT32_MAX || start < 0 || count < 0 || start + count > n ||
+      (count > 0 && !out_indices))
+    return FMS_ERR_INVALID_ARG;
+  if (launch_select_seeds(n, rng_seed, start, count, out_indices,
+                          static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  return FMS_OK;
+}
+
+namespace {
+struct StepLayout {
+  size_t off_Xs, off_Ys, off_active, off_part, off_ctl, off_status, total;
+  int DP, DA, R, grid_ctas, C, Lc;
+};
+
+StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
+  StepLayout L{};
+  L.DP = padded_dim(d);
+  L.DA = step_accumulators(d);
+  L.R = step_seeds_per_warp(d);
+  L.grid_ctas = (sms > 0 ? sms : 1) * kCtasPerSm;
+  Tiling tl{L.grid_ctas * 8, 256};
+  choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = o;
+    o += align256(bytes > 0 ? bytes : 1);
+    return at_;
+  };
+  L.off_Xs = take((size_t)n * L.DP * 4);
+  L.off_Ys = take((size_t)m * L.DP * 4);
+  L.off_active = take((size_t)m * 4);
+  L.off_part = take((size_t)L.C * (size_t)m * L.DA * 4);
+  L.off_ctl = take(sizeof(IterCtl));
+  L.off_status = take(64);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t fms_step_workspace_size(int64_t n, int32_t d, int64_t m) {
+  if (n < 1 || n > INT32_MAX || d < 1 || d > FMS_MAX_DIM || m < 1 || m > INT32_MAX) return 0;
+  return step_layout(n, d, m, device_info().sms).total;
+}
+
+fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float h,
+                               const float* seeds, int64_t m, float* out_seeds, float* out_wsum,
+                               void* workspace, size_t workspace_bytes, void* stream_) {
+  if (!points || !seeds || !out_seeds || n < 1 || n > INT32_MAX || d < 1 || d > FMS_MAX_DIM ||
+      m < 1 || m > INT32_MAX || !(h > 0.0f) || !isfinite(h))
+    return FMS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const Dev dv = device_info();
+  if (dv.sms <= 0) return FMS_ERR_CUDA;
+  const StepLayout L = step_layout(n, d, m, dv.sms);
+  fms_status rc = FMS_OK;
+  bool owns = false;
+  void* ws = workspace;
+  uint32_t hstatus = 0;
+  if (ws) {
+    if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+      return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns = true;
+  }
+  {
+    const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    float* Xs = at<float>(ws, L.off_Xs);
+    float* Ys = at<float>(ws, L.off_Ys);
+    int32_t* active = at<int32_t>(ws, L.off_active);
+    float* part = at<float>(ws, L.off_part);
+    IterCtl* ctl = at<IterCtl>(ws, L.off_ctl);
+    uint32_t* status = at<uint32_t>(ws, L.off_status);
+    FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
+    FMS_CUDA(launch_pack_points(points, n, d, L.DP, (float)scale, Xs, status, st));
+    FMS_CUDA(launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st));
+    FMS_CUDA(launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st));
+    FMS_CUDA(launch_ms_step(Xs, n, d, L.DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
+                            L.grid_ctas, st, nullptr));
+    FMS_CUDA(launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum,
+                                (int)m, st));
+    if (owns) {
+      FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+      FMS_CUDA(cudaStreamSynchronize(st));
+      if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+    }
+  }
+done:
+  if (owns) cudaFreeAsync(ws, st);
+  return rc;
+}
+
+fms_status fms_label_points(const float* points, int64_t n, int32_t d, const float* modes,
+                            int32_t M, int32_t* labels, float* margins, void* stream) {
+  if (!points || !modes || !labels || n < 1 || d < 1 || d > FMS_MAX_DIM || M < 1)
+    return FMS_ERR_INVALID_ARG;
+  if (launch_label(points, n, d, modes, nullptr, M, labels, margins,
+                   static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  return FMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Internal declarations shared by the CUDA translation units of the library.
+//
+// Layout conventions on the device (all in the caller's workspace):
+//   Xs      [n][DP] float   points pre-scaled by s = sqrt(log2(e) / (2 h^2)), so
+//                           that the Gaussian weight exp(-||y-x||^2/(2h^2)) is
+//                           exp2(-||ys - xs||^2); padded to DP floats per row
+//                           (DP = 4 for d <= 4, 8 for d <= 8, else d rounded
+//                           up to a multiple of 4), pad lanes are 0.
+//   seeds   slot i = rank i in the seed sequence: point index, scaled position
+//           y[i][DP], updates done it[i], convergence update conv[i] (-1 if
+//           none) and state[i] (RUNNING / CONVERGED / FAILED / EXHAUSTED).
+//   active  the seed slots that take the next update, in slot order.
+//   part    per-(chunk, active position) partial sums [C][s][DA] float:
+//           DA accumulators per seed = (sum w, sum w*(x-y)_0..d-1, pad).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fms {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+#define FMS_MAX_DIM_PAD 64
+
+// device status bits (OR-ed into the status word)
+enum : uint32_t {
+  kStNonFinite = 1u,
+  kStTimeout = 2u,
+  kStCapacity = 4u,
+  kStBadArg = 8u,
+};
+
+// per-seed state
+enum : int32_t { kRunning = 0, kConverged = 1, kFailed = 2, kExhausted = 3 };
+
+// Control block of one iteration loop, written by the device.
+struct IterCtl {
+  int32_t s;          // active seeds in the next update
+  int32_t C;          // point chunks of the next update
+  int32_t Lc;         // points per chunk (multiple of 32)
+  int32_t r;          // global updates completed in this round
+  int32_t done;       // 1: the round has stopped
+  int32_t N;          // seeds in play (slots [0, N))
+  int32_t target;     // ceil(gamma * N): converged seeds needed to stop
+  int32_t max_iter;
+  int32_t n_converged;
+  int32_t n_failed;
+  int32_t n_exhausted;
+  int32_t steps;      // updates that had at least one active seed
+  int64_t evals;      // seed-point evaluations issued
+};
+
+// Control block of the prune / refine phase.
+struct MergeCtl {
+  int32_t K;              // candidates of the prune (kept seeds)
+  int32_t C;              // chunks of the score pass over the candidates
+  int32_t Lc;
+  int32_t M;              // modes accepted by the prune
+  int32_t next_N;         // N of the next round (== N when not doubling)
+  int32_t t_star;         // stop update of the round
+  int32_t Mr;             // modes after refinement and the second prune
+  int32_t Cr;             // chunks of a refinement pass (one mode per warp task)
+  int32_t Lcr;
+  int32_t refine_active;  // modes still moving
+  int32_t refine_iters;
+  int32_t pad0;
+  int64_t evals;          // evaluations of prune scores and refinement
+};
+
+// Tiling of a (seed-group x point-chunk) warp-task grid.
+struct Tiling {
+  int32_t target_warps;   // warps the step grid runs (gridDim.x * warps per CTA)
+  int32_t min_chunk;      // smallest chunk in points (multiple of 32)
+};
+
+// Chunk count and length for s active seeds of R per warp over n points.
+__host__ __device__ inline void choose_chunks(int64_t n, int32_t s, int32_t R, Tiling t,
+                                              int32_t* C, int32_t* Lc) {
+  if (s <= 0) {
+    *C = 0;
+    *Lc = 0;
+    return;
+  }
+  int64_t G = (s + R - 1) / R;
+  int64_t want = (8LL * t.target_warps + G - 1) / G;
+  int64_t cmax = (n + t.min_chunk - 1) / t.min_chunk;
+  if (cmax < 1) cmax = 1;
+  int64_t c = want < 1 ? 1 : want;
+  if (c > cmax) c = cmax;
+  int64_t lc = (n + c - 1) / c;
+  lc = (lc + 31) / 32 * 32;
+  c = (n + lc - 1) / lc;
+  *C = (int32_t)c;
+  *Lc = (int32_t)lc;
+}
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Block-wide helpers (every thread of the block must call them).
+__device__ inline int block_exclusive_scan(int v, int* total, int* warp_sums) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sums[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  const int before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+  *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__device__ inline int block_sum(int v, int* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int t = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+__device__ inline int block_min(int v, int* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int t = INT32_MAX;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = min(t, red[i]);
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (host functions defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+// k_iter.cu
+cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
+                               uint32_t* status, cudaStream_t st);
+cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
+                             const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
+                             int32_t count, int32_t* seed_idx, float* y, int32_t* it,
+                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st);
+cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
+                                int32_t* out, cudaStream_t st);
+cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
+                              const int32_t* conv, int32_t* active, int64_t n, int32_t R,
+                              Tiling tl, int N, int target, int max_iter, cudaStream_t st);
+cudaError_t launch_update(const float* part, const int32_t* active, IterCtl* ctl, float* y,
+                          int32_t* it, int32_t* conv, int32_t* state, int d, int DP, int DA,
+                          float tol2_s, int max_iter, cudaStream_t st, int grid);
+cudaError_t launch_compact(IterCtl* ctl, const int32_t* state, const int32_t* it,
+                           const int32_t* conv, int32_t* active, int64_t n, int32_t R, Tiling tl,
+                           int N, int target, int max_iter, cudaStream_t st);
+
+cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
+                              cudaStream_t st);
+cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
+                               int DA, double inv_scale, float* out_seeds, float* out_wsum,
+                               int m, cudaStream_t st);
+
+// k_step.cu: one update's partial sums for the active seeds
+cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
+                           const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
+                           const int32_t* Lc_ptr, float* part, int grid_ctas,
+                           cudaStream_t st, int32_t* s_log = nullptr);
+int step_seeds_per_warp(int d);
+int step_accumulators(int d);
+
+// k_merge.cu
+cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int32_t* conv,
+                             int keep_exhausted, int32_t* kept, MergeCtl* mctl, int64_t n,
+                             int32_t R, Tiling tl, cudaStream_t st);
+cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA, float* score,
+                                int max_K, cudaStream_t st);
+cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
+                                  const float* score, const float* pos, int DP, int d, float r2,
+                                  int32_t* alive, int32_t* accepted, int32_t* M_out,
+                                  cudaStream_t st);
+cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
+                                  int DP, int d, double r2, int32_t* alive, int32_t* accepted,
+                                  int32_t* M_out, cudaStream_t st);
+cudaError_t launch_doubling_decision(MergeCtl* mctl, int32_t N, int64_t n, float L, int allow,
+                                     cudaStream_t st);
+cudaError_t launch_refine_init(const float* y, const int32_t* kept, const int32_t* accepted,
+                               MergeCtl* mctl, int DP, double* ym, int32_t* mdone, int64_t n,
+                               Tiling tl, int max_M, cudaStream_t st);
+cudaError_t launch_refine_step(const float* Xs, int64_t n, int d, int DP, const double* ym,
+                               const int32_t* mdone, const MergeCtl* mctl, double* part64,
+                               int grid_ctas, cudaStream_t st);
+cudaError_t launch_refine_update(const double* part64, MergeCtl* mctl, double* ym,
+                                 int32_t* mdone, double* mscore, int d, int DP, double tol2_s,
+                                 int score_only, int max_M, cudaStream_t st);
+cudaError_t launch_refine_count(MergeCtl* mctl, const int32_t* mdone, cudaStream_t st);
+cudaError_t launch_canonical_order(const double* ym, const double* mscore,
+                                   const int32_t* accepted, const int32_t* M_ptr, int d, int DP,
+                                   double inv_scale, float* out_modes, int32_t max_modes,
+                                   float* modes_full, float* out_scores, int max_M,
+                                   cudaStream_t st);
+cudaError_t launch_unrefined_modes(const float* y, const int32_t* kept, const int32_t* accepted,
+                                   const float* score, const MergeCtl* mctl, int DP, double* ym,
+                                   double* mscore, int max_M, cudaStream_t st);
+cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
+                         const int32_t* M_dev, int32_t M_host, int32_t* labels, float* margins,
+                         cudaStream_t st);
+
+}  // namespace fms

@@ -1,0 +1,415 @@
+// Point packing, Seed Selection, the per-update seed update and the
+// Early-Stopping bookkeeping that compacts the active set.
+#include "fms_internal.cuh"
+
+namespace fms {
+
+// ---------------------------------------------------------------------------
+// Packing: Xs = s * X, padded to DP floats per row; flags non-finite input.
+// ---------------------------------------------------------------------------
+__global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d, int DP,
+                                   float scale, float* __restrict__ Xs, uint32_t* status) {
+  const int64_t total = n * DP;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / DP;
+    const int k = (int)(e - j * DP);
+    float v = 0.0f;
+    if (k < d) {
+      v = X[j * d + k];
+      if (!isfinite(v)) bad = true;
+      v *= scale;
+    }
+    Xs[e] = v;
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStNonFinite);
+}
+
+cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
+                               uint32_t* status, cudaStream_t st) {
+  int64_t total = n * DP;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  pack_points_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Seed Selection (Alg. 2 line 2): entry r of a keyed permutation of [0, n).
+// A balanced Feistel network on 2*hb bits, cycle-walked into [0, n).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct FeistelKey {
+  uint64_t k[6];
+  int hb;
+};
+
+static FeistelKey make_key(int64_t n, uint64_t rng_seed) {
+  FeistelKey f;
+  for (int r = 0; r < 6; ++r) f.k[r] = mix64(rng_seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
+  int hb = 1;
+  while ((int64_t(1) << (2 * hb)) < n) ++hb;
+  f.hb = hb;
+  return f;
+}
+
+__device__ __forceinline__ uint64_t feistel(uint64_t x, const FeistelKey& f) {
+  const uint64_t mask = (uint64_t(1) << f.hb) - 1;
+  uint64_t L = x >> f.hb, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    const uint64_t nl = R;
+    R = L ^ (mix64(f.k[r] ^ R) & mask);
+    L = nl;
+  }
+  return (L << f.hb) | R;
+}
+
+__device__ __forceinline__ int64_t permute(int64_t r, int64_t n, const FeistelKey& f) {
+  uint64_t x = feistel((uint64_t)r, f);
+  // cycle walking: the walk stays on r's cycle of the bijection of [0, 4^hb)
+  // and that cycle contains r < n, so it ends within 4^hb steps
+  while (x >= (uint64_t)n) x = feistel(x, f);
+  return (int64_t)x;
+}
+
+__global__ void select_seeds_kernel(int64_t n, FeistelKey f, int64_t start, int64_t count,
+                                    int32_t* __restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (int32_t)permute(start + t, n, f);
+}
+
+cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
+                                int32_t* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const FeistelKey f = make_key(n, rng_seed);
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  select_seeds_kernel<<<(int)blocks, 256, 0, st>>>(n, f, start, count, out);
+  return cudaGetLastError();
+}
+
+// Initialise seed slots [slot0, slot0+count): point index from the explicit
+// list or the permutation (rank0 + t), position Xs[idx], state RUNNING.
+__global__ void seed_init_kernel(const float* __restrict__ Xs, int64_t n, int DP, FeistelKey f,
+                                 const int32_t* __restrict__ explicit_idx, int64_t rank0,
+                                 int32_t slot0, int32_t count, int32_t* __restrict__ seed_idx,
+                                 float* __restrict__ y, int32_t* __restrict__ it,
+                                 int32_t* __restrict__ conv, int32_t* __restrict__ state,
+                                 uint32_t* status) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    int64_t idx;
+    if (explicit_idx) {
+      idx = explicit_idx[t];
+      if (idx < 0 || idx >= n) {
+        atomicOr(status, kStBadArg);
+        idx = 0;
+      }
+    } else {
+      idx = permute(rank0 + t, n, f);
+    }
+    const int64_t slot = slot0 + t;
+    seed_idx[slot] = (int32_t)idx;
+    for (int k = 0; k < DP; ++k) y[slot * DP + k] = Xs[idx * DP + k];
+    it[slot] = 0;
+    conv[slot] = -1;
+    state[slot] = kRunning;
+  }
+}
+
+cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
+                             const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
+                             int32_t count, int32_t* seed_idx, float* y, int32_t* it,
+                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const FeistelKey f = make_key(n, rng_seed);
+  int blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  seed_init_kernel<<<blocks, 256, 0, st>>>(Xs, n, DP, f, explicit_idx, rank0, slot0, count,
+                                           seed_idx, y, it, conv, state, status);
+  return cudaGetLastError();
+}
+
+// Cross-chunk sum of the partials of active position p: lane l sums chunks
+// l, l+32, ... in chunk order for every accumulator, then a fixed xor tree
+// combines the 32 lane sums.  On return lane k holds accumulator k (W for
+// k = 0, S_{k-1} otherwise) in a[k >> 5], for k <= d.
+__device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, int s, int p, int C,
+                                              int DA, int d, int lane, float (&a)[3]) {
+  for (int k0 = 0; k0 <= d; k0 += 4) {
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    for (int c = lane; c < C; c += 32) {
+      const float* q = part + ((int64_t)c * s + p) * DA + k0;
+      v0 += q[0];
+      if (k0 + 1 <= d) v1 += q[1];
+      if (k0 + 2 <= d) v2 += q[2];
+      if (k0 + 3 <= d) v3 += q[3];
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      v0 += __shfl_xor_sync(kFull, v0, o);
+      v1 += __shfl_xor_sync(kFull, v1, o);
+      v2 += __shfl_xor_sync(kFull, v2, o);
+      v3 += __shfl_xor_sync(kFull, v3, o);
+    }
+    const float vals[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = k0 + e;
+      if (k <= d && (k & 31) == lane) a[k >> 5] = vals[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seed update: y <- y + S/W for every active seed; convergence test; state.
+// One warp per active position.
+// ---------------------------------------------------------------------------
+__global__ void update_kernel(const float* __restrict__ part, const int32_t* __restrict__ active,
+                              const IterCtl* __restrict__ ctl, float* __restrict__ y,
+                              int32_t* __restrict__ it, int32_t* __restrict__ conv,
+                              int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s,
+                              int max_iter) {
+  const int s = ctl->s;
+  if (s <= 0) return;
+  const int C = ctl->C;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
+    const int64_t slot = active[p];
+    // lane l sums chunks l, l+32, ... (chunk order) for every accumulator; a
+    // fixed xor tree then combines the 32 lane sums.  Accumulator k ends up in
+    // every lane; lane k keeps W (k = 0) or S_{k-1}.
+    float a[3] = {0.f, 0.f, 0.f};
+    reduce_chunks(part, s, p, C, DA, d, lane, a);
+    const float W = __shfl_sync(kFull, a[0], 0);
+    float step2 = 0.0f;
+    float delta[3] = {0.f, 0.f, 0.f};
+    const bool ok = (W > 0.0f) && isfinite(W);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;  // accumulator index; coordinate k-1
+      if (ok && k >= 1 && k <= d) {
+        delta[u] = a[u] / W;
+        step2 = fmaf(delta[u], delta[u], step2);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
+    const bool finite = ok && isfinite(step2);
+    if (finite) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) y[slot * DP + (k - 1)] += delta[u];
+      }
+    }
+    if (lane == 0) {
+      const int t = it[slot] + 1;
+      it[slot] = t;
+      if (!finite) {
+        state[slot] = kFailed;
+      } else if (step2 <= tol2_s) {
+        state[slot] = kConverged;
+        conv[slot] = t;
+      } else if (t >= max_iter) {
+        state[slot] = kExhausted;
+      }
+    }
+  }
+}
+
+cudaError_t launch_update(const float* part, const int32_t* active, IterCtl* ctl, float* y,
+                          int32_t* it, int32_t* conv, int32_t* state, int d, int DP, int DA,
+                          float tol2_s, int max_iter, cudaStream_t st, int grid) {
+  update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
+                                      max_iter);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Early Stopping bookkeeping (Sec. II-C), one CTA of 1024 threads.
+//
+// The clock r counts updates.  A seed takes update r+1 when it is RUNNING and
+// has made exactly r updates, so seeds added by a doubling start at 0 while
+// seeds left unconverged by an earlier round wait until the clock reaches
+// their count: the round then behaves exactly like a fresh run over all N
+// seeds.  After each update the kernel counts the seeds whose convergence
+// update is <= r and stops the round once that count reaches
+// target = ceil(gamma*N), when no seed is RUNNING, or at max_iter.
+// When no seed is due at r but the round goes on, the clock jumps to the next
+// event (a waiting seed's count or a convergence update of an earlier round).
+// ---------------------------------------------------------------------------
+constexpr int kCompactThreads = 1024;
+
+// Scan at clock r: writes the active list, returns (via smem) its size, the
+// count of seeds converged by r, the number still RUNNING and the next event.
+__device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
+                           const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
+                           int32_t* __restrict__ active, int* s_out, int* conv_out,
+                           int* running_out, int* next_event_out, int* scratch) {
+  int base = 0, convd = 0, running = 0, nxt = INT32_MAX;
+  for (int b = 0; b < N; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    int take = 0;
+    if (i < N) {
+      const int stt = state[i];
+      const int ti = it[i];
+      if (stt == kRunning) {
+        ++running;
+        if (ti == r) take = 1;
+        else if (ti > r) nxt = min(nxt, ti);
+      } else if (stt == kConverged) {
+        const int ci = conv[i];
+        if (ci <= r) ++convd;
+        else nxt = min(nxt, ci);
+      }
+    }
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) active[base + off] = i;
+    base += tot;
+  }
+  convd = block_sum(convd, scratch);
+  running = block_sum(running, scratch);
+  nxt = block_min(nxt, scratch);
+  *s_out = base;
+  *conv_out = convd;
+  *running_out = running;
+  *next_event_out = nxt;
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    compact_kernel(IterCtl* ctl, const int32_t* __restrict__ state, const int32_t* __restrict__ it,
+                   const int32_t* __restrict__ conv, int32_t* __restrict__ active, int64_t n,
+                   int32_t R, Tiling tl, int begin, int N, int target, int max_iter) {
+  __shared__ int scratch[64];
+  __shared__ int sh_done;
+  if (!begin && ctl->done) return;
+  int r = begin ? 0 : ctl->r + 1;
+  const int prev_s = begin ? 0 : ctl->s;
+  int s = 0, convd = 0, running = 0, nxt = 0;
+  int done = 0;
+  for (int guard = 0; guard <= max_iter + 2; ++guard) {
+    scan_clock(r, N, state, it, conv, active, &s, &convd, &running, &nxt, scratch);
+    done = (convd >= target) || (r >= max_iter);
+    if (!done && s == 0) {
+      // nothing is due at r: move the clock to the next event (a waiting
+      // seed's update count or a convergence update of an earlier round);
+      // with no event left the round ends at max_iter
+      r = (nxt == INT32_MAX || nxt > max_iter) ? max_iter : nxt;
+      continue;
+    }
+    break;
+  }
+  if (threadIdx.x == 0) sh_done = done;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    done = sh_done;
+    ctl->N = N;
+    ctl->target = target;
+    ctl->max_iter = max_iter;
+    ctl->r = r;
+    ctl->done = done;
+    ctl->n_converged = convd;
+    if (prev_s > 0) ctl->steps += 1;
+    ctl->s = done ? 0 : s;
+    int C = 0, Lc = 0;
+    if (!done) choose_chunks(n, s, R, tl, &C, &Lc);
+    ctl->C = C;
+    ctl->Lc = Lc;
+    if (!done) ctl->evals += (int64_t)s * n;
+  }
+}
+
+cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
+                              const int32_t* conv, int32_t* active, int64_t n, int32_t R,
+                              Tiling tl, int N, int target, int max_iter, cudaStream_t st) {
+  compact_kernel<<<1, kCompactThreads, 0, st>>>(ctl, state, it, conv, active, n, R, tl, 1, N,
+                                                target, max_iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(IterCtl* ctl, const int32_t* state, const int32_t* it,
+                           const int32_t* conv, int32_t* active, int64_t n, int32_t R, Tiling tl,
+                           int N, int target, int max_iter, cudaStream_t st) {
+  compact_kernel<<<1, kCompactThreads, 0, st>>>(ctl, state, it, conv, active, n, R, tl, 0, N,
+                                                target, max_iter);
+  return cudaGetLastError();
+}
+
+}  // namespace fms
+
+namespace fms {
+
+// ---------------------------------------------------------------------------
+// Stand-alone single update (fms_mean_shift_step): every seed is active.
+// ---------------------------------------------------------------------------
+__global__ void step_setup_kernel(int32_t* __restrict__ active, int32_t m, IterCtl* ctl, int32_t C,
+                                  int32_t Lc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    active[i] = i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->s = m;
+    ctl->C = C;
+    ctl->Lc = Lc;
+  }
+}
+
+cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
+                              cudaStream_t st) {
+  int blocks = (m + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  step_setup_kernel<<<blocks, 256, 0, st>>>(active, m, ctl, C, Lc);
+  return cudaGetLastError();
+}
+
+// out_seeds[i] = seeds[i] + (S_i / W_i) / scale (original units), out_wsum[i] = W_i.
+__global__ void step_finish_kernel(const float* __restrict__ part, const IterCtl* __restrict__ ctl,
+                                   const float* __restrict__ seeds, int d, int DA, double inv_scale,
+                                   float* __restrict__ out_seeds, float* __restrict__ out_wsum) {
+  const int s = ctl->s, C = ctl->C;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
+    float a[3] = {0.f, 0.f, 0.f};
+    reduce_chunks(part, s, p, C, DA, d, lane, a);
+    const float W = __shfl_sync(kFull, a[0], 0);
+    // every lane reads its own coordinate before anyone writes (seeds may alias out_seeds)
+    float v[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;
+      v[u] = (k >= 1 && k <= d) ? seeds[(int64_t)p * d + (k - 1)] : 0.0f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;
+      if (k >= 1 && k <= d)
+        out_seeds[(int64_t)p * d + (k - 1)] = (float)((double)v[u] + (double)(a[u] / W) * inv_scale);
+    }
+    if (lane == 0 && out_wsum) out_wsum[p] = W;
+  }
+}
+
+cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
+                               int DA, double inv_scale, float* out_seeds, float* out_wsum,
+                               int m, cudaStream_t st) {
+  int blocks = (m + 7) / 8;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  step_finish_kernel<<<blocks, 256, 0, st>>>(part, ctl, seeds, d, DA, inv_scale, out_seeds,
+                                             out_wsum);
+  return cudaGetLastError();
+}
+
+}  // namespace fms

@@ -1,0 +1,511 @@
+// Prune (mode merging), the seed-count decision, FP64-accumulated refinement,
+// canonical ordering and nearest-mode labelling.
+#include <float.h>
+
+#include "fms_internal.cuh"
+
+namespace fms {
+
+// ---------------------------------------------------------------------------
+// Kept seeds after Early Stopping (Sec. II-C): converged by the stop update
+// t* (gamma < 1), or every seed that did not fail (gamma = 1, Alg. 1).
+// One CTA; slot order (= seed rank order) is preserved.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    kept_list_kernel(const IterCtl* __restrict__ ctl, const int32_t* __restrict__ state,
+                     const int32_t* __restrict__ conv, int keep_exhausted,
+                     int32_t* __restrict__ kept, MergeCtl* mctl, int64_t n, int32_t R, Tiling tl) {
+  __shared__ int scratch[64];
+  const int N = ctl->N;
+  const int t_star = ctl->r;
+  int base = 0;
+  for (int b = 0; b < N; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    int take = 0;
+    if (i < N) {
+      const int st = state[i];
+      if (keep_exhausted) take = (st == kConverged) || (st == kExhausted);
+      else take = (st == kConverged) && (conv[i] <= t_star);
+    }
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) kept[base + off] = i;
+    base += tot;
+  }
+  if (threadIdx.x == 0) {
+    mctl->K = base;
+    mctl->t_star = t_star;
+    int C, Lc;
+    choose_chunks(n, base, R, tl, &C, &Lc);
+    mctl->C = C;
+    mctl->Lc = Lc;
+    mctl->evals += (int64_t)base * n;
+  }
+}
+
+cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int32_t* conv,
+                             int keep_exhausted, int32_t* kept, MergeCtl* mctl, int64_t n,
+                             int32_t R, Tiling tl, cudaStream_t st) {
+  kept_list_kernel<<<1, 1024, 0, st>>>(ctl, state, conv, keep_exhausted, kept, mctl, n, R, tl);
+  return cudaGetLastError();
+}
+
+// score[q] = sum over chunks of the W partials of candidate q (one warp per
+// candidate: lane l takes chunks l, l+32, ... in order, then a fixed xor tree).
+__global__ void score_reduce_kernel(const float* __restrict__ part, const MergeCtl* mctl, int DA,
+                                    float* __restrict__ score) {
+  const int K = mctl->K, C = mctl->C;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < K; q += nw) {
+    float s = 0.0f;
+    for (int c = lane; c < C; c += 32) s += part[((int64_t)c * K + q) * DA];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) score[q] = s;
+  }
+}
+
+cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA, float* score,
+                                int max_K, cudaStream_t st) {
+  int blocks = (max_K + 7) / 8;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  score_reduce_kernel<<<blocks, 256, 0, st>>>(part, mctl, DA, score);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Prune modes (Alg. 1 line 13, Alg. 2 line 10): greedy radius suppression in
+// order of (score descending, rank ascending).  Implemented as repeated
+// "take the best live candidate, accept it, kill every live candidate closer
+// than r" -- the same accepted set as visiting the sorted list once.
+// One CTA of 1024 threads; candidate q has rank q.
+// ---------------------------------------------------------------------------
+template <typename PT, typename ST>
+__global__ void __launch_bounds__(1024)
+    greedy_merge_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
+                        const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
+                        PT r2, int32_t* __restrict__ alive, int32_t* __restrict__ accepted,
+                        int32_t* __restrict__ M_out) {
+  __shared__ ST sh_s[32];
+  __shared__ int sh_q[32];
+  __shared__ PT sh_pos[FMS_MAX_DIM_PAD];
+  __shared__ int sh_best;
+  const int K = *K_ptr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) alive[q] = 1;
+  __syncthreads();
+  int M = 0;
+  for (int round = 0; round < K; ++round) {
+    ST best = -INFINITY;
+    int bq = INT32_MAX;
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+      if (!alive[q]) continue;
+      const ST sc = score[q];
+      if (sc > best || (sc == best && q < bq)) {
+        best = sc;
+        bq = q;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const ST os = __shfl_xor_sync(kFull, best, o);
+      const int oq = __shfl_xor_sync(kFull, bq, o);
+      if (os > best || (os == best && oq < bq)) {
+        best = os;
+        bq = oq;
+      }
+    }
+    if (lane == 0) {
+      sh_s[wid] = best;
+      sh_q[wid] = bq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ST b = sh_s[0];
+      int bb = sh_q[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        if (sh_s[w] > b || (sh_s[w] == b && sh_q[w] < bb)) {
+          b = sh_s[w];
+          bb = sh_q[w];
+        }
+      }
+      sh_best = bb;
+      if (bb != INT32_MAX) accepted[M] = bb;
+    }
+    __syncthreads();
+    const int win = sh_best;
+    if (win == INT32_MAX) break;
+    ++M;
+    const int64_t wrow = cand_row ? cand_row[win] : win;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) sh_pos[k] = pos[wrow * DP + k];
+    __syncthreads();
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+      if (!alive[q]) continue;
+      const int64_t row = cand_row ? cand_row[q] : q;
+      PT d2 = 0;
+      for (int k = 0; k < d; ++k) {
+        const PT e = pos[row * DP + k] - sh_pos[k];
+        d2 += e * e;
+      }
+      if (d2 < r2) alive[q] = 0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *M_out = M;
+}
+
+cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
+                                  const float* score, const float* pos, int DP, int d, float r2,
+                                  int32_t* alive, int32_t* accepted, int32_t* M_out,
+                                  cudaStream_t st) {
+  greedy_merge_kernel<float, float><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
+                                                        alive, accepted, M_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
+                                  int DP, int d, double r2, int32_t* alive, int32_t* accepted,
+                                  int32_t* M_out, cudaStream_t st) {
+  greedy_merge_kernel<double, double><<<1, 1024, 0, st>>>(nullptr, K_ptr, score, pos, DP, d, r2,
+                                                          alive, accepted, M_out);
+  return cudaGetLastError();
+}
+
+// Seed-count control (Sec. II-D): double N while N < L*M (and N < n).
+__global__ void doubling_kernel(MergeCtl* mctl, int32_t N, int64_t n, float L, int allow) {
+  const int M = mctl->M;
+  int next = N;
+  if (allow && (float)N < L * (float)M && (int64_t)N < n) {
+    const int64_t t = 2LL * N;
+    next = (int32_t)(t < n ? t : n);
+  }
+  mctl->next_N = next;
+}
+
+cudaError_t launch_doubling_decision(MergeCtl* mctl, int32_t N, int64_t n, float L, int allow,
+                                     cudaStream_t st) {
+  doubling_kernel<<<1, 1, 0, st>>>(mctl, N, n, L, allow);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Refinement: more updates of each merged mode with FP64 positions and
+// FP64 accumulation across chunks.  Distances use exact FP32 differences
+// against the position split into hi + lo floats; within one warp task the
+// sums are FP32 (at most Lc/32 terms per lane, then a fixed shuffle tree).
+// ---------------------------------------------------------------------------
+__global__ void refine_init_kernel(const float* __restrict__ y, const int32_t* __restrict__ kept,
+                                   const int32_t* __restrict__ accepted, MergeCtl* mctl, int DP,
+                                   double* __restrict__ ym, int32_t* __restrict__ mdone,
+                                   int64_t n, Tiling tl) {
+  const int M = mctl->M;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * DP; e += gridDim.x * blockDim.x) {
+    const int m = e / DP, k = e % DP;
+    ym[e] = (double)y[(int64_t)kept[accepted[m]] * DP + k];
+    if (k == 0) mdone[m] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int C, Lc;
+    Tiling rt = tl;
+    rt.min_chunk = 2048;
+    choose_chunks(n, M, 1, rt, &C, &Lc);
+    mctl->Cr = C;
+    mctl->Lcr = Lc;
+    mctl->refine_iters = 0;
+    mctl->refine_active = M;
+  }
+}
+
+cudaError_t launch_refine_init(const float* y, const int32_t* kept, const int32_t* accepted,
+                               MergeCtl* mctl, int DP, double* ym, int32_t* mdone, int64_t n,
+                               Tiling tl, int max_M, cudaStream_t st) {
+  int blocks = (max_M * DP + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  refine_init_kernel<<<blocks, 256, 0, st>>>(y, kept, accepted, mctl, DP, ym, mdone, n, tl);
+  return cudaGetLastError();
+}
+
+template <int DPAD>
+__global__ void __launch_bounds__(256)
+    refine_step_kernel(const float* __restrict__ Xs, int64_t n, int d, int DP,
+                       const double* __restrict__ ym, const int32_t* __restrict__ mdone,
+                       const MergeCtl* __restrict__ mctl, double* __restrict__ part64) {
+  const int M = mctl->M;
+  const int C = mctl->Cr, Lc = mctl->Lcr;
+  const int64_t T = (int64_t)M * C;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+       task += nw) {
+    const int m = (int)(task % M);
+    const int c = (int)(task / M);
+    if (mdone[m]) continue;
+    float yh[DPAD], yl[DPAD], acc[DPAD + 1];
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) {
+      const double v = k < DP ? ym[(int64_t)m * DP + k] : 0.0;
+      yh[k] = (float)v;
+      yl[k] = (float)(v - (double)yh[k]);
+      acc[k + 1] = 0.0f;
+    }
+    acc[0] = 0.0f;
+    const int64_t j0 = (int64_t)c * Lc;
+    const int64_t j1 = j0 + Lc < n ? j0 + Lc : n;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      float dx[DPAD];
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) dx[k] = k < DP ? (Xs[j * DP + k] - yh[k]) - yl[k] : 0.0f;
+      float t = -dx[0] * dx[0];
+#pragma unroll
+      for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
+      const float w = ex2_ftz(t);
+      acc[0] += w;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) acc[1 + k] = fmaf(w, dx[k], acc[1 + k]);
+    }
+#pragma unroll
+    for (int k = 0; k <= DPAD; ++k) {
+      float v = acc[k];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      acc[k] = v;
+    }
+    double* o = part64 + ((int64_t)c * M + m) * (d + 1);
+#pragma unroll
+    for (int k = 0; k <= DPAD; ++k)
+      if ((k & 31) == lane && k <= d) o[k] = (double)acc[k];
+  }
+}
+
+cudaError_t launch_refine_step(const float* Xs, int64_t n, int d, int DP, const double* ym,
+                               const int32_t* mdone, const MergeCtl* mctl, double* part64,
+                               int grid_ctas, cudaStream_t st) {
+  if (d <= 4)
+    refine_step_kernel<4><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
+  else if (d <= 8)
+    refine_step_kernel<8><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
+  else if (d <= 16)
+    refine_step_kernel<16><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
+  else if (d <= 32)
+    refine_step_kernel<32><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
+  else
+    refine_step_kernel<64><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
+  return cudaGetLastError();
+}
+
+// One warp per mode: FP64 sums over chunks (chunk order), then move the mode
+// (or, with score_only, record W = sum_j w_j at the current position).
+__global__ void refine_update_kernel(const double* __restrict__ part64, MergeCtl* mctl,
+                                     double* __restrict__ ym, int32_t* __restrict__ mdone,
+                                     double* __restrict__ mscore, int d, int DP, double tol2_s,
+                                     int score_only) {
+  const int M = mctl->M;
+  const int C = mctl->Cr;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += nw) {
+    if (!score_only && mdone[m]) continue;
+    // lane l sums chunks l, l+32, ... in order; a fixed xor tree combines them
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k <= d; ++k) {
+      double v = 0.0;
+      for (int c = lane; c < C; c += 32) v += part64[((int64_t)c * M + m) * (d + 1) + k];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if ((k & 31) == lane) a[k >> 5] = v;
+    }
+    const double W = __shfl_sync(kFull, a[0], 0);
+    if (score_only) {
+      if (lane == 0) mscore[m] = W;
+      continue;
+    }
+    const bool ok = W > 0.0 && isfinite(W);
+    double step2 = 0.0, delta[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;
+      if (ok && k >= 1 && k <= d) {
+        delta[u] = a[u] / W;
+        step2 += delta[u] * delta[u];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) ym[(int64_t)m * DP + (k - 1)] += delta[u];
+      }
+    }
+    if (lane == 0 && (!ok || step2 <= tol2_s)) mdone[m] = 1;
+  }
+  if (!score_only && blockIdx.x == 0 && threadIdx.x == 0) mctl->refine_iters += 1;
+}
+
+cudaError_t launch_refine_update(const double* part64, MergeCtl* mctl, double* ym,
+                                 int32_t* mdone, double* mscore, int d, int DP, double tol2_s,
+                                 int score_only, int max_M, cudaStream_t st) {
+  int blocks = (max_M + 7) / 8;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  refine_update_kernel<<<blocks, 256, 0, st>>>(part64, mctl, ym, mdone, mscore, d, DP, tol2_s,
+                                               score_only);
+  return cudaGetLastError();
+}
+
+__global__ void refine_count_kernel(MergeCtl* mctl, const int32_t* __restrict__ mdone) {
+  __shared__ int red[32];
+  const int M = mctl->M;
+  int c = 0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) c += mdone[m] ? 0 : 1;
+  c = block_sum(c, red);
+  if (threadIdx.x == 0) mctl->refine_active = c;
+}
+
+cudaError_t launch_refine_count(MergeCtl* mctl, const int32_t* mdone, cudaStream_t st) {
+  refine_count_kernel<<<1, 1024, 0, st>>>(mctl, mdone);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Canonical order: score descending, ties by lexicographic coordinates.
+// rank_i = #{j : key_j < key_i}; modes are written in original units.
+// ---------------------------------------------------------------------------
+template <typename PT>
+__device__ __forceinline__ bool key_less(double sa, const PT* a, double sb, const PT* b, int d) {
+  if (sa != sb) return sa > sb;
+  for (int k = 0; k < d; ++k)
+    if (a[k] != b[k]) return a[k] < b[k];
+  return false;
+}
+
+__global__ void canonical_order_kernel(const double* __restrict__ ym,
+                                       const double* __restrict__ mscore,
+                                       const int32_t* __restrict__ accepted,
+                                       const int32_t* __restrict__ M_ptr, int d, int DP,
+                                       double inv_scale, float* __restrict__ out_modes,
+                                       int32_t max_modes, float* __restrict__ modes_full,
+                                       float* __restrict__ out_scores) {
+  const int M = *M_ptr;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int ai = accepted ? accepted[i] : i;
+    const double* pa = ym + (int64_t)ai * DP;
+    const double sa = mscore[ai];
+    int rank = 0;
+    for (int j = 0; j < M; ++j) {
+      const int aj = accepted ? accepted[j] : j;
+      if (j != i && key_less(mscore[aj], ym + (int64_t)aj * DP, sa, pa, d)) ++rank;
+    }
+    for (int k = 0; k < d; ++k) {
+      const float v = (float)(pa[k] * inv_scale);
+      modes_full[(int64_t)rank * d + k] = v;
+      if (out_modes && rank < max_modes) out_modes[(int64_t)rank * d + k] = v;
+    }
+    if (out_scores) out_scores[rank] = (float)sa;
+  }
+}
+
+cudaError_t launch_canonical_order(const double* ym, const double* mscore,
+                                   const int32_t* accepted, const int32_t* M_ptr, int d, int DP,
+                                   double inv_scale, float* out_modes, int32_t max_modes,
+                                   float* modes_full, float* out_scores, int max_M,
+                                   cudaStream_t st) {
+  int blocks = (max_M + 127) / 128;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  canonical_order_kernel<<<blocks, 128, 0, st>>>(ym, mscore, accepted, M_ptr, d, DP, inv_scale,
+                                                 out_modes, max_modes, modes_full, out_scores);
+  return cudaGetLastError();
+}
+
+// Positions of the accepted seeds (no refinement): FP64 copies + FP64 scores
+// from the FP32 prune scores, so the same ordering kernel applies.
+__global__ void unrefined_modes_kernel(const float* __restrict__ y,
+                                       const int32_t* __restrict__ kept,
+                                       const int32_t* __restrict__ accepted,
+                                       const float* __restrict__ score, const MergeCtl* mctl,
+                                       int DP, double* __restrict__ ym,
+                                       double* __restrict__ mscore) {
+  const int M = mctl->M;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * DP; e += gridDim.x * blockDim.x) {
+    const int m = e / DP, k = e % DP;
+    const int q = accepted[m];
+    ym[e] = (double)y[(int64_t)kept[q] * DP + k];
+    if (k == 0) mscore[m] = (double)score[q];
+  }
+}
+
+cudaError_t launch_unrefined_modes(const float* y, const int32_t* kept, const int32_t* accepted,
+                                   const float* score, const MergeCtl* mctl, int DP, double* ym,
+                                   double* mscore, int max_M, cudaStream_t st) {
+  int blocks = (max_M * DP + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  unrefined_modes_kernel<<<blocks, 256, 0, st>>>(y, kept, accepted, score, mctl, DP, ym, mscore);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Nearest-mode labels (Alg. 2 lines 11-13).  One thread per point; modes are
+// staged through shared memory in tiles.  Ties go to the lowest index.
+// ---------------------------------------------------------------------------
+constexpr int kLabelTileFloats = 8192;
+
+__global__ void __launch_bounds__(256)
+    label_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ modes,
+                 const int32_t* __restrict__ M_ptr, int M_host, int32_t* __restrict__ labels,
+                 float* __restrict__ margins) {
+  __shared__ float sm[kLabelTileFloats];
+  const int M = M_ptr ? *M_ptr : M_host;
+  const int tile = kLabelTileFloats / d;
+  for (int64_t jb = (int64_t)blockIdx.x * blockDim.x; jb < n; jb += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = jb + threadIdx.x;
+    float x[FMS_MAX_DIM_PAD];
+    if (j < n)
+      for (int k = 0; k < d; ++k) x[k] = X[j * d + k];
+    float b1 = INFINITY, b2 = INFINITY;
+    int arg = -1;
+    for (int m0 = 0; m0 < M; m0 += tile) {
+      const int mt = min(tile, M - m0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < mt * d; e += blockDim.x) sm[e] = modes[(int64_t)m0 * d + e];
+      __syncthreads();
+      if (j < n) {
+        for (int m = 0; m < mt; ++m) {
+          float d2 = 0.0f;
+          for (int k = 0; k < d; ++k) {
+            const float e = x[k] - sm[m * d + k];
+            d2 = fmaf(e, e, d2);
+          }
+          if (d2 < b1) {
+            b2 = b1;
+            b1 = d2;
+            arg = m0 + m;
+          } else if (d2 < b2) {
+            b2 = d2;
+          }
+        }
+      }
+    }
+    if (j < n) {
+      labels[j] = arg;
+      if (margins) margins[j] = (M > 1) ? sqrtf(b2) - sqrtf(b1) : INFINITY;
+    }
+  }
+}
+
+cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
+                         const int32_t* M_dev, int32_t M_host, int32_t* labels, float* margins,
+                         cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  label_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins);
+  return cudaGetLastError();
+}
+
+}  // namespace fms

@@ -1,0 +1,350 @@
+"""Benchmark: ms per 200K-point Faster Mean-shift clustering on GB300.
+
+One step = one fms_cluster call (Seed Selection, mean-shift updates under
+Early Stopping, prune, seed doubling, FP64-accumulated refinement, labels) on
+the paper-scale 3-D workload: n = 200,000 points, 20 Dirichlet-sized blobs plus
+2% uniform noise, h = 5 (synthetic stand-in for the paper's 200K-point Table I
+case).  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MB write) between timed steps, outside the per-step CUDA events.
+
+Extra measurements on the same line:
+  roofline      ms_step (the dominant kernel): seed-point evaluations per
+                second from CUDA events around each launch, against the FP32
+                pipe bound of the minimal formulation (2d+2 FP32 ops per eval).
+  e2e           the same clustering through the C ABI with host buffers: the
+                pinned host -> device copy of the points and the device -> host
+                copy of labels and modes are inside the timed region.
+  cpu_baseline  the FP64 oracle on the host cores (rank 0, N = 1 only).
+  clocks        nvidia-smi samples taken during the timed region.
+
+--impl reference times the FP64 oracle (the reference arm of this project) on
+the same workload and prints the same line with "impl": "reference".
+Multi-GPU (torchrun): independent replicas, one point set per rank, no
+data-path collective ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ms per 200K-point clustering"
+N_POINTS, DIM = 200_000, 3
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_desc():
+    return {"workload": "paper_3d: n=200000 points in 3-D, 20 Gaussian blobs (centres U[0,200]^3, "
+                        "sigma U[1,3], Dirichlet(2) sizes) + 2% uniform noise, h=5, tol=1e-3*h; "
+                        "Seed Selection (N0=128, L=8) + Early Stopping (gamma=0.95), FP64 refine",
+            "n": N_POINTS, "d": DIM, "h": 5.0,
+            "l2": "flushed between timed steps (256 MB write outside the step events)"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_input(rank):
+    import fms_inputs as fi
+    return fi.paper_3d(seed=rank)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def run_oracle_sample(w, seconds=12.0):
+    """Time the FP64 oracle's full clustering of the workload on the host cores."""
+    import oracle as orc
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or runs >= 20:
+            break
+    return el / runs * 1e3, runs
+
+
+def oracle_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_input(0)
+    import oracle as orc
+    for _ in range(args.warmup):
+        orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
+    ms = (time.perf_counter() - t0) / args.steps * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_desc(),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": f"full FP64 oracle clustering of the workload, {args.steps} runs"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def bench_fms(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import paper_2112_13891_gb300 as fms
+
+    w = make_input(rank)
+    X = torch.from_numpy(w.X).to(dev)
+    n, d = X.shape
+    ws = fms.Workspace(fms.workspace_size(n, d), dev)
+    modes = torch.empty((n, d), dtype=torch.float32, device=dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    margins = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(profile=False):
+        return fms.cluster(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0, workspace=ws,
+                           out=(modes, labels, margins), profile=profile)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        r = step()
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    time.sleep(0.5)          # let nvidia-smi start sampling before the timed steps
+    t_wall = time.perf_counter()
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(st)
+        r = step()
+        ev[i][1].record(st)
+        launches += r.stats["kernel_launches"] + 0
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = float(sum(step_ms))
+    if pg is not None:
+        t = torch.tensor([t_total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = t_total / (args.steps * world)          # ms per clustering, whole job
+    ms_per_step = t_total / args.steps
+
+    # --- roofline of ms_step: CUDA events around each launch (profile mode) ---
+    prof_ms, prof_ev, prof_launch = 0.0, 0, 0
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        rp = step(profile=True)
+        prof_ms += rp.stats["step_kernel_ms"]
+        prof_ev += rp.stats["step_evals"]
+        prof_launch += rp.stats["step_launches"]
+    barrier()
+    avg_launch_ms = prof_ms / max(prof_launch, 1)
+    evals_per_launch = prof_ev / max(prof_launch, 1)
+    achieved = evals_per_launch / (avg_launch_ms * 1e-3) / 1e9          # Geval/s
+    ops_per_eval = 2 * d + 2
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ops_per_eval / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ms_step_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # --- end to end through the C ABI with host buffers ---
+    Xh = torch.from_numpy(w.X).pin_memory()
+    lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    modes_h = torch.empty((n, d), dtype=torch.float32).pin_memory()
+    Xd = torch.empty_like(X)
+    barrier()
+    e2e_ms = []
+    d2h_bytes = 0
+    for i in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        Xd.copy_(Xh, non_blocking=True)
+        rr = fms.cluster(Xd, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0, workspace=ws,
+                         out=(modes, labels, margins))
+        M = rr.stats["n_modes"]
+        lab_h.copy_(labels, non_blocking=True)
+        modes_h[:M].copy_(modes[:M], non_blocking=True)
+        b.record(st)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        d2h_bytes = n * 4 + M * d * 4 + 4
+    e2e = float(np.mean(e2e_ms))
+    if pg is not None:
+        t = torch.tensor([e2e], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e = float(t.item()) / world
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_cpu, runs = run_oracle_sample(w, seconds=args.cpu_seconds)
+        cpu = {"value": ms_cpu, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
+               "sample": f"full FP64 oracle clustering of the same 200K-point workload, "
+                         f"{runs} run(s), OpenMP over seeds"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": dict(workload_desc(), parallelism=f"replicas{world}"),
+                "roofline": {"bound": "alu", "kernel": "ms_step", "achieved": achieved,
+                             "peak": peak, "unit": "Geval/s", "frac": achieved / peak,
+                             "traffic": traffic,
+                             "peak_basis": f"FP32 pipe {FP32_LANES_PER_SM} lanes/clk/SM x {SM_COUNT} SMs x "
+                                           f"{sm_max:.0f} MHz / {ops_per_eval} FP32 ops per eval (2d+2)",
+                             "avg_launch_us": avg_launch_ms * 1e3,
+                             "evals_per_launch": evals_per_launch, "launches": prof_launch},
+                "evals_per_s": r.stats["evals"] / (ms_per_step * 1e-3),
+                "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": n * d * 4,
+                        "d2h_bytes_per_step": d2h_bytes},
+                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "wall_s_timed": wall,
+                "stats": {k: r.stats[k] for k in ("iterations", "rounds", "n_seeds_final",
+                                                   "n_modes", "refine_iterations", "evals",
+                                                   "score_evals", "kernel_launches")}}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def kernel_probe(m, reps=3):
+    """One ms_step-only case: m seeds (the first m points) against all 200K points."""
+    import torch
+    import paper_2112_13891_gb300 as fms
+    w = make_input(0)
+    X = torch.from_numpy(w.X).cuda()
+    Y = X[:m].clone()
+    ws = fms.Workspace(fms._lib.fms_step_workspace_size(X.shape[0], X.shape[1], m), X.device)
+    for _ in range(reps):
+        out = fms.mean_shift_step(X, Y, w.h, workspace=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_probe": m, "first": out[0].tolist()}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fms", choices=["fms", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",
+                    help="only run fms_mean_shift_step with M seeds on the workload's points "
+                         "(a small case for ncu captures of ms_step), then exit")
+    args = ap.parse_args()
+    if args.kernel_probe:
+        kernel_probe(args.kernel_probe)
+        return
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_fms(args)
+
+
+if __name__ == "__main__":
+    main()

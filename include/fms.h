@@ -88,7 +88,7 @@ typedef struct fms_stats {
   int32_t n_modes;          /* M                                                  */
   int32_t refine_iterations;/* FP64-accumulated refinement updates                */
   int32_t t_star_last;      /* stop iteration of the last round                   */
-  int32_t reserved0;
+  int32_t kernel_launches;  /* CUDA kernels this call launched                    */
   int64_t evals;            /* seed-point kernel evaluations in mean-shift updates */
   int64_t score_evals;      /* evaluations spent on prune scores and refinement   */
   uint64_t workspace_bytes; /* bytes of workspace the call used                   */

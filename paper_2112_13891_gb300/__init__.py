@@ -42,7 +42,7 @@ class FmsStats(ctypes.Structure):
                 ("n_seeds_final", ctypes.c_int32), ("n_converged", ctypes.c_int32),
                 ("n_discarded", ctypes.c_int32), ("n_kept", ctypes.c_int32),
                 ("n_modes", ctypes.c_int32), ("refine_iterations", ctypes.c_int32),
-                ("t_star_last", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("t_star_last", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("evals", ctypes.c_int64), ("score_evals", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_uint64), ("step_kernel_ms", ctypes.c_double),
                 ("step_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),

@@ -17,7 +17,6 @@ namespace {
 constexpr int kUpdatesPerBatch = 8;   // updates issued between host checks
 constexpr int kRefineMaxIter = 50;    // refinement cap (updates per mode)
 constexpr double kRefineTolFactor = 1e-5;
-constexpr int kCtasPerSm = 3;         // resident ms_step CTAs per SM (<= 80 registers)
 
 struct Dev {
   int sms = 0;
@@ -56,8 +55,8 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
   L.DP = padded_dim(d);
   L.DA = step_accumulators(d);
   L.R = step_seeds_per_warp(d);
-  L.grid_ctas = (sms > 0 ? sms : 1) * kCtasPerSm;
-  L.tl.target_warps = L.grid_ctas * 8;
+  L.tl.target_warps = (sms > 0 ? sms : 1) * step_resident_warps_per_sm(d);
+  L.grid_ctas = (L.tl.target_warps + 7) / 8;
   L.tl.min_chunk = 256;
   L.Ncap = Ncap;
   const int64_t TW8 = 8LL * L.tl.target_warps;
@@ -123,6 +122,13 @@ int64_t seed_capacity(int64_t n, const fms_options& o) {
       rc = FMS_ERR_CUDA;                        \
       goto done;                                \
     }                                           \
+  } while (0)
+
+// FMS_LAUNCH: a kernel launch (counted for fms_stats.kernel_launches)
+#define FMS_LAUNCH(call)                        \
+  do {                                          \
+    ++n_launches;                               \
+    FMS_CUDA(call);                             \
   } while (0)
 
 template <typename T>
@@ -200,6 +206,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
   MergeCtl hm{};
   uint32_t hstatus = 0;
   int32_t N = 0, rounds = 0, Mfinal = 0, K_last = 0;
+  int n_launches = 0;
 
   if (ws) {
     if (workspace_bytes < Lo.total || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
@@ -251,27 +258,27 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         cudaEventRecord(a, st);
         lg = slog + n_slog;
         cudaError_t e = launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part,
-                                       Lo.grid_ctas, st, lg);
+                                       Lo.tl.target_warps, st, lg);
         cudaEventRecord(b, st);
         evs.push_back(a);
         evs.push_back(b);
         ev_slot.push_back(n_slog++);
         return e;
       }
-      return launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part, Lo.grid_ctas, st,
-                            nullptr);
+      return launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part,
+                            Lo.tl.target_warps, st, nullptr);
     };
 
     FMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IterCtl), st));
     FMS_CUDA(cudaMemsetAsync(mctl, 0, sizeof(MergeCtl), st));
     FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
-    FMS_CUDA(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
+    FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
 
     // --- Seed Selection (Alg. 2 line 2) ---
     if (o.all_seeds) N = (int32_t)n;
     else if (o.seed_indices) N = o.n_seed_indices;
     else N = (int32_t)(o.n_initial < n ? o.n_initial : n);
-    FMS_CUDA(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y, it,
+    FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y, it,
                               conv, state, status, st));
 
     for (;;) {
@@ -280,14 +287,14 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (target < 1) target = 1;
       if (target > N) target = N;
       // --- mean-shift iterations under Early Stopping (Sec. II-C) ---
-      FMS_CUDA(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
+      FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
                                  st));
       for (;;) {
         for (int b = 0; b < kUpdatesPerBatch; ++b) {
-          FMS_CUDA(step_launch(active, &ctl->s, &ctl->C, &ctl->Lc));
-          FMS_CUDA(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
+          FMS_LAUNCH(step_launch(active, &ctl->s, &ctl->C, &ctl->Lc));
+          FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
                                  max_iter, st, update_grid));
-          FMS_CUDA(launch_compact(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
+          FMS_LAUNCH(launch_compact(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
                                   st));
         }
         FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
@@ -297,19 +304,19 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         if (hctl.done) break;
       }
       // --- prune (Alg. 2 line 10) ---
-      FMS_CUDA(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
+      FMS_LAUNCH(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
                                 Lo.tl, st));
-      FMS_CUDA(step_launch(kept, &mctl->K, &mctl->C, &mctl->Lc));
-      FMS_CUDA(launch_score_reduce(part, mctl, DA, score, N, st));
-      FMS_CUDA(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
+      FMS_LAUNCH(step_launch(kept, &mctl->K, &mctl->C, &mctl->Lc));
+      FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
+      FMS_LAUNCH(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
                                      &mctl->M, st));
       // --- seed-count control (Sec. II-D) ---
-      FMS_CUDA(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
+      FMS_LAUNCH(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
       FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
       FMS_CUDA(cudaStreamSynchronize(st));
       K_last = hm.K;
       if (hm.next_N > N) {
-        FMS_CUDA(launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, N, N, hm.next_N - N, seed_idx,
+        FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, N, N, hm.next_N - N, seed_idx,
                                   y, it, conv, state, status, st));
         N = hm.next_N;
         continue;
@@ -319,39 +326,39 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
 
     // --- refinement and second prune ---
     if (!o.skip_refine && hm.M > 0) {
-      FMS_CUDA(launch_refine_init(y, kept, acc1, mctl, DP, ym, mdone, n, Lo.tl, hm.M, st));
+      FMS_LAUNCH(launch_refine_init(y, kept, acc1, mctl, DP, ym, mdone, n, Lo.tl, hm.M, st));
       const double rtol_s = kRefineTolFactor * (double)h * scale;
       int iters = 0;
       while (iters < kRefineMaxIter) {
         const int b = kRefineMaxIter - iters < kUpdatesPerBatch ? kRefineMaxIter - iters
                                                                  : kUpdatesPerBatch;
         for (int i = 0; i < b; ++i) {
-          FMS_CUDA(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
-          FMS_CUDA(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, rtol_s * rtol_s,
+          FMS_LAUNCH(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
+          FMS_LAUNCH(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, rtol_s * rtol_s,
                                         0, hm.M, st));
         }
         iters += b;
-        FMS_CUDA(launch_refine_count(mctl, mdone, st));
+        FMS_LAUNCH(launch_refine_count(mctl, mdone, st));
         FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
         FMS_CUDA(cudaStreamSynchronize(st));
         if (hm.refine_active == 0) break;
       }
       // density at the refined modes (FP64-accumulated), for the second prune
       FMS_CUDA(cudaMemsetAsync(mdone, 0, (size_t)hm.M * 4, st));
-      FMS_CUDA(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
-      FMS_CUDA(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, 0.0, 1, hm.M, st));
-      FMS_CUDA(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
+      FMS_LAUNCH(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
+      FMS_LAUNCH(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, 0.0, 1, hm.M, st));
+      FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                      st));
-      FMS_CUDA(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale, out_modes,
+      FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale, out_modes,
                                       max_modes, modes_full, nullptr, hm.M, st));
     } else {
-      FMS_CUDA(launch_unrefined_modes(y, kept, acc1, score, mctl, DP, ym, mscore, hm.M, st));
+      FMS_LAUNCH(launch_unrefined_modes(y, kept, acc1, score, mctl, DP, ym, mscore, hm.M, st));
       FMS_CUDA(cudaMemcpyAsync(&mctl->Mr, &mctl->M, 4, cudaMemcpyDeviceToDevice, st));
-      FMS_CUDA(launch_canonical_order(ym, mscore, nullptr, &mctl->Mr, d, DP, 1.0 / scale,
+      FMS_LAUNCH(launch_canonical_order(ym, mscore, nullptr, &mctl->Mr, d, DP, 1.0 / scale,
                                       out_modes, max_modes, modes_full, nullptr, hm.M, st));
     }
     // --- labels (Alg. 2 lines 11-13) ---
-    FMS_CUDA(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
+    FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
     FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
@@ -374,6 +381,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       stats->n_modes = Mfinal;
       stats->refine_iterations = hm.refine_iters;
       stats->t_star_last = hm.t_star;
+      stats->kernel_launches = n_launches;
       stats->evals = hctl.evals;
       stats->score_evals = hm.evals;
       stats->workspace_bytes = Lo.total;
@@ -433,8 +441,8 @@ StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
   L.DP = padded_dim(d);
   L.DA = step_accumulators(d);
   L.R = step_seeds_per_warp(d);
-  L.grid_ctas = (sms > 0 ? sms : 1) * kCtasPerSm;
-  Tiling tl{L.grid_ctas * 8, 256};
+  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), 256};
+  L.grid_ctas = (tl.target_warps + 7) / 8;
   choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -492,7 +500,7 @@ fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float 
     FMS_CUDA(launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st));
     FMS_CUDA(launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st));
     FMS_CUDA(launch_ms_step(Xs, n, d, L.DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
-                            L.grid_ctas, st, nullptr));
+                            L.grid_ctas * 8, st, nullptr));
     FMS_CUDA(launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum,
                                 (int)m, st));
     if (owns) {

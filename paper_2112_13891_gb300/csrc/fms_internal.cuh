@@ -184,9 +184,10 @@ cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const floa
 // k_step.cu: one update's partial sums for the active seeds
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
-                           const int32_t* Lc_ptr, float* part, int grid_ctas,
+                           const int32_t* Lc_ptr, float* part, int target_warps,
                            cudaStream_t st, int32_t* s_log = nullptr);
 int step_seeds_per_warp(int d);
+int step_resident_warps_per_sm(int d);
 int step_accumulators(int d);
 
 // k_merge.cu

@@ -37,26 +37,68 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
   return v[0];
 }
 
-template <int D, int DP>
-__device__ __forceinline__ void load_point(const float* __restrict__ Xs, int64_t j, float (&x)[D]) {
+// A point as loaded by one lane: DP = 4 -> one float4, DP = 8 -> two.
+template <int DP>
+struct Pt;
+template <>
+struct Pt<4> {
+  float4 a;
+};
+template <>
+struct Pt<8> {
+  float4 a, b;
+};
+
+// Load point j, or a point so far away that its weight is exactly 0 (and
+// w * (x - y) = 0) when j is past the end of the chunk.  Coordinates of 1e18
+// give squared distances of ~1e36 (finite), so exp2 underflows to 0.
+template <int DP>
+__device__ __forceinline__ Pt<DP> load_pt(const float* __restrict__ Xs, int j, int j1) {
+  Pt<DP> p;
+  const float4 far = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
   if constexpr (DP == 4) {
-    const float4 p = __ldg(reinterpret_cast<const float4*>(Xs) + j);
-    x[0] = p.x;
-    if constexpr (D > 1) x[1] = p.y;
-    if constexpr (D > 2) x[2] = p.z;
-    if constexpr (D > 3) x[3] = p.w;
+    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + j) : far;
   } else {
-    static_assert(DP == 8, "low-d path uses DP 4 or 8");
-    const float4 p = __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j);
-    const float4 q = __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j + 1);
-    const float t[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j) : far;
+    p.b = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j + 1) : far;
+  }
+  return p;
+}
+
+template <int D, int DP>
+__device__ __forceinline__ void coords(const Pt<DP>& p, float (&x)[D]) {
+  const float t[8] = {p.a.x, p.a.y, p.a.z, p.a.w,
+                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.x : 0.f,
+                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.y : 0.f,
+                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.z : 0.f,
+                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.w : 0.f};
 #pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = t[k];
+  for (int k = 0; k < D; ++k) x[k] = t[k];
+}
+
+// R seeds in registers against one point: exact differences, one exp2 each.
+template <int D, int R, int DA>
+__device__ __forceinline__ void eval_point(const float (&x)[D], const float (&ys)[R][D],
+                                           float (&acc)[R][DA]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float dx[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) dx[k] = x[k] - ys[r][k];
+    float t = -dx[0] * dx[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
+    const float w = ex2_ftz(t);
+    acc[r][0] += w;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
   }
 }
 
 // Low-dimensional path: D <= 7, DA accumulators per seed (sum w, d sums, pad),
-// R = 32 / DA seeds per warp task.
+// R = 32 / DA seeds per warp task.  Each lane keeps a ring of four points in
+// flight (the loads for points i+4..i+7 are issued before points i..i+3 are
+// evaluated), which hides the L1/L2 latency of the point stream.
 template <int D, int DP, int DA>
 __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs, int64_t n,
                                                     const float* __restrict__ y,
@@ -96,25 +138,26 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
 #pragma unroll
       for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
 
-    const int64_t j0 = (int64_t)c * Lc;
-    const int64_t j1 = j0 + Lc < n ? j0 + Lc : n;
-#pragma unroll 2
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
+    const int j0 = c * Lc;
+    const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
+    int j = j0 + lane;
+    Pt<DP> b0 = load_pt<DP>(Xs, j, j1), b1 = load_pt<DP>(Xs, j + 32, j1);
+    Pt<DP> b2 = load_pt<DP>(Xs, j + 64, j1), b3 = load_pt<DP>(Xs, j + 96, j1);
+    for (; j < j1; j += 128) {
+      const Pt<DP> p0 = b0, p1 = b1, p2 = b2, p3 = b3;
+      b0 = load_pt<DP>(Xs, j + 128, j1);
+      b1 = load_pt<DP>(Xs, j + 160, j1);
+      b2 = load_pt<DP>(Xs, j + 192, j1);
+      b3 = load_pt<DP>(Xs, j + 224, j1);
       float x[D];
-      load_point<D, DP>(Xs, j, x);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float dx[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) dx[k] = x[k] - ys[r][k];
-        float t = -dx[0] * dx[0];
-#pragma unroll
-        for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
-        const float w = ex2_ftz(t);
-        acc[r][0] += w;
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
-      }
+      coords<D, DP>(p0, x);
+      eval_point<D, R, DA>(x, ys, acc);
+      coords<D, DP>(p1, x);
+      eval_point<D, R, DA>(x, ys, acc);
+      coords<D, DP>(p2, x);
+      eval_point<D, R, DA>(x, ys, acc);
+      coords<D, DP>(p3, x);
+      eval_point<D, R, DA>(x, ys, acc);
     }
     float v[32];
 #pragma unroll
@@ -225,11 +268,42 @@ int step_accumulators(int d) {
   return 68;
 }
 
+
+// Resident warps per SM of the ms_step kernel used for dimension d (queried
+// once per dimension from the occupancy calculator).
+int step_resident_warps_per_sm(int d) {
+  static int cache[FMS_MAX_DIM_PAD + 1] = {0};
+  if (d < 1 || d > FMS_MAX_DIM_PAD) return 8;
+  if (cache[d]) return cache[d];
+  int blocks = 0, threads = 256;
+  cudaError_t e = cudaSuccess;
+  switch (d) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<1, 4, 2>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<2, 4, 4>, 256, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<3, 4, 4>, 256, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<4, 4, 8>, 256, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<5, 8, 8>, 256, 0); break;
+    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<6, 8, 8>, 256, 0); break;
+    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<7, 8, 8>, 256, 0); break;
+    default:
+      threads = 128;
+      if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<8, 4>, 128, 0);
+      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<16, 2>, 128, 0);
+      else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1>, 128, 0);
+      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1>, 128, 0);
+      break;
+  }
+  if (e != cudaSuccess || blocks < 1) blocks = 1;
+  cache[d] = blocks * threads / 32;
+  return cache[d];
+}
+
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
-                           const int32_t* Lc_ptr, float* part, int grid_ctas, cudaStream_t st,
+                           const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
                            int32_t* s_log) {
-  const dim3 g(grid_ctas);
+  const dim3 g((target_warps + 7) / 8);
+  const int grid_ctas = (int)g.x;
   switch (d) {
     case 1: ms_step_lowd<1, 4, 2><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
     case 2: ms_step_lowd<2, 4, 4><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;

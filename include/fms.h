@@ -170,6 +170,37 @@ fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float 
                                void* stream);
 
 /*
+ * One mean-shift update, as fms_mean_shift_step, for callers that cannot
+ * allocate device memory: real-time or allocator-free runtimes where
+ * cudaMalloc / cudaFree (which may synchronise the device) are not allowed
+ * while work is in flight, and hosts that have no memory pool to lend the
+ * library a workspace.  The paper has no counterpart; this is a deployment
+ * convenience.
+ *
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Its scratch is one fixed array of FMS_NOALLOC_SCRATCH_BYTES that
+ * is part of the library image, so every GPU on which the library is loaded
+ * holds that much device memory until the process exits.  A request whose
+ * scratch would not fit -- fms_step_workspace_size(n, d, m) larger than
+ * FMS_NOALLOC_SCRATCH_BYTES -- is refused with FMS_ERR_WORKSPACE before any
+ * device work.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before capturing the stream into a graph.
+ *
+ * All calls share the one array and it keeps the previous call's contents:
+ * the call clears what must start at zero itself, but calls that overlap on
+ * the GPU (other streams, other host threads) race on the array and must be
+ * serialised by the caller.
+ *   points [n x d], seeds/out_seeds [m x d] float32, device; out_wsum [m] or
+ *   NULL.  Asynchronous on `stream`; non-finite input is not reported (the
+ *   outputs are then not finite).
+ */
+#define FMS_NOALLOC_SCRATCH_BYTES (16u << 20)
+fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n, int32_t d, float h,
+                                       const float* seeds, int64_t m, float* out_seeds,
+                                       float* out_wsum, void* stream);
+
+/*
  * Nearest-mode labelling (Alg. 2 lines 11-13): labels[j] = argmin_k
  * ||x_j - modes_k|| (ties -> lowest k) and, if margins is non-NULL,
  * margins[j] = second-nearest minus nearest distance (+inf when M = 1).

@@ -227,30 +227,41 @@ def bench_fms(args):
     value = t_total / (args.steps * world)          # ms per clustering, whole job
     ms_per_step = t_total / args.steps
 
-    # --- roofline of ms_step: CUDA events around each launch (profile mode) ---
-    prof_ms, prof_ev, prof_launch = 0.0, 0, 0
+    # --- roofline of the dominant kernel: CUDA events around each launch (profile mode) ---
+    prof = {"step_ms": 0.0, "step_ev": 0, "step_n": 0, "round_ms": 0.0, "round_ev": 0,
+            "round_n": 0, "phase": [0.0, 0.0, 0.0, 0.0]}
     barrier()
     for i in range(args.steps):
         flush.zero_()
-        rp = step(profile=True)
-        prof_ms += rp.stats["step_kernel_ms"]
-        prof_ev += rp.stats["step_evals"]
-        prof_launch += rp.stats["step_launches"]
+        rp = step(profile=True).stats
+        prof["step_ms"] += rp["step_kernel_ms"]
+        prof["step_ev"] += rp["step_evals"]
+        prof["step_n"] += rp["step_launches"]
+        prof["round_ms"] += rp["round_kernel_ms"]
+        prof["round_ev"] += rp["round_evals"]
+        prof["round_n"] += rp["round_launches"]
+        prof["phase"] = [a + b for a, b in zip(prof["phase"], rp["phase_ms"])]
     barrier()
-    avg_launch_ms = prof_ms / max(prof_launch, 1)
-    evals_per_launch = prof_ev / max(prof_launch, 1)
+    if prof["round_ms"] >= prof["step_ms"] and prof["round_n"] > 0:
+        kname, kms, kev, kn = "ms_round", prof["round_ms"], prof["round_ev"], prof["round_n"]
+    else:
+        kname, kms, kev, kn = "ms_step", prof["step_ms"], prof["step_ev"], prof["step_n"]
+    avg_launch_ms = kms / max(kn, 1)
+    evals_per_launch = kev / max(kn, 1)
     achieved = evals_per_launch / (avg_launch_ms * 1e-3) / 1e9          # Geval/s
     ops_per_eval = 2 * d + 2
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ops_per_eval / 1e9
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "ms_step_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", f"{kname}_traffic.json")
     if os.path.exists(tfile):
         try:
             traffic = json.load(open(tfile)).get("bytes_per_launch")
         except Exception:
             traffic = None
+    phases = {k: v / args.steps for k, v in zip(("rounds", "prunes", "refine", "labels"),
+                                               prof["phase"])}
 
     # --- end to end through the C ABI with host buffers ---
     Xh = torch.from_numpy(w.X).pin_memory()
@@ -291,13 +302,15 @@ def bench_fms(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": dict(workload_desc(), parallelism=f"replicas{world}"),
-                "roofline": {"bound": "alu", "kernel": "ms_step", "achieved": achieved,
+                "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
                              "peak": peak, "unit": "Geval/s", "frac": achieved / peak,
                              "traffic": traffic,
                              "peak_basis": f"FP32 pipe {FP32_LANES_PER_SM} lanes/clk/SM x {SM_COUNT} SMs x "
                                            f"{sm_max:.0f} MHz / {ops_per_eval} FP32 ops per eval (2d+2)",
                              "avg_launch_us": avg_launch_ms * 1e3,
-                             "evals_per_launch": evals_per_launch, "launches": prof_launch},
+                             "evals_per_launch": evals_per_launch, "launches": kn,
+                             "share_of_step": kms / max(sum(prof["phase"]), 1e-9)},
+                "phase_ms": phases,
                 "evals_per_s": r.stats["evals"] / (ms_per_step * 1e-3),
                 "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": n * d * 4,
                         "d2h_bytes_per_step": d2h_bytes},

@@ -97,6 +97,13 @@ typedef struct fms_stats {
   int32_t step_launches;    /* ms_step launches that had work                     */
   int32_t reserved1;
   int64_t step_evals;       /* seed-point evaluations of those launches           */
+  double round_kernel_ms;   /* summed device time of the cluster round launches   */
+  int64_t round_evals;      /* evaluations of those launches                      */
+  int32_t round_launches;
+  int32_t reserved2;
+  double phase_ms[4];       /* device time of: seed rounds (selection, updates,
+                               stop), prunes + doubling, refinement + ordering,
+                               labels                                            */
 } fms_stats;
 
 /* Human-readable name of a status code (static storage). */

@@ -46,10 +46,18 @@ class FmsStats(ctypes.Structure):
                 ("evals", ctypes.c_int64), ("score_evals", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_uint64), ("step_kernel_ms", ctypes.c_double),
                 ("step_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
-                ("step_evals", ctypes.c_int64)]
+                ("step_evals", ctypes.c_int64), ("round_kernel_ms", ctypes.c_double),
+                ("round_evals", ctypes.c_int64), ("round_launches", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32), ("phase_ms", ctypes.c_double * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+        out = {}
+        for k, _ in self._fields_:
+            if k.startswith("reserved"):
+                continue
+            v = getattr(self, k)
+            out[k] = list(v) if k == "phase_ms" else v
+        return out
 
 
 _P, _I32, _I64, _F32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kUpdatesPerBatch = 8;   // updates issued between host checks
 constexpr int kRefineMaxIter = 50;    // refinement cap (updates per mode)
+constexpr int kHistCap = 65536;       // convergence histogram entries (cluster rounds)
 constexpr double kRefineTolFactor = 1e-5;
 
 struct Dev {
@@ -42,7 +43,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 struct Layout {
   size_t off_Xs, off_y, off_seed_idx, off_it, off_conv, off_state, off_active, off_kept,
       off_alive, off_acc1, off_acc2, off_score, off_ym, off_mdone, off_mscore, off_modes_full,
-      off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, total;
+      off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, off_yf, off_ract, off_rctl,
+      off_hist, off_S, total;
   int DP, DA, R, grid_ctas;
   int64_t Ncap;
   Tiling tl;
@@ -57,12 +59,12 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
   L.R = step_seeds_per_warp(d);
   L.tl.target_warps = (sms > 0 ? sms : 1) * step_resident_warps_per_sm(d);
   L.grid_ctas = (L.tl.target_warps + 7) / 8;
-  L.tl.min_chunk = 256;
+  L.tl.min_chunk = kStepMinChunk;
   L.Ncap = Ncap;
   const int64_t TW8 = 8LL * L.tl.target_warps;
   const int64_t Gmax = (Ncap + L.R - 1) / L.R;
   const size_t part_floats = (size_t)(TW8 + Gmax + 1) * L.R * L.DA;
-  const size_t part64_doubles = (size_t)(TW8 + Ncap + 1) * (d + 1);
+  const size_t part64_doubles = 1;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -91,6 +93,11 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
   L.off_mctl = take(sizeof(MergeCtl));
   L.off_status = take(64);
   L.off_slog = take((size_t)kSlogCap * 4);
+  L.off_yf = take((size_t)Ncap * L.DP * 4);
+  L.off_ract = take((size_t)Ncap * 4);
+  L.off_rctl = take(sizeof(IterCtl));
+  L.off_hist = take((size_t)(kHistCap + 2) * 4);
+  L.off_S = take(64);
   L.total = o;
   return L;
 }
@@ -202,7 +209,11 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
   void* ws = workspace;
   std::vector<cudaEvent_t> evs;
   std::vector<int> ev_slot;
-  IterCtl hctl{};
+  std::vector<cudaEvent_t> round_evs;      // pairs around cluster round launches
+  cudaEvent_t phase_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double phase_acc[4] = {0, 0, 0, 0};
+  int64_t round_evals_total = 0;
+  IterCtl hctl{}, hrctl{};
   MergeCtl hm{};
   uint32_t hstatus = 0;
   int32_t N = 0, rounds = 0, Mfinal = 0, K_last = 0;
@@ -233,11 +244,16 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     double* mscore = at<double>(ws, Lo.off_mscore);
     float* modes_full = at<float>(ws, Lo.off_modes_full);
     float* part = at<float>(ws, Lo.off_part);
-    double* part64 = at<double>(ws, Lo.off_part64);
     IterCtl* ctl = at<IterCtl>(ws, Lo.off_ctl);
     MergeCtl* mctl = at<MergeCtl>(ws, Lo.off_mctl);
     uint32_t* status = at<uint32_t>(ws, Lo.off_status);
     int32_t* slog = at<int32_t>(ws, Lo.off_slog);
+    float* yf = at<float>(ws, Lo.off_yf);
+    int32_t* ract = at<int32_t>(ws, Lo.off_ract);
+    IterCtl* rctl = at<IterCtl>(ws, Lo.off_rctl);
+    int32_t* hist = at<int32_t>(ws, Lo.off_hist);
+    int32_t* S_dev = at<int32_t>(ws, Lo.off_S);
+    const int qmax = d <= 7 ? round_max_clusters(d) : 0;
 
     const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
     const double tol_s = (double)tol * scale;
@@ -245,11 +261,15 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     const double r_merge = o.merge_radius > 0.0f ? (double)o.merge_radius : (double)h;
     const double r2_s = (r_merge * scale) * (r_merge * scale);
     const bool allow_doubling = !o.all_seeds && !o.seed_indices;
-    const int update_grid = dv.sms * 8;
+    auto update_grid = [&](int64_t m) -> int {
+      int64_t g = (m + 7) / 8;
+      if (g > (int64_t)dv.sms * 8) g = (int64_t)dv.sms * 8;
+      return g < 1 ? 1 : (int)g;
+    };
     int n_slog = 0;
 
-    auto step_launch = [&](const int32_t* list, const int32_t* s_ptr, const int32_t* C_ptr,
-                           const int32_t* Lc_ptr) -> cudaError_t {
+    auto step_launch = [&](const float* pos, const int32_t* list, const int32_t* s_ptr,
+                           const int32_t* C_ptr, const int32_t* Lc_ptr) -> cudaError_t {
       int32_t* lg = nullptr;
       if (o.profile && n_slog < kSlogCap) {
         cudaEvent_t a, b;
@@ -257,7 +277,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           return cudaErrorUnknown;
         cudaEventRecord(a, st);
         lg = slog + n_slog;
-        cudaError_t e = launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part,
+        cudaError_t e = launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
                                        Lo.tl.target_warps, st, lg);
         cudaEventRecord(b, st);
         evs.push_back(a);
@@ -265,13 +285,32 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         ev_slot.push_back(n_slog++);
         return e;
       }
-      return launch_ms_step(Xs, n, d, DP, y, list, s_ptr, C_ptr, Lc_ptr, part,
+      return launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
                             Lo.tl.target_warps, st, nullptr);
     };
 
     FMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IterCtl), st));
     FMS_CUDA(cudaMemsetAsync(mctl, 0, sizeof(MergeCtl), st));
+    FMS_CUDA(cudaMemsetAsync(rctl, 0, sizeof(IterCtl), st));
+    FMS_CUDA(cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, st));
     FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
+    if (o.profile)
+      for (int i = 0; i < 5; ++i)
+        if (cudaEventCreate(&phase_ev[i]) != cudaSuccess) {
+          rc = FMS_ERR_CUDA;
+          goto done;
+        }
+    auto mark = [&](int i) {
+      if (o.profile) cudaEventRecord(phase_ev[i], st);
+    };
+    // phase accounting: [0] rounds, [1] prunes + doubling, [2] refine + order, [3] labels
+    auto phase_add = [&](int slot, int a, int b) {
+      if (!o.profile) return;
+      float t = 0.f;
+      cudaEventSynchronize(phase_ev[b]);
+      if (cudaEventElapsedTime(&t, phase_ev[a], phase_ev[b]) == cudaSuccess) phase_acc[slot] += t;
+    };
+    mark(0);
     FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
 
     // --- Seed Selection (Alg. 2 line 2) ---
@@ -287,35 +326,63 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (target < 1) target = 1;
       if (target > N) target = N;
       // --- mean-shift iterations under Early Stopping (Sec. II-C) ---
-      FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
-                                 st));
-      for (;;) {
-        for (int b = 0; b < kUpdatesPerBatch; ++b) {
-          FMS_LAUNCH(step_launch(active, &ctl->s, &ctl->C, &ctl->Lc));
-          FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
-                                 max_iter, st, update_grid));
-          FMS_LAUNCH(launch_compact(ctl, state, it, conv, active, n, R, Lo.tl, N, target, max_iter,
-                                  st));
+      const bool use_clusters =
+          qmax > 0 && N <= qmax * kSeedsPerCluster && max_iter <= kHistCap;
+      if (use_clusters) {
+        // cluster-persistent round: ~8 seeds per cluster, no host round trips
+        int clusters = (N + 7) / 8;
+        if (clusters > qmax) clusters = qmax;
+        FMS_LAUNCH(launch_round_list(state, N, active, S_dev, st));
+        cudaEvent_t ra = nullptr, rb = nullptr;
+        if (o.profile) {
+          cudaEventCreate(&ra);
+          cudaEventCreate(&rb);
+          cudaEventRecord(ra, st);
+          round_evs.push_back(ra);
+          round_evs.push_back(rb);
         }
-        FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
-        FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
-        FMS_CUDA(cudaStreamSynchronize(st));
-        if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
-        if (hctl.done) break;
+        FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
+                                   target, max_iter, tol2_s,
+                                   reinterpret_cast<unsigned long long*>(&ctl->evals), st));
+        if (o.profile) cudaEventRecord(rb, st);
+        FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N,
+                                       o.gamma >= 1.0f ? 1 : 0, kept, mctl, ctl, n, R, Lo.tl,
+                                       st));
+        mark(1);
+      } else {
+        FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target,
+                                     max_iter, st));
+        for (;;) {
+          for (int b = 0; b < kUpdatesPerBatch; ++b) {
+            FMS_LAUNCH(step_launch(y, active, &ctl->s, &ctl->C, &ctl->Lc));
+            FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
+                                     max_iter, n, R, Lo.tl, N, target, st, update_grid(N)));
+          }
+          FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+          FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+          FMS_CUDA(cudaStreamSynchronize(st));
+          if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
+          if (hctl.done) break;
+        }
+        // --- prune candidates (Alg. 2 line 10) ---
+        FMS_LAUNCH(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
+                                    Lo.tl, st));
+        mark(1);
       }
-      // --- prune (Alg. 2 line 10) ---
-      FMS_LAUNCH(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
-                                Lo.tl, st));
-      FMS_LAUNCH(step_launch(kept, &mctl->K, &mctl->C, &mctl->Lc));
+      FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
       FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
       FMS_LAUNCH(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
-                                     &mctl->M, st));
+                                       &mctl->M, N, st));
       // --- seed-count control (Sec. II-D) ---
       FMS_LAUNCH(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
+      mark(2);
       FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
       FMS_CUDA(cudaStreamSynchronize(st));
+      phase_add(0, 0, 1);
+      phase_add(1, 1, 2);
       K_last = hm.K;
       if (hm.next_N > N) {
+        mark(0);
         FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, N, N, hm.next_N - N, seed_idx,
                                   y, it, conv, state, status, st));
         N = hm.next_N;
@@ -324,33 +391,45 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       break;
     }
 
+    mark(2);
     // --- refinement and second prune ---
-    if (!o.skip_refine && hm.M > 0) {
-      FMS_LAUNCH(launch_refine_init(y, kept, acc1, mctl, DP, ym, mdone, n, Lo.tl, hm.M, st));
+    if (!o.skip_refine && hm.M > 0 && qmax > 0 && hm.M <= qmax * kModesPerCluster) {
+      // cluster-persistent refinement (updates and the density pass in one launch)
       const double rtol_s = kRefineTolFactor * (double)h * scale;
-      int iters = 0;
-      while (iters < kRefineMaxIter) {
-        const int b = kRefineMaxIter - iters < kUpdatesPerBatch ? kRefineMaxIter - iters
-                                                                 : kUpdatesPerBatch;
-        for (int i = 0; i < b; ++i) {
-          FMS_LAUNCH(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
-          FMS_LAUNCH(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, rtol_s * rtol_s,
-                                        0, hm.M, st));
-        }
-        iters += b;
-        FMS_LAUNCH(launch_refine_count(mctl, mdone, st));
-        FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
-        FMS_CUDA(cudaStreamSynchronize(st));
-        if (hm.refine_active == 0) break;
-      }
-      // density at the refined modes (FP64-accumulated), for the second prune
-      FMS_CUDA(cudaMemsetAsync(mdone, 0, (size_t)hm.M * 4, st));
-      FMS_LAUNCH(launch_refine_step(Xs, n, d, DP, ym, mdone, mctl, part64, Lo.grid_ctas, st));
-      FMS_LAUNCH(launch_refine_update(part64, mctl, ym, mdone, mscore, d, DP, 0.0, 1, hm.M, st));
+      const int clusters = hm.M < qmax ? hm.M : qmax;
+      FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
+                                  rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
+                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st));
       FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
-                                     st));
-      FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale, out_modes,
-                                      max_modes, modes_full, nullptr, hm.M, st));
+                                       hm.M, st));
+      FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,
+                                        out_modes, max_modes, modes_full, nullptr, hm.M, st));
+    } else if (!o.skip_refine && hm.M > 0) {
+      // refinement with the ms_step kernel (many modes, or d > 7)
+      const double rtol_s = kRefineTolFactor * (double)h * scale;
+      FMS_LAUNCH(launch_refine_setup(y, kept, acc1, &mctl->M, DP, ym, yf, ract, mdone, rctl, 1, n,
+                                     R, Lo.tl, hm.M, st));
+      for (int batch = 0; batch * kUpdatesPerBatch < kRefineMaxIter; ++batch) {
+        for (int i = 0; i < kUpdatesPerBatch && batch * kUpdatesPerBatch + i < kRefineMaxIter; ++i) {
+          FMS_LAUNCH(step_launch(yf, ract, &rctl->s, &rctl->C, &rctl->Lc));
+          FMS_LAUNCH(launch_refine_update(part, ract, rctl, ym, yf, mdone, mscore, d, DP, DA,
+                                          rtol_s * rtol_s, kRefineMaxIter, 0, n, R, Lo.tl, hm.M,
+                                          st));
+        }
+        FMS_CUDA(cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+        FMS_CUDA(cudaStreamSynchronize(st));
+        if (hrctl.done) break;
+      }
+      // density at the refined modes (FP64 sums over chunks), for the second prune
+      FMS_LAUNCH(launch_refine_setup(y, kept, acc1, &mctl->M, DP, ym, yf, ract, mdone, rctl, 0, n,
+                                     R, Lo.tl, hm.M, st));
+      FMS_LAUNCH(step_launch(yf, ract, &rctl->s, &rctl->C, &rctl->Lc));
+      FMS_LAUNCH(launch_refine_update(part, ract, rctl, ym, yf, mdone, mscore, d, DP, DA, 0.0,
+                                      kRefineMaxIter, 1, n, R, Lo.tl, hm.M, st));
+      FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
+                                       hm.M, st));
+      FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,
+                                        out_modes, max_modes, modes_full, nullptr, hm.M, st));
     } else {
       FMS_LAUNCH(launch_unrefined_modes(y, kept, acc1, score, mctl, DP, ym, mscore, hm.M, st));
       FMS_CUDA(cudaMemcpyAsync(&mctl->Mr, &mctl->M, 4, cudaMemcpyDeviceToDevice, st));
@@ -358,9 +437,12 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                       out_modes, max_modes, modes_full, nullptr, hm.M, st));
     }
     // --- labels (Alg. 2 lines 11-13) ---
+    mark(3);
     FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
+    mark(4);
     FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+    FMS_CUDA(cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> hslog(n_slog);
     if (n_slog > 0)
@@ -379,13 +461,24 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       stats->n_kept = K_last;
       stats->n_discarded = N - K_last;
       stats->n_modes = Mfinal;
-      stats->refine_iterations = hm.refine_iters;
+      stats->refine_iterations = hrctl.steps;
       stats->t_star_last = hm.t_star;
       stats->kernel_launches = n_launches;
       stats->evals = hctl.evals;
-      stats->score_evals = hm.evals;
+      stats->score_evals = hm.evals + hrctl.evals + (int64_t)hm.M * n;
       stats->workspace_bytes = Lo.total;
       if (o.profile) {
+        phase_add(2, 2, 3);
+        phase_add(3, 3, 4);
+        for (int i = 0; i < 4; ++i) stats->phase_ms[i] = phase_acc[i];
+        double rms = 0.0;
+        for (size_t i = 0; i + 1 < round_evs.size(); i += 2) {
+          float t = 0.f;
+          if (cudaEventElapsedTime(&t, round_evs[i], round_evs[i + 1]) == cudaSuccess) rms += t;
+        }
+        stats->round_kernel_ms = rms;
+        stats->round_launches = (int32_t)(round_evs.size() / 2);
+        stats->round_evals = hctl.evals;
         double ms = 0.0;
         int launches = 0;
         int64_t ev = 0;
@@ -410,6 +503,9 @@ device_error:
   else rc = FMS_ERR_INVALID_ARG;
 done:
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  for (cudaEvent_t e : round_evs) cudaEventDestroy(e);
+  for (cudaEvent_t e : phase_ev)
+    if (e) cudaEventDestroy(e);
   if (owns_ws) {
     cudaFreeAsync(ws, st);
     if (rc == FMS_OK || rc == FMS_ERR_CAPACITY) {
@@ -441,7 +537,7 @@ StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
   L.DP = padded_dim(d);
   L.DA = step_accumulators(d);
   L.R = step_seeds_per_warp(d);
-  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), 256};
+  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), kStepMinChunk};
   L.grid_ctas = (tl.target_warps + 7) / 8;
   choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
   size_t o = 0;

@@ -48,6 +48,8 @@ struct IterCtl {
   int32_t n_failed;
   int32_t n_exhausted;
   int32_t steps;      // updates that had at least one active seed
+  int32_t blocks_done;  // blocks of the current update launch that finished
+  int32_t pad0;
   int64_t evals;      // seed-point evaluations issued
 };
 
@@ -68,6 +70,17 @@ struct MergeCtl {
   int64_t evals;          // evaluations of prune scores and refinement
 };
 
+// Smallest point chunk of a warp task (points): below this the per-task work
+// (seed loads, the warp reduction and one store) stops being small next to
+// the evaluations.
+constexpr int kStepMinChunk = 512;
+
+// Cluster-persistent rounds (k_round.cu): CTAs per cluster and the most seeds
+// one cluster owns.
+constexpr int kClusterCtas = 8;
+constexpr int kSeedsPerCluster = 64;
+constexpr int kModesPerCluster = 32;   // refinement: modes one cluster owns
+
 // Tiling of a (seed-group x point-chunk) warp-task grid.
 struct Tiling {
   int32_t target_warps;   // warps the step grid runs (gridDim.x * warps per CTA)
@@ -75,6 +88,9 @@ struct Tiling {
 };
 
 // Chunk count and length for s active seeds of R per warp over n points.
+// The warp-task grid is G = ceil(s/R) seed groups x C chunks, run by
+// target_warps persistent warps.  C is chosen to fill the last wave of warp
+// tasks best (ties: fewer chunks), with chunks of at least min_chunk points.
 __host__ __device__ inline void choose_chunks(int64_t n, int32_t s, int32_t R, Tiling t,
                                               int32_t* C, int32_t* Lc) {
   if (s <= 0) {
@@ -82,16 +98,32 @@ __host__ __device__ inline void choose_chunks(int64_t n, int32_t s, int32_t R, T
     *Lc = 0;
     return;
   }
-  int64_t G = (s + R - 1) / R;
-  int64_t want = (8LL * t.target_warps + G - 1) / G;
-  int64_t cmax = (n + t.min_chunk - 1) / t.min_chunk;
+  const int64_t G = (s + R - 1) / R;
+  const int64_t TW = t.target_warps > 0 ? t.target_warps : 1;
+  int64_t cmax = n / t.min_chunk;
   if (cmax < 1) cmax = 1;
-  int64_t c = want < 1 ? 1 : want;
-  if (c > cmax) c = cmax;
-  int64_t lc = (n + c - 1) / c;
+  const int64_t cwant = (4 * TW + G - 1) / G;  // never more than ~4 waves of tasks
+  if (cmax > cwant) cmax = cwant;
+  // the best C for k waves is the largest C with G*C <= k*TW; try k = 1..4
+  int64_t best_c = 1;
+  int64_t best_num = -1, best_den = 1;  // efficiency as a fraction
+  for (int k = 0; k <= 4; ++k) {
+    int64_t c = k == 0 ? cmax : (k * TW) / G;
+    if (c > cmax) c = cmax;
+    if (c < 1) c = 1;
+    const int64_t tasks = G * c;
+    const int64_t waves = (tasks + TW - 1) / TW;
+    // eff = tasks / (waves * TW); compare fractions exactly; ties -> fewer chunks
+    if (tasks * best_den > best_num * (waves * TW) ||
+        (tasks * best_den == best_num * (waves * TW) && c < best_c)) {
+      best_num = tasks;
+      best_den = waves * TW;
+      best_c = c;
+    }
+  }
+  int64_t lc = (n + best_c - 1) / best_c;
   lc = (lc + 31) / 32 * 32;
-  c = (n + lc - 1) / lc;
-  *C = (int32_t)c;
+  *C = (int32_t)((n + lc - 1) / lc);
   *Lc = (int32_t)lc;
 }
 
@@ -168,18 +200,34 @@ cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int
 cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
                               const int32_t* conv, int32_t* active, int64_t n, int32_t R,
                               Tiling tl, int N, int target, int max_iter, cudaStream_t st);
-cudaError_t launch_update(const float* part, const int32_t* active, IterCtl* ctl, float* y,
-                          int32_t* it, int32_t* conv, int32_t* state, int d, int DP, int DA,
-                          float tol2_s, int max_iter, cudaStream_t st, int grid);
-cudaError_t launch_compact(IterCtl* ctl, const int32_t* state, const int32_t* it,
-                           const int32_t* conv, int32_t* active, int64_t n, int32_t R, Tiling tl,
-                           int N, int target, int max_iter, cudaStream_t st);
-
+cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
+                          int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
+                          int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
+                          cudaStream_t st, int grid);
 cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
                               cudaStream_t st);
 cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
                                int DA, double inv_scale, float* out_seeds, float* out_wsum,
                                int m, cudaStream_t st);
+
+// k_round.cu
+cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t* it,
+                            int32_t* conv, int32_t* state, const int32_t* list,
+                            const int32_t* S_ptr, int clusters, int32_t* hist, int target,
+                            int max_iter, float tol2_s, unsigned long long* evals,
+                            cudaStream_t st);
+int round_max_clusters(int d);
+cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
+                             const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
+                             int clusters, double* ym, float* yf, double* mscore, double tol2_s,
+                             int max_iter, int32_t* iters_out, unsigned long long* evals,
+                             cudaStream_t st);
+cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
+                              cudaStream_t st);
+cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
+                                const int32_t* state, const int32_t* conv, int N,
+                                int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
+                                int64_t n, int32_t R, Tiling tl, cudaStream_t st);
 
 // k_step.cu: one update's partial sums for the active seeds
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
@@ -198,23 +246,21 @@ cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA,
                                 int max_K, cudaStream_t st);
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
                                   const float* score, const float* pos, int DP, int d, float r2,
-                                  int32_t* alive, int32_t* accepted, int32_t* M_out,
+                                  int32_t* alive, int32_t* accepted, int32_t* M_out, int max_K,
                                   cudaStream_t st);
 cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
                                   int DP, int d, double r2, int32_t* alive, int32_t* accepted,
-                                  int32_t* M_out, cudaStream_t st);
+                                  int32_t* M_out, int max_K, cudaStream_t st);
 cudaError_t launch_doubling_decision(MergeCtl* mctl, int32_t N, int64_t n, float L, int allow,
                                      cudaStream_t st);
-cudaError_t launch_refine_init(const float* y, const int32_t* kept, const int32_t* accepted,
-                               MergeCtl* mctl, int DP, double* ym, int32_t* mdone, int64_t n,
-                               Tiling tl, int max_M, cudaStream_t st);
-cudaError_t launch_refine_step(const float* Xs, int64_t n, int d, int DP, const double* ym,
-                               const int32_t* mdone, const MergeCtl* mctl, double* part64,
-                               int grid_ctas, cudaStream_t st);
-cudaError_t launch_refine_update(const double* part64, MergeCtl* mctl, double* ym,
-                                 int32_t* mdone, double* mscore, int d, int DP, double tol2_s,
-                                 int score_only, int max_M, cudaStream_t st);
-cudaError_t launch_refine_count(MergeCtl* mctl, const int32_t* mdone, cudaStream_t st);
+cudaError_t launch_refine_setup(const float* y, const int32_t* kept, const int32_t* accepted,
+                                const int32_t* M_ptr, int DP, double* ym, float* yf,
+                                int32_t* active, int32_t* mdone, IterCtl* rctl, int init_pos,
+                                int64_t n, int32_t R, Tiling tl, int max_M, cudaStream_t st);
+cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
+                                 float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
+                                 double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
+                                 Tiling tl, int max_M, cudaStream_t st);
 cudaError_t launch_canonical_order(const double* ym, const double* mscore,
                                    const int32_t* accepted, const int32_t* M_ptr, int d, int DP,
                                    double inv_scale, float* out_modes, int32_t max_modes,

@@ -138,19 +138,29 @@ cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_se
 }
 
 // Cross-chunk sum of the partials of active position p: lane l sums chunks
-// l, l+32, ... in chunk order for every accumulator, then a fixed xor tree
-// combines the 32 lane sums.  On return lane k holds accumulator k (W for
-// k = 0, S_{k-1} otherwise) in a[k >> 5], for k <= d.
+// l, l+32, ... in chunk order for every accumulator (16-byte loads), then a
+// fixed xor tree combines the 32 lane sums.  On return lane k holds
+// accumulator k (W for k = 0, S_{k-1} otherwise) in a[k >> 5], for k <= d.
 __device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, int s, int p, int C,
                                               int DA, int d, int lane, float (&a)[3]) {
   for (int k0 = 0; k0 <= d; k0 += 4) {
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    for (int c = lane; c < C; c += 32) {
-      const float* q = part + ((int64_t)c * s + p) * DA + k0;
-      v0 += q[0];
-      if (k0 + 1 <= d) v1 += q[1];
-      if (k0 + 2 <= d) v2 += q[2];
-      if (k0 + 3 <= d) v3 += q[3];
+    if ((DA & 3) == 0) {
+#pragma unroll 4
+      for (int c = lane; c < C; c += 32) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)c * s + p) * DA + k0));
+        v0 += q.x;
+        v1 += q.y;
+        v2 += q.z;
+        v3 += q.w;
+      }
+    } else {  // DA == 2 (d == 1)
+#pragma unroll 4
+      for (int c = lane; c < C; c += 32) {
+        const float2 q = __ldcg(reinterpret_cast<const float2*>(part + ((int64_t)c * s + p) * DA));
+        v0 += q.x;
+        v1 += q.y;
+      }
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -169,24 +179,126 @@ __device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, in
 }
 
 // ---------------------------------------------------------------------------
-// Seed update: y <- y + S/W for every active seed; convergence test; state.
-// One warp per active position.
+// Early Stopping bookkeeping (Sec. II-C).
+//
+// The clock r counts updates.  A seed takes update r+1 when it is RUNNING and
+// has made exactly r updates, so seeds added by a doubling start at 0 while
+// seeds left unconverged by an earlier round wait until the clock reaches
+// their count: the round then behaves exactly like a fresh run over all N
+// seeds.  After each update the seeds whose convergence update is <= r are
+// counted and the round stops once that count reaches target =
+// ceil(gamma*N), or at max_iter.  When no seed is due at r but the round goes
+// on, the clock jumps to the next event (a waiting seed's count or a
+// convergence update of an earlier round).  Runs on one block (any size that
+// is a multiple of 32); reads bypass L1 because other blocks of the same
+// launch wrote the seed states.
 // ---------------------------------------------------------------------------
-__global__ void update_kernel(const float* __restrict__ part, const int32_t* __restrict__ active,
-                              const IterCtl* __restrict__ ctl, float* __restrict__ y,
-                              int32_t* __restrict__ it, int32_t* __restrict__ conv,
-                              int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s,
-                              int max_iter) {
-  const int s = ctl->s;
-  if (s <= 0) return;
-  const int C = ctl->C;
+__device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
+                           const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
+                           int32_t* __restrict__ active, int* s_out, int* conv_out,
+                           int* next_event_out, int* scratch) {
+  int base = 0, convd = 0, nxt = INT32_MAX;
+  for (int b = 0; b < N; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    int take = 0;
+    if (i < N) {
+      const int stt = __ldcg(state + i);
+      if (stt == kRunning) {
+        const int ti = __ldcg(it + i);
+        if (ti == r) take = 1;
+        else if (ti > r) nxt = min(nxt, ti);
+      } else if (stt == kConverged) {
+        const int ci = __ldcg(conv + i);
+        if (ci <= r) ++convd;
+        else nxt = min(nxt, ci);
+      }
+    }
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) active[base + off] = i;
+    base += tot;
+  }
+  convd = block_sum(convd, scratch);
+  nxt = block_min(nxt, scratch);
+  *s_out = base;
+  *conv_out = convd;
+  *next_event_out = nxt;
+}
+
+__device__ void compaction_body(IterCtl* ctl, const int32_t* __restrict__ state,
+                                const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
+                                int32_t* __restrict__ active, int64_t n, int32_t R, Tiling tl,
+                                int begin, int N, int target, int max_iter, int* scratch) {
+  int r = begin ? 0 : __ldcg(&ctl->r) + 1;
+  const int prev_s = begin ? 0 : __ldcg(&ctl->s);
+  int s = 0, convd = 0, nxt = 0, done = 0;
+  for (int guard = 0; guard <= max_iter + 2; ++guard) {
+    scan_clock(r, N, state, it, conv, active, &s, &convd, &nxt, scratch);
+    done = (convd >= target) || (r >= max_iter);
+    if (!done && s == 0) {
+      // nothing is due at r: move the clock to the next event; with no event
+      // left the round ends at max_iter
+      r = (nxt == INT32_MAX || nxt > max_iter) ? max_iter : nxt;
+      continue;
+    }
+    break;
+  }
+  if (threadIdx.x == 0) {
+    ctl->N = N;
+    ctl->target = target;
+    ctl->max_iter = max_iter;
+    ctl->r = r;
+    ctl->done = done;
+    ctl->n_converged = convd;
+    if (prev_s > 0) ctl->steps += 1;
+    ctl->s = done ? 0 : s;
+    int C = 0, Lc = 0;
+    if (!done) choose_chunks(n, s, R, tl, &C, &Lc);
+    ctl->C = C;
+    ctl->Lc = Lc;
+    if (!done) ctl->evals += (int64_t)s * n;
+    ctl->blocks_done = 0;
+  }
+}
+
+// Start of a round: the active list for update 1.
+__global__ void __launch_bounds__(1024)
+    iter_begin_kernel(IterCtl* ctl, const int32_t* __restrict__ state,
+                      const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
+                      int32_t* __restrict__ active, int64_t n, int32_t R, Tiling tl, int N,
+                      int target, int max_iter) {
+  __shared__ int scratch[64];
+  compaction_body(ctl, state, it, conv, active, n, R, tl, 1, N, target, max_iter, scratch);
+}
+
+cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
+                              const int32_t* conv, int32_t* active, int64_t n, int32_t R,
+                              Tiling tl, int N, int target, int max_iter, cudaStream_t st) {
+  iter_begin_kernel<<<1, 1024, 0, st>>>(ctl, state, it, conv, active, n, R, tl, N, target,
+                                        max_iter);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Seed update: y <- y + S/W for every active seed, the convergence test
+// ||S/W|| <= tol, and the seed's state.  One warp per active position.  The
+// last block to finish (atomic ticket after a fence, no waiting) then runs the
+// Early Stopping bookkeeping above for the next update.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    update_kernel(const float* __restrict__ part, int32_t* __restrict__ active, IterCtl* ctl,
+                  float* __restrict__ y, int32_t* __restrict__ it, int32_t* __restrict__ conv,
+                  int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s, int64_t n,
+                  int32_t R, Tiling tl, int N, int target, int max_iter) {
+  __shared__ int scratch[64];
+  __shared__ int sh_last;
+  if (__ldcg(&ctl->done)) return;  // uniform for the whole launch
+  const int s = __ldcg(&ctl->s);
+  const int C = __ldcg(&ctl->C);
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
-    const int64_t slot = active[p];
-    // lane l sums chunks l, l+32, ... (chunk order) for every accumulator; a
-    // fixed xor tree then combines the 32 lane sums.  Accumulator k ends up in
-    // every lane; lane k keeps W (k = 0) or S_{k-1}.
+    const int64_t slot = __ldcg(active + p);
     float a[3] = {0.f, 0.f, 0.f};
     reduce_chunks(part, s, p, C, DA, d, lane, a);
     const float W = __shfl_sync(kFull, a[0], 0);
@@ -224,124 +336,22 @@ __global__ void update_kernel(const float* __restrict__ part, const int32_t* __r
       }
     }
   }
-}
-
-cudaError_t launch_update(const float* part, const int32_t* active, IterCtl* ctl, float* y,
-                          int32_t* it, int32_t* conv, int32_t* state, int d, int DP, int DA,
-                          float tol2_s, int max_iter, cudaStream_t st, int grid) {
-  update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
-                                      max_iter);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Early Stopping bookkeeping (Sec. II-C), one CTA of 1024 threads.
-//
-// The clock r counts updates.  A seed takes update r+1 when it is RUNNING and
-// has made exactly r updates, so seeds added by a doubling start at 0 while
-// seeds left unconverged by an earlier round wait until the clock reaches
-// their count: the round then behaves exactly like a fresh run over all N
-// seeds.  After each update the kernel counts the seeds whose convergence
-// update is <= r and stops the round once that count reaches
-// target = ceil(gamma*N), when no seed is RUNNING, or at max_iter.
-// When no seed is due at r but the round goes on, the clock jumps to the next
-// event (a waiting seed's count or a convergence update of an earlier round).
-// ---------------------------------------------------------------------------
-constexpr int kCompactThreads = 1024;
-
-// Scan at clock r: writes the active list, returns (via smem) its size, the
-// count of seeds converged by r, the number still RUNNING and the next event.
-__device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
-                           const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
-                           int32_t* __restrict__ active, int* s_out, int* conv_out,
-                           int* running_out, int* next_event_out, int* scratch) {
-  int base = 0, convd = 0, running = 0, nxt = INT32_MAX;
-  for (int b = 0; b < N; b += blockDim.x) {
-    const int i = b + threadIdx.x;
-    int take = 0;
-    if (i < N) {
-      const int stt = state[i];
-      const int ti = it[i];
-      if (stt == kRunning) {
-        ++running;
-        if (ti == r) take = 1;
-        else if (ti > r) nxt = min(nxt, ti);
-      } else if (stt == kConverged) {
-        const int ci = conv[i];
-        if (ci <= r) ++convd;
-        else nxt = min(nxt, ci);
-      }
-    }
-    int tot;
-    const int off = block_exclusive_scan(take, &tot, scratch);
-    if (take) active[base + off] = i;
-    base += tot;
-  }
-  convd = block_sum(convd, scratch);
-  running = block_sum(running, scratch);
-  nxt = block_min(nxt, scratch);
-  *s_out = base;
-  *conv_out = convd;
-  *running_out = running;
-  *next_event_out = nxt;
-}
-
-__global__ void __launch_bounds__(kCompactThreads)
-    compact_kernel(IterCtl* ctl, const int32_t* __restrict__ state, const int32_t* __restrict__ it,
-                   const int32_t* __restrict__ conv, int32_t* __restrict__ active, int64_t n,
-                   int32_t R, Tiling tl, int begin, int N, int target, int max_iter) {
-  __shared__ int scratch[64];
-  __shared__ int sh_done;
-  if (!begin && ctl->done) return;
-  int r = begin ? 0 : ctl->r + 1;
-  const int prev_s = begin ? 0 : ctl->s;
-  int s = 0, convd = 0, running = 0, nxt = 0;
-  int done = 0;
-  for (int guard = 0; guard <= max_iter + 2; ++guard) {
-    scan_clock(r, N, state, it, conv, active, &s, &convd, &running, &nxt, scratch);
-    done = (convd >= target) || (r >= max_iter);
-    if (!done && s == 0) {
-      // nothing is due at r: move the clock to the next event (a waiting
-      // seed's update count or a convergence update of an earlier round);
-      // with no event left the round ends at max_iter
-      r = (nxt == INT32_MAX || nxt > max_iter) ? max_iter : nxt;
-      continue;
-    }
-    break;
-  }
-  if (threadIdx.x == 0) sh_done = done;
+  // last block to finish runs the bookkeeping for the next update
+  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    done = sh_done;
-    ctl->N = N;
-    ctl->target = target;
-    ctl->max_iter = max_iter;
-    ctl->r = r;
-    ctl->done = done;
-    ctl->n_converged = convd;
-    if (prev_s > 0) ctl->steps += 1;
-    ctl->s = done ? 0 : s;
-    int C = 0, Lc = 0;
-    if (!done) choose_chunks(n, s, R, tl, &C, &Lc);
-    ctl->C = C;
-    ctl->Lc = Lc;
-    if (!done) ctl->evals += (int64_t)s * n;
-  }
+  if (threadIdx.x == 0) sh_last = (atomicAdd(&ctl->blocks_done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  compaction_body(ctl, state, it, conv, active, n, R, tl, 0, N, target, max_iter, scratch);
 }
 
-cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
-                              const int32_t* conv, int32_t* active, int64_t n, int32_t R,
-                              Tiling tl, int N, int target, int max_iter, cudaStream_t st) {
-  compact_kernel<<<1, kCompactThreads, 0, st>>>(ctl, state, it, conv, active, n, R, tl, 1, N,
-                                                target, max_iter);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_compact(IterCtl* ctl, const int32_t* state, const int32_t* it,
-                           const int32_t* conv, int32_t* active, int64_t n, int32_t R, Tiling tl,
-                           int N, int target, int max_iter, cudaStream_t st) {
-  compact_kernel<<<1, kCompactThreads, 0, st>>>(ctl, state, it, conv, active, n, R, tl, 0, N,
-                                                target, max_iter);
+cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
+                          int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
+                          int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
+                          cudaStream_t st, int grid) {
+  update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s, n,
+                                      R, tl, N, target, max_iter);
   return cudaGetLastError();
 }
 

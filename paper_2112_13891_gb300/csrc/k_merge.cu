@@ -156,10 +156,132 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) *M_out = M;
 }
 
+// Same prune with the candidates in shared memory, in two parallel stages:
+// (1) the block sorts the candidates by (score descending, rank ascending)
+// with a bitonic sort; (2) one warp walks the sorted list 32 candidates at a
+// time: every lane tests its candidate against the modes accepted so far, and
+// the survivors of a batch are resolved in order (the lowest surviving lane is
+// accepted and removes the later lanes within r).  The accepted set and its
+// order are those of the one-by-one greedy visit.
+template <typename PT, typename ST>
+__global__ void __launch_bounds__(1024)
+    greedy_sorted_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
+                         const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
+                         PT r2, int32_t* __restrict__ accepted, int32_t* __restrict__ M_out,
+                         int P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = *K_ptr;
+  // layout: keys[P] (ST), idx[P] (int), spos[K*d] (PT, sorted order), apos[K*d] (PT)
+  ST* keys = reinterpret_cast<ST*>(smem);
+  int* idx = reinterpret_cast<int*>(keys + P);
+  PT* spos = reinterpret_cast<PT*>(smem + (((size_t)P * (sizeof(ST) + 4) + 15) / 16) * 16);
+  PT* apos = spos + (size_t)K * d;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    keys[i] = i < K ? score[i] : (ST)-INFINITY;
+    idx[i] = i < K ? i : INT32_MAX;
+  }
+  __syncthreads();
+  // bitonic sort: "a before b" iff a.key > b.key, or equal keys and a.idx < b.idx
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const ST ka = keys[i], kb = keys[l];
+          const int ia = idx[i], ib = idx[l];
+          const bool a_first = (ka > kb) || (ka == kb && ia < ib);
+          const bool up = (i & k) == 0;
+          if (up != a_first) {
+            keys[i] = kb;
+            keys[l] = ka;
+            idx[i] = ib;
+            idx[l] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = threadIdx.x; e < K * d; e += blockDim.x) {
+    const int i = e / d, k = e - i * d;
+    const int q = idx[i];
+    const int64_t row = cand_row ? cand_row[q] : q;
+    spos[e] = pos[row * DP + k];
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int nacc = 0;
+  for (int base = 0; base < K; base += 32) {
+    const int i = base + lane;
+    bool alive = i < K;
+    const PT* cp = spos + (size_t)(alive ? i : 0) * d;
+    for (int a = 0; a < nacc && __any_sync(kFull, alive); ++a) {
+      if (alive) {
+        const PT* ap = apos + (size_t)a * d;
+        PT d2 = 0;
+        for (int k = 0; k < d; ++k) {
+          const PT e = cp[k] - ap[k];
+          d2 += e * e;
+        }
+        if (d2 < r2) alive = false;
+      }
+    }
+    for (;;) {
+      const unsigned m = __ballot_sync(kFull, alive);
+      if (!m) break;
+      const int w = __ffs(m) - 1;
+      if (lane == w) {
+        accepted[nacc] = idx[i];
+        for (int k = 0; k < d; ++k) apos[(size_t)nacc * d + k] = cp[k];
+      }
+      __syncwarp();
+      const PT* wp = apos + (size_t)nacc * d;
+      ++nacc;
+      if (alive) {
+        if (lane == w) {
+          alive = false;
+        } else {
+          PT d2 = 0;
+          for (int k = 0; k < d; ++k) {
+            const PT e = cp[k] - wp[k];
+            d2 += e * e;
+          }
+          if (d2 < r2) alive = false;
+        }
+      }
+    }
+  }
+  if (lane == 0) *M_out = nacc;
+}
+
+template <typename PT, typename ST>
+size_t greedy_sorted_bytes(int K, int d, int* P_out) {
+  int P = 1;
+  while (P < K) P <<= 1;
+  *P_out = P;
+  return (((size_t)P * (sizeof(ST) + 4) + 15) / 16) * 16 + 2 * (size_t)K * d * sizeof(PT);
+}
+
+constexpr size_t kGreedySmemMax = 200 * 1024;
+
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
                                   const float* score, const float* pos, int DP, int d, float r2,
-                                  int32_t* alive, int32_t* accepted, int32_t* M_out,
+                                  int32_t* alive, int32_t* accepted, int32_t* M_out, int max_K,
                                   cudaStream_t st) {
+  int P = 1;
+  const size_t sm = greedy_sorted_bytes<float, float>(max_K, d, &P);
+  if (sm <= kGreedySmemMax) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(greedy_sorted_kernel<float, float>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
+      attr = true;
+    }
+    greedy_sorted_kernel<float, float><<<1, 1024, sm, st>>>(cand_row, K_ptr, score, pos, DP, d,
+                                                            r2, accepted, M_out, P);
+    return cudaGetLastError();
+  }
   greedy_merge_kernel<float, float><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
                                                         alive, accepted, M_out);
   return cudaGetLastError();
@@ -167,7 +289,20 @@ cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
 
 cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
                                   int DP, int d, double r2, int32_t* alive, int32_t* accepted,
-                                  int32_t* M_out, cudaStream_t st) {
+                                  int32_t* M_out, int max_K, cudaStream_t st) {
+  int P = 1;
+  const size_t sm = greedy_sorted_bytes<double, double>(max_K, d, &P);
+  if (sm <= kGreedySmemMax) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(greedy_sorted_kernel<double, double>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
+      attr = true;
+    }
+    greedy_sorted_kernel<double, double><<<1, 1024, sm, st>>>(nullptr, K_ptr, score, pos, DP, d,
+                                                              r2, accepted, M_out, P);
+    return cudaGetLastError();
+  }
   greedy_merge_kernel<double, double><<<1, 1024, 0, st>>>(nullptr, K_ptr, score, pos, DP, d, r2,
                                                           alive, accepted, M_out);
   return cudaGetLastError();
@@ -191,131 +326,104 @@ cudaError_t launch_doubling_decision(MergeCtl* mctl, int32_t N, int64_t n, float
 }
 
 // ---------------------------------------------------------------------------
-// Refinement: more updates of each merged mode with FP64 positions and
-// FP64 accumulation across chunks.  Distances use exact FP32 differences
-// against the position split into hi + lo floats; within one warp task the
-// sums are FP32 (at most Lc/32 terms per lane, then a fixed shuffle tree).
+// Refinement: more updates of each merged mode, run by ms_step on the FP32
+// rounding yf of an FP64 position ym.  With S, W the FP32 chunk partials
+// against yf, summed over chunks in FP64, the update is
+//   ym <- ym + S/W - (ym - yf)        (= m(yf), in FP64)
+// so positions keep FP64 resolution and the convergence test
+// ||step|| <= 1e-5*h is taken in FP64.  At most 50 updates per mode.
 // ---------------------------------------------------------------------------
-__global__ void refine_init_kernel(const float* __restrict__ y, const int32_t* __restrict__ kept,
-                                   const int32_t* __restrict__ accepted, MergeCtl* mctl, int DP,
-                                   double* __restrict__ ym, int32_t* __restrict__ mdone,
-                                   int64_t n, Tiling tl) {
-  const int M = mctl->M;
+__global__ void refine_setup_kernel(const float* __restrict__ y, const int32_t* __restrict__ kept,
+                                    const int32_t* __restrict__ accepted, const int32_t* M_ptr,
+                                    int DP, double* __restrict__ ym, float* __restrict__ yf,
+                                    int32_t* __restrict__ active, int32_t* __restrict__ mdone,
+                                    IterCtl* rctl, int init_pos, int64_t n, int32_t R, Tiling tl) {
+  const int M = *M_ptr;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * DP; e += gridDim.x * blockDim.x) {
     const int m = e / DP, k = e % DP;
-    ym[e] = (double)y[(int64_t)kept[accepted[m]] * DP + k];
-    if (k == 0) mdone[m] = 0;
+    if (init_pos) {
+      const float v = y[(int64_t)kept[accepted[m]] * DP + k];
+      ym[e] = (double)v;
+      yf[e] = v;
+    }
+    if (k == 0) {
+      active[m] = m;
+      if (init_pos) mdone[m] = 0;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    int C, Lc;
-    Tiling rt = tl;
-    rt.min_chunk = 2048;
-    choose_chunks(n, M, 1, rt, &C, &Lc);
-    mctl->Cr = C;
-    mctl->Lcr = Lc;
-    mctl->refine_iters = 0;
-    mctl->refine_active = M;
+    int C = 0, Lc = 0;
+    choose_chunks(n, M, R, tl, &C, &Lc);
+    rctl->s = M;
+    rctl->C = C;
+    rctl->Lc = Lc;
+    rctl->r = 0;
+    rctl->done = M > 0 ? 0 : 1;
+    rctl->N = M;
+    rctl->blocks_done = 0;
+    if (init_pos) rctl->steps = 0;
   }
 }
 
-cudaError_t launch_refine_init(const float* y, const int32_t* kept, const int32_t* accepted,
-                               MergeCtl* mctl, int DP, double* ym, int32_t* mdone, int64_t n,
-                               Tiling tl, int max_M, cudaStream_t st) {
+cudaError_t launch_refine_setup(const float* y, const int32_t* kept, const int32_t* accepted,
+                                const int32_t* M_ptr, int DP, double* ym, float* yf,
+                                int32_t* active, int32_t* mdone, IterCtl* rctl, int init_pos,
+                                int64_t n, int32_t R, Tiling tl, int max_M, cudaStream_t st) {
   int blocks = (max_M * DP + 255) / 256;
   if (blocks < 1) blocks = 1;
   if (blocks > 1024) blocks = 1024;
-  refine_init_kernel<<<blocks, 256, 0, st>>>(y, kept, accepted, mctl, DP, ym, mdone, n, tl);
+  refine_setup_kernel<<<blocks, 256, 0, st>>>(y, kept, accepted, M_ptr, DP, ym, yf, active, mdone,
+                                              rctl, init_pos, n, R, tl);
   return cudaGetLastError();
 }
 
-template <int DPAD>
 __global__ void __launch_bounds__(256)
-    refine_step_kernel(const float* __restrict__ Xs, int64_t n, int d, int DP,
-                       const double* __restrict__ ym, const int32_t* __restrict__ mdone,
-                       const MergeCtl* __restrict__ mctl, double* __restrict__ part64) {
-  const int M = mctl->M;
-  const int C = mctl->Cr, Lc = mctl->Lcr;
-  const int64_t T = (int64_t)M * C;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
-       task += nw) {
-    const int m = (int)(task % M);
-    const int c = (int)(task / M);
-    if (mdone[m]) continue;
-    float yh[DPAD], yl[DPAD], acc[DPAD + 1];
-#pragma unroll
-    for (int k = 0; k < DPAD; ++k) {
-      const double v = k < DP ? ym[(int64_t)m * DP + k] : 0.0;
-      yh[k] = (float)v;
-      yl[k] = (float)(v - (double)yh[k]);
-      acc[k + 1] = 0.0f;
-    }
-    acc[0] = 0.0f;
-    const int64_t j0 = (int64_t)c * Lc;
-    const int64_t j1 = j0 + Lc < n ? j0 + Lc : n;
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
-      float dx[DPAD];
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) dx[k] = k < DP ? (Xs[j * DP + k] - yh[k]) - yl[k] : 0.0f;
-      float t = -dx[0] * dx[0];
-#pragma unroll
-      for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
-      const float w = ex2_ftz(t);
-      acc[0] += w;
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) acc[1 + k] = fmaf(w, dx[k], acc[1 + k]);
-    }
-#pragma unroll
-    for (int k = 0; k <= DPAD; ++k) {
-      float v = acc[k];
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      acc[k] = v;
-    }
-    double* o = part64 + ((int64_t)c * M + m) * (d + 1);
-#pragma unroll
-    for (int k = 0; k <= DPAD; ++k)
-      if ((k & 31) == lane && k <= d) o[k] = (double)acc[k];
-  }
-}
-
-cudaError_t launch_refine_step(const float* Xs, int64_t n, int d, int DP, const double* ym,
-                               const int32_t* mdone, const MergeCtl* mctl, double* part64,
-                               int grid_ctas, cudaStream_t st) {
-  if (d <= 4)
-    refine_step_kernel<4><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
-  else if (d <= 8)
-    refine_step_kernel<8><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
-  else if (d <= 16)
-    refine_step_kernel<16><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
-  else if (d <= 32)
-    refine_step_kernel<32><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
-  else
-    refine_step_kernel<64><<<grid_ctas, 256, 0, st>>>(Xs, n, d, DP, ym, mdone, mctl, part64);
-  return cudaGetLastError();
-}
-
-// One warp per mode: FP64 sums over chunks (chunk order), then move the mode
-// (or, with score_only, record W = sum_j w_j at the current position).
-__global__ void refine_update_kernel(const double* __restrict__ part64, MergeCtl* mctl,
-                                     double* __restrict__ ym, int32_t* __restrict__ mdone,
-                                     double* __restrict__ mscore, int d, int DP, double tol2_s,
-                                     int score_only) {
-  const int M = mctl->M;
-  const int C = mctl->Cr;
+    refine_update_kernel(const float* __restrict__ part, int32_t* __restrict__ active,
+                         IterCtl* rctl, double* __restrict__ ym, float* __restrict__ yf,
+                         int32_t* __restrict__ mdone, double* __restrict__ mscore, int d, int DP,
+                         int DA, double tol2_s, int max_iter, int score_only, int64_t n,
+                         int32_t R, Tiling tl) {
+  __shared__ int scratch[64];
+  __shared__ int sh_last;
+  if (__ldcg(&rctl->done)) return;
+  const int s = __ldcg(&rctl->s), C = __ldcg(&rctl->C);
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += nw) {
-    if (!score_only && mdone[m]) continue;
-    // lane l sums chunks l, l+32, ... in order; a fixed xor tree combines them
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
+    const int m = __ldcg(active + p);
+    // lane l sums chunks l, l+32, ... in FP64; fixed xor tree; lane k keeps
+    // accumulator k (W for k = 0, S_{k-1} otherwise)
     double a[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k <= d; ++k) {
-      double v = 0.0;
-      for (int c = lane; c < C; c += 32) v += part64[((int64_t)c * M + m) * (d + 1) + k];
+    for (int k0 = 0; k0 <= d; k0 += 4) {
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      if ((DA & 3) == 0) {
+        for (int c = lane; c < C; c += 32) {
+          const float4 q = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)c * s + p) * DA + k0));
+          v0 += (double)q.x;
+          v1 += (double)q.y;
+          v2 += (double)q.z;
+          v3 += (double)q.w;
+        }
+      } else {
+        for (int c = lane; c < C; c += 32) {
+          const float2 q = __ldcg(reinterpret_cast<const float2*>(part + ((int64_t)c * s + p) * DA));
+          v0 += (double)q.x;
+          v1 += (double)q.y;
+        }
+      }
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if ((k & 31) == lane) a[k >> 5] = v;
+      for (int o = 16; o >= 1; o >>= 1) {
+        v0 += __shfl_xor_sync(kFull, v0, o);
+        v1 += __shfl_xor_sync(kFull, v1, o);
+        v2 += __shfl_xor_sync(kFull, v2, o);
+        v3 += __shfl_xor_sync(kFull, v3, o);
+      }
+      const double vals[4] = {v0, v1, v2, v3};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = k0 + e;
+        if (k <= d && (k & 31) == lane) a[k >> 5] = vals[e];
+      }
     }
     const double W = __shfl_sync(kFull, a[0], 0);
     if (score_only) {
@@ -328,7 +436,8 @@ __global__ void refine_update_kernel(const double* __restrict__ part64, MergeCtl
     for (int u = 0; u < 3; ++u) {
       const int k = lane + 32 * u;
       if (ok && k >= 1 && k <= d) {
-        delta[u] = a[u] / W;
+        const int64_t e = (int64_t)m * DP + (k - 1);
+        delta[u] = a[u] / W - (ym[e] - (double)yf[e]);
         step2 += delta[u] * delta[u];
       }
     }
@@ -338,36 +447,59 @@ __global__ void refine_update_kernel(const double* __restrict__ part64, MergeCtl
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int k = lane + 32 * u;
-        if (k >= 1 && k <= d) ym[(int64_t)m * DP + (k - 1)] += delta[u];
+        if (k >= 1 && k <= d) {
+          const int64_t e = (int64_t)m * DP + (k - 1);
+          const double v = ym[e] + delta[u];
+          ym[e] = v;
+          yf[e] = (float)v;
+        }
       }
     }
     if (lane == 0 && (!ok || step2 <= tol2_s)) mdone[m] = 1;
   }
-  if (!score_only && blockIdx.x == 0 && threadIdx.x == 0) mctl->refine_iters += 1;
+  if (score_only) return;
+  // last block: the modes still moving take the next update
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sh_last = (atomicAdd(&rctl->blocks_done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  const int M = __ldcg(&rctl->N);
+  int base = 0;
+  for (int b0 = 0; b0 < M; b0 += blockDim.x) {
+    const int m = b0 + threadIdx.x;
+    const int take = (m < M && !__ldcg(mdone + m)) ? 1 : 0;
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) active[base + off] = m;
+    base += tot;
+  }
+  if (threadIdx.x == 0) {
+    const int r = __ldcg(&rctl->r) + 1;
+    const int done = (base == 0) || (r >= max_iter);
+    rctl->r = r;
+    rctl->steps = r;
+    rctl->done = done;
+    rctl->s = done ? 0 : base;
+    int Cn = 0, Lcn = 0;
+    if (!done) choose_chunks(n, base, R, tl, &Cn, &Lcn);
+    rctl->C = Cn;
+    rctl->Lc = Lcn;
+    if (!done) rctl->evals += (int64_t)base * n;
+    rctl->blocks_done = 0;
+  }
 }
 
-cudaError_t launch_refine_update(const double* part64, MergeCtl* mctl, double* ym,
-                                 int32_t* mdone, double* mscore, int d, int DP, double tol2_s,
-                                 int score_only, int max_M, cudaStream_t st) {
+cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
+                                 float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
+                                 double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
+                                 Tiling tl, int max_M, cudaStream_t st) {
   int blocks = (max_M + 7) / 8;
   if (blocks < 1) blocks = 1;
-  if (blocks > 1024) blocks = 1024;
-  refine_update_kernel<<<blocks, 256, 0, st>>>(part64, mctl, ym, mdone, mscore, d, DP, tol2_s,
-                                               score_only);
-  return cudaGetLastError();
-}
-
-__global__ void refine_count_kernel(MergeCtl* mctl, const int32_t* __restrict__ mdone) {
-  __shared__ int red[32];
-  const int M = mctl->M;
-  int c = 0;
-  for (int m = threadIdx.x; m < M; m += blockDim.x) c += mdone[m] ? 0 : 1;
-  c = block_sum(c, red);
-  if (threadIdx.x == 0) mctl->refine_active = c;
-}
-
-cudaError_t launch_refine_count(MergeCtl* mctl, const int32_t* mdone, cudaStream_t st) {
-  refine_count_kernel<<<1, 1024, 0, st>>>(mctl, mdone);
+  if (blocks > 1216) blocks = 1216;
+  refine_update_kernel<<<blocks, 256, 0, st>>>(part, active, rctl, ym, yf, mdone, mscore, d, DP,
+                                               DA, tol2_s, max_iter, score_only, n, R, tl);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,659 @@
+// ms_round: one Seed-Selection round of Gaussian mean-shift updates, run by
+// thread-block clusters that own disjoint seed subsets and iterate them with
+// no grid-wide synchronisation.
+//
+// Decomposition.  A cluster of kClusterCtas CTAs (one per SM, 16 warps each)
+// owns up to kSeedsPerCluster seeds.  CTA rank r of the cluster owns a fixed
+// slice of the points, split again into a fixed sub-slice per warp.  In each
+// update every warp evaluates all active seeds of its cluster (groups of R
+// seeds in registers) against its sub-slice; the warp partials are summed in
+// warp order, then the CTA partials are summed in rank order through
+// distributed shared memory.  Every CTA computes the same update from the same
+// sums, so the seed state stays replicated in shared memory; rank 0 writes it
+// back to global memory.  A seed's summation order depends only on n and the
+// slice layout, never on which other seeds are active, so results do not
+// depend on timing.
+//
+// Early Stopping (Sec. II-C) without a barrier across clusters.  Converging
+// seeds add 1 to hist[c] (c = the update at which they converged).  With
+// count(r) = sum_{c<=r} hist[c] over all seeds of all rounds, the stop update
+// of a fresh run is t* = min{r : count(r) >= ceil(gamma*N)} and a seed is kept
+// iff it converged at c <= t*.  A seed that has made k updates without
+// converging may stop as soon as count(k) >= target: then t* <= k < c, so it
+// cannot be kept whatever happens elsewhere.  count only grows, so a stale
+// read only delays a stop; no seed is ever stopped wrongly and the kept set is
+// exactly that of the synchronous rule.  Stopped seeds stay RUNNING with their
+// update count (a later round may resume them).
+#include <cooperative_groups.h>
+
+#include "fms_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fms {
+
+constexpr int kRoundWarps = 16;
+
+__device__ __forceinline__ float rs32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0];
+}
+
+template <int DP>
+struct RPt;
+template <>
+struct RPt<4> {
+  float4 a;
+};
+template <>
+struct RPt<8> {
+  float4 a, b;
+};
+
+template <int DP>
+__device__ __forceinline__ RPt<DP> rload(const float* __restrict__ Xs, int j, int j1) {
+  RPt<DP> p;
+  const float4 far = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
+  if constexpr (DP == 4) {
+    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + j) : far;
+  } else {
+    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j) : far;
+    p.b = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j + 1) : far;
+  }
+  return p;
+}
+
+template <int D, int DP>
+__device__ __forceinline__ void rcoords(const RPt<DP>& p, float (&x)[D]) {
+  float t[8];
+  t[0] = p.a.x;
+  t[1] = p.a.y;
+  t[2] = p.a.z;
+  t[3] = p.a.w;
+  if constexpr (DP == 8) {
+    t[4] = reinterpret_cast<const RPt<8>&>(p).b.x;
+    t[5] = reinterpret_cast<const RPt<8>&>(p).b.y;
+    t[6] = reinterpret_cast<const RPt<8>&>(p).b.z;
+    t[7] = reinterpret_cast<const RPt<8>&>(p).b.w;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = t[k];
+}
+
+template <int D, int R, int DA>
+__device__ __forceinline__ void reval(const float (&x)[D], const float (&ys)[R][D],
+                                      float (&acc)[R][DA]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float dx[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) dx[k] = x[k] - ys[r][k];
+    float t = -dx[0] * dx[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
+    const float w = ex2_ftz(t);
+    acc[r][0] += w;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
+  }
+}
+
+// Partial sums of RR seeds (active positions a0..a0+RR-1, clamped to A-1)
+// over the points [w0, w1) handled by this warp: lane l returns accumulator
+// l % DA of seed l / DA (zero for seed slots beyond RR).  The arithmetic of a
+// seed does not depend on RR.
+template <int D, int DP, int DA, int RR>
+__device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int w0, int w1,
+                                               int lane, const int* alist, int a0, int A,
+                                               const float (*sy)[D]) {
+  float ys[RR][D];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    const int i = alist[min(a0 + r, A - 1)];
+#pragma unroll
+    for (int k = 0; k < D; ++k) ys[r][k] = sy[i][k];
+  }
+  float acc[RR][DA];
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
+  int j = w0 + lane;
+  RPt<DP> b0 = rload<DP>(Xs, j, w1), b1 = rload<DP>(Xs, j + 32, w1);
+  RPt<DP> b2 = rload<DP>(Xs, j + 64, w1), b3 = rload<DP>(Xs, j + 96, w1);
+  for (; j < w1; j += 128) {
+    const RPt<DP> p0 = b0, p1 = b1, p2 = b2, p3 = b3;
+    b0 = rload<DP>(Xs, j + 128, w1);
+    b1 = rload<DP>(Xs, j + 160, w1);
+    b2 = rload<DP>(Xs, j + 192, w1);
+    b3 = rload<DP>(Xs, j + 224, w1);
+    float x[D];
+    rcoords<D, DP>(p0, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p1, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p2, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p3, x);
+    reval<D, RR, DA>(x, ys, acc);
+  }
+  float v[32];
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) v[r * DA + k] = acc[r][k];
+  return rs32(v, lane);
+}
+
+template <int D, int DP, int DA>
+__global__ void __launch_bounds__(kRoundWarps * 32, 1)
+    ms_round_kernel(const float* __restrict__ Xs, int n, float* __restrict__ y,
+                    int32_t* __restrict__ it, int32_t* __restrict__ conv,
+                    int32_t* __restrict__ state, const int32_t* __restrict__ list,
+                    const int32_t* __restrict__ S_ptr, int32_t* hist, int target, int max_iter,
+                    float tol2_s, unsigned long long* evals) {
+  constexpr int R = 32 / DA;
+  constexpr int SMAX = kSeedsPerCluster;
+  constexpr int GMAX = (SMAX + R - 1) / R;
+  __shared__ float sy[SMAX][D];
+  __shared__ int sit[SMAX];
+  __shared__ int sslot[SMAX];
+  __shared__ int sact[SMAX];   // 1: takes updates in this round
+  __shared__ int alist[SMAX];
+  __shared__ int sstop[SMAX];  // rank 0's stop decisions, read by the other ranks
+  __shared__ float wb[kRoundWarps][GMAX][32];
+  __shared__ float cpart[SMAX][DA];   // this CTA's sums, read by every rank
+  __shared__ float tot[SMAX][DA];
+  __shared__ int sA;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int ncl = (int)cluster.num_blocks();
+  const int q = blockIdx.x / ncl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // seeds of the round, split evenly over the clusters of the grid (the host
+  // only takes this path when S <= clusters * kSeedsPerCluster)
+  const int S = *S_ptr;
+  const int nclusters = gridDim.x / ncl;
+  const int per_cluster = min(SMAX, (S + nclusters - 1) / nclusters);
+  const int s0 = q * per_cluster;
+  const int ns = max(0, min(per_cluster, S - s0));
+
+  // the cluster's seeds, replicated in every CTA
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    const int slot = list[s0 + i];
+    sslot[i] = slot;
+    sit[i] = it[slot];
+    sact[i] = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sy[i][k] = y[(int64_t)slot * DP + k];
+  }
+  // fixed point slices: rank -> [cb, ce), warp -> [wb0, we)
+  const int per_cta = ((n + ncl - 1) / ncl + 31) / 32 * 32;
+  const int cb = min(n, rank * per_cta), ce = min(n, cb + per_cta);
+  const int per_warp = ((ce - cb + kRoundWarps - 1) / kRoundWarps + 31) / 32 * 32;
+  const int w0 = min(ce, cb + warp * per_warp), w1 = min(ce, w0 + per_warp);
+  __syncthreads();
+
+  for (int guard = 0; guard <= max_iter; ++guard) {
+    // active list (identical in every CTA: built from replicated state)
+    if (warp == 0) {
+      int base = 0;
+      for (int b0 = 0; b0 < ns; b0 += 32) {
+        const int i = b0 + lane;
+        const int take = (i < ns) && sact[i];
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) alist[base + __popc(m & ((1u << lane) - 1))] = i;
+        base += __popc(m);
+      }
+      if (lane == 0) sA = base;
+    }
+    __syncthreads();
+    const int A = sA;
+    if (A == 0) break;
+    const int G = (A + R - 1) / R;
+
+    // partial sums of every active seed over this warp's points; a group with
+    // fewer than R live seeds keeps only the next power of two in registers
+    for (int g = 0; g < G; ++g) {
+      const int cnt = min(R, A - g * R);
+      float res;
+      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 1) res = group_partial<D, DP, DA, 2>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else res = group_partial<D, DP, DA, 1>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      wb[warp][g][lane] = res;
+    }
+    __syncthreads();
+    // this CTA's sums, warps in order
+    for (int t = threadIdx.x; t < G * 32; t += blockDim.x) {
+      const int g = t >> 5, l = t & 31;
+      float sum = 0.0f;
+      for (int w = 0; w < kRoundWarps; ++w) sum += wb[w][g][l];
+      const int a = g * R + l / DA;
+      if (a < A) cpart[a][l % DA] = sum;
+    }
+    cluster.sync();
+    // cluster sums, ranks in order (every CTA computes the same totals)
+    for (int t = threadIdx.x; t < A * DA; t += blockDim.x) {
+      const int a = t / DA, k = t - a * DA;
+      float sum = 0.0f;
+      for (int rr = 0; rr < ncl; ++rr) sum += cluster.map_shared_rank(&cpart[0][0], rr)[a * DA + k];
+      tot[a][k] = sum;
+    }
+    __syncthreads();
+    // update, convergence test and stop decision of each active seed
+    for (int a = threadIdx.x; a < A; a += blockDim.x) {
+      const int i = alist[a];
+      const float W = tot[a][0];
+      bool ok = (W > 0.0f) && isfinite(W);
+      float step2 = 0.0f, dl[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dl[k] = ok ? tot[a][1 + k] / W : 0.0f;
+        step2 = fmaf(dl[k], dl[k], step2);
+      }
+      ok = ok && isfinite(step2);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sy[i][k] += dl[k];
+      }
+      const int t = sit[i] + 1;
+      sit[i] = t;
+      int st = kRunning;
+      if (!ok) st = kFailed;
+      else if (step2 <= tol2_s) st = kConverged;
+      else if (t >= max_iter) st = kExhausted;
+      int stop = st != kRunning;
+      if (rank == 0) {
+        const int64_t slot = sslot[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) y[slot * DP + k] = sy[i][k];
+        it[slot] = t;
+        if (st == kConverged) {
+          conv[slot] = t;
+          atomicAdd(hist + t, 1);
+        }
+        state[slot] = st;
+        if (!stop) {
+          // count(t) >= target: t* <= t, so this seed cannot be kept any more
+          int c = 0;
+          for (int u = 1; u <= t; ++u) c += *((volatile int32_t*)hist + u);
+          stop = c >= target;
+        }
+        sstop[a] = stop;
+      }
+    }
+    if (rank == 0 && threadIdx.x == 0) atomicAdd(evals, (unsigned long long)A * (unsigned long long)n);
+    cluster.sync();
+    // every rank applies rank 0's decisions
+    for (int a = threadIdx.x; a < A; a += blockDim.x)
+      if (cluster.map_shared_rank(&sstop[0], 0)[a]) sact[alist[a]] = 0;
+    __syncthreads();
+  }
+  // keep this CTA's shared memory alive until no rank can still read it
+  cluster.sync();
+}
+
+template <int D, int DP, int DA>
+static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it, int32_t* conv,
+                                  int32_t* state, const int32_t* list, const int32_t* S_ptr,
+                                  int clusters, int32_t* hist, int target, int max_iter,
+                                  float tol2_s, unsigned long long* evals, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * kClusterCtas);
+  cfg.blockDim = dim3(kRoundWarps * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA>, Xs, n, y, it, conv, state, list,
+                            S_ptr, hist, target, max_iter, tol2_s, evals);
+}
+
+template <int D, int DP, int DA>
+static int max_clusters_t() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(kRoundWarps * 32);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int c = 0;
+  if (cudaOccupancyMaxActiveClusters(&c, ms_round_kernel<D, DP, DA>, &cfg) != cudaSuccess) c = 0;
+  return c;
+}
+
+int round_max_clusters(int d) {
+  static int cache[8] = {0};
+  if (d < 1 || d > 7) return 0;
+  if (cache[d]) return cache[d];
+  int c = 0;
+  switch (d) {
+    case 1: c = max_clusters_t<1, 4, 2>(); break;
+    case 2: c = max_clusters_t<2, 4, 4>(); break;
+    case 3: c = max_clusters_t<3, 4, 4>(); break;
+    case 4: c = max_clusters_t<4, 4, 8>(); break;
+    case 5: c = max_clusters_t<5, 8, 8>(); break;
+    case 6: c = max_clusters_t<6, 8, 8>(); break;
+    case 7: c = max_clusters_t<7, 8, 8>(); break;
+  }
+  cache[d] = c > 0 ? c : -1;
+  return c;
+}
+
+cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t* it,
+                            int32_t* conv, int32_t* state, const int32_t* list,
+                            const int32_t* S_ptr, int clusters, int32_t* hist, int target,
+                            int max_iter, float tol2_s, unsigned long long* evals,
+                            cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_round_t<1, 4, 2>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 2: return launch_round_t<2, 4, 4>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 3: return launch_round_t<3, 4, 4>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 4: return launch_round_t<4, 4, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 5: return launch_round_t<5, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 6: return launch_round_t<6, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 7: return launch_round_t<7, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// ms_refine: the merged modes take more updates with FP64 positions, on the
+// same cluster decomposition.  Each CTA keeps ym (FP64) and yf = fl32(ym) of
+// its cluster's modes in shared memory; warps evaluate the FP32 partials
+// against yf over their fixed sub-slices (exactly as in ms_round); the warp
+// sums are combined in FP64 across warps and across ranks; then
+//   ym <- ym + S/W - (ym - yf)   (= m(yf))
+// and a mode stops once ||step|| <= tol (FP64) or after max_iter updates.  A
+// final pass records W = sum_j w_j at each refined mode (its density, used to
+// order the second prune).  Partial buffers are double-buffered, so one
+// cluster barrier per update suffices.
+// ---------------------------------------------------------------------------
+template <int D, int DP, int DA>
+__global__ void __launch_bounds__(kRoundWarps * 32, 1)
+    ms_refine_kernel(const float* __restrict__ Xs, int n, const float* __restrict__ y,
+                     const int32_t* __restrict__ kept, const int32_t* __restrict__ accepted,
+                     const int32_t* __restrict__ M_ptr, double* __restrict__ ym,
+                     float* __restrict__ yf, double* __restrict__ mscore, double tol2_s,
+                     int max_iter, int32_t* iters_out, unsigned long long* evals) {
+  constexpr int R = 32 / DA;
+  constexpr int SMAX = kModesPerCluster;
+  constexpr int GMAX = (SMAX + R - 1) / R;
+  __shared__ float sy[SMAX][D];
+  __shared__ double sym[SMAX][D];
+  __shared__ int sact[SMAX];
+  __shared__ int alist[SMAX];
+  __shared__ float wb[kRoundWarps][GMAX][32];
+  __shared__ double cpart[2][SMAX][DA];
+  __shared__ double tot[SMAX][DA];
+  __shared__ int sA;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int ncl = (int)cluster.num_blocks();
+  const int q = blockIdx.x / ncl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M = *M_ptr;
+  const int nclusters = gridDim.x / ncl;
+  const int per_cluster = min(SMAX, (M + nclusters - 1) / nclusters);
+  const int s0 = q * per_cluster;
+  const int ns = max(0, min(per_cluster, M - s0));
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    const int64_t src = kept[accepted[s0 + i]];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float v = y[src * DP + k];
+      sy[i][k] = v;
+      sym[i][k] = (double)v;
+    }
+    sact[i] = 1;
+  }
+  const int per_cta = ((n + ncl - 1) / ncl + 31) / 32 * 32;
+  const int cb = min(n, rank * per_cta), ce = min(n, cb + per_cta);
+  const int per_warp = ((ce - cb + kRoundWarps - 1) / kRoundWarps + 31) / 32 * 32;
+  const int w0 = min(ce, cb + warp * per_warp), w1 = min(ce, w0 + per_warp);
+  __syncthreads();
+
+  int iters = 0;
+  // pass 0..max_iter-1: updates; the pass after the loop: densities only
+  for (int pass = 0;; ++pass) {
+    const bool score_pass = (pass >= max_iter);
+    if (warp == 0) {
+      int base = 0;
+      for (int b0 = 0; b0 < ns; b0 += 32) {
+        const int i = b0 + lane;
+        const int take = (i < ns) && (score_pass || sact[i]);
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) alist[base + __popc(m & ((1u << lane) - 1))] = i;
+        base += __popc(m);
+      }
+      if (lane == 0) sA = base;
+    }
+    __syncthreads();
+    int A = sA;
+    if (A == 0 && !score_pass) {
+      // every mode has converged: go to the density pass
+      pass = max_iter - 1;
+      __syncthreads();
+      continue;
+    }
+    const int G = (A + R - 1) / R;
+    for (int g = 0; g < G; ++g) {
+      const int cnt = min(R, A - g * R);
+      float res;
+      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 1) res = group_partial<D, DP, DA, 2>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else res = group_partial<D, DP, DA, 1>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      wb[warp][g][lane] = res;
+    }
+    __syncthreads();
+    const int buf = pass & 1;
+    for (int t = threadIdx.x; t < G * 32; t += blockDim.x) {
+      const int g = t >> 5, l = t & 31;
+      double sum = 0.0;
+      for (int w = 0; w < kRoundWarps; ++w) sum += (double)wb[w][g][l];
+      const int a = g * R + l / DA;
+      if (a < A) cpart[buf][a][l % DA] = sum;
+    }
+    cluster.sync();
+    for (int t = threadIdx.x; t < A * DA; t += blockDim.x) {
+      const int a = t / DA, k = t - a * DA;
+      double sum = 0.0;
+      for (int rr = 0; rr < ncl; ++rr)
+        sum += cluster.map_shared_rank(&cpart[buf][0][0], rr)[a * DA + k];
+      tot[a][k] = sum;
+    }
+    __syncthreads();
+    if (rank == 0 && threadIdx.x == 0 && A > 0)
+      atomicAdd(evals, (unsigned long long)A * (unsigned long long)n);
+    if (score_pass) {
+      if (rank == 0)
+        for (int a = threadIdx.x; a < A; a += blockDim.x) mscore[s0 + alist[a]] = tot[a][0];
+      break;
+    }
+    ++iters;
+    for (int a = threadIdx.x; a < A; a += blockDim.x) {
+      const int i = alist[a];
+      const double W = tot[a][0];
+      bool ok = W > 0.0 && isfinite(W);
+      double step2 = 0.0, dl[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dl[k] = ok ? tot[a][1 + k] / W - (sym[i][k] - (double)sy[i][k]) : 0.0;
+        step2 += dl[k] * dl[k];
+      }
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          sym[i][k] += dl[k];
+          sy[i][k] = (float)sym[i][k];
+        }
+      }
+      if (!ok || step2 <= tol2_s) sact[i] = 0;
+    }
+    __syncthreads();
+  }
+  if (rank == 0) {
+    for (int e = threadIdx.x; e < ns * D; e += blockDim.x) {
+      const int i = e / D, k = e - i * D;
+      ym[(int64_t)(s0 + i) * DP + k] = sym[i][k];
+      yf[(int64_t)(s0 + i) * DP + k] = sy[i][k];
+    }
+    if (threadIdx.x == 0 && ns > 0) atomicMax(iters_out, iters);
+  }
+  cluster.sync();
+}
+
+template <int D, int DP, int DA>
+static cudaError_t launch_refine_t(const float* Xs, int n, const float* y, const int32_t* kept,
+                                   const int32_t* accepted, const int32_t* M_ptr, int clusters,
+                                   double* ym, float* yf, double* mscore, double tol2_s,
+                                   int max_iter, int32_t* iters_out, unsigned long long* evals,
+                                   cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * kClusterCtas);
+  cfg.blockDim = dim3(kRoundWarps * 32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ms_refine_kernel<D, DP, DA>, Xs, n, y, kept, accepted, M_ptr,
+                            ym, yf, mscore, tol2_s, max_iter, iters_out, evals);
+}
+
+cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
+                             const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
+                             int clusters, double* ym, float* yf, double* mscore, double tol2_s,
+                             int max_iter, int32_t* iters_out, unsigned long long* evals,
+                             cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_refine_t<1, 4, 2>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 2: return launch_refine_t<2, 4, 4>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 3: return launch_refine_t<3, 4, 4>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 4: return launch_refine_t<4, 4, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 5: return launch_refine_t<5, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 6: return launch_refine_t<6, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 7: return launch_refine_t<7, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Round bookkeeping.  round_list: the RUNNING seeds (they take part in the
+// round), in slot order.  round_finish: t* from the histogram; the kept list
+// (converged by t*), counters for the prune.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    round_list_kernel(const int32_t* __restrict__ state, int N, int32_t* __restrict__ list,
+                      int32_t* S_out) {
+  __shared__ int scratch[64];
+  int base = 0;
+  for (int b = 0; b < N; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    const int take = (i < N) && state[i] == kRunning;
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) list[base + off] = i;
+    base += tot;
+  }
+  if (threadIdx.x == 0) *S_out = base;
+}
+
+cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
+                              cudaStream_t st) {
+  round_list_kernel<<<1, 1024, 0, st>>>(state, N, list, S_out);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(1024)
+    round_finish_kernel(const int32_t* __restrict__ hist, int target, int max_iter,
+                        const int32_t* __restrict__ state, const int32_t* __restrict__ conv, int N,
+                        int keep_exhausted, int32_t* __restrict__ kept, MergeCtl* mctl,
+                        IterCtl* ctl, int64_t n, int32_t R, Tiling tl) {
+  __shared__ int scratch[64];
+  __shared__ int sh_t;
+  if (threadIdx.x == 0) {
+    int c = 0, t = max_iter;
+    for (int r = 1; r <= max_iter; ++r) {
+      c += hist[r];
+      if (c >= target) {
+        t = r;
+        break;
+      }
+    }
+    sh_t = t;
+  }
+  __syncthreads();
+  const int t_star = sh_t;
+  int base = 0, convd = 0;
+  for (int b = 0; b < N; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    int take = 0;
+    if (i < N) {
+      const int st = state[i];
+      const int ok = st == kConverged && conv[i] <= t_star;
+      convd += ok;
+      take = keep_exhausted ? (st == kConverged || st == kExhausted) : ok;
+    }
+    int tot;
+    const int off = block_exclusive_scan(take, &tot, scratch);
+    if (take) kept[base + off] = i;
+    base += tot;
+  }
+  convd = block_sum(convd, scratch);
+  if (threadIdx.x == 0) {
+    mctl->K = base;
+    mctl->t_star = t_star;
+    int C, Lc;
+    choose_chunks(n, base, R, tl, &C, &Lc);
+    mctl->C = C;
+    mctl->Lc = Lc;
+    mctl->evals += (int64_t)base * n;
+    ctl->N = N;
+    ctl->r = t_star;
+    ctl->n_converged = convd;
+    ctl->done = 1;
+    ctl->s = 0;
+    ctl->steps += t_star;
+  }
+}
+
+cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
+                                const int32_t* state, const int32_t* conv, int N,
+                                int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
+                                int64_t n, int32_t R, Tiling tl, cudaStream_t st) {
+  round_finish_kernel<<<1, 1024, 0, st>>>(hist, target, max_iter, state, conv, N, keep_exhausted,
+                                          kept, mctl, ctl, n, R, tl);
+  return cudaGetLastError();
+}
+
+}  // namespace fms

@@ -216,6 +216,44 @@ fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n, int32_t d
 fms_status fms_label_points(const float* points, int64_t n, int32_t d, const float* modes,
                             int32_t M, int32_t* labels, float* margins, void* stream);
 
+/*
+ * Differentiable unrolled mean shift: T Gaussian updates of every seed of B
+ * independent sets (no Seed Selection, no stopping; all seeds move T times),
+ * and the adjoint of that map, for training embeddings through the
+ * clustering.  The paper has no counterpart; the update is Eq. 6 with the
+ * Gaussian weight.  With p_ij = w_ij / sum_j w_ij, mu_i = sum_j p_ij x_j,
+ * g_i = dL/dmu_i and a_ij = g_i . (x_j - mu_i), one update contributes
+ *   dL/dy_i  = (1/h^2) sum_j p_ij a_ij (x_j - mu_i)
+ *   dL/dx_j += p_ij [g_i - a_ij (x_j - y_i)/h^2]
+ *   dL/dh   += (1/h^3) sum_ij p_ij ||y_i - x_j||^2 a_ij.
+ * Weights are recomputed tile by tile (nothing of size m x n is stored); the
+ * forward stores the positions every k updates in `ckpt` and the backward
+ * recomputes one segment of k updates at a time.
+ *
+ *   points  [B x n x d], seeds0 [B x m x d], out_seeds [B x m x d]: float32,
+ *           device, row-major; 1 <= d <= 32.  h > 0, T >= 1, k >= 1.
+ *   ckpt    opaque device buffer of fms_unrolled_ckpt_size() bytes (16-byte
+ *           aligned), written by the forward and read by the backward.
+ *   ws      device workspace of fms_unrolled_workspace_size() bytes, 256-byte
+ *           aligned (the same size serves both directions).
+ *   grad_out [B x m x d] = dL/dY_T; grad_points [B x n x d] and grad_seeds0
+ *           [B x m x d] are overwritten; grad_h [B] (float64, device) receives
+ *           dL/dh of each set.
+ * Both calls are asynchronous on `stream`.
+ */
+size_t fms_unrolled_ckpt_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T, int32_t k);
+size_t fms_unrolled_workspace_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
+                                   int32_t k);
+fms_status fms_unrolled_forward(const float* points, const float* seeds0, int32_t B, int64_t n,
+                                int64_t m, int32_t d, float h, int32_t T, int32_t k,
+                                float* out_seeds, void* ckpt, size_t ckpt_bytes, void* ws,
+                                size_t ws_bytes, void* stream);
+fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int64_t m, int32_t d,
+                                 float h, int32_t T, int32_t k, const void* ckpt,
+                                 size_t ckpt_bytes, const float* grad_out, float* grad_points,
+                                 float* grad_seeds0, double* grad_h, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -230,3 +230,85 @@ def label_points(points: torch.Tensor, modes: torch.Tensor, with_margins=True):
     _check(_lib.fms_label_points(_ptr(X), n, d, _ptr(Mo), Mo.shape[0], _ptr(labels), _ptr(mar),
                                  _stream()), "fms_label_points")
     return (labels, mar) if with_margins else labels
+
+
+# ---------------------------------------------------------------------------
+# Differentiable unrolled steps (fms_unrolled_forward / fms_unrolled_backward)
+# ---------------------------------------------------------------------------
+
+_lib.fms_unrolled_ckpt_size.restype = _SZ
+_lib.fms_unrolled_ckpt_size.argtypes = [_I32, _I64, _I64, _I32, _I32, _I32]
+_lib.fms_unrolled_workspace_size.restype = _SZ
+_lib.fms_unrolled_workspace_size.argtypes = [_I32, _I64, _I64, _I32, _I32, _I32]
+_lib.fms_unrolled_forward.restype = ctypes.c_int
+_lib.fms_unrolled_forward.argtypes = [_P, _P, _I32, _I64, _I64, _I32, _F32, _I32, _I32, _P, _P,
+                                      _SZ, _P, _SZ, _P]
+_lib.fms_unrolled_backward.restype = ctypes.c_int
+_lib.fms_unrolled_backward.argtypes = [_P, _I32, _I64, _I64, _I32, _F32, _I32, _I32, _P, _SZ, _P,
+                                       _P, _P, _P, _P, _SZ, _P]
+
+
+def _batched(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not x.is_cuda or x.dim() != 3:
+        raise ValueError(f"{name} must be a CUDA tensor [B, rows, d]")
+    return x.to(torch.float32).contiguous()
+
+
+def unrolled_forward(X: torch.Tensor, Y0: torch.Tensor, h: float, T: int, k: int):
+    """T Gaussian updates of every row of Y0 (per set) against X; returns (Y_T, ckpt)."""
+    X, Y0 = _batched(X, "X"), _batched(Y0, "Y0")
+    B, n, d = X.shape
+    m = Y0.shape[1]
+    cb = int(_lib.fms_unrolled_ckpt_size(B, n, m, d, T, k))
+    wb = int(_lib.fms_unrolled_workspace_size(B, n, m, d, T, k))
+    if cb == 0 or wb == 0:
+        raise FmsError(FMS_ERR_INVALID_ARG, "fms_unrolled_forward")
+    ckpt = torch.empty(cb, dtype=torch.uint8, device=X.device)
+    ws = torch.empty(wb, dtype=torch.uint8, device=X.device)
+    out = torch.empty_like(Y0)
+    _check(_lib.fms_unrolled_forward(_ptr(X), _ptr(Y0), B, n, m, d, float(h), int(T), int(k),
+                                     _ptr(out), _ptr(ckpt), cb, _ptr(ws), wb, _stream()),
+           "fms_unrolled_forward")
+    return out, ckpt
+
+
+def unrolled_backward(X: torch.Tensor, ckpt: torch.Tensor, m: int, h: float, T: int, k: int,
+                      grad_out: torch.Tensor):
+    """Adjoint of unrolled_forward: returns (dL/dX, dL/dY0, dL/dh per set as float64)."""
+    X, G = _batched(X, "X"), _batched(grad_out, "grad_out")
+    B, n, d = X.shape
+    wb = int(_lib.fms_unrolled_workspace_size(B, n, m, d, T, k))
+    ws = torch.empty(wb, dtype=torch.uint8, device=X.device)
+    dX = torch.empty_like(X)
+    dY = torch.empty((B, m, d), dtype=torch.float32, device=X.device)
+    dh = torch.empty(B, dtype=torch.float64, device=X.device)
+    _check(_lib.fms_unrolled_backward(_ptr(X), B, n, m, d, float(h), int(T), int(k), _ptr(ckpt),
+                                      ckpt.numel(), _ptr(G), _ptr(dX), _ptr(dY), _ptr(dh),
+                                      _ptr(ws), wb, _stream()), "fms_unrolled_backward")
+    return dX, dY, dh
+
+
+class UnrolledMeanShift(torch.autograd.Function):
+    """Y_T = T Gaussian mean-shift updates of Y0 against X (per set), differentiable
+    in X, Y0 and h by the library's adjoint kernels (weights recomputed tile by
+    tile, positions checkpointed every k updates)."""
+
+    @staticmethod
+    def forward(ctx, X, Y0, h, T, k):
+        hv = float(h)
+        out, ckpt = unrolled_forward(X.detach(), Y0.detach(), hv, T, k)
+        ctx.save_for_backward(X.detach(), ckpt)
+        ctx.cfg = (hv, int(T), int(k), Y0.shape[1], torch.is_tensor(h))
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        X, ckpt = ctx.saved_tensors
+        hv, T, k, m, h_is_tensor = ctx.cfg
+        dX, dY, dh = unrolled_backward(X, ckpt, m, hv, T, k, grad_out)
+        gh = dh.sum().to(torch.float32).reshape(()) if h_is_tensor else None
+        return dX, dY, gh, None, None
+
+
+def unrolled_mean_shift(X: torch.Tensor, Y0: torch.Tensor, h, T: int = 20, k: int = 5):
+    return UnrolledMeanShift.apply(X, Y0, h, T, k)

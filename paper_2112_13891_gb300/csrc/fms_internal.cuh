@@ -229,6 +229,23 @@ cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
                                 int64_t n, int32_t R, Tiling tl, cudaStream_t st);
 
+// k_unroll.cu: unrolled steps and their adjoint
+struct UGeom {
+  int B, n, m, d, DP;  // DP: padded row length (multiple of 4) of the packed copies
+  int Cp, Lp;          // point chunks of the seed-major passes (Lp points each)
+  int Cs, Ls;          // seed chunks of the point-major pass (Ls seeds each)
+};
+cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
+                            float* Ynext, float* Wout, int grid, cudaStream_t st);
+cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
+                            const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
+                            float* part_s, float* part_p, float* gmu, float* dh_part, float* Gprev,
+                            float* dX, double* dh, int grid, cudaStream_t st);
+cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
+                             cudaStream_t st);
+cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
+                               cudaStream_t st);
+
 // k_step.cu: one update's partial sums for the active seeds
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,

@@ -1,0 +1,237 @@
+// C ABI of the differentiable unrolled mean-shift steps (see k_unroll.cu for
+// the kernels and the adjoint formulas).
+#include <math.h>
+#include <string.h>
+
+#include "../../include/fms.h"
+#include "fms_internal.cuh"
+
+
+using namespace fms;
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+bool valid(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T, int32_t k) {
+  return B >= 1 && n >= 1 && m >= 1 && n <= INT32_MAX && m <= INT32_MAX && d >= 1 && d <= 32 &&
+         T >= 1 && k >= 1 && (int64_t)B * n <= INT32_MAX && (int64_t)B * m <= INT32_MAX;
+}
+
+int sm_count() {
+  int dev = 0, s = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return s;
+}
+
+// Chunks so that (sets x groups of 32 outputs x chunks) ~ 8 tasks per resident warp.
+void chunks(int64_t groups, int64_t len, int sms, int* C, int* L) {
+  const int64_t target = (int64_t)(sms > 0 ? sms : 1) * 16 * 8;
+  int64_t c = (target + groups - 1) / groups;
+  if (c < 1) c = 1;
+  if (c > (len + 63) / 64) c = (len + 63) / 64;
+  if (c < 1) c = 1;
+  int64_t l = (len + c - 1) / c;
+  *C = (int)((len + l - 1) / l);
+  *L = (int)l;
+}
+
+UGeom geom(int32_t B, int64_t n, int64_t m, int32_t d) {
+  UGeom g{};
+  g.B = B;
+  g.n = (int)n;
+  g.m = (int)m;
+  g.d = d;
+  g.DP = (d + 3) / 4 * 4;
+  const int sms = sm_count();
+  chunks((int64_t)B * ((m + 31) / 32), n, sms, &g.Cp, &g.Lp);
+  chunks((int64_t)B * ((n + 31) / 32), m, sms, &g.Cs, &g.Ls);
+  return g;
+}
+
+int grid_blocks() {
+  const int s = sm_count();
+  return (s > 0 ? s : 1) * 8;
+}
+
+int n_ckpt(int32_t T, int32_t k) { return (T + k - 1) / k; }
+
+struct FwdLayout {
+  size_t Xp, Ya, Yb, part, total;
+};
+FwdLayout fwd_layout(const UGeom& g) {
+  FwdLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o += a256(b > 0 ? b : 1);
+    return at;
+  };
+  L.Xp = take((size_t)g.B * g.n * g.DP * 4);
+  L.Ya = take((size_t)g.B * g.m * g.DP * 4);
+  L.Yb = take((size_t)g.B * g.m * g.DP * 4);
+  L.part = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * 4);
+  L.total = o;
+  return L;
+}
+
+struct BwdLayout {
+  size_t Xp, seg, Wseg, Ga, Gb, part_s, part_p, gmu, dh_part, dXp, dh, total;
+};
+BwdLayout bwd_layout(const UGeom& g, int32_t k) {
+  BwdLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o += a256(b > 0 ? b : 1);
+    return at;
+  };
+  const size_t rowsY = (size_t)g.B * g.m;
+  L.Xp = take((size_t)g.B * g.n * g.DP * 4);
+  L.seg = take((size_t)(k + 1) * rowsY * g.DP * 4);
+  L.Wseg = take((size_t)k * rowsY * 4);
+  L.Ga = take(rowsY * g.DP * 4);
+  L.Gb = take(rowsY * g.DP * 4);
+  L.part_s = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * 4);
+  L.part_p = take((size_t)g.B * g.Cs * g.n * g.DP * 4);
+  L.gmu = take(rowsY * 4);
+  L.dh_part = take(rowsY * 4);
+  L.dXp = take((size_t)g.B * g.n * g.DP * 4);
+  L.dh = take((size_t)g.B * 8);
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fms_unrolled_ckpt_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T, int32_t k) {
+  if (!valid(B, n, m, d, T, k)) return 0;
+  const int DP = (d + 3) / 4 * 4;
+  return (size_t)n_ckpt(T, k) * B * m * DP * 4;
+}
+
+size_t fms_unrolled_workspace_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
+                                   int32_t k) {
+  if (!valid(B, n, m, d, T, k)) return 0;
+  const UGeom g = geom(B, n, m, d);
+  const size_t f = fwd_layout(g).total, b = bwd_layout(g, k).total;
+  return f > b ? f : b;
+}
+
+fms_status fms_unrolled_forward(const float* points, const float* seeds0, int32_t B, int64_t n,
+                                int64_t m, int32_t d, float h, int32_t T, int32_t k,
+                                float* out_seeds, void* ckpt, size_t ckpt_bytes, void* ws,
+                                size_t ws_bytes, void* stream) {
+  if (!points || !seeds0 || !out_seeds || !valid(B, n, m, d, T, k) || !(h > 0.f) || !isfinite(h))
+    return FMS_ERR_INVALID_ARG;
+  if (!ws || !ckpt) return FMS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const UGeom g = geom(B, n, m, d);
+  const FwdLayout L = fwd_layout(g);
+  if (ws_bytes < L.total || ckpt_bytes < fms_unrolled_ckpt_size(B, n, m, d, T, k) ||
+      (reinterpret_cast<uintptr_t>(ws) & 255u) || (reinterpret_cast<uintptr_t>(ckpt) & 15u))
+    return FMS_ERR_WORKSPACE;
+  float* Xp = at<float>(ws, L.Xp);
+  float* Ya = at<float>(ws, L.Ya);
+  float* Yb = at<float>(ws, L.Yb);
+  float* part = at<float>(ws, L.part);
+  float* C = static_cast<float*>(ckpt);
+  const size_t rowsY = (size_t)B * m;
+  const float c = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
+  const int grid = grid_blocks();
+  if (unroll_pack_rows(points, (int64_t)B * n, d, g.DP, Xp, st) != cudaSuccess ||
+      unroll_pack_rows(seeds0, (int64_t)rowsY, d, g.DP, Ya, st) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  for (int t = 0; t < T; ++t) {
+    if (t % k == 0 &&
+        cudaMemcpyAsync(C + (size_t)(t / k) * rowsY * g.DP, Ya, rowsY * g.DP * 4,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return FMS_ERR_CUDA;
+    if (unroll_fwd_step(Xp, Ya, g, c, part, Yb, nullptr, grid, st) != cudaSuccess)
+      return FMS_ERR_CUDA;
+    float* tmp = Ya;
+    Ya = Yb;
+    Yb = tmp;
+  }
+  if (unroll_unpack_rows(Ya, (int64_t)rowsY, d, g.DP, out_seeds, st) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  return FMS_OK;
+}
+
+fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int64_t m, int32_t d,
+                                 float h, int32_t T, int32_t k, const void* ckpt,
+                                 size_t ckpt_bytes, const float* grad_out, float* grad_points,
+                                 float* grad_seeds0, double* grad_h, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (!points || !grad_out || !grad_points || !grad_seeds0 || !grad_h ||
+      !valid(B, n, m, d, T, k) || !(h > 0.f) || !isfinite(h))
+    return FMS_ERR_INVALID_ARG;
+  if (!ws || !ckpt) return FMS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const UGeom g = geom(B, n, m, d);
+  const BwdLayout L = bwd_layout(g, k);
+  if (ws_bytes < L.total || ckpt_bytes < fms_unrolled_ckpt_size(B, n, m, d, T, k) ||
+      (reinterpret_cast<uintptr_t>(ws) & 255u) || (reinterpret_cast<uintptr_t>(ckpt) & 15u))
+    return FMS_ERR_WORKSPACE;
+  float* Xp = at<float>(ws, L.Xp);
+  float* seg = at<float>(ws, L.seg);
+  float* Wseg = at<float>(ws, L.Wseg);
+  float* Ga = at<float>(ws, L.Ga);
+  float* Gb = at<float>(ws, L.Gb);
+  float* part_s = at<float>(ws, L.part_s);
+  float* part_p = at<float>(ws, L.part_p);
+  float* gmu = at<float>(ws, L.gmu);
+  float* dh_part = at<float>(ws, L.dh_part);
+  float* dXp = at<float>(ws, L.dXp);
+  double* dh = at<double>(ws, L.dh);
+  const float* Ck = static_cast<const float*>(ckpt);
+  const size_t rowsY = (size_t)B * m;
+  const size_t rowY = rowsY * g.DP;
+  const double hd = (double)h;
+  const float c = (float)(1.4426950408889634 / (2.0 * hd * hd));
+  const float inv_h2 = (float)(1.0 / (hd * hd)), inv_h3 = (float)(1.0 / (hd * hd * hd));
+  const int grid = grid_blocks();
+  if (unroll_pack_rows(points, (int64_t)B * n, d, g.DP, Xp, st) != cudaSuccess ||
+      unroll_pack_rows(grad_out, (int64_t)rowsY, d, g.DP, Ga, st) != cudaSuccess ||
+      cudaMemsetAsync(dXp, 0, (size_t)B * n * g.DP * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(dh, 0, (size_t)B * 8, st) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  float* G = Ga;
+  float* Gp = Gb;
+  for (int s = n_ckpt(T, k) - 1; s >= 0; --s) {
+    const int t0 = s * k;
+    const int len = (t0 + k <= T) ? k : T - t0;
+    // recompute the segment: seg[0] = Y_t0, seg[u+1] = Y_{t0+u+1}, Wseg[u] = W_{t0+u}
+    if (cudaMemcpyAsync(seg, Ck + (size_t)s * rowY, rowY * 4, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return FMS_ERR_CUDA;
+    for (int u = 0; u < len; ++u)
+      if (unroll_fwd_step(Xp, seg + (size_t)u * rowY, g, c, part_s, seg + (size_t)(u + 1) * rowY,
+                          Wseg + (size_t)u * rowsY, grid, st) != cudaSuccess)
+        return FMS_ERR_CUDA;
+    for (int u = len - 1; u >= 0; --u) {
+      if (unroll_bwd_step(Xp, seg + (size_t)u * rowY, seg + (size_t)(u + 1) * rowY, G,
+                          Wseg + (size_t)u * rowsY, g, c, inv_h2, inv_h3, part_s, part_p, gmu,
+                          dh_part, Gp, dXp, dh, grid, st) != cudaSuccess)
+        return FMS_ERR_CUDA;
+      float* tmp = G;
+      G = Gp;
+      Gp = tmp;
+    }
+  }
+  if (unroll_unpack_rows(G, (int64_t)rowsY, d, g.DP, grad_seeds0, st) != cudaSuccess ||
+      unroll_unpack_rows(dXp, (int64_t)B * n, d, g.DP, grad_points, st) != cudaSuccess ||
+      cudaMemcpyAsync(grad_h, dh, (size_t)B * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  return FMS_OK;
+}
+
+}  // extern "C"

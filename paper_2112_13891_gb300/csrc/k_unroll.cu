@@ -1,0 +1,369 @@
+// Differentiable unrolled mean-shift steps: T Gaussian updates of every seed
+// (for B independent sets at once) and their adjoint.
+//
+// Forward (Eq. 6 with the Gaussian weight), for each set and seed i:
+//   W_i = sum_j w_ij,  y_i <- mu_i = sum_j w_ij x_j / W_i,
+//   w_ij = exp(-||y_i - x_j||^2 / (2h^2)) = exp2(-c ||y_i - x_j||^2), c = log2(e)/(2h^2).
+// Adjoint of one update, with p_ij = w_ij / W_i, g_i = dL/dmu_i and
+// a_ij = g_i . (x_j - mu_i) (derived by differentiating log w_ij):
+//   dL/dy_i  = (1/h^2) sum_j p_ij a_ij (x_j - mu_i)
+//   dL/dx_j += p_ij [g_i - a_ij (x_j - y_i) / h^2]
+//   dL/dh   += (1/h^3) sum_ij p_ij ||y_i - x_j||^2 a_ij
+// The weights are recomputed tile by tile: nothing of size m x n is stored.
+// Positions Y_t are checkpointed every k updates; the backward recomputes one
+// segment of k updates from its checkpoint, then walks it in reverse.
+//
+// Kernels (all FP32, exact differences, fixed-order reductions):
+//   fwd_partial   lanes own seeds, points streamed with warp-uniform loads,
+//                 partial (W, S = sum w (x - y)) per point chunk
+//   fwd_finish    y' = y + S/W, W_t kept for the backward
+//   bwd_seed      lanes own seeds: partial sum_j p a (x - mu) and
+//                 sum_j p a ||y - x||^2 per point chunk
+//   bwd_point     lanes own points, seeds streamed: partial
+//                 sum_i p_ij [g_i - a_ij (x_j - y_i)/h^2] per seed chunk
+//   finish kernels sum the chunk partials in chunk order.
+#include "fms_internal.cuh"
+
+namespace fms {
+
+template <int DPAD>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, int DP, float (&v)[DPAD]) {
+#pragma unroll
+  for (int q = 0; q < DPAD / 4; ++q) {
+    const float4 t = (4 * q < DP) ? __ldg(reinterpret_cast<const float4*>(p) + q)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
+// ---- forward partials: grid-stride over (set, seed group of 32, point chunk)
+template <int DPAD>
+__global__ void __launch_bounds__(128)
+    unroll_fwd_partial(const float* __restrict__ X, const float* __restrict__ Y, UGeom g,
+                       float c, float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int Gs = (g.m + 31) / 32;
+  const int64_t T = (int64_t)g.B * Gs * g.Cp;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+       task += nw) {
+    const int ch = (int)(task % g.Cp);
+    const int64_t rest = task / g.Cp;
+    const int gs = (int)(rest % Gs);
+    const int b = (int)(rest / Gs);
+    const int i = min(gs * 32 + lane, g.m - 1);
+    const float* Xb = X + (int64_t)b * g.n * g.DP;
+    float y[DPAD], S[DPAD], W = 0.f;
+    load_row<DPAD>(Y + ((int64_t)b * g.m + i) * g.DP, g.DP, y);
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) S[k] = 0.f;
+    const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
+    for (int j = j0; j < j1; ++j) {
+      float x[DPAD];
+      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      float dx[DPAD], D2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) {
+        dx[k] = x[k] - y[k];
+        D2 = fmaf(dx[k], dx[k], D2);
+      }
+      const float w = ex2_ftz(-c * D2);
+      W += w;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) S[k] = fmaf(w, dx[k], S[k]);
+    }
+    if (gs * 32 + lane < g.m) {
+      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1);
+      o[0] = W;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k)
+        if (k < g.d) o[1 + k] = S[k];
+    }
+  }
+}
+
+// y_next = y + S/W (sums over chunks in chunk order), W kept for the backward.
+__global__ void unroll_fwd_finish(const float* __restrict__ part, const float* __restrict__ Y,
+                                  UGeom g, float* __restrict__ Ynext, float* __restrict__ Wout) {
+  const int64_t total = (int64_t)g.B * g.m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / g.m), i = (int)(e % g.m);
+    float W = 0.f;
+    for (int ch = 0; ch < g.Cp; ++ch) W += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1)];
+    if (Wout) Wout[e] = W;
+    for (int k = 0; k < g.DP; ++k) {
+      float v = 0.f;
+      if (k < g.d) {
+        float S = 0.f;
+        for (int ch = 0; ch < g.Cp; ++ch)
+          S += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1) + 1 + k];
+        v = Y[e * g.DP + k] + S / W;
+      }
+      Ynext[e * g.DP + k] = v;
+    }
+  }
+}
+
+// ---- backward, seed-major: partial sums over point chunks of
+//   DY_i = sum_j p_ij a_ij (x_j - mu_i),  DH_i = sum_j p_ij a_ij ||y_i - x_j||^2
+template <int DPAD>
+__global__ void __launch_bounds__(128)
+    unroll_bwd_seed(const float* __restrict__ X, const float* __restrict__ Y,
+                    const float* __restrict__ MU, const float* __restrict__ G,
+                    const float* __restrict__ Wt, UGeom g, float c, float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int Gs = (g.m + 31) / 32;
+  const int64_t T = (int64_t)g.B * Gs * g.Cp;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+       task += nw) {
+    const int ch = (int)(task % g.Cp);
+    const int64_t rest = task / g.Cp;
+    const int gs = (int)(rest % Gs);
+    const int b = (int)(rest / Gs);
+    const int i = min(gs * 32 + lane, g.m - 1);
+    const int64_t row = (int64_t)b * g.m + i;
+    const float* Xb = X + (int64_t)b * g.n * g.DP;
+    float y[DPAD], mu[DPAD], gg[DPAD], DY[DPAD], DH = 0.f;
+    load_row<DPAD>(Y + row * g.DP, g.DP, y);
+    load_row<DPAD>(MU + row * g.DP, g.DP, mu);
+    load_row<DPAD>(G + row * g.DP, g.DP, gg);
+    const float invW = 1.0f / Wt[row];
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) DY[k] = 0.f;
+    const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
+    for (int j = j0; j < j1; ++j) {
+      float x[DPAD];
+      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      float D2 = 0.f, a = 0.f, e[DPAD];
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) {
+        const float dx = x[k] - y[k];
+        D2 = fmaf(dx, dx, D2);
+        e[k] = x[k] - mu[k];
+        a = fmaf(gg[k], e[k], a);
+      }
+      const float pa = ex2_ftz(-c * D2) * invW * a;
+      DH = fmaf(pa, D2, DH);
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) DY[k] = fmaf(pa, e[k], DY[k]);
+    }
+    if (gs * 32 + lane < g.m) {
+      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1);
+      o[0] = DH;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k)
+        if (k < g.d) o[1 + k] = DY[k];
+    }
+  }
+}
+
+// G_prev = DY / h^2 (the gradient w.r.t. the positions before this update);
+// dh_part[b*m + i] = DH_i / h^3.
+__global__ void unroll_bwd_seed_finish(const float* __restrict__ part, UGeom g, float inv_h2,
+                                       float inv_h3, float* __restrict__ Gprev,
+                                       float* __restrict__ dh_part) {
+  const int64_t total = (int64_t)g.B * g.m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / g.m), i = (int)(e % g.m);
+    float DH = 0.f;
+    for (int ch = 0; ch < g.Cp; ++ch) DH += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1)];
+    dh_part[e] = DH * inv_h3;
+    for (int k = 0; k < g.DP; ++k) {
+      float v = 0.f;
+      if (k < g.d) {
+        for (int ch = 0; ch < g.Cp; ++ch)
+          v += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1) + 1 + k];
+        v *= inv_h2;
+      }
+      Gprev[e * g.DP + k] = v;
+    }
+  }
+}
+
+// ---- backward, point-major: partial over seed chunks of
+//   DX_j = sum_i p_ij g_i - (1/h^2) sum_i p_ij a_ij (x_j - y_i)
+// with a_ij = g_i . x_j - (g_i . mu_i).  Per-seed data (y_i, g_i, 1/W_i,
+// g_i . mu_i) are read with warp-uniform loads.
+template <int DPAD>
+__global__ void __launch_bounds__(128)
+    unroll_bwd_point(const float* __restrict__ X, const float* __restrict__ Y,
+                     const float* __restrict__ G, const float* __restrict__ Wt,
+                     const float* __restrict__ gmu, UGeom g, float c, float inv_h2,
+                     float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int Gp = (g.n + 31) / 32;
+  const int64_t T = (int64_t)g.B * Gp * g.Cs;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+       task += nw) {
+    const int ch = (int)(task % g.Cs);
+    const int64_t rest = task / g.Cs;
+    const int gp = (int)(rest % Gp);
+    const int b = (int)(rest / Gp);
+    const int j = min(gp * 32 + lane, g.n - 1);
+    float x[DPAD], DX[DPAD];
+    load_row<DPAD>(X + ((int64_t)b * g.n + j) * g.DP, g.DP, x);
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) DX[k] = 0.f;
+    const int i0 = ch * g.Ls, i1 = min(g.m, i0 + g.Ls);
+    for (int i = i0; i < i1; ++i) {
+      const int64_t row = (int64_t)b * g.m + i;
+      float y[DPAD], gg[DPAD];
+      load_row<DPAD>(Y + row * g.DP, g.DP, y);
+      load_row<DPAD>(G + row * g.DP, g.DP, gg);
+      const float invW = 1.0f / __ldg(Wt + row);
+      const float gm = __ldg(gmu + row);
+      float dx[DPAD], D2 = 0.f, gx = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) {
+        dx[k] = x[k] - y[k];
+        D2 = fmaf(dx[k], dx[k], D2);
+        gx = fmaf(gg[k], x[k], gx);
+      }
+      const float p = ex2_ftz(-c * D2) * invW;
+      const float q = p * (gx - gm) * inv_h2;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) DX[k] = fmaf(p, gg[k], fmaf(-q, dx[k], DX[k]));
+    }
+    if (gp * 32 + lane < g.n) {
+      float* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * g.DP;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k)
+        if (k < g.DP) o[k] = k < g.d ? DX[k] : 0.f;
+    }
+  }
+}
+
+// dX += sum over seed chunks (chunk order).
+__global__ void unroll_bwd_point_finish(const float* __restrict__ part, UGeom g,
+                                        float* __restrict__ dX) {
+  const int64_t total = (int64_t)g.B * g.n * g.DP;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bj = e / g.DP;
+    const int k = (int)(e % g.DP);
+    const int b = (int)(bj / g.n), j = (int)(bj % g.n);
+    float v = 0.f;
+    for (int ch = 0; ch < g.Cs; ++ch) v += part[(((int64_t)b * g.Cs + ch) * g.n + j) * g.DP + k];
+    dX[e] += v;
+  }
+}
+
+// g_i . mu_i for every seed (for the point-major pass).
+__global__ void unroll_gmu(const float* __restrict__ G, const float* __restrict__ MU, UGeom g,
+                           float* __restrict__ gmu) {
+  const int64_t total = (int64_t)g.B * g.m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < g.d; ++k) s = fmaf(G[e * g.DP + k], MU[e * g.DP + k], s);
+    gmu[e] = s;
+  }
+}
+
+// dh[b] += sum_i dh_part[b, i] in FP64, seeds in order (one block per set).
+__global__ void unroll_dh_reduce(const float* __restrict__ dh_part, UGeom g,
+                                 double* __restrict__ dh) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < g.m; i += blockDim.x) s += (double)dh_part[(int64_t)b * g.m + i];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    dh[b] += t;
+  }
+}
+
+// Row repacking between the caller's [rows x d] and the padded [rows x DP].
+__global__ void unroll_pack(const float* __restrict__ src, int64_t rows, int d, int DP,
+                            float* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * DP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / DP;
+    const int k = (int)(e % DP);
+    dst[e] = k < d ? src[r * d + k] : 0.f;
+  }
+}
+
+__global__ void unroll_unpack(const float* __restrict__ src, int64_t rows, int d, int DP,
+                              float* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / d;
+    const int k = (int)(e % d);
+    dst[e] = src[r * DP + k];
+  }
+}
+
+static int blocks_for(int64_t work, int per = 256) {
+  int64_t b = (work + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > 8192) b = 8192;
+  return (int)b;
+}
+
+template <int DPAD>
+static cudaError_t fwd_step_t(const float* X, const float* Y, const UGeom& g, float c, float* part,
+                              float* Ynext, float* Wout, int grid, cudaStream_t st) {
+  unroll_fwd_partial<DPAD><<<grid, 128, 0, st>>>(X, Y, g, c, part);
+  unroll_fwd_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout);
+  return cudaGetLastError();
+}
+
+cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
+                            float* Ynext, float* Wout, int grid, cudaStream_t st) {
+  if (g.DP <= 4) return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, grid, st);
+  if (g.DP <= 8) return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, grid, st);
+  if (g.DP <= 16) return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, grid, st);
+  return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, grid, st);
+}
+
+template <int DPAD>
+static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, const float* G,
+                              const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
+                              float* part_s, float* part_p, float* gmu, float* dh_part,
+                              float* Gprev, float* dX, double* dh, int grid, cudaStream_t st) {
+  unroll_gmu<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(G, MU, g, gmu);
+  unroll_bwd_point<DPAD><<<grid, 128, 0, st>>>(X, Y, G, Wt, gmu, g, c, inv_h2, part_p);
+  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, Y, MU, G, Wt, g, c, part_s);
+  unroll_bwd_point_finish<<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
+  unroll_bwd_seed_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2, inv_h3,
+                                                                         Gprev, dh_part);
+  unroll_dh_reduce<<<g.B, 256, 0, st>>>(dh_part, g, dh);
+  return cudaGetLastError();
+}
+
+cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
+                            const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
+                            float* part_s, float* part_p, float* gmu, float* dh_part, float* Gprev,
+                            float* dX, double* dh, int grid, cudaStream_t st) {
+  if (g.DP <= 4) return bwd_step_t<4>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  if (g.DP <= 8) return bwd_step_t<8>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  if (g.DP <= 16) return bwd_step_t<16>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  return bwd_step_t<32>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+}
+
+cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
+                             cudaStream_t st) {
+  unroll_pack<<<blocks_for(rows * DP), 256, 0, st>>>(src, rows, d, DP, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
+                               cudaStream_t st) {
+  unroll_unpack<<<blocks_for(rows * d), 256, 0, st>>>(src, rows, d, DP, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace fms

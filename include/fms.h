@@ -148,6 +148,37 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                        fms_stats* stats, void* stream);
 
 /*
+ * Batched Faster Mean-shift: B independent point sets of uneven size
+ * clustered together, every phase of Alg. 2 (Sec. II-C/D) one launch for all
+ * sets (the sets share h, tol, max_iter and the options).  The paper clusters
+ * one set per call; batching has no counterpart there.
+ *
+ *   points       [offsets[B] x d] float32, device: set b is rows
+ *                offsets[b] .. offsets[b+1]-1.
+ *   offsets      HOST int64[B+1], offsets[0] = 0, strictly increasing.
+ *   out_modes    [B x max_modes x d] float32, device: set b's modes at
+ *                out_modes + b*max_modes*d, canonical order.
+ *   out_n_modes  DEVICE int32[B]: each set's mode count (FMS_ERR_CAPACITY if
+ *                any exceeds max_modes; the counts are still written).
+ *   out_labels   [offsets[B]] int32, device: index of the nearest mode of the
+ *                point's own set; out_margins as in fms_cluster (nullable).
+ *   workspace    fms_batched_workspace_size(offsets, B, d, opt) bytes or NULL.
+ * opt->seed_indices must be NULL.  A set whose seed count outgrows the
+ * on-chip prune (about 1,400 seeds at d = 16) gives FMS_ERR_UNSUPPORTED.
+ * The step kernel's tiling is chosen by a built-in autotuner the first time
+ * a shape (d, size class of the total, size class of B) is seen on a device:
+ * it times one update with each candidate tiling and keeps the fastest.
+ * Synchronises `stream` a few times per seed round.
+ */
+size_t fms_batched_workspace_size(const int64_t* offsets, int32_t B, int32_t d,
+                                  const fms_options* opt);
+fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int32_t B, int32_t d,
+                               float h, float tol, int32_t max_iter, const fms_options* opt,
+                               float* out_modes, int32_t max_modes, int32_t* out_n_modes,
+                               int32_t* out_labels, float* out_margins, void* workspace,
+                               size_t workspace_bytes, fms_stats* stats, void* stream);
+
+/*
  * Seed Selection (Alg. 2 line 2): writes entries [start, start+count) of a
  * keyed pseudo-random permutation pi of [0, n) to out_indices (device int32).
  * pi(i) applies a balanced 6-round Feistel network on 2*hb bits (4^hb the

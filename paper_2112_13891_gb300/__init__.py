@@ -312,3 +312,67 @@ class UnrolledMeanShift(torch.autograd.Function):
 
 def unrolled_mean_shift(X: torch.Tensor, Y0: torch.Tensor, h, T: int = 20, k: int = 5):
     return UnrolledMeanShift.apply(X, Y0, h, T, k)
+
+
+# ---------------------------------------------------------------------------
+# Batched clustering (fms_cluster_batched)
+# ---------------------------------------------------------------------------
+
+_lib.fms_batched_workspace_size.restype = _SZ
+_lib.fms_batched_workspace_size.argtypes = [_P, _I32, _I32, ctypes.POINTER(FmsOptions)]
+_lib.fms_cluster_batched.restype = ctypes.c_int
+_lib.fms_cluster_batched.argtypes = [_P, _P, _I32, _I32, _F32, _F32, _I32,
+                                     ctypes.POINTER(FmsOptions), _P, _I32, _P, _P, _P, _P, _SZ,
+                                     ctypes.POINTER(FmsStats), _P]
+
+
+@dataclass
+class BatchedResult:
+    modes: list            # per set: [M_b, d] float32 tensors (views of one buffer)
+    n_modes: torch.Tensor  # [B] int32 (device)
+    labels: torch.Tensor   # [total] int32, indices into the point's own set's modes
+    margins: torch.Tensor
+    stats: dict
+    status: int
+
+
+def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, offsets=None,
+                    n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0, skip_refine=False,
+                    all_seeds=False, rng_seed=0, max_modes=256, margins=True,
+                    workspace: Workspace = None) -> BatchedResult:
+    """Cluster many point sets at once.  `points` is a list of [n_b, d] CUDA
+    tensors, or one [total, d] tensor with host `offsets` (B+1 ints)."""
+    import numpy as np
+    if offsets is None:
+        sizes = [int(p.shape[0]) for p in points]
+        X = torch.cat([_points(p) for p in points], dim=0)
+        offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    else:
+        X = _points(points)
+        offsets = np.asarray(offsets, dtype=np.int64)
+    B = len(offsets) - 1
+    total, d = X.shape
+    o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
+                     merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed)
+    offs = np.ascontiguousarray(offsets)
+    optr = offs.ctypes.data_as(ctypes.c_void_p)
+    need = int(_lib.fms_batched_workspace_size(optr, B, d, ctypes.byref(o)))
+    if need == 0:
+        raise FmsError(FMS_ERR_INVALID_ARG, "fms_batched_workspace_size")
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, X.device)
+    modes = torch.empty((B, max(int(max_modes), 1), d), dtype=torch.float32, device=X.device)
+    n_modes = torch.empty(B, dtype=torch.int32, device=X.device)
+    labels = torch.empty(total, dtype=torch.int32, device=X.device)
+    mar = torch.empty(total, dtype=torch.float32, device=X.device) if margins else None
+    st = FmsStats()
+    code = _lib.fms_cluster_batched(_ptr(X), optr, B, d, float(h), float(tol), int(max_iter),
+                                    ctypes.byref(o), _ptr(modes), int(max_modes), _ptr(n_modes),
+                                    _ptr(labels), _ptr(mar), _ptr(workspace.buf), workspace.nbytes,
+                                    ctypes.byref(st), _stream())
+    if code not in (FMS_OK, FMS_ERR_CAPACITY):
+        raise FmsError(code, "fms_cluster_batched")
+    counts = n_modes.cpu().tolist()
+    per = [modes[b, : min(counts[b], int(max_modes))] for b in range(B)]
+    return BatchedResult(modes=per, n_modes=n_modes, labels=labels, margins=mar,
+                         stats=st.as_dict(), status=code)

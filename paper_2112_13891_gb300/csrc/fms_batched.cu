@@ -1,0 +1,507 @@
+// C ABI of the batched clustering (fms_cluster_batched): many independent
+// point sets, every phase one launch for all sets (k_batched.cu), plus the
+// project's tile autotuner for the batched step kernel.
+#include <math.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fms.h"
+#include "fms_internal.cuh"
+
+namespace fms {
+cudaError_t launch_batched_seed_init(SetCtl* sc, int B, const float* Xs, int DP, uint64_t seed,
+                                     float* y, int32_t* it, int32_t* conv, int32_t* state,
+                                     cudaStream_t st);
+cudaError_t launch_batched_compact(SetCtl* sc, int B, const int32_t* state, const int32_t* it,
+                                   const int32_t* conv, int32_t* active, int begin, int max_iter,
+                                   int R, int DA, Tiling tl, int64_t* task_off, int64_t* part_off,
+                                   int64_t* list_off, int64_t* totals, int32_t* blocks_done,
+                                   int32_t* sets_running, cudaStream_t st);
+cudaError_t launch_batched_step(const float* Xs, int d, int DP, const float* y,
+                                const int32_t* list, const SetCtl* sc, int B, int kind,
+                                const int64_t* task_off, const int64_t* part_off,
+                                const int64_t* totals, float* part, int target_warps,
+                                cudaStream_t st);
+cudaError_t launch_batched_update(const float* part, const int32_t* active, const SetCtl* sc,
+                                  int B, const int64_t* list_off, const int64_t* part_off,
+                                  const int64_t* totals, float* y, int32_t* it, int32_t* conv,
+                                  int32_t* state, int d, int DP, int DA, float tol2_s,
+                                  int max_iter, int grid, cudaStream_t st);
+cudaError_t launch_batched_kept(SetCtl* sc, int B, const int32_t* state, const int32_t* conv,
+                                int keep_exhausted, int32_t* kept, int R, int DA, Tiling tl,
+                                int64_t* task_off, int64_t* part_off, int64_t* list_off,
+                                int64_t* totals, int32_t* blocks_done, cudaStream_t st);
+cudaError_t launch_batched_score(const float* part, const SetCtl* sc, int B,
+                                 const int64_t* list_off, const int64_t* part_off,
+                                 const int64_t* totals, int DA, float* score, int grid,
+                                 cudaStream_t st);
+cudaError_t launch_batched_prune_f(SetCtl* sc, int B, const int32_t* kept, const float* score,
+                                   const float* pos, int DP, int d, float r2, int32_t* accepted,
+                                   int maxK, cudaStream_t st);
+cudaError_t launch_batched_prune_d(SetCtl* sc, int B, const double* score, const double* pos,
+                                   int DP, int d, double r2, int32_t* accepted, int maxK,
+                                   cudaStream_t st);
+cudaError_t launch_batched_doubling(SetCtl* sc, int B, float L, int allow, int32_t* any,
+                                    cudaStream_t st);
+cudaError_t launch_batched_next_round(SetCtl* sc, int B, float gamma, cudaStream_t st);
+cudaError_t launch_batched_refine_setup(SetCtl* sc, int B, const float* y, const int32_t* kept,
+                                        const int32_t* accepted, int DP, double* ym, float* yf,
+                                        int32_t* ract, int32_t* mdone, int init_pos, int R,
+                                        Tiling tl, cudaStream_t st);
+cudaError_t launch_plan(const SetCtl* sc, int B, int kind, int R, int DA, int64_t* task_off,
+                        int64_t* part_off, int64_t* list_off, int64_t* totals, cudaStream_t st);
+cudaError_t launch_batched_refine_update(const float* part, const int32_t* ract, const SetCtl* sc,
+                                         int B, const int64_t* list_off, const int64_t* part_off,
+                                         const int64_t* totals, double* ym, float* yf,
+                                         int32_t* mdone, double* mscore, int d, int DP, int DA,
+                                         double tol2_s, int score_only, int grid,
+                                         cudaStream_t st);
+cudaError_t launch_batched_refine_compact(SetCtl* sc, int B, const int32_t* mdone, int32_t* ract,
+                                          int max_iter, int R, int DA, Tiling tl,
+                                          int64_t* task_off, int64_t* part_off, int64_t* list_off,
+                                          int64_t* totals, int32_t* blocks_done,
+                                          int32_t* sets_running, cudaStream_t st);
+cudaError_t launch_batched_canonical(const SetCtl* sc, int B, const double* ym,
+                                     const double* mscore, const int32_t* acc2, int d, int DP,
+                                     double inv_scale, float* out_modes, int max_modes,
+                                     float* modes_full, int32_t* out_n, cudaStream_t st);
+cudaError_t launch_batched_label(const float* X, const int64_t* pt_off, int B, int d,
+                                 const SetCtl* sc, const float* modes_full, int32_t* labels,
+                                 float* margins, int64_t total, cudaStream_t st);
+size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P);
+}  // namespace fms
+
+using namespace fms;
+
+namespace {
+
+constexpr int kBatchUpdates = 8;
+constexpr int kTwMultMax = 2;  // largest warp multiplier the autotuner tries
+constexpr int kRefineMax = 50;
+enum : int { kPlanActive = 0, kPlanKept = 1, kPlanModes = 2 };
+
+size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+int padded(int d) {
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  return (d + 3) / 4 * 4;
+}
+
+int sms_now() {
+  int dev = 0, s = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return s;
+}
+
+struct BLayout {
+  size_t Xs, y, it, conv, state, active, kept, acc1, acc2, score, ym, yf, ract, mdone, mscore,
+      modes_full, part, sc, task_off, part_off, list_off, totals, counters, pt_off, status, total;
+  int DP, DA, R, TW;
+  Tiling tl;
+};
+
+// Partial-sum capacity: per set C_b * cnt_b * DA with C_b from choose_chunks
+// (<= 4 * tl.target_warps / G_b + 1), so sum_b <= (4 * TWb * B + total_groups) * R * DA.
+BLayout make_blayout(int64_t total, int B, int d, int sms, int tw_mult, int min_chunk) {
+  BLayout L{};
+  L.DP = padded(d);
+  L.DA = step_accumulators(d);
+  L.R = step_seeds_per_warp(d);
+  L.TW = (sms > 0 ? sms : 1) * step_resident_warps_per_sm(d);
+  // every set gets a share of the GPU's warps for its chunking (all sets run
+  // in the same launches)
+  int twb = (L.TW * tw_mult) / (B > 0 ? B : 1);
+  if (twb < 32) twb = 32;
+  L.tl.target_warps = twb;
+  L.tl.min_chunk = min_chunk;
+  // partial sums sized for the largest autotuner candidate, so that every
+  // candidate tiling fits the same layout
+  int twb_max = (L.TW * kTwMultMax) / (B > 0 ? B : 1);
+  if (twb_max < 32) twb_max = 32;
+  const int64_t groups = total / L.R + B;
+  const size_t part_floats = (size_t)(4 * (int64_t)twb_max * B + groups + 1) * L.R * L.DA;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o += a256(b > 0 ? b : 1);
+    return at;
+  };
+  L.Xs = take((size_t)total * L.DP * 4);
+  L.y = take((size_t)total * L.DP * 4);
+  L.it = take((size_t)total * 4);
+  L.conv = take((size_t)total * 4);
+  L.state = take((size_t)total * 4);
+  L.active = take((size_t)total * 4);
+  L.kept = take((size_t)total * 4);
+  L.acc1 = take((size_t)total * 4);
+  L.acc2 = take((size_t)total * 4);
+  L.score = take((size_t)total * 4);
+  L.ym = take((size_t)total * L.DP * 8);
+  L.yf = take((size_t)total * L.DP * 4);
+  L.ract = take((size_t)total * 4);
+  L.mdone = take((size_t)total * 4);
+  L.mscore = take((size_t)total * 8);
+  L.modes_full = take((size_t)total * d * 4);
+  L.part = take(part_floats * 4);
+  L.sc = take((size_t)B * sizeof(SetCtl));
+  L.task_off = take((size_t)(B + 1) * 8);
+  L.part_off = take((size_t)(B + 1) * 8);
+  L.list_off = take((size_t)(B + 1) * 8);
+  L.totals = take(64);
+  L.counters = take(64);
+  L.pt_off = take((size_t)(B + 1) * 8);
+  L.status = take(64);
+  L.total = o;
+  return L;
+}
+
+// Autotuner state: best (tw_mult, min_chunk) per (device, d, log2 total, B bucket).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
+const int kTwMults[2] = {1, 2};
+const int kMinChunks[3] = {256, 512, 1024};
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+int ilog2(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << (r + 1)) <= x) ++r;
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fms_batched_workspace_size(const int64_t* offsets, int32_t B, int32_t d,
+                                  const fms_options* opt) {
+  (void)opt;
+  if (!offsets || B < 1 || d < 1 || d > FMS_MAX_DIM) return 0;
+  const int64_t total = offsets[B] - offsets[0];
+  if (total < 1 || total > INT32_MAX) return 0;
+  return make_blayout(total, B, d, sms_now(), kTwMults[0], kMinChunks[0]).total;
+}
+
+fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int32_t B, int32_t d,
+                               float h, float tol, int32_t max_iter, const fms_options* opt_in,
+                               float* out_modes, int32_t max_modes, int32_t* out_n_modes,
+                               int32_t* out_labels, float* out_margins, void* workspace,
+                               size_t workspace_bytes, fms_stats* stats, void* stream_) {
+  fms_options o;
+  fms_options_default(&o);
+  if (opt_in) {
+    o.all_seeds = opt_in->all_seeds;
+    if (opt_in->n_initial > 0) o.n_initial = opt_in->n_initial;
+    if (opt_in->L > 0.f) o.L = opt_in->L;
+    if (opt_in->gamma > 0.f) o.gamma = opt_in->gamma;
+    if (opt_in->merge_radius > 0.f) o.merge_radius = opt_in->merge_radius;
+    o.skip_refine = opt_in->skip_refine;
+    o.rng_seed = opt_in->rng_seed;
+    o.seed_indices = opt_in->seed_indices;
+    o.profile = opt_in->profile;
+  }
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!points || !offsets || B < 1 || d < 1 || d > FMS_MAX_DIM || !(h > 0.f) || !isfinite(h) ||
+      !(tol >= 0.f) || max_iter < 1 || !out_labels || !out_n_modes || max_modes < 0 ||
+      (max_modes > 0 && !out_modes) || o.seed_indices || !(o.gamma > 0.f && o.gamma <= 1.f))
+    return FMS_ERR_INVALID_ARG;
+  if (offsets[0] != 0) return FMS_ERR_INVALID_ARG;
+  for (int b = 0; b < B; ++b)
+    if (offsets[b + 1] <= offsets[b]) return FMS_ERR_INVALID_ARG;
+  const int64_t total = offsets[B];
+  if (total > INT32_MAX) return FMS_ERR_INVALID_ARG;
+  if (tol == 0.f) tol = 1e-3f * h;
+  if (o.all_seeds) o.gamma = 1.f;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const int sms = sms_now();
+  if (sms <= 0) return FMS_ERR_CUDA;
+
+  // tuned tiling for this shape (or the first candidate until tuned)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, (int)d, ilog2(total), ilog2(B));
+  bool tuned = false;
+  std::pair<int, int> cfg{kTwMults[0], kMinChunks[1]};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto itc = g_tuned.find(key);
+    if (itc != g_tuned.end()) {
+      cfg = itc->second;
+      tuned = true;
+    }
+  }
+  BLayout Lo = make_blayout(total, B, d, sms, cfg.first, cfg.second);
+  const size_t need = Lo.total;  // identical for every candidate tiling
+  bool owns = false;
+  void* ws = workspace;
+  if (ws) {
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u)) return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns = true;
+  }
+  fms_status rc = FMS_OK;
+  int launches = 0;
+  int rounds = 0, refine_batches = 0;
+  std::vector<SetCtl> hsc(B);
+  int64_t htot[2] = {0, 0};
+  int32_t hcnt[4] = {0, 0, 0, 0};
+  uint32_t hstatus = 0;
+#define BC(call)                \
+  do {                          \
+    if ((call) != cudaSuccess) { \
+      rc = FMS_ERR_CUDA;        \
+      goto done;                \
+    }                           \
+  } while (0)
+#define BL(call)   \
+  do {             \
+    ++launches;    \
+    BC(call);      \
+  } while (0)
+  {
+    const int DP = Lo.DP, DA = Lo.DA, R = Lo.R;
+    float* Xs = at<float>(ws, Lo.Xs);
+    float* y = at<float>(ws, Lo.y);
+    int32_t* it = at<int32_t>(ws, Lo.it);
+    int32_t* conv = at<int32_t>(ws, Lo.conv);
+    int32_t* state = at<int32_t>(ws, Lo.state);
+    int32_t* active = at<int32_t>(ws, Lo.active);
+    int32_t* kept = at<int32_t>(ws, Lo.kept);
+    int32_t* acc1 = at<int32_t>(ws, Lo.acc1);
+    int32_t* acc2 = at<int32_t>(ws, Lo.acc2);
+    float* score = at<float>(ws, Lo.score);
+    double* ym = at<double>(ws, Lo.ym);
+    float* yf = at<float>(ws, Lo.yf);
+    int32_t* ract = at<int32_t>(ws, Lo.ract);
+    int32_t* mdone = at<int32_t>(ws, Lo.mdone);
+    double* mscore = at<double>(ws, Lo.mscore);
+    float* modes_full = at<float>(ws, Lo.modes_full);
+    float* part = at<float>(ws, Lo.part);
+    SetCtl* sc = at<SetCtl>(ws, Lo.sc);
+    int64_t* task_off = at<int64_t>(ws, Lo.task_off);
+    int64_t* part_off = at<int64_t>(ws, Lo.part_off);
+    int64_t* list_off = at<int64_t>(ws, Lo.list_off);
+    int64_t* totals = at<int64_t>(ws, Lo.totals);
+    int32_t* counters = at<int32_t>(ws, Lo.counters);  // [0] blocks_done [1] running [2] any
+    int64_t* pt_off = at<int64_t>(ws, Lo.pt_off);
+    uint32_t* status = at<uint32_t>(ws, Lo.status);
+    const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    const double tol_s = (double)tol * scale;
+    const float tol2_s = (float)(tol_s * tol_s);
+    const double r_merge = o.merge_radius > 0.f ? (double)o.merge_radius : (double)h;
+    const double r2_s = (r_merge * scale) * (r_merge * scale);
+    const int grid_upd = sms * 8;
+    int maxN = 0;
+
+    for (int b = 0; b < B; ++b) {
+      SetCtl& c = hsc[b];
+      memset(&c, 0, sizeof(c));
+      c.n = (int32_t)(offsets[b + 1] - offsets[b]);
+      c.p0 = (int32_t)offsets[b];
+      c.N = o.all_seeds ? c.n : (o.n_initial < c.n ? o.n_initial : c.n);
+      c.prevN = 0;
+      const int t = (int)ceil((double)o.gamma * (double)c.N);
+      c.target = t < 1 ? 1 : (t > c.N ? c.N : t);
+      if (c.N > maxN) maxN = c.N;
+    }
+    BC(cudaMemcpyAsync(sc, hsc.data(), (size_t)B * sizeof(SetCtl), cudaMemcpyHostToDevice, st));
+    BC(cudaMemcpyAsync(pt_off, offsets, (size_t)(B + 1) * 8, cudaMemcpyHostToDevice, st));
+    BC(cudaMemsetAsync(counters, 0, 64, st));
+    BC(cudaMemsetAsync(status, 0, 64, st));
+    BL(launch_pack_points(points, total, d, DP, (float)scale, Xs, status, st));
+    BL(launch_batched_seed_init(sc, B, Xs, DP, o.rng_seed, y, it, conv, state, st));
+
+    // --- autotune the step tiling once per shape: time one update per candidate ---
+    if (!tuned) {
+      BL(launch_batched_compact(sc, B, state, it, conv, active, 1, max_iter, R, DA, Lo.tl,
+                                task_off, part_off, list_off, totals, counters, counters + 1, st));
+      float best_ms = 1e30f;
+      std::pair<int, int> best = cfg;
+      cudaEvent_t e0, e1;
+      BC(cudaEventCreate(&e0));
+      BC(cudaEventCreate(&e1));
+      for (int tm : kTwMults)
+        for (int mc : kMinChunks) {
+          const BLayout Lc = make_blayout(total, B, d, sms, tm, mc);
+          BL(launch_batched_compact(sc, B, state, it, conv, active, 1, max_iter, R, DA, Lc.tl,
+                                    task_off, part_off, list_off, totals, counters, counters + 1,
+                                    st));
+          BC(cudaEventRecord(e0, st));
+          BL(launch_batched_step(Xs, d, DP, y, active, sc, B, kPlanActive, task_off, part_off,
+                                 totals, part, Lc.TW, st));
+          BC(cudaEventRecord(e1, st));
+          BC(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = {tm, mc};
+          }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      // the trial compactions counted evaluations: start the real run afresh
+      BC(cudaMemcpyAsync(sc, hsc.data(), (size_t)B * sizeof(SetCtl), cudaMemcpyHostToDevice, st));
+      cfg = best;
+      Lo = make_blayout(total, B, d, sms, cfg.first, cfg.second);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = cfg;
+    }
+    const Tiling tl = Lo.tl;
+
+    for (;;) {
+      ++rounds;
+      BL(launch_batched_compact(sc, B, state, it, conv, active, 1, max_iter, R, DA, tl, task_off,
+                                part_off, list_off, totals, counters, counters + 1, st));
+      for (;;) {
+        for (int i = 0; i < kBatchUpdates; ++i) {
+          BL(launch_batched_step(Xs, d, DP, y, active, sc, B, kPlanActive, task_off, part_off,
+                                 totals, part, Lo.TW, st));
+          BL(launch_batched_update(part, active, sc, B, list_off, part_off, totals, y, it, conv,
+                                   state, d, DP, DA, tol2_s, max_iter, grid_upd, st));
+          BL(launch_batched_compact(sc, B, state, it, conv, active, 0, max_iter, R, DA, tl,
+                                    task_off, part_off, list_off, totals, counters,
+                                    counters + 1, st));
+        }
+        BC(cudaMemcpyAsync(htot, totals, 16, cudaMemcpyDeviceToHost, st));
+        BC(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+        BC(cudaStreamSynchronize(st));
+        if (hstatus & kStNonFinite) {
+          rc = FMS_ERR_NONFINITE;
+          goto done;
+        }
+        if (htot[1] == 0) break;
+      }
+      // prune: kept seeds, their densities, sorted greedy; doubling decision
+      BL(launch_batched_kept(sc, B, state, conv, o.gamma >= 1.f ? 1 : 0, kept, R, DA, tl,
+                             task_off, part_off, list_off, totals, counters, st));
+      BL(launch_batched_step(Xs, d, DP, y, kept, sc, B, kPlanKept, task_off, part_off, totals,
+                             part, Lo.TW, st));
+      BL(launch_batched_score(part, sc, B, list_off, part_off, totals, DA, score, grid_upd, st));
+      {
+      int P = 1;
+      if (batched_prune_smem(maxN, d, 4, 4, &P) > 200 * 1024) {
+        rc = FMS_ERR_UNSUPPORTED;  // a set's seed count exceeds the on-chip prune
+        goto done;
+      }
+    }
+    BL(launch_batched_prune_f(sc, B, kept, score, y, DP, d, (float)r2_s, acc1, maxN, st));
+      BC(cudaMemsetAsync(counters + 2, 0, 4, st));
+      BL(launch_batched_doubling(sc, B, o.L, o.all_seeds ? 0 : 1, counters + 2, st));
+      BC(cudaMemcpyAsync(hcnt, counters, 16, cudaMemcpyDeviceToHost, st));
+      BC(cudaStreamSynchronize(st));
+      if (hcnt[2] == 0) break;
+      BL(launch_batched_next_round(sc, B, o.gamma, st));
+      BL(launch_batched_seed_init(sc, B, Xs, DP, o.rng_seed, y, it, conv, state, st));
+      maxN = maxN * 2 < INT32_MAX / 2 ? maxN * 2 : maxN;
+      {
+        BC(cudaMemcpyAsync(hsc.data(), sc, (size_t)B * sizeof(SetCtl), cudaMemcpyDeviceToHost, st));
+        BC(cudaStreamSynchronize(st));
+        maxN = 0;
+        for (int b = 0; b < B; ++b) maxN = hsc[b].N > maxN ? hsc[b].N : maxN;
+      }
+    }
+
+    // refinement (FP64 positions), density pass, second prune, order, labels
+    if (!o.skip_refine) {
+      const double rtol_s = 1e-5 * (double)h * scale;
+      BL(launch_batched_refine_setup(sc, B, y, kept, acc1, DP, ym, yf, ract, mdone, 1, R, tl, st));
+      BL(launch_plan(sc, B, kPlanModes, R, DA, task_off, part_off, list_off, totals, st));
+      for (int done_it = 0; done_it < kRefineMax; done_it += kBatchUpdates) {
+        ++refine_batches;
+        for (int i = 0; i < kBatchUpdates && done_it + i < kRefineMax; ++i) {
+          BL(launch_batched_step(Xs, d, DP, yf, ract, sc, B, kPlanModes, task_off, part_off,
+                                 totals, part, Lo.TW, st));
+          BL(launch_batched_refine_update(part, ract, sc, B, list_off, part_off, totals, ym, yf,
+                                          mdone, mscore, d, DP, DA, rtol_s * rtol_s, 0, grid_upd,
+                                          st));
+          BL(launch_batched_refine_compact(sc, B, mdone, ract, kRefineMax, R, DA, tl, task_off,
+                                           part_off, list_off, totals, counters, counters + 1,
+                                           st));
+        }
+        BC(cudaMemcpyAsync(htot, totals, 16, cudaMemcpyDeviceToHost, st));
+        BC(cudaStreamSynchronize(st));
+        if (htot[1] == 0) break;
+      }
+      BL(launch_batched_refine_setup(sc, B, y, kept, acc1, DP, ym, yf, ract, mdone, 0, R, tl, st));
+      BL(launch_plan(sc, B, kPlanModes, R, DA, task_off, part_off, list_off, totals, st));
+      BL(launch_batched_step(Xs, d, DP, yf, ract, sc, B, kPlanModes, task_off, part_off, totals,
+                             part, Lo.TW, st));
+      BL(launch_batched_refine_update(part, ract, sc, B, list_off, part_off, totals, ym, yf, mdone,
+                                      mscore, d, DP, DA, 0.0, 1, grid_upd, st));
+    } else {
+      // unrefined: the accepted seeds are the modes (density from the prune pass)
+      BL(launch_batched_refine_setup(sc, B, y, kept, acc1, DP, ym, yf, ract, mdone, 1, R, tl, st));
+      BL(launch_plan(sc, B, kPlanModes, R, DA, task_off, part_off, list_off, totals, st));
+      BL(launch_batched_step(Xs, d, DP, yf, ract, sc, B, kPlanModes, task_off, part_off, totals,
+                             part, Lo.TW, st));
+      BL(launch_batched_refine_update(part, ract, sc, B, list_off, part_off, totals, ym, yf, mdone,
+                                      mscore, d, DP, DA, 0.0, 1, grid_upd, st));
+    }
+    BC(cudaMemcpyAsync(hsc.data(), sc, (size_t)B * sizeof(SetCtl), cudaMemcpyDeviceToHost, st));
+    BC(cudaStreamSynchronize(st));
+    int maxM = 0;
+    for (int b = 0; b < B; ++b) maxM = hsc[b].M > maxM ? hsc[b].M : maxM;
+    {
+      int P = 1;
+      if (batched_prune_smem(maxM > 0 ? maxM : 1, d, 8, 8, &P) > 200 * 1024) {
+        rc = FMS_ERR_UNSUPPORTED;
+        goto done;
+      }
+    }
+    BL(launch_batched_prune_d(sc, B, mscore, ym, DP, d, r2_s, acc2, maxM > 0 ? maxM : 1, st));
+    BL(launch_batched_canonical(sc, B, ym, mscore, acc2, d, DP, 1.0 / scale, out_modes, max_modes,
+                                modes_full, out_n_modes, st));
+    BL(launch_batched_label(points, pt_off, B, d, sc, modes_full, out_labels, out_margins, total,
+                            st));
+    BC(cudaMemcpyAsync(hsc.data(), sc, (size_t)B * sizeof(SetCtl), cudaMemcpyDeviceToHost, st));
+    BC(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+    BC(cudaStreamSynchronize(st));
+    if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+    int64_t ev = 0;
+    int maxMr = 0, iters = 0, conv_n = 0, kept_n = 0, seeds = 0, modes = 0;
+    for (int b = 0; b < B; ++b) {
+      ev += hsc[b].evals;
+      maxMr = hsc[b].Mr > maxMr ? hsc[b].Mr : maxMr;
+      iters = hsc[b].steps > iters ? hsc[b].steps : iters;
+      conv_n += hsc[b].n_conv;
+      kept_n += hsc[b].K;
+      seeds += hsc[b].N;
+      modes += hsc[b].Mr;
+    }
+    if (rc == FMS_OK && maxMr > max_modes) rc = FMS_ERR_CAPACITY;
+    if (stats) {
+      stats->iterations = iters;
+      stats->rounds = rounds;
+      stats->n_seeds_final = seeds;
+      stats->n_converged = conv_n;
+      stats->n_kept = kept_n;
+      stats->n_discarded = seeds - kept_n;
+      stats->n_modes = modes;
+      stats->refine_iterations = refine_batches;
+      stats->kernel_launches = launches;
+      stats->evals = ev;
+      stats->workspace_bytes = need;
+    }
+  }
+done:
+  if (owns) {
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+  }
+  return rc;
+#undef BC
+#undef BL
+}
+
+}  // extern "C"

@@ -81,6 +81,34 @@ constexpr int kClusterCtas = 8;
 constexpr int kSeedsPerCluster = 64;
 constexpr int kModesPerCluster = 32;   // refinement: modes one cluster owns
 
+// Per-set control block of the batched path (k_batched.cu).
+struct SetCtl {
+  int32_t n;       // points of the set
+  int32_t p0;      // first point, first seed slot and first list entry of the set
+  int32_t N;       // seeds in play
+  int32_t prevN;   // seeds before the last doubling (new seeds: ranks prevN..N-1)
+  int32_t target;  // ceil(gamma * N)
+  int32_t r;       // Early Stopping clock
+  int32_t done;    // round finished
+  int32_t s;       // active seeds of the next update
+  int32_t C, Lc;   // chunks of the next update
+  int32_t steps;
+  int32_t n_conv;
+  int32_t K;       // kept seeds (prune candidates)
+  int32_t Ck, Lck; // chunks of the density pass
+  int32_t M;       // modes accepted by the first prune
+  int32_t next_N;
+  int32_t t_star;
+  int32_t final_;  // 1: no further doubling; the set's prune result is final
+  int32_t rs;      // refinement: active modes
+  int32_t rC, rLc;
+  int32_t rr;      // refinement clock
+  int32_t rdone;
+  int32_t Mr;      // modes after refinement and the second prune
+  int32_t pad0;
+  int64_t evals;
+};
+
 // Tiling of a (seed-group x point-chunk) warp-task grid.
 struct Tiling {
   int32_t target_warps;   // warps the step grid runs (gridDim.x * warps per CTA)

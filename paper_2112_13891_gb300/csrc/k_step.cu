@@ -16,84 +16,9 @@
 // writes its 32 partial sums with one coalesced store.  The summation order of
 // a seed does not depend on which slot of the task it occupies, so a seed's
 // trajectory is the same whatever other seeds are active.
-#include "fms_internal.cuh"
+#include "fms_step_body.cuh"
 
 namespace fms {
-
-// Butterfly reduce-scatter over a warp: on return lane l holds the warp-wide
-// sum of v[l].  31 shuffles for 32 values; the pairing tree is the same for
-// every value index.
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = up ? v[i] : v[i + o];
-      const float keep = up ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(kFull, send, o);
-    }
-  }
-  return v[0];
-}
-
-// A point as loaded by one lane: DP = 4 -> one float4, DP = 8 -> two.
-template <int DP>
-struct Pt;
-template <>
-struct Pt<4> {
-  float4 a;
-};
-template <>
-struct Pt<8> {
-  float4 a, b;
-};
-
-// Load point j, or a point so far away that its weight is exactly 0 (and
-// w * (x - y) = 0) when j is past the end of the chunk.  Coordinates of 1e18
-// give squared distances of ~1e36 (finite), so exp2 underflows to 0.
-template <int DP>
-__device__ __forceinline__ Pt<DP> load_pt(const float* __restrict__ Xs, int j, int j1) {
-  Pt<DP> p;
-  const float4 far = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
-  if constexpr (DP == 4) {
-    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + j) : far;
-  } else {
-    p.a = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j) : far;
-    p.b = j < j1 ? __ldg(reinterpret_cast<const float4*>(Xs) + 2 * j + 1) : far;
-  }
-  return p;
-}
-
-template <int D, int DP>
-__device__ __forceinline__ void coords(const Pt<DP>& p, float (&x)[D]) {
-  const float t[8] = {p.a.x, p.a.y, p.a.z, p.a.w,
-                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.x : 0.f,
-                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.y : 0.f,
-                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.z : 0.f,
-                      DP == 8 ? reinterpret_cast<const Pt<8>&>(p).b.w : 0.f};
-#pragma unroll
-  for (int k = 0; k < D; ++k) x[k] = t[k];
-}
-
-// R seeds in registers against one point: exact differences, one exp2 each.
-template <int D, int R, int DA>
-__device__ __forceinline__ void eval_point(const float (&x)[D], const float (&ys)[R][D],
-                                           float (&acc)[R][DA]) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    float dx[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) dx[k] = x[k] - ys[r][k];
-    float t = -dx[0] * dx[0];
-#pragma unroll
-    for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
-    const float w = ex2_ftz(t);
-    acc[r][0] += w;
-#pragma unroll
-    for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
-  }
-}
 
 // Low-dimensional path: D <= 7, DA accumulators per seed (sum w, d sums, pad),
 // R = 32 / DA seeds per warp task.  Each lane keeps a ring of four points in
@@ -123,50 +48,9 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
        task += nw) {
     const int g = (int)(task % G);
     const int c = (int)(task / G);
-    float ys[R][D];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      int p = g * R + r;
-      p = p < s ? p : s - 1;
-      const int64_t slot = __ldg(active + p);
-#pragma unroll
-      for (int k = 0; k < D; ++k) ys[r][k] = __ldg(y + slot * DP + k);
-    }
-    float acc[R][DA];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
-
     const int j0 = c * Lc;
     const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
-    int j = j0 + lane;
-    Pt<DP> b0 = load_pt<DP>(Xs, j, j1), b1 = load_pt<DP>(Xs, j + 32, j1);
-    Pt<DP> b2 = load_pt<DP>(Xs, j + 64, j1), b3 = load_pt<DP>(Xs, j + 96, j1);
-    for (; j < j1; j += 128) {
-      const Pt<DP> p0 = b0, p1 = b1, p2 = b2, p3 = b3;
-      b0 = load_pt<DP>(Xs, j + 128, j1);
-      b1 = load_pt<DP>(Xs, j + 160, j1);
-      b2 = load_pt<DP>(Xs, j + 192, j1);
-      b3 = load_pt<DP>(Xs, j + 224, j1);
-      float x[D];
-      coords<D, DP>(p0, x);
-      eval_point<D, R, DA>(x, ys, acc);
-      coords<D, DP>(p1, x);
-      eval_point<D, R, DA>(x, ys, acc);
-      coords<D, DP>(p2, x);
-      eval_point<D, R, DA>(x, ys, acc);
-      coords<D, DP>(p3, x);
-      eval_point<D, R, DA>(x, ys, acc);
-    }
-    float v[32];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int k = 0; k < DA; ++k) v[r * DA + k] = acc[r][k];
-    const float tot = reduce_scatter32(v, lane);
-    const int p = g * R + lane / DA;
-    if (p < s) part[((int64_t)c * s + p) * DA + (lane % DA)] = tot;
+    lowd_task<D, DP, DA>(Xs, j0, j1, y, active, s, g, c, part, lane);
   }
 }
 
@@ -198,54 +82,9 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
        task += nw) {
     const int g = (int)(task % G);
     const int c = (int)(task / G);
-    float ys[RG][DPAD];
-    float acc[RG][DPAD + 1];
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      int p = g * SPW + r * 32 + lane;
-      p = p < s ? p : s - 1;
-      const int64_t slot = __ldg(active + p);
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) ys[r][k] = k < DP ? __ldg(y + slot * DP + k) : 0.0f;
-#pragma unroll
-      for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
-    }
-    const int64_t j0 = (int64_t)c * Lc;
-    const int64_t j1 = j0 + Lc < n ? j0 + Lc : n;
-    for (int64_t j = j0; j < j1; ++j) {
-      float x[DPAD];
-      const float4* xp = reinterpret_cast<const float4*>(Xs + j * DP);
-#pragma unroll
-      for (int q = 0; q < DPAD / 4; ++q) {
-        float4 v = (4 * q < DP) ? __ldg(xp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-        x[4 * q] = v.x;
-        x[4 * q + 1] = v.y;
-        x[4 * q + 2] = v.z;
-        x[4 * q + 3] = v.w;
-      }
-#pragma unroll
-      for (int r = 0; r < RG; ++r) {
-        float dx[DPAD];
-#pragma unroll
-        for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
-        float t = -dx[0] * dx[0];
-#pragma unroll
-        for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
-        const float w = ex2_ftz(t);
-        acc[r][0] += w;
-#pragma unroll
-        for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      const int p = g * SPW + r * 32 + lane;
-      if (p < s) {
-        float* o = part + ((int64_t)c * s + p) * DA;
-#pragma unroll
-        for (int k = 0; k <= DPAD; ++k) o[k] = acc[r][k];
-      }
-    }
+    const int j0 = c * Lc;
+    const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
+    wide_task<DPAD, RG>(Xs, DP, j0, j1, y, active, s, g, c, part, lane);
   }
 }
 

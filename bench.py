@@ -338,6 +338,108 @@ def kernel_probe(m, reps=3):
     print(json.dumps({"kernel_probe": m, "first": out[0].tolist()}))
 
 
+def _events_ms(fn, reps, flush=None):
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.median(out)), out
+
+
+def bench_extra(args):
+    """Measurements of the other hot-path rows (one JSON line each; not the headline)."""
+    import torch
+    import fms_inputs as fi
+    import paper_2112_13891_gb300 as fms
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    line = {"workload": args.workload, "data": "synthetic"}
+    if args.workload == "all_seeds_3d":
+        w = fi.paper_3d()
+        X = torch.from_numpy(w.X).cuda()
+        ws = fms.Workspace(fms.workspace_size(X.shape[0], 3, all_seeds=True), X.device)
+        run = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, all_seeds=True, workspace=ws)
+        r = run()
+        ms, _ = _events_ms(run, max(2, args.steps // 50), flush)
+        rp = fms.cluster(X, w.h, w.tol, w.max_iter, all_seeds=True, workspace=ws, profile=True)
+        st = rp.stats
+        fast = fms.cluster(X, w.h, w.tol, w.max_iter, workspace=fms.Workspace(
+            fms.workspace_size(X.shape[0], 3), X.device))
+        fms_ms, _ = _events_ms(lambda: fms.cluster(X, w.h, w.tol, w.max_iter), 20, flush)
+        line.update({"metric": "ms per 200K-point clustering, every point a seed (Alg. 1)",
+                     "value": ms, "unit": "ms", "n_modes": r.stats["n_modes"],
+                     "evals": r.stats["evals"], "evals_per_s": r.stats["evals"] / (ms * 1e-3),
+                     "step_kernel": {"launches": st["step_launches"], "ms": st["step_kernel_ms"],
+                                     "evals_per_s": st["step_evals"] / max(st["step_kernel_ms"], 1e-9) * 1e3},
+                     "faster_path_ms": fms_ms, "speedup_faster_over_all_seeds": ms / fms_ms,
+                     "faster_path_modes": fast.stats["n_modes"]})
+    elif args.workload == "batched_16d":
+        sets = fi.batched_16d()
+        X = [torch.from_numpy(w.X).cuda() for w in sets]
+        Xc = torch.cat(X)
+        offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in X])]).astype(np.int64)
+        ws = fms.Workspace(fms._lib.fms_batched_workspace_size(
+            offs.ctypes.data_as(__import__("ctypes").c_void_p), len(X), 16,
+            __import__("ctypes").byref(fms.make_options())), Xc.device)
+        run = lambda: fms.cluster_batched(Xc, 2.5, 2.5e-3, 300, offsets=offs, max_modes=128,
+                                          workspace=ws)
+        r = run()   # first call tunes the tiling
+        ms, _ = _events_ms(run, 5, flush)
+        wss = fms.Workspace(max(fms.workspace_size(x.shape[0], 16) for x in X), Xc.device)
+        loop = lambda: [fms.cluster(x, 2.5, 2.5e-3, 300, workspace=wss, max_modes=128) for x in X]
+        loop()
+        ms_loop, _ = _events_ms(loop, 3, flush)
+        line.update({"metric": "ms per batch of 256 point sets (3.2M points, d=16)",
+                     "value": ms, "unit": "ms", "per_set_calls_ms": ms_loop,
+                     "speedup_batched_over_per_set": ms_loop / ms,
+                     "total_points": int(offs[-1]), "evals": r.stats["evals"],
+                     "kernel_launches": r.stats["kernel_launches"]})
+    elif args.workload == "unrolled_16d":
+        w = fi.unrolled_16d()
+        X = torch.from_numpy(w.X).cuda()
+        G = torch.randn_like(X)
+        fwd = lambda: fms.unrolled_forward(X, X, w.h, w.T, w.k_ckpt)
+        out, ck = fwd()
+        ms_f, _ = _events_ms(fwd, 3)
+        bwd = lambda: fms.unrolled_backward(X, ck, X.shape[1], w.h, w.T, w.k_ckpt, G)
+        bwd()
+        ms_b, _ = _events_ms(bwd, 3)
+        B, n, d = X.shape
+        pairs = B * n * n * w.T
+        line.update({"metric": "ms per forward / backward of 20 unrolled steps (8 x 16384 x 16)",
+                     "forward_ms": ms_f, "backward_ms": ms_b, "unit": "ms",
+                     "forward_evals_per_s": pairs / (ms_f * 1e-3),
+                     "backward_pair_evals_per_s": 3 * pairs / (ms_b * 1e-3)})
+    elif args.workload == "embedding_32d":
+        w = fi.embedding_32d()
+        X = torch.from_numpy(w.X).cuda()
+        line.update({"metric": "ms per 65,536-point d=32 clustering", "unit": "ms"})
+        for prec in ("tensor", "fp32"):
+            ws = fms.Workspace(fms.workspace_size(X.shape[0], 32, precision=prec), X.device)
+            run = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, precision=prec)
+            r = run()
+            ms, _ = _events_ms(run, max(1, min(10, args.steps)), flush)
+            st = fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, precision=prec,
+                             profile=True).stats
+            rec = {"ms": ms, "n_modes": r.stats["n_modes"], "iterations": r.stats["iterations"],
+                   "evals": r.stats["evals"], "evals_per_s": r.stats["evals"] / (ms * 1e-3),
+                   "fp32_step": {"launches": st["step_launches"], "ms": st["step_kernel_ms"],
+                                 "evals": st["step_evals"]},
+                   "coarse_step": {"launches": st["coarse_launches"],
+                                   "ms": st["coarse_kernel_ms"], "evals": st["coarse_evals"]},
+                   "phase_ms": st["phase_ms"]}
+            line[prec] = rec
+        line["value"] = line["tensor"]["ms"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,12 +448,20 @@ def main():
     ap.add_argument("--impl", default="fms", choices=["fms", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="paper_3d",
+                    choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
+                             "embedding_32d"],
+                    help="paper_3d is the headline line; the others print one line of "
+                         "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",
                     help="only run fms_mean_shift_step with M seeds on the workload's points "
                          "(a small case for ncu captures of ms_step), then exit")
     args = ap.parse_args()
     if args.kernel_probe:
         kernel_probe(args.kernel_probe)
+        return
+    if args.workload != "paper_3d":
+        bench_extra(args)
         return
     if args.impl == "reference":
         bench_reference(args)

@@ -74,8 +74,24 @@ typedef struct fms_options {
   int32_t n_seed_indices;   /* its length                                         */
   int32_t profile;          /* 1: time every ms_step launch with CUDA events and
                                report it in fms_stats (adds event records)        */
-  int32_t reserved[6];      /* must be zero                                       */
+  int32_t precision;        /* arithmetic of the seed updates (FMS_PRECISION_*):
+                               AUTO (0) = TENSOR for 9 <= d <= 32, else FP32.
+                               FP32 (1): every update evaluates the weights in
+                                  FP32 from exact differences.
+                               TENSOR (2, 8 <= d <= 32; FP32 elsewhere): a
+                                  seed's updates take the coarse tensor-core
+                                  step (BF16 weights, FP32 sums; see
+                                  fms_mean_shift_step_coarse) until one moves
+                                  it by <= 10*tol, then FP32 updates, so
+                                  convergence is always decided by an FP32
+                                  update.  Modes agree with FP32 within the
+                                  tolerance; a seed's update count may differ. */
+  int32_t reserved[5];      /* must be zero                                       */
 } fms_options;
+
+#define FMS_PRECISION_AUTO 0
+#define FMS_PRECISION_FP32 1
+#define FMS_PRECISION_TENSOR 2
 
 /* Statistics of one clustering call (host struct, filled when non-NULL). */
 typedef struct fms_stats {
@@ -95,7 +111,7 @@ typedef struct fms_stats {
   /* filled when opt->profile = 1 (else zero): */
   double step_kernel_ms;    /* summed device time of ms_step launches that had work */
   int32_t step_launches;    /* ms_step launches that had work                     */
-  int32_t reserved1;
+  int32_t coarse_launches;  /* tensor-core coarse step launches that had work     */
   int64_t step_evals;       /* seed-point evaluations of those launches           */
   double round_kernel_ms;   /* summed device time of the cluster round launches   */
   int64_t round_evals;      /* evaluations of those launches                      */
@@ -104,6 +120,8 @@ typedef struct fms_stats {
   double phase_ms[4];       /* device time of: seed rounds (selection, updates,
                                stop), prunes + doubling, refinement + ordering,
                                labels                                            */
+  double coarse_kernel_ms;  /* summed device time of those coarse step launches   */
+  int64_t coarse_evals;     /* evaluations of those launches                      */
 } fms_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -206,6 +224,31 @@ fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float 
                                const float* seeds, int64_t m, float* out_seeds,
                                float* out_wsum, void* workspace, size_t workspace_bytes,
                                void* stream);
+
+/*
+ * One coarse mean-shift update on the tensor cores, for 1 <= d <= 32
+ * (FMS_ERR_UNSUPPORTED above): the same update as fms_mean_shift_step with the
+ * weights evaluated at reduced precision.  In scaled coordinates
+ * (u = s*x, s = sqrt(log2(e)/(2h^2)), so w = 2^-||u_y - u_x||^2), the cross
+ * term u_y.u_x is a tensor-core product of BF16 hi/lo splits of both
+ * operands (hi*hi + hi*lo + lo*hi, FP32 accumulation), the squared norms are
+ * FP32, w = 2^(2 u_y.u_x - ||u_y||^2 - ||u_x||^2) is rounded to BF16, and
+ * sum w and sum w*x are a second tensor-core product of those weights with
+ * the BF16 hi/lo split of the points (FP32 accumulation).  The result agrees
+ * with the FP32 update to about 2^-8 relative in each weight; it is the
+ * "coarse" step that fms_cluster's FMS_PRECISION_TENSOR uses until a seed's
+ * move drops to 10*tol.  The paper (Sec. II-B) evaluates every weight in full
+ * precision; this step is the library's tensor-core formulation of the same
+ * sums.  Arguments as fms_mean_shift_step; workspace
+ * >= fms_coarse_step_workspace_size(n, d, m) bytes (0 for unsupported sizes)
+ * or NULL.  FMS_ERR_TIMEOUT if a bounded wait for the tensor cores gave up
+ * (reported only when workspace is NULL, i.e. when the call synchronises).
+ */
+size_t fms_coarse_step_workspace_size(int64_t n, int32_t d, int64_t m);
+fms_status fms_mean_shift_step_coarse(const float* points, int64_t n, int32_t d, float h,
+                                      const float* seeds, int64_t m, float* out_seeds,
+                                      float* out_wsum, void* workspace, size_t workspace_bytes,
+                                      void* stream);
 
 /*
  * One mean-shift update, as fms_mean_shift_step, for callers that cannot

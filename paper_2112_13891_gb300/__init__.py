@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 FMS_OK, FMS_ERR_INVALID_ARG, FMS_ERR_NONFINITE, FMS_ERR_CAPACITY = 0, 1, 2, 3
 FMS_ERR_TIMEOUT, FMS_ERR_CUDA, FMS_ERR_WORKSPACE, FMS_ERR_UNSUPPORTED = 4, 5, 6, 7
+PRECISION = {"auto": 0, "fp32": 1, "tensor": 2}
 MAX_DIM = 64
 
 
@@ -34,7 +35,7 @@ class FmsOptions(ctypes.Structure):
                 ("merge_radius", ctypes.c_float), ("skip_refine", ctypes.c_int32),
                 ("rng_seed", ctypes.c_uint64), ("seed_indices", ctypes.c_void_p),
                 ("n_seed_indices", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class FmsStats(ctypes.Structure):
@@ -45,10 +46,11 @@ class FmsStats(ctypes.Structure):
                 ("t_star_last", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("evals", ctypes.c_int64), ("score_evals", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_uint64), ("step_kernel_ms", ctypes.c_double),
-                ("step_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("step_launches", ctypes.c_int32), ("coarse_launches", ctypes.c_int32),
                 ("step_evals", ctypes.c_int64), ("round_kernel_ms", ctypes.c_double),
                 ("round_evals", ctypes.c_int64), ("round_launches", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32), ("phase_ms", ctypes.c_double * 4)]
+                ("reserved2", ctypes.c_int32), ("phase_ms", ctypes.c_double * 4),
+                ("coarse_kernel_ms", ctypes.c_double), ("coarse_evals", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -78,6 +80,10 @@ _lib.fms_step_workspace_size.restype = _SZ
 _lib.fms_step_workspace_size.argtypes = [_I64, _I32, _I64]
 _lib.fms_mean_shift_step.restype = ctypes.c_int
 _lib.fms_mean_shift_step.argtypes = [_P, _I64, _I32, _F32, _P, _I64, _P, _P, _P, _SZ, _P]
+_lib.fms_coarse_step_workspace_size.restype = _SZ
+_lib.fms_coarse_step_workspace_size.argtypes = [_I64, _I32, _I64]
+_lib.fms_mean_shift_step_coarse.restype = ctypes.c_int
+_lib.fms_mean_shift_step_coarse.argtypes = [_P, _I64, _I32, _F32, _P, _I64, _P, _P, _P, _SZ, _P]
 _lib.fms_label_points.restype = ctypes.c_int
 _lib.fms_label_points.argtypes = [_P, _I64, _I32, _P, _I32, _P, _P, _P]
 
@@ -114,7 +120,8 @@ def _points(x: torch.Tensor) -> torch.Tensor:
 
 
 def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
-                 skip_refine=False, rng_seed=0, seed_indices=None, profile=False) -> FmsOptions:
+                 skip_refine=False, rng_seed=0, seed_indices=None, profile=False,
+                 precision="auto") -> FmsOptions:
     o = FmsOptions()
     _lib.fms_options_default(ctypes.byref(o))
     o.all_seeds = int(bool(all_seeds))
@@ -128,6 +135,7 @@ def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_rad
         o.seed_indices = seed_indices.data_ptr()
         o.n_seed_indices = int(seed_indices.numel())
     o.profile = int(bool(profile))
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     return o
 
 
@@ -159,7 +167,8 @@ class Workspace:
 def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 300, *,
             all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
             skip_refine=False, rng_seed=0, seed_indices=None, max_modes=None, margins=True,
-            workspace: Workspace = None, profile=False, out=None) -> ClusterResult:
+            workspace: Workspace = None, profile=False, precision="auto",
+            out=None) -> ClusterResult:
     """Faster Mean-shift clustering of the rows of `points` (fms_cluster).
 
     `out` may pass preallocated (modes [max_modes, d], labels [n], margins [n]).
@@ -170,7 +179,7 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
         seed_indices = seed_indices.to(device=X.device, dtype=torch.int32).contiguous()
     o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
                      merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
-                     seed_indices=seed_indices, profile=profile)
+                     seed_indices=seed_indices, profile=profile, precision=precision)
     if out is not None:
         modes, labels, mar = out
         cap = modes.shape[0]
@@ -217,6 +226,28 @@ def mean_shift_step(points: torch.Tensor, seeds: torch.Tensor, h: float, with_ws
     _check(_lib.fms_mean_shift_step(_ptr(X), n, d, float(h), _ptr(Y), m, _ptr(out), _ptr(wsum),
                                     _ptr(workspace.buf), workspace.nbytes, _stream()),
            "fms_mean_shift_step")
+    return (out, wsum) if with_wsum else out
+
+
+def mean_shift_step_coarse(points: torch.Tensor, seeds: torch.Tensor, h: float,
+                           with_wsum=False, workspace: Workspace = None):
+    """One coarse (tensor-core, BF16-weight) update of each row of `seeds`
+    (fms_mean_shift_step_coarse); 1 <= d <= 32."""
+    X = _points(points)
+    Y = _points(seeds)
+    n, d = X.shape
+    m = Y.shape[0]
+    out = torch.empty_like(Y)
+    wsum = torch.empty(m, dtype=torch.float32, device=X.device) if with_wsum else None
+    need = int(_lib.fms_coarse_step_workspace_size(n, d, m))
+    if need == 0:
+        raise FmsError(FMS_ERR_UNSUPPORTED, "fms_mean_shift_step_coarse")
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, X.device)
+    _check(_lib.fms_mean_shift_step_coarse(_ptr(X), n, d, float(h), _ptr(Y), m, _ptr(out),
+                                           _ptr(wsum), _ptr(workspace.buf), workspace.nbytes,
+                                           _stream()),
+           "fms_mean_shift_step_coarse")
     return (out, wsum) if with_wsum else out
 
 

@@ -44,26 +44,40 @@ struct Layout {
   size_t off_Xs, off_y, off_seed_idx, off_it, off_conv, off_state, off_active, off_kept,
       off_alive, off_acc1, off_acc2, off_score, off_ym, off_mdone, off_mscore, off_modes_full,
       off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, off_yf, off_ract, off_rctl,
-      off_hist, off_S, total;
+      off_hist, off_S, off_img, total;
   int DP, DA, R, grid_ctas;
   int64_t Ncap;
   Tiling tl;
+  int tc_ctas;   // > 0: seed updates start on the tensor-core step (grid size)
 };
 
 constexpr int kSlogCap = 4096;
 
-Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
+// Whether a call's seed updates start on the tensor-core step.
+bool use_tensor_step(int d, int32_t precision) {
+  if (precision == FMS_PRECISION_TENSOR) return d >= 8 && d <= kTcMaxDim;
+  if (precision == FMS_PRECISION_AUTO) return d >= 9 && d <= kTcMaxDim;
+  return false;
+}
+
+Layout make_layout(int64_t n, int d, int64_t Ncap, int sms, bool tensor) {
   Layout L{};
   L.DP = padded_dim(d);
   L.DA = step_accumulators(d);
   L.R = step_seeds_per_warp(d);
   L.tl.target_warps = (sms > 0 ? sms : 1) * step_resident_warps_per_sm(d);
   L.grid_ctas = (L.tl.target_warps + 7) / 8;
-  L.tl.min_chunk = kStepMinChunk;
+  L.tl.min_chunk = step_min_chunk(d);
   L.Ncap = Ncap;
   const int64_t TW8 = 8LL * L.tl.target_warps;
   const int64_t Gmax = (Ncap + L.R - 1) / L.R;
-  const size_t part_floats = (size_t)(TW8 + Gmax + 1) * L.R * L.DA;
+  size_t part_floats = (size_t)(TW8 + Gmax + 1) * L.R * L.DA;
+  L.tc_ctas = tensor ? tc_grid(d) : 0;
+  if (tensor) {
+    // tensor-core chunking: C <= 4 grid / G + 1 chunks of s <= 2 * 128 G seeds
+    const size_t tc_floats = ((size_t)8 * L.tc_ctas * kTcTile + (size_t)Ncap + kTcTile) * L.DA;
+    if (tc_floats > part_floats) part_floats = tc_floats;
+  }
   const size_t part64_doubles = 1;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -92,12 +106,13 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms) {
   L.off_ctl = take(sizeof(IterCtl));
   L.off_mctl = take(sizeof(MergeCtl));
   L.off_status = take(64);
-  L.off_slog = take((size_t)kSlogCap * 4);
+  L.off_slog = take((size_t)kSlogCap * 2 * 4);   // ms_step log, coarse step log
   L.off_yf = take((size_t)Ncap * L.DP * 4);
   L.off_ract = take((size_t)Ncap * 4);
   L.off_rctl = take(sizeof(IterCtl));
   L.off_hist = take((size_t)(kHistCap + 2) * 4);
   L.off_S = take(64);
+  L.off_img = take(tensor ? tc_image_bytes(n, d) : 0);
   L.total = o;
   return L;
 }
@@ -115,6 +130,8 @@ void fill_defaults(const fms_options* in, fms_options* o) {
   o->seed_indices = in->seed_indices;
   o->n_seed_indices = in->n_seed_indices;
   o->profile = in->profile;
+  o->precision = in->precision;
+  for (int i = 0; i < 5; ++i) o->reserved[i] = in->reserved[i];
 }
 
 int64_t seed_capacity(int64_t n, const fms_options& o) {
@@ -176,7 +193,7 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt) {
   fill_defaults(opt, &o);
   const int64_t Ncap = seed_capacity(n, o);
   if (Ncap < 1) return 0;
-  return make_layout(n, d, Ncap, device_info().sms).total;
+  return make_layout(n, d, Ncap, device_info().sms, use_tensor_step(d, o.precision)).total;
 }
 
 fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
@@ -195,21 +212,26 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       !(o.gamma > 0.0f && o.gamma <= 1.0f) || !(o.L > 0.0f) || !isfinite(o.merge_radius) ||
       o.merge_radius < 0.0f || (o.seed_indices && o.n_seed_indices < 1))
     return FMS_ERR_INVALID_ARG;
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (o.reserved[i] != 0) return FMS_ERR_INVALID_ARG;
+  if (o.precision < FMS_PRECISION_AUTO || o.precision > FMS_PRECISION_TENSOR)
+    return FMS_ERR_INVALID_ARG;
   if (tol == 0.0f) tol = 1e-3f * h;
   if (o.all_seeds) o.gamma = 1.0f;
 
   const Dev dv = device_info();
   if (dv.sms <= 0) return FMS_ERR_CUDA;
   const int64_t Ncap = seed_capacity(n, o);
-  const Layout Lo = make_layout(n, d, Ncap, dv.sms);
+  const bool tensor = use_tensor_step(d, o.precision);
+  const Layout Lo = make_layout(n, d, Ncap, dv.sms, tensor);
   const int DP = Lo.DP, DA = Lo.DA, R = Lo.R;
   bool owns_ws = false;
   void* ws = workspace;
   std::vector<cudaEvent_t> evs;
   std::vector<int> ev_slot;
   std::vector<cudaEvent_t> round_evs;      // pairs around cluster round launches
+  std::vector<cudaEvent_t> tc_evs;         // pairs around tensor-core step launches
+  std::vector<int> tc_slot;
   cudaEvent_t phase_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double phase_acc[4] = {0, 0, 0, 0};
   int64_t round_evals_total = 0;
@@ -253,11 +275,17 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     IterCtl* rctl = at<IterCtl>(ws, Lo.off_rctl);
     int32_t* hist = at<int32_t>(ws, Lo.off_hist);
     int32_t* S_dev = at<int32_t>(ws, Lo.off_S);
+    unsigned char* img = at<unsigned char>(ws, Lo.off_img);
+    int32_t* tclog = slog + kSlogCap;
+    Tiling tl_iter = Lo.tl;   // the seed-update loop (tensor-core chunking when on)
+    tl_iter.tc_ctas = Lo.tc_ctas;
+    const int32_t init_state = tensor ? kCoarse : kRunning;
     const int qmax = d <= 7 ? round_max_clusters(d) : 0;
 
     const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
     const double tol_s = (double)tol * scale;
     const float tol2_s = (float)(tol_s * tol_s);
+    const float coarse_tol2_s = (float)(100.0 * tol_s * tol_s);   // (10 tol)^2
     const double r_merge = o.merge_radius > 0.0f ? (double)o.merge_radius : (double)h;
     const double r2_s = (r_merge * scale) * (r_merge * scale);
     const bool allow_doubling = !o.all_seeds && !o.seed_indices;
@@ -266,10 +294,11 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (g > (int64_t)dv.sms * 8) g = (int64_t)dv.sms * 8;
       return g < 1 ? 1 : (int)g;
     };
-    int n_slog = 0;
+    int n_slog = 0, n_tclog = 0;
 
     auto step_launch = [&](const float* pos, const int32_t* list, const int32_t* s_ptr,
-                           const int32_t* C_ptr, const int32_t* Lc_ptr) -> cudaError_t {
+                           const int32_t* C_ptr, const int32_t* Lc_ptr,
+                           const int32_t* p_lo = nullptr) -> cudaError_t {
       int32_t* lg = nullptr;
       if (o.profile && n_slog < kSlogCap) {
         cudaEvent_t a, b;
@@ -278,7 +307,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         cudaEventRecord(a, st);
         lg = slog + n_slog;
         cudaError_t e = launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                                       Lo.tl.target_warps, st, lg);
+                                       Lo.tl.target_warps, st, lg, p_lo);
         cudaEventRecord(b, st);
         evs.push_back(a);
         evs.push_back(b);
@@ -286,7 +315,27 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         return e;
       }
       return launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                            Lo.tl.target_warps, st, nullptr);
+                            Lo.tl.target_warps, st, nullptr, p_lo);
+    };
+    // the coarse step for active positions [0, ctl->s_tc)
+    auto tc_launch = [&]() -> cudaError_t {
+      int32_t* lg = nullptr;
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (o.profile && n_tclog < kSlogCap) {
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+          return cudaErrorUnknown;
+        cudaEventRecord(a, st);
+        lg = tclog + n_tclog;
+      }
+      cudaError_t e = launch_ms_step_tc(img, n, d, DP, DA, y, active, &ctl->s, &ctl->s_tc,
+                                        &ctl->C, &ctl->Lc, part, status, st, lg);
+      if (lg) {
+        cudaEventRecord(b, st);
+        tc_evs.push_back(a);
+        tc_evs.push_back(b);
+        tc_slot.push_back(n_tclog++);
+      }
+      return e;
     };
 
     FMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IterCtl), st));
@@ -312,13 +361,14 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     };
     mark(0);
     FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
+    if (tensor) FMS_LAUNCH(launch_tc_pack(Xs, n, d, DP, img, st));
 
     // --- Seed Selection (Alg. 2 line 2) ---
     if (o.all_seeds) N = (int32_t)n;
     else if (o.seed_indices) N = o.n_seed_indices;
     else N = (int32_t)(o.n_initial < n ? o.n_initial : n);
     FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y, it,
-                              conv, state, status, st));
+                              conv, state, status, st, init_state));
 
     for (;;) {
       ++rounds;
@@ -350,18 +400,28 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                        st));
         mark(1);
       } else {
-        FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, Lo.tl, N, target,
+        FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, tl_iter, N, target,
                                      max_iter, st));
         for (;;) {
           for (int b = 0; b < kUpdatesPerBatch; ++b) {
-            FMS_LAUNCH(step_launch(y, active, &ctl->s, &ctl->C, &ctl->Lc));
+            if (tensor) {
+              FMS_LAUNCH(tc_launch());
+              FMS_LAUNCH(step_launch(y, active, &ctl->s, &ctl->C, &ctl->Lc, &ctl->s_tc));
+            } else {
+              FMS_LAUNCH(step_launch(y, active, &ctl->s, &ctl->C, &ctl->Lc));
+            }
             FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
-                                     max_iter, n, R, Lo.tl, N, target, st, update_grid(N)));
+                                     max_iter, n, R, tl_iter, N, target, st, update_grid(N),
+                                     coarse_tol2_s));
           }
           FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
           FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
           FMS_CUDA(cudaStreamSynchronize(st));
           if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
+          if (hstatus & kStTimeout) {
+            rc = FMS_ERR_TIMEOUT;
+            goto done;
+          }
           if (hctl.done) break;
         }
         // --- prune candidates (Alg. 2 line 10) ---
@@ -384,7 +444,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (hm.next_N > N) {
         mark(0);
         FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, N, N, hm.next_N - N, seed_idx,
-                                  y, it, conv, state, status, st));
+                                  y, it, conv, state, status, st, init_state));
         N = hm.next_N;
         continue;
       }
@@ -444,14 +504,21 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
     FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> hslog(n_slog);
+    std::vector<int32_t> hslog(n_slog), htclog(n_tclog);
     if (n_slog > 0)
       FMS_CUDA(cudaMemcpyAsync(hslog.data(), slog, (size_t)n_slog * 4, cudaMemcpyDeviceToHost, st));
+    if (n_tclog > 0)
+      FMS_CUDA(cudaMemcpyAsync(htclog.data(), tclog, (size_t)n_tclog * 4, cudaMemcpyDeviceToHost,
+                               st));
     FMS_CUDA(cudaStreamSynchronize(st));
     Mfinal = hm.Mr;
     *out_n_modes = Mfinal;
     if (hstatus & kStNonFinite) goto device_error;
     if (hstatus & kStBadArg) goto device_error;
+    if (hstatus & kStTimeout) {
+      rc = FMS_ERR_TIMEOUT;
+      goto done;
+    }
     if (Mfinal > max_modes) rc = FMS_ERR_CAPACITY;
     if (stats) {
       stats->iterations = hctl.steps;
@@ -494,6 +561,21 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         stats->step_kernel_ms = ms;
         stats->step_launches = launches;
         stats->step_evals = ev;
+        double tms = 0.0;
+        int tl_n = 0;
+        int64_t tev = 0;
+        for (size_t i = 0; i < tc_slot.size(); ++i) {
+          const int s_i = htclog[tc_slot[i]];
+          if (s_i <= 0) continue;
+          float t = 0.0f;
+          cudaEventElapsedTime(&t, tc_evs[2 * i], tc_evs[2 * i + 1]);
+          tms += t;
+          ++tl_n;
+          tev += (int64_t)s_i * n;
+        }
+        stats->coarse_kernel_ms = tms;
+        stats->coarse_launches = tl_n;
+        stats->coarse_evals = tev;
       }
     }
     goto done;
@@ -504,6 +586,7 @@ device_error:
 done:
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
   for (cudaEvent_t e : round_evs) cudaEventDestroy(e);
+  for (cudaEvent_t e : tc_evs) cudaEventDestroy(e);
   for (cudaEvent_t e : phase_ev)
     if (e) cudaEventDestroy(e);
   if (owns_ws) {
@@ -537,7 +620,7 @@ StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
   L.DP = padded_dim(d);
   L.DA = step_accumulators(d);
   L.R = step_seeds_per_warp(d);
-  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), kStepMinChunk};
+  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), step_min_chunk(d)};
   L.grid_ctas = (tl.target_warps + 7) / 8;
   choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
   size_t o = 0;
@@ -603,6 +686,94 @@ fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float 
       FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
       FMS_CUDA(cudaStreamSynchronize(st));
       if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+    }
+  }
+done:
+  if (owns) cudaFreeAsync(ws, st);
+  return rc;
+}
+
+namespace {
+struct CoarseLayout {
+  size_t off_Xs, off_img, off_Ys, off_active, off_part, off_ctl, off_status, total;
+  int DP, DA, C, Lc, grid;
+};
+
+CoarseLayout coarse_layout(int64_t n, int d, int64_t m) {
+  CoarseLayout L{};
+  L.DP = padded_dim(d);
+  L.DA = L.DP + 4;
+  L.grid = tc_grid(d);
+  tc_choose_chunks(n, (int32_t)m, L.grid, &L.C, &L.Lc);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = o;
+    o += align256(bytes > 0 ? bytes : 1);
+    return at_;
+  };
+  L.off_Xs = take((size_t)n * L.DP * 4);
+  L.off_img = take(tc_image_bytes(n, d));
+  L.off_Ys = take((size_t)m * L.DP * 4);
+  L.off_active = take((size_t)m * 4);
+  L.off_part = take((size_t)L.C * (size_t)m * L.DA * 4);
+  L.off_ctl = take(sizeof(IterCtl));
+  L.off_status = take(64);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t fms_coarse_step_workspace_size(int64_t n, int32_t d, int64_t m) {
+  if (n < 1 || n > INT32_MAX || d < 1 || d > kTcMaxDim || m < 1 || m > INT32_MAX) return 0;
+  return coarse_layout(n, d, m).total;
+}
+
+fms_status fms_mean_shift_step_coarse(const float* points, int64_t n, int32_t d, float h,
+                                      const float* seeds, int64_t m, float* out_seeds,
+                                      float* out_wsum, void* workspace, size_t workspace_bytes,
+                                      void* stream_) {
+  if (!points || !seeds || !out_seeds || n < 1 || n > INT32_MAX || d < 1 || d > FMS_MAX_DIM ||
+      m < 1 || m > INT32_MAX || !(h > 0.0f) || !isfinite(h))
+    return FMS_ERR_INVALID_ARG;
+  if (d > kTcMaxDim) return FMS_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  if (device_info().sms <= 0) return FMS_ERR_CUDA;
+  const CoarseLayout L = coarse_layout(n, d, m);
+  fms_status rc = FMS_OK;
+  bool owns = false;
+  void* ws = workspace;
+  uint32_t hstatus = 0;
+  if (ws) {
+    if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+      return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns = true;
+  }
+  {
+    const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    float* Xs = at<float>(ws, L.off_Xs);
+    unsigned char* img = at<unsigned char>(ws, L.off_img);
+    float* Ys = at<float>(ws, L.off_Ys);
+    int32_t* active = at<int32_t>(ws, L.off_active);
+    float* part = at<float>(ws, L.off_part);
+    IterCtl* ctl = at<IterCtl>(ws, L.off_ctl);
+    uint32_t* status = at<uint32_t>(ws, L.off_status);
+    FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
+    FMS_CUDA(launch_pack_points(points, n, d, L.DP, (float)scale, Xs, status, st));
+    FMS_CUDA(launch_tc_pack(Xs, n, d, L.DP, img, st));
+    FMS_CUDA(launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st));
+    FMS_CUDA(launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st));
+    FMS_CUDA(launch_ms_step_tc(img, n, d, L.DP, L.DA, Ys, active, &ctl->s, &ctl->s, &ctl->C,
+                               &ctl->Lc, part, status, st));
+    FMS_CUDA(launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum,
+                                (int)m, st));
+    if (owns) {
+      FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
+      FMS_CUDA(cudaStreamSynchronize(st));
+      if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+      else if (hstatus & kStTimeout) rc = FMS_ERR_TIMEOUT;
+      else if (hstatus & kStBadArg) rc = FMS_ERR_INVALID_ARG;
     }
   }
 done:

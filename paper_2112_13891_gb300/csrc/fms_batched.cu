@@ -165,7 +165,8 @@ BLayout make_blayout(int64_t total, int B, int d, int sms, int tw_mult, int min_
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
 const int kTwMults[2] = {1, 2};
-const int kMinChunks[3] = {256, 512, 1024};
+const int kMinChunksLow[3] = {256, 512, 1024};
+const int kMinChunksWide[3] = {32, 64, 128};
 
 template <typename T>
 T* at(void* base, size_t off) {
@@ -188,7 +189,7 @@ size_t fms_batched_workspace_size(const int64_t* offsets, int32_t B, int32_t d,
   if (!offsets || B < 1 || d < 1 || d > FMS_MAX_DIM) return 0;
   const int64_t total = offsets[B] - offsets[0];
   if (total < 1 || total > INT32_MAX) return 0;
-  return make_blayout(total, B, d, sms_now(), kTwMults[0], kMinChunks[0]).total;
+  return make_blayout(total, B, d, sms_now(), kTwMults[0], 32).total;
 }
 
 fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int32_t B, int32_t d,
@@ -230,7 +231,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
   cudaGetDevice(&dev);
   const auto key = std::make_tuple(dev, (int)d, ilog2(total), ilog2(B));
   bool tuned = false;
-  std::pair<int, int> cfg{kTwMults[0], kMinChunks[1]};
+  std::pair<int, int> cfg{kTwMults[0], d <= 7 ? kMinChunksLow[1] : kMinChunksWide[1]};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto itc = g_tuned.find(key);
@@ -330,8 +331,10 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
       cudaEvent_t e0, e1;
       BC(cudaEventCreate(&e0));
       BC(cudaEventCreate(&e1));
+      const int* cands = d <= 7 ? kMinChunksLow : kMinChunksWide;
       for (int tm : kTwMults)
-        for (int mc : kMinChunks) {
+        for (int ci = 0; ci < 3; ++ci) {
+          const int mc = cands[ci];
           const BLayout Lc = make_blayout(total, B, d, sms, tm, mc);
           BL(launch_batched_compact(sc, B, state, it, conv, active, 1, max_iter, R, DA, Lc.tl,
                                     task_off, part_off, list_off, totals, counters, counters + 1,

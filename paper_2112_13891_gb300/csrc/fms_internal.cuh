@@ -8,8 +8,11 @@
 //                           up to a multiple of 4), pad lanes are 0.
 //   seeds   slot i = rank i in the seed sequence: point index, scaled position
 //           y[i][DP], updates done it[i], convergence update conv[i] (-1 if
-//           none) and state[i] (RUNNING / CONVERGED / FAILED / EXHAUSTED).
-//   active  the seed slots that take the next update, in slot order.
+//           none) and state[i] (RUNNING / COARSE / CONVERGED / FAILED /
+//           EXHAUSTED); COARSE is a running seed whose updates still take the
+//           tensor-core (BF16) step.
+//   active  the seed slots that take the next update, in slot order (with
+//           the tensor-core step on: COARSE seeds first, then RUNNING ones).
 //   part    per-(chunk, active position) partial sums [C][s][DA] float:
 //           DA accumulators per seed = (sum w, sum w*(x-y)_0..d-1, pad).
 #pragma once
@@ -32,7 +35,7 @@ enum : uint32_t {
 };
 
 // per-seed state
-enum : int32_t { kRunning = 0, kConverged = 1, kFailed = 2, kExhausted = 3 };
+enum : int32_t { kRunning = 0, kConverged = 1, kFailed = 2, kExhausted = 3, kCoarse = 4 };
 
 // Control block of one iteration loop, written by the device.
 struct IterCtl {
@@ -49,7 +52,7 @@ struct IterCtl {
   int32_t n_exhausted;
   int32_t steps;      // updates that had at least one active seed
   int32_t blocks_done;  // blocks of the current update launch that finished
-  int32_t pad0;
+  int32_t s_tc;       // active positions [0, s_tc) take the tensor-core step
   int64_t evals;      // seed-point evaluations issued
 };
 
@@ -113,6 +116,8 @@ struct SetCtl {
 struct Tiling {
   int32_t target_warps;   // warps the step grid runs (gridDim.x * warps per CTA)
   int32_t min_chunk;      // smallest chunk in points (multiple of 32)
+  int32_t tc_ctas;        // > 0: COARSE seeds take the tensor-core step, whose grid
+                          // has this many CTAs; chunks are then whole 128-point tiles
 };
 
 // Chunk count and length for s active seeds of R per warp over n points.
@@ -153,6 +158,53 @@ __host__ __device__ inline void choose_chunks(int64_t n, int32_t s, int32_t R, T
   lc = (lc + 31) / 32 * 32;
   *C = (int32_t)((n + lc - 1) / lc);
   *Lc = (int32_t)lc;
+}
+
+// Points per tile of the tensor-core step (k_step_tc.cu).
+constexpr int kTcTile = 128;
+
+// Chunks for the tensor-core step: s seeds in tiles of 128 x chunks of whole
+// 128-point tiles, run by a persistent grid of `grid` CTAs.  Picks the chunk
+// count (at least kTcMinTiles tiles per chunk) whose last wave is fullest over
+// 1..4 waves; ties -> fewer chunks.
+constexpr int kTcMinTiles = 2;
+__host__ __device__ inline void tc_choose_chunks(int64_t n, int32_t s, int32_t grid, int32_t* C,
+                                                 int32_t* Lc) {
+  if (s <= 0) {
+    *C = 0;
+    *Lc = 0;
+    return;
+  }
+  const int64_t nt = (n + kTcTile - 1) / kTcTile;
+  const int64_t G = (s + kTcTile - 1) / kTcTile;
+  const int64_t P = grid > 0 ? grid : 1;
+  int64_t best_tpc = nt, best_num = -1, best_den = 1, best_c = 1;
+  for (int k = 1; k <= 4; ++k) {
+    int64_t c = (k * P) / G;
+    if (c < 1) c = 1;
+    int64_t tpc = (nt + c - 1) / c;
+    if (tpc < kTcMinTiles) tpc = kTcMinTiles < nt ? kTcMinTiles : nt;
+    c = (nt + tpc - 1) / tpc;
+    const int64_t tasks = G * c;
+    const int64_t waves = (tasks + P - 1) / P;
+    if (tasks * best_den > best_num * (waves * P) ||
+        (tasks * best_den == best_num * (waves * P) && c < best_c)) {
+      best_num = tasks;
+      best_den = waves * P;
+      best_c = c;
+      best_tpc = tpc;
+    }
+  }
+  *C = (int32_t)best_c;
+  *Lc = (int32_t)(best_tpc * kTcTile);
+}
+
+// Chunk length rounded up to whole tensor-core tiles (C recomputed).
+__host__ __device__ inline void tc_round_chunks(int64_t n, int32_t* C, int32_t* Lc) {
+  if (*C <= 0) return;
+  const int64_t lc = ((int64_t)*Lc + kTcTile - 1) / kTcTile * kTcTile;
+  *Lc = (int32_t)lc;
+  *C = (int32_t)((n + lc - 1) / lc);
 }
 
 __device__ __forceinline__ float ex2_ftz(float x) {
@@ -222,7 +274,8 @@ cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float s
 cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
                              const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
                              int32_t count, int32_t* seed_idx, float* y, int32_t* it,
-                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st);
+                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st,
+                             int32_t init_state = kRunning);
 cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
                                 int32_t* out, cudaStream_t st);
 cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
@@ -231,7 +284,7 @@ cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t*
 cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
-                          cudaStream_t st, int grid);
+                          cudaStream_t st, int grid, float coarse_tol2_s = 0.0f);
 cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
                               cudaStream_t st);
 cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
@@ -278,10 +331,29 @@ cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, fl
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps,
-                           cudaStream_t st, int32_t* s_log = nullptr);
+                           cudaStream_t st, int32_t* s_log = nullptr,
+                           const int32_t* p_lo_ptr = nullptr);
 int step_seeds_per_warp(int d);
 int step_resident_warps_per_sm(int d);
+// smallest chunk (points) of a warp task: the low-d kernel splits a chunk over
+// 32 lanes, the wide kernel gives every point to all 32 lanes
+inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : 64; }
 int step_accumulators(int d);
+
+// k_step_tc.cu: the coarse step on the tensor cores (1 <= d <= 32).  The
+// point tile images are built once per call by launch_tc_pack; the step
+// handles active positions [0, *count_ptr) of a list whose partials have the
+// stride *s_total_ptr, with chunks of *Lc_ptr (a multiple of 128) points.
+constexpr int kTcMaxDim = 32;
+size_t tc_image_bytes(int64_t n, int d);
+cudaError_t launch_tc_pack(const float* Xs, int64_t n, int d, int DP, unsigned char* img,
+                           cudaStream_t st);
+int tc_grid(int d);
+cudaError_t launch_ms_step_tc(const unsigned char* img, int64_t n, int d, int DP, int DA,
+                              const float* y, const int32_t* active, const int32_t* s_total_ptr,
+                              const int32_t* count_ptr, const int32_t* C_ptr,
+                              const int32_t* Lc_ptr, float* part, uint32_t* status,
+                              cudaStream_t st, int32_t* s_log = nullptr);
 
 // k_merge.cu
 cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int32_t* conv,

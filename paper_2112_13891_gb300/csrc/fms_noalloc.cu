@@ -75,7 +75,7 @@ extern "C" fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n
   const int DP = padded_dim_of(d);
   const int DA = step_accumulators(d);
   const int R = step_seeds_per_warp(d);
-  Tiling tl{sms * step_resident_warps_per_sm(d), kStepMinChunk};
+  Tiling tl{sms * step_resident_warps_per_sm(d), step_min_chunk(d)};
   int32_t C = 0, Lc = 0;
   choose_chunks(n, (int32_t)m, R, tl, &C, &Lc);
   const size_t off_Xs = 0;

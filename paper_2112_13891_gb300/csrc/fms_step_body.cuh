@@ -134,19 +134,21 @@ __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, 
 }
 
 // One wide warp task: lanes own seeds (RG per lane, 32*RG seeds per task),
-// points [j0, j1) read with warp-uniform loads; DA = DPAD + 4.
+// points [j0, j1) read with warp-uniform loads; DA = DPAD + 4.  Group g covers
+// active positions p_lo + g*32*RG ... (positions below p_lo belong to the
+// tensor-core step).
 template <int DPAD, int RG>
 __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, int j0, int j1,
                                           const float* __restrict__ y,
                                           const int32_t* __restrict__ active, int s, int g, int c,
-                                          float* __restrict__ part, int lane) {
+                                          float* __restrict__ part, int lane, int p_lo = 0) {
   constexpr int DA = DPAD + 4;
   constexpr int SPW = 32 * RG;
   float ys[RG][DPAD];
   float acc[RG][DPAD + 1];
 #pragma unroll
   for (int r = 0; r < RG; ++r) {
-    int p = g * SPW + r * 32 + lane;
+    int p = p_lo + g * SPW + r * 32 + lane;
     p = p < s ? p : s - 1;
     const int64_t slot = __ldg(active + p);
 #pragma unroll
@@ -181,7 +183,7 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
   }
 #pragma unroll
   for (int r = 0; r < RG; ++r) {
-    const int p = g * SPW + r * 32 + lane;
+    const int p = p_lo + g * SPW + r * 32 + lane;
     if (p < s) {
       float* o = part + ((int64_t)c * s + p) * DA;
 #pragma unroll

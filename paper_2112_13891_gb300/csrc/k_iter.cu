@@ -103,7 +103,7 @@ __global__ void seed_init_kernel(const float* __restrict__ Xs, int64_t n, int DP
                                  int32_t slot0, int32_t count, int32_t* __restrict__ seed_idx,
                                  float* __restrict__ y, int32_t* __restrict__ it,
                                  int32_t* __restrict__ conv, int32_t* __restrict__ state,
-                                 uint32_t* status) {
+                                 uint32_t* status, int32_t init_state) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
     int64_t idx;
     if (explicit_idx) {
@@ -120,20 +120,21 @@ __global__ void seed_init_kernel(const float* __restrict__ Xs, int64_t n, int DP
     for (int k = 0; k < DP; ++k) y[slot * DP + k] = Xs[idx * DP + k];
     it[slot] = 0;
     conv[slot] = -1;
-    state[slot] = kRunning;
+    state[slot] = init_state;
   }
 }
 
 cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
                              const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
                              int32_t count, int32_t* seed_idx, float* y, int32_t* it,
-                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st) {
+                             int32_t* conv, int32_t* state, uint32_t* status, cudaStream_t st,
+                             int32_t init_state) {
   if (count <= 0) return cudaSuccess;
   const FeistelKey f = make_key(n, rng_seed);
   int blocks = (count + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   seed_init_kernel<<<blocks, 256, 0, st>>>(Xs, n, DP, f, explicit_idx, rank0, slot0, count,
-                                           seed_idx, y, it, conv, state, status);
+                                           seed_idx, y, it, conv, state, status, init_state);
   return cudaGetLastError();
 }
 
@@ -191,11 +192,14 @@ __device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, in
 // on, the clock jumps to the next event (a waiting seed's count or a
 // convergence update of an earlier round).  Runs on one block (any size that
 // is a multiple of 32); reads bypass L1 because other blocks of the same
-// launch wrote the seed states.
+// launch wrote the seed states.  With the tensor-core step on, the due seeds
+// are listed in two passes, COARSE ones first, so that one contiguous range
+// of the list goes to each step kernel; the order within a pass is slot order.
 // ---------------------------------------------------------------------------
+// want: -1 lists every due running seed, else only those in state `want`.
 __device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
                            const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
-                           int32_t* __restrict__ active, int* s_out, int* conv_out,
+                           int32_t* __restrict__ active, int want, int* s_out, int* conv_out,
                            int* next_event_out, int* scratch) {
   int base = 0, convd = 0, nxt = INT32_MAX;
   for (int b = 0; b < N; b += blockDim.x) {
@@ -203,9 +207,9 @@ __device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
     int take = 0;
     if (i < N) {
       const int stt = __ldcg(state + i);
-      if (stt == kRunning) {
+      if (stt == kRunning || stt == kCoarse) {
         const int ti = __ldcg(it + i);
-        if (ti == r) take = 1;
+        if (ti == r) take = (want < 0 || stt == want) ? 1 : 0;
         else if (ti > r) nxt = min(nxt, ti);
       } else if (stt == kConverged) {
         const int ci = __ldcg(conv + i);
@@ -231,9 +235,16 @@ __device__ void compaction_body(IterCtl* ctl, const int32_t* __restrict__ state,
                                 int begin, int N, int target, int max_iter, int* scratch) {
   int r = begin ? 0 : __ldcg(&ctl->r) + 1;
   const int prev_s = begin ? 0 : __ldcg(&ctl->s);
-  int s = 0, convd = 0, nxt = 0, done = 0;
+  int s = 0, s_c = 0, convd = 0, nxt = 0, done = 0;
   for (int guard = 0; guard <= max_iter + 2; ++guard) {
-    scan_clock(r, N, state, it, conv, active, &s, &convd, &nxt, scratch);
+    if (tl.tc_ctas > 0) {
+      int s_f = 0;
+      scan_clock(r, N, state, it, conv, active, kCoarse, &s_c, &convd, &nxt, scratch);
+      scan_clock(r, N, state, it, conv, active + s_c, kRunning, &s_f, &convd, &nxt, scratch);
+      s = s_c + s_f;
+    } else {
+      scan_clock(r, N, state, it, conv, active, -1, &s, &convd, &nxt, scratch);
+    }
     done = (convd >= target) || (r >= max_iter);
     if (!done && s == 0) {
       // nothing is due at r: move the clock to the next event; with no event
@@ -252,8 +263,16 @@ __device__ void compaction_body(IterCtl* ctl, const int32_t* __restrict__ state,
     ctl->n_converged = convd;
     if (prev_s > 0) ctl->steps += 1;
     ctl->s = done ? 0 : s;
+    ctl->s_tc = done ? 0 : s_c;
     int C = 0, Lc = 0;
-    if (!done) choose_chunks(n, s, R, tl, &C, &Lc);
+    if (!done) {
+      if (tl.tc_ctas > 0 && s_c >= s - s_c) {
+        tc_choose_chunks(n, s_c, tl.tc_ctas, &C, &Lc);
+      } else {
+        choose_chunks(n, s - s_c, R, tl, &C, &Lc);
+        if (tl.tc_ctas > 0) tc_round_chunks(n, &C, &Lc);
+      }
+    }
     ctl->C = C;
     ctl->Lc = Lc;
     if (!done) ctl->evals += (int64_t)s * n;
@@ -284,12 +303,16 @@ cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t*
 // ||S/W|| <= tol, and the seed's state.  One warp per active position.  The
 // last block to finish (atomic ticket after a fence, no waiting) then runs the
 // Early Stopping bookkeeping above for the next update.
+//
+// A COARSE seed's S/W came from the tensor-core step (BF16 weights): it moves
+// by it, and once ||S/W|| <= coarse_tol (10 tol) it turns RUNNING, so the
+// updates that decide convergence are always exact FP32 ones.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
     update_kernel(const float* __restrict__ part, int32_t* __restrict__ active, IterCtl* ctl,
                   float* __restrict__ y, int32_t* __restrict__ it, int32_t* __restrict__ conv,
                   int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s, int64_t n,
-                  int32_t R, Tiling tl, int N, int target, int max_iter) {
+                  int32_t R, Tiling tl, int N, int target, int max_iter, float coarse_tol2_s) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
   if (__ldcg(&ctl->done)) return;  // uniform for the whole launch
@@ -326,8 +349,12 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) {
       const int t = it[slot] + 1;
       it[slot] = t;
+      const bool coarse = state[slot] == kCoarse;
       if (!finite) {
         state[slot] = kFailed;
+      } else if (coarse) {
+        if (step2 <= coarse_tol2_s) state[slot] = kRunning;
+        if (t >= max_iter) state[slot] = kExhausted;
       } else if (step2 <= tol2_s) {
         state[slot] = kConverged;
         conv[slot] = t;
@@ -349,9 +376,9 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
-                          cudaStream_t st, int grid) {
+                          cudaStream_t st, int grid, float coarse_tol2_s) {
   update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s, n,
-                                      R, tl, N, target, max_iter);
+                                      R, tl, N, target, max_iter, coarse_tol2_s);
   return cudaGetLastError();
 }
 

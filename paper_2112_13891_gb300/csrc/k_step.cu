@@ -66,15 +66,17 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
                                                     const int32_t* __restrict__ C_ptr,
                                                     const int32_t* __restrict__ Lc_ptr,
                                                     float* __restrict__ part,
-                                                    int32_t* __restrict__ s_log) {
+                                                    int32_t* __restrict__ s_log,
+                                                    const int32_t* __restrict__ p_lo_ptr) {
   constexpr int DA = DPAD + 4;
   constexpr int SPW = 32 * RG;  // seeds per warp task
   const int s = *s_ptr;
-  if (s_log && blockIdx.x == 0 && threadIdx.x == 0) *s_log = s;
-  if (s <= 0) return;
+  const int p_lo = p_lo_ptr ? *p_lo_ptr : 0;
+  if (s_log && blockIdx.x == 0 && threadIdx.x == 0) *s_log = s - p_lo;
+  if (s - p_lo <= 0) return;
   const int C = *C_ptr;
   const int Lc = *Lc_ptr;
-  const int G = (s + SPW - 1) / SPW;
+  const int G = (s - p_lo + SPW - 1) / SPW;
   const int64_t T = (int64_t)G * C;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
     const int c = (int)(task / G);
     const int j0 = c * Lc;
     const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
-    wide_task<DPAD, RG>(Xs, DP, j0, j1, y, active, s, g, c, part, lane);
+    wide_task<DPAD, RG>(Xs, DP, j0, j1, y, active, s, g, c, part, lane, p_lo);
   }
 }
 
@@ -140,7 +142,7 @@ int step_resident_warps_per_sm(int d) {
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
-                           int32_t* s_log) {
+                           int32_t* s_log, const int32_t* p_lo_ptr) {
   const dim3 g((target_warps + 7) / 8);
   const int grid_ctas = (int)g.x;
   switch (d) {
@@ -153,13 +155,13 @@ cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const floa
     case 7: ms_step_lowd<7, 8, 8><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
     default:
       if (d <= 8)
-        ms_step_wide<8, 4><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log);
+        ms_step_wide<8, 4><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 16)
-        ms_step_wide<16, 2><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log);
+        ms_step_wide<16, 2><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 32)
-        ms_step_wide<32, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log);
+        ms_step_wide<32, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else
-        ms_step_wide<64, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log);
+        ms_step_wide<64, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       break;
   }
   return cudaGetLastError();

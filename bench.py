@@ -437,6 +437,36 @@ def bench_extra(args):
                    "phase_ms": st["phase_ms"]}
             line[prec] = rec
         line["value"] = line["tensor"]["ms"]
+    elif args.workload == "step_wide":
+        # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
+        peaks = measured_peaks()
+        for d in (16, 32):
+            w = fi.embedding_32d(d=d)
+            X = torch.from_numpy(w.X).cuda()
+            n = X.shape[0]
+            rec = {"n": n, "m": n, "evals": n * n}
+            for kind, fn, size in (("coarse", fms.mean_shift_step_coarse, fms._lib.fms_coarse_step_workspace_size),
+                                   ("fp32", fms.mean_shift_step, fms._lib.fms_step_workspace_size)):
+                ws = fms.Workspace(int(size(n, d, n)), X.device)
+                run = lambda: fn(X, X, w.h, workspace=ws)
+                run()
+                ms, _ = _events_ms(run, max(3, min(10, args.steps)), flush)
+                rec[kind] = {"ms": ms, "evals_per_s": n * n / (ms * 1e-3)}
+            dpad = 16 if d <= 16 else 32
+            # issued MMA work per seed-point pair: S = three BF16 split products
+            # (K = dpad each) plus the 16-wide norm block; P [Xh | Xl | 1 ..]
+            # (N = 2 dpad + 16)
+            mma_flops = 2.0 * (3 * dpad + 16 + 2 * dpad + 16) * n * n
+            alg_flops = (4.0 * d + 2) * n * n
+            tf = peaks.get("bf16_tflops")
+            rec["coarse"]["mma_tflops"] = mma_flops / (rec["coarse"]["ms"] * 1e-3) / 1e12
+            rec["coarse"]["algorithmic_tflops"] = alg_flops / (rec["coarse"]["ms"] * 1e-3) / 1e12
+            if tf:
+                rec["coarse"]["mma_frac_of_measured_bf16"] = rec["coarse"]["mma_tflops"] / tf
+            rec["speedup_coarse_over_fp32"] = rec["fp32"]["ms"] / rec["coarse"]["ms"]
+            line[f"d{d}"] = rec
+        line["metric"] = "ms per update of 65,536 seeds against 65,536 points"
+        line["unit"] = "ms"
     print(json.dumps(line), flush=True)
 
 
@@ -450,7 +480,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
-                             "embedding_32d"],
+                             "embedding_32d", "step_wide"],
                     help="paper_3d is the headline line; the others print one line of "
                          "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",

@@ -74,8 +74,9 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms, bool tensor) {
   size_t part_floats = (size_t)(TW8 + Gmax + 1) * L.R * L.DA;
   L.tc_ctas = tensor ? tc_grid(d) : 0;
   if (tensor) {
-    // tensor-core chunking: C <= 4 grid / G + 1 chunks of s <= 2 * 128 G seeds
-    const size_t tc_floats = ((size_t)8 * L.tc_ctas * kTcTile + (size_t)Ncap + kTcTile) * L.DA;
+    // tensor-core chunking: C <= max(4, 4 grid / G + 1) chunks of s <= 2 * 128 G seeds
+    const size_t tc_floats =
+        ((size_t)8 * L.tc_ctas * kTcTile + (size_t)4 * Ncap + kTcTile) * L.DA;
     if (tc_floats > part_floats) part_floats = tc_floats;
   }
   const size_t part64_doubles = 1;

@@ -164,9 +164,10 @@ __host__ __device__ inline void choose_chunks(int64_t n, int32_t s, int32_t R, T
 constexpr int kTcTile = 128;
 
 // Chunks for the tensor-core step: s seeds in tiles of 128 x chunks of whole
-// 128-point tiles, run by a persistent grid of `grid` CTAs.  Picks the chunk
-// count (at least kTcMinTiles tiles per chunk) whose last wave is fullest over
-// 1..4 waves; ties -> fewer chunks.
+// 128-point tiles, run by a persistent grid of `grid` CTAs.  Candidate chunk
+// counts are 1..4 and the counts that make k = 1..4 full waves; the one whose
+// last wave is fullest wins (ties -> fewer chunks), with at least kTcMinTiles
+// tiles per chunk.  C <= max(4, 4 grid / G + 1).
 constexpr int kTcMinTiles = 2;
 __host__ __device__ inline void tc_choose_chunks(int64_t n, int32_t s, int32_t grid, int32_t* C,
                                                  int32_t* Lc) {
@@ -179,8 +180,8 @@ __host__ __device__ inline void tc_choose_chunks(int64_t n, int32_t s, int32_t g
   const int64_t G = (s + kTcTile - 1) / kTcTile;
   const int64_t P = grid > 0 ? grid : 1;
   int64_t best_tpc = nt, best_num = -1, best_den = 1, best_c = 1;
-  for (int k = 1; k <= 4; ++k) {
-    int64_t c = (k * P) / G;
+  for (int cand = 0; cand < 8; ++cand) {
+    int64_t c = cand < 4 ? cand + 1 : ((cand - 3) * P) / G;
     if (c < 1) c = 1;
     int64_t tpc = (nt + c - 1) / c;
     if (tpc < kTcMinTiles) tpc = kTcMinTiles < nt ? kTcMinTiles : nt;

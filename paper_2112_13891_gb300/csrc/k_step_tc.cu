@@ -1,4 +1,4 @@
-// ms_step on the 5th-generation tensor cores (tcgen05), for 9 <= d <= 32.
+// ms_step on the 5th-generation tensor cores (tcgen05), for 1 <= d <= 32.
 //
 // For a tile of 128 seeds (rows) and a tile of 128 points, in scaled
 // coordinates (w = exp2(-||y - x||^2)):
@@ -7,20 +7,28 @@
 //                       S ~= Yh Xh^T + Yh Xl^T + Yl Xh^T (three MMAs per K
 //                       step), which keeps the cancellation in
 //                       ||y||^2 + ||x||^2 - 2 y.x at ~2^-16 relative.
-//   w = exp2(2S - ||y||^2 - ||x||^2)   epilogue: TMEM -> registers (one seed
-//                       row per thread), FP32 norms, MUFU.EX2, BF16 P -> smem.
-//   [W, sum w x] = P [1 | Xh | Xl]     a second MMA, accumulated in TMEM over
-//                       the point tiles of the chunk.
+//                       A fourth K block adds -||x||^2 / 2 to S: the tile
+//                       carries it as three BF16 pieces (e0 + e1 + e2, 24
+//                       significant bits) that meet a constant [0 1 1 1 0..]
+//                       block of Y, so D = y.x - ||x||^2 / 2 in FP32.
+//   w = exp2(2D - ||y||^2)   epilogue: TMEM -> registers, one FFMA with the
+//                       seed's FP32 norm, MUFU.EX2, BF16 weights P -> smem.
+//   [sum w x_hi | sum w x_lo | sum w] = P [Xh | Xl | 1]   second product, the
+//                       point tile read as an MN-major B operand; accumulated
+//                       in TMEM over the point tiles of the chunk.
 // The chunk's partials are written as (W, sum w (x - y)) -- the layout of the
 // FP32 kernels -- so the same update kernel consumes them.  This is the
 // coarse ("precision") step: weights carry BF16 rounding (2^-9 relative), so
 // seeds switch to the exact FP32 step before their convergence is decided.
 //
 // Point tiles come from a packed image per 128 points (built once per call):
-//   [Xh | Xl]  B operand of the first MMA (128 rows x DPAD, K-major core
-//              matrices, no swizzle); [XT] B operand of the second MMA
-//   (N2 = 1 + 2 DPAD padded to 16 rows x 128 points); [nx] 128 FP32 norms
-//   (+inf for padding points, so their weight is exactly 0).
+//   X2 = [Xh | Xl | 1 e0 e1 e2 0 .. 0]  128 points x N2 (N2 = 2 DPAD + 16)
+//              BF16, in core matrices of 8 points x 8 columns (16 B rows, no
+//              swizzle); e0 + e1 + e2 = -||x||^2 / 2 (e0 = -inf, e1 = e2 = 0 for
+//              padding points, so their weight is exactly 0).  Its Xh, Xl and
+//              last column ranges are K-major B operands of the first product;
+//              the whole of it is the MN-major B of the second (whose columns
+//              2 DPAD + 1 .. are never read).
 // One TMA bulk copy (cp.async.bulk) per tile; every wait is bounded and sets
 // an error bit instead of hanging.
 #include <cuda_bf16.h>
@@ -33,22 +41,26 @@ namespace tc {
 
 constexpr int kM = 128;       // seeds per tile (MMA M)
 constexpr int kP = 128;       // points per tile (MMA N of the first product, K of the second)
-constexpr int kThreads = 128; // one warpgroup: thread r owns seed row r in the epilogue
+constexpr int kEpiWarps = 16;  // epilogue warps: (TMEM lane quarter) x (column quarter)
+constexpr int kThreads = (kEpiWarps + 2) * 32;  // + loader / S-issuer warp + P-issuer warp
 constexpr long kSpin = 1l << 24;
 
 template <int DPAD>
 struct Geo {
-  static constexpr int N2 = ((1 + 2 * DPAD) + 15) / 16 * 16;
-  static constexpr int kXBytes = kP * DPAD * 2;          // one of Xh / Xl
-  static constexpr int kXTBytes = N2 * kP * 2;
-  static constexpr int kTileBytes = 2 * kXBytes + kXTBytes + kP * 4;
+  static constexpr int N2 = 2 * DPAD + 16;               // [Xh | Xl | 1 e0 e1 e2 0 ..]
+  static constexpr int kX2Bytes = kP * N2 * 2;
+  static constexpr int kTileBytes = kX2Bytes;
+  static constexpr int kYextBytes = kM * 16 * 2;        // constant [0 1 1 1 0 ..] rows
   static constexpr int kYBytes = kM * DPAD * 2;          // one of Yh / Yl
   static constexpr int kPBytes = kM * kP * 2;
-  // smem: Yh, Yl, tile image, P; requested as at least 80 KB so that no more
-  // than two CTAs (2 x 256 TMEM columns) share an SM
-  static constexpr int kSmemUsed = 2 * kYBytes + kTileBytes + kPBytes;
-  static constexpr int kSmem = kSmemUsed > 80 * 1024 ? kSmemUsed : 80 * 1024;
-  static constexpr int kTmemCols = 256;                  // D1 (128) + D2 (<= 80)
+  static constexpr int kStages = 6;                      // tile ring
+  // smem: Yh, Yl, Yext, P x 2, ring of kStages tile images (200 KB for DPAD = 32)
+  static constexpr int kSmem = 2 * kYBytes + kYextBytes + 2 * kPBytes + kStages * kTileBytes;
+  // TMEM: S accumulators D1 x 3 (3 x 128 columns), D2 = [hi sums | lo sums | W]
+  static constexpr int kD2 = 3 * 128;
+  static constexpr int kTmemCols = 512;
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+  static_assert(kD2 + N2 <= kTmemCols, "tensor memory");
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -99,6 +111,37 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {
   return false;
 }
 
+// bounded wait that also gives up when another role has set the abort flag.
+// The single-thread issuers poll with the non-suspending test_wait (their
+// hand-offs are on the critical path); the epilogue warps use try_wait, which
+// may suspend the warp and leaves its issue slots to the other warps.
+template <bool kPoll>
+__device__ __forceinline__ bool wait_bar_abort(uint64_t* bar, uint32_t phase,
+                                               volatile int* abort_flag) {
+  for (long it = 0; it < kSpin; ++it) {
+    uint32_t ok;
+    if (kPoll)
+      asm volatile(
+          "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(ok)
+          : "r"(su32(bar)), "r"(phase)
+          : "memory");
+    else
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(ok)
+          : "r"(su32(bar)), "r"(phase)
+          : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -120,6 +163,29 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.ld of 16 columns without waiting; the registers are valid only after
+// wait_ld16 on the same array (which names them as read-write operands, so no
+// use can be scheduled before the wait)
+__device__ __forceinline__ void ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void wait_ld16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
@@ -150,57 +216,86 @@ __global__ void tc_pack_tiles(const float* __restrict__ Xs, int n, int DP,
   using G = tc::Geo<DPAD>;
   const int t = blockIdx.x;
   unsigned char* base = img + (size_t)t * G::kTileBytes;
-  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(base);
-  __nv_bfloat16* xl = reinterpret_cast<__nv_bfloat16*>(base + G::kXBytes);
-  __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(base + 2 * G::kXBytes);
-  float* nx = reinterpret_cast<float*>(base + 2 * G::kXBytes + G::kXTBytes);
+  __nv_bfloat16* x2 = reinterpret_cast<__nv_bfloat16*>(base);
   for (int e = threadIdx.x; e < tc::kP * DPAD; e += blockDim.x) {
     const int p = e / DPAD, k = e % DPAD;
     const int j = t * tc::kP + p;
     const float v = (j < n && k < DP) ? Xs[(size_t)j * DP + k] : 0.f;
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    xh[tc::core_index(p, k, DPAD)] = hi;
-    xl[tc::core_index(p, k, DPAD)] = lo;
-    // XT rows: 0 = ones, 1..DPAD = hi, DPAD+1..2DPAD = lo, rest zero
-    xt[tc::core_index(1 + k, p, tc::kP)] = hi;
-    xt[tc::core_index(1 + DPAD + k, p, tc::kP)] = lo;
+    x2[tc::core_index(p, k, G::N2)] = hi;
+    x2[tc::core_index(p, DPAD + k, G::N2)] = lo;
   }
   for (int e = threadIdx.x; e < tc::kP; e += blockDim.x) {
     const int j = t * tc::kP + e;
-    xt[tc::core_index(0, e, tc::kP)] = __float2bfloat16_rn(j < n ? 1.f : 0.f);
-    for (int r = 1 + 2 * DPAD; r < G::N2; ++r) xt[tc::core_index(r, e, tc::kP)] = __float2bfloat16_rn(0.f);
-    float s = INFINITY;
+    // e0 + e1 + e2 = -||x||^2 / 2 (FP32 norm, split into three BF16 pieces)
+    float e0 = -INFINITY, e1 = 0.f, e2 = 0.f;
     if (j < n) {
-      s = 0.f;
+      float s = 0.f;
       for (int k = 0; k < DP; ++k) {
         const float v = Xs[(size_t)j * DP + k];
         s = fmaf(v, v, s);
       }
+      const float h = -0.5f * s;
+      e0 = __bfloat162float(__float2bfloat16_rn(h));
+      e1 = __bfloat162float(__float2bfloat16_rn(h - e0));
+      e2 = h - e0 - e1;
     }
-    nx[e] = s;
+    for (int k = 0; k < 16; ++k) {
+      const float v = k == 0 ? 1.f : k == 1 ? e0 : k == 2 ? e1 : k == 3 ? e2 : 0.f;
+      x2[tc::core_index(e, 2 * DPAD + k, G::N2)] = __float2bfloat16_rn(v);
+    }
   }
 }
 
 // The coarse step for active positions [0, count) of a list of s_total;
-// chunks of Lc points (a multiple of 128); grid-stride over (seed tile,
-// chunk) tasks.  Partial (c, p): part[(c * s_total + p) * DA + k], k <= DP.
+// chunks of Lc points (a multiple of 128).  A persistent grid (one CTA per SM
+// holding all 512 TMEM columns) walks (seed tile, chunk) tasks.
+// Partial (c, p): part[(c * s_total + p) * DA + k], k <= DP.
+//
+// Warp roles (warp-specialised, no CTA-wide barrier inside a task).  One
+// thread issues at most one tcgen05.mma per ~70-90 clocks, so the MMAs of a
+// tile are split between two issuing threads:
+//   warp 16, lane 0 (loader): bulk copies up to kStages tiles ahead into a
+//       ring of tile buffers (a buffer is refilled once P(j) has read it), and
+//       S(j+2) = Y X(j+2)^T into the one of three TMEM accumulators that the
+//       epilogue of tile j-1 released.
+//   warp 17, lane 0 (P issuer): P(j) = P_j [Xh | Xl | 1] into D2 as soon as
+//       the epilogue of tile j has signalled.
+//   warps 0..15 (epilogue): for tile j, warp w takes TMEM lanes 32 (w % 4) ..
+//       +31 (seed rows) and columns 32 (w / 4) .. +31 (points): w = exp2(2S -
+//       ny - nx), rounded to BF16 into P buffer j % 2 (two buffers, so the
+//       epilogue of tile j+1 overlaps the product of tile j).
+// mbarriers (tile / product numbers are counted across the CTA's tasks):
+// bar_load[b] (copy landed), bar_s[j % 3] (S(j) done), bar_o[j % 3] (P(j)
+// done: its P buffer and tile buffer are free, D2 final), bar_p[j % 3] (the
+// epilogue warps wrote P of tile j and read its S accumulator; waited by both
+// issuers), bar_y (the epilogue warps wrote the Y tile of a non-empty task and
+// read the previous task's D2).  The loader waits for P(j-1) before it issues
+// S(j+2), so no role can run two phases ahead of a waiter.  Every wait is for
+// the current or the just-completed phase of its barrier (checked with a
+// model of the three roles over random interleavings) and bounded; a wait
+// that gives up sets kStTimeout and a shared abort flag that ends every
+// role's loop.
 template <int DPAD>
-__global__ void __launch_bounds__(tc::kThreads)
+__global__ void __launch_bounds__(tc::kThreads, 1)
     ms_step_tc(const unsigned char* __restrict__ img, int n, const float* __restrict__ y, int DP,
                int DA, const int32_t* __restrict__ active, const int32_t* __restrict__ s_total_ptr,
                const int32_t* __restrict__ count_ptr, const int32_t* __restrict__ C_ptr,
                const int32_t* __restrict__ Lc_ptr, float* __restrict__ part, uint32_t* status,
                int32_t* __restrict__ s_log) {
   using G = tc::Geo<DPAD>;
+  constexpr int S = G::kStages;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ __align__(8) uint64_t bar_load[S], bar_s[3], bar_o[3], bar_p[3], bar_y;
   __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
   unsigned char* sYh = smem;
   unsigned char* sYl = smem + G::kYBytes;
-  unsigned char* sT = smem + 2 * G::kYBytes;
-  unsigned char* sP = sT + G::kTileBytes;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* sYext = smem + 2 * G::kYBytes;
+  unsigned char* sP = sYext + G::kYextBytes;             // P[0], P[1]
+  unsigned char* sRing = sP + 2 * G::kPBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s_total = *s_total_ptr;
   const int count = *count_ptr;  // coarse seeds: positions [0, count)
   const int C = *C_ptr, Lc = *Lc_ptr;
@@ -214,12 +309,30 @@ __global__ void __launch_bounds__(tc::kThreads)
   const long T = (long)ntile_seed * C;
   if ((long)blockIdx.x >= T) return;
 
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar_load)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar_mma)));
+  constexpr int kCtl = tc::kEpiWarps;  // the loader warp; kCtl + 1: the P-issuer warp
+  if (tid == kCtl * 32) {
+    for (int i = 0; i < S; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar_load[i])));
+    for (int i = 0; i < 3; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar_s[i])));
+    for (int i = 0; i < 3; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar_o[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::su32(&bar_p[i])),
+                   "r"(tc::kEpiWarps));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::su32(&bar_y)),
+                 "r"(tc::kEpiWarps));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
-  if (warp == 0) {
+  // constant Y extension rows [0 1 1 1 0 .. 0] (K-major core matrices of 16 columns)
+  for (int e = tid; e < tc::kM * 16; e += blockDim.x) {
+    const int row = e >> 4, k = e & 15;
+    reinterpret_cast<__nv_bfloat16*>(sYext)[tc::core_index(row, k, 16)] =
+        __float2bfloat16_rn((k >= 1 && k <= 3) ? 1.f : 0.f);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == kCtl) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      tc::su32(&tmem_base)),
                  "r"(G::kTmemCols)
@@ -230,161 +343,273 @@ __global__ void __launch_bounds__(tc::kThreads)
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t tD1 = tmem, tD2 = tmem + 128;
-  const uint32_t id1 = tc::idesc_bf16(tc::kM, tc::kP), id2 = tc::idesc_bf16(tc::kM, G::N2);
-  uint32_t ph_load = 0, ph_mma = 0;
-  bool bad = false;
+  const uint32_t tD2 = tmem + G::kD2;                  // D1[i] = tmem + 128 i, i < 3
   const int tiles_per_chunk = Lc / tc::kP;
   const int ntiles_total = (n + tc::kP - 1) / tc::kP;
-
-  for (long task = blockIdx.x; task < T; task += gridDim.x) {
-    const int st = (int)(task % ntile_seed);
-    const int c = (int)(task / ntile_seed);
-    // this thread's seed row
-    const int prow = st * tc::kM + tid;
-    const bool valid = prow < count;
-    const int64_t slot = __ldg(active + (valid ? prow : count - 1));
-    float yv[DPAD];
-    float ny = 0.f;
-#pragma unroll
-    for (int k = 0; k < DPAD; ++k) {
-      yv[k] = k < DP ? __ldg(y + slot * DP + k) : 0.f;
-      ny = fmaf(yv[k], yv[k], ny);
+  bool bad = false;
+  const bool issuer = warp >= kCtl;
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (!(issuer ? tc::wait_bar_abort<true>(bar, parity, &s_abort)
+                 : tc::wait_bar_abort<false>(bar, parity, &s_abort))) {
+      bad = true;
+      s_abort = 1;
+      return false;
     }
-    if (!valid) ny = INFINITY;
-    // Y tile (hi / lo, K-major core matrices), 8 k per 16-byte store
-#pragma unroll
-    for (int k0 = 0; k0 < DPAD; k0 += 8) {
-      uint32_t h4[4], l4[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float a = yv[k0 + 2 * q], b = yv[k0 + 2 * q + 1];
-        const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
-        h4[q] = tc::pack_bf16(__bfloat162float(ah), __bfloat162float(bh));
-        l4[q] = tc::pack_bf16(a - __bfloat162float(ah), b - __bfloat162float(bh));
-      }
-      const int off = tc::core_index(tid, k0, DPAD) * 2;
-      *reinterpret_cast<uint4*>(sYh + off) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
-      *reinterpret_cast<uint4*>(sYl + off) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
+    return true;
+  };
 
-    const int t0 = c * tiles_per_chunk;
-    const int t1 = min(ntiles_total, t0 + tiles_per_chunk);
-    for (int t = t0; t < t1; ++t) {
-      // tile image -> smem (TMA bulk copy)
-      if (tid == 0) {
+  if (warp == kCtl) {
+    if (lane == 0) {
+      // ------------------------------ loader ------------------------------
+      const uint32_t id1 = tc::idesc_bf16(tc::kM, tc::kP);
+      const uint32_t x_row = (G::N2 / 8) * 128;        // X2: next 8-point block
+      uint32_t n_load = 0, n_lw = 0, n_s = 0, n_task = 0;
+      auto issue_load = [&](int t) {
+        const uint32_t b = n_load % S;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                         tc::su32(&bar_load)),
+                         tc::su32(&bar_load[b])),
                      "r"((uint32_t)G::kTileBytes)
                      : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc::su32(sT)),
+                tc::su32(sRing + b * G::kTileBytes)),
             "l"(img + (size_t)t * G::kTileBytes), "r"((uint32_t)G::kTileBytes),
-            "r"(tc::su32(&bar_load))
+            "r"(tc::su32(&bar_load[b]))
             : "memory");
-      }
-      if (!tc::wait_bar(&bar_load, ph_load)) bad = true;
-      ph_load ^= 1u;
-      // S = Yh Xh^T + Yh Xl^T + Yl Xh^T
-      if (tid == 0) {
-        tc::fence_after();
+        ++n_load;
+      };
+      // S = Yh Xh^T + Yh Xl^T + Yl Xh^T for the tile in ring buffer `buf`
+      auto issue_s = [&](uint32_t buf) {
+        const unsigned char* sT = sRing + buf * G::kTileBytes;
+        const uint32_t dt = tmem + (n_s % 3u) * 128u;
         const uint32_t sbo = (DPAD / 8) * 128;
+#pragma unroll
         for (int ks = 0; ks < DPAD / 16; ++ks) {
           const uint64_t ah = tc::sdesc(tc::su32(sYh) + ks * 256, 128, sbo);
           const uint64_t al = tc::sdesc(tc::su32(sYl) + ks * 256, 128, sbo);
-          const uint64_t bh = tc::sdesc(tc::su32(sT) + ks * 256, 128, sbo);
-          const uint64_t bl = tc::sdesc(tc::su32(sT + G::kXBytes) + ks * 256, 128, sbo);
-          tc::mma(tD1, ah, bh, id1, ks > 0 ? 1u : 0u);
-          tc::mma(tD1, ah, bl, id1, 1u);
-          tc::mma(tD1, al, bh, id1, 1u);
+          const uint64_t bh = tc::sdesc(tc::su32(sT) + ks * 256, 128, x_row);
+          const uint64_t bl = tc::sdesc(tc::su32(sT) + (DPAD / 8) * 128 + ks * 256, 128, x_row);
+          tc::mma(dt, ah, bh, id1, ks > 0 ? 1u : 0u);
+          tc::mma(dt, ah, bl, id1, 1u);
+          tc::mma(dt, al, bh, id1, 1u);
         }
-        tc::commit(&bar_mma);
-      }
-      if (!tc::wait_bar(&bar_mma, ph_mma)) bad = true;
-      ph_mma ^= 1u;
-      tc::fence_after();
-      // epilogue: w = exp2(2 S - ny - nx) -> BF16 P[row][point]
-      const float* nx = reinterpret_cast<const float*>(sT + 2 * G::kXBytes + G::kXTBytes);
-#pragma unroll 1
-      for (int c0 = 0; c0 < tc::kP; c0 += 32) {
-        float sv[32];
-        tc::ld32(tD1 + ((uint32_t)(warp * 32) << 16) + c0, sv);
-#pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += 8) {
-          uint32_t p4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = j0 + 2 * q;
-            const float u0 = fmaf(2.f, sv[j], -(ny + nx[c0 + j]));
-            const float u1 = fmaf(2.f, sv[j + 1], -(ny + nx[c0 + j + 1]));
-            p4[q] = tc::pack_bf16(ex2_ftz(u0), ex2_ftz(u1));
+        // + [0 1 1 1 0 ..] . [1 e0 e1 e2 0 ..] = -||x||^2 / 2
+        tc::mma(dt, tc::sdesc(tc::su32(sYext), 128, 256),
+                tc::sdesc(tc::su32(sT) + (2 * DPAD / 8) * 128, 128, x_row), id1, 1u);
+        tc::commit(&bar_s[n_s % 3u]);
+        ++n_s;
+      };
+      auto wait_load = [&](uint32_t L) -> bool {
+        const bool ok = wait(&bar_load[L % S], (L / S) & 1u);
+        ++n_lw;
+        return ok;
+      };
+      uint32_t g0 = 0;                                 // global number of the task's tile 0
+      for (long task = blockIdx.x; task < T && !s_abort; task += gridDim.x) {
+        const int c = (int)(task / ntile_seed);
+        const int t0 = c * tiles_per_chunk;
+        const int nt = max(0, min(ntiles_total, t0 + tiles_per_chunk) - t0);
+        if (nt == 0) continue;                         // (no handshake for an empty task)
+        if (!wait(&bar_y, n_task & 1u)) break;         // Y tile written, last D2 read
+        ++n_task;
+        tc::fence_after();
+        const uint32_t base = n_load;                  // load number of tile 0 (== g0)
+        for (int i = 0; i < nt && i < S; ++i) issue_load(t0 + i);
+        if (!wait_load(base)) break;
+        issue_s(base % S);
+        if (nt > 1) {
+          if (!wait_load(base + 1)) break;
+          issue_s((base + 1) % S);
+        }
+        for (int j = 0; j < nt; ++j) {
+          const uint32_t g = g0 + (uint32_t)j;
+          if (j >= 1 && j - 1 + S < nt) {              // refill the buffer of tile j-1
+            if (!wait(&bar_o[(g - 1) % 3u], ((g - 1) / 3u) & 1u)) break;  // P(j-1) read it
+            issue_load(t0 + j - 1 + S);
           }
-          const int off = tc::core_index(tid, c0 + j0, tc::kP) * 2;
-          *reinterpret_cast<uint4*>(sP + off) = make_uint4(p4[0], p4[1], p4[2], p4[3]);
+          if (j + 2 < nt) {                            // S(j+2) into the accumulator
+            if (j >= 1 && !wait(&bar_p[(g - 1) % 3u], ((g - 1) / 3u) & 1u)) break;
+            tc::fence_after();                         // that tile j-1 released
+            if (!wait_load(base + j + 2)) break;
+            issue_s((base + j + 2) % S);
+          }
+        }
+        g0 += (uint32_t)nt;
+      }
+      if (bad || s_abort) {
+        // one more bounded wait for every copy and product still in flight,
+        // before the shared memory and the accumulators are released
+        for (uint32_t L = n_lw; L < n_load; ++L) tc::wait_bar(&bar_load[L % S], (L / S) & 1u);
+        if (n_s > 0) tc::wait_bar(&bar_s[(n_s - 1) % 3u], ((n_s - 1) / 3u) & 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kCtl + 1) {
+    if (lane == 0) {
+      // ---------------------------- P issuer -----------------------------
+      const uint32_t id2 = tc::idesc_bf16(tc::kM, G::N2) | (1u << 16);  // B MN-major
+      const uint32_t x_row = (G::N2 / 8) * 128;
+      const uint32_t a_sbo = (tc::kP / 8) * 128;
+      uint32_t n_o = 0;
+      for (long task = blockIdx.x; task < T && !s_abort; task += gridDim.x) {
+        const int c = (int)(task / ntile_seed);
+        const int t0 = c * tiles_per_chunk;
+        const int nt = max(0, min(ntiles_total, t0 + tiles_per_chunk) - t0);
+        for (int j = 0; j < nt; ++j) {
+          if (!wait(&bar_p[n_o % 3u], (n_o / 3u) & 1u)) break;  // epilogue of tile j done
+          tc::fence_after();
+          const unsigned char* sT = sRing + (n_o % S) * G::kTileBytes;
+          const unsigned char* sPj = sP + (n_o & 1u) * G::kPBytes;
+#pragma unroll
+          for (int ks = 0; ks < tc::kP / 16; ++ks) {
+            // MN-major B: LBO = next 8 points (K), SBO = next 8 columns (N)
+            const uint64_t a = tc::sdesc(tc::su32(sPj) + ks * 256, 128, a_sbo);
+            const uint64_t b = tc::sdesc(tc::su32(sT) + ks * 2 * x_row, x_row, 128);
+            tc::mma(tD2, a, b, id2, (j > 0 || ks > 0) ? 1u : 0u);
+          }
+          tc::commit(&bar_o[n_o % 3u]);
+          ++n_o;
         }
       }
+      if (bad || s_abort) {
+        if (n_o > 0) tc::wait_bar(&bar_o[(n_o - 1) % 3u], ((n_o - 1) / 3u) & 1u);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int q = warp & 3, cq = warp >> 2;
+    const int r_row = q * 32 + lane;                   // this thread's seed row
+    const int c0 = cq * 32;                            // this warp's point columns
+    const uint32_t row_lane = (uint32_t)(q * 32) << 16;
+    uint32_t n_s = 0, n_o = 0, n_t = 0;   // S products consumed, P products, tiles
+    for (long task = blockIdx.x; task < T && !s_abort; task += gridDim.x) {
+      const int st = (int)(task % ntile_seed);
+      const int c = (int)(task / ntile_seed);
+      const int t0 = c * tiles_per_chunk;
+      const int nt = max(0, min(ntiles_total, t0 + tiles_per_chunk) - t0);
+      const int prow = st * tc::kM + r_row;
+      const bool valid = prow < count;
+      if (nt == 0) {                                   // (no handshake for an empty task)
+        if (cq == 0 && valid) {
+          float* o = part + ((int64_t)c * s_total + prow) * DA;
+          for (int k = 0; k <= DP; ++k) o[k] = 0.f;
+        }
+        continue;
+      }
+      const int64_t slot = __ldg(active + (valid ? prow : count - 1));
+      const float* yrow = y + slot * DP;
+      float ny = 0.f;
+      // Y tile (hi / lo, K-major core matrices): warp column quarter cq writes
+      // the 8-wide k chunks k0 with k0 / 8 == cq (mod 4)
+#pragma unroll
+      for (int k0 = 0; k0 < DPAD; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          v[e] = k0 + e < DP ? __ldg(yrow + k0 + e) : 0.f;
+          ny = fmaf(v[e], v[e], ny);
+        }
+        if (((k0 >> 3) & 3) != cq) continue;
+        uint32_t h4[4], l4[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const float a = v[2 * qq], b = v[2 * qq + 1];
+          const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+          h4[qq] = tc::pack_bf16(__bfloat162float(ah), __bfloat162float(bh));
+          l4[qq] = tc::pack_bf16(a - __bfloat162float(ah), b - __bfloat162float(bh));
+        }
+        const int off = tc::core_index(r_row, k0, DPAD) * 2;
+        *reinterpret_cast<uint4*>(sYh + off) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<uint4*>(sYl + off) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+      }
+      if (!valid) ny = INFINITY;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::fence_before();
-      const int abort_now = __syncthreads_or(bad ? 1 : 0);
-      tc::fence_after();
-      if (abort_now) break;  // uniform: a bounded wait gave up somewhere in the CTA
-      // [W, sum w x] += P [1 | Xh | Xl]
-      if (tid == 0) {
-        const uint32_t sbo = (tc::kP / 8) * 128;
-        for (int ks = 0; ks < tc::kP / 16; ++ks) {
-          const uint64_t a = tc::sdesc(tc::su32(sP) + ks * 256, 128, sbo);
-          const uint64_t b = tc::sdesc(tc::su32(sT + 2 * G::kXBytes) + ks * 256, 128, sbo);
-          tc::mma(tD2, a, b, id2, (t > t0 || ks > 0) ? 1u : 0u);
+      __syncwarp();
+      if (lane == 0) tc::arrive(&bar_y);
+      // software pipeline over 16-column halves: the TMEM load of the next half
+      // (of this tile, or of tile j+1) is in flight while a half is computed
+      // w = exp2(2 D - ||y||^2), D = y.x - ||x||^2 / 2 from the S accumulator
+      auto compute_half = [&](int h, const uint32_t (&rr)[16], uint32_t* pk) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float u0 = fmaf(2.f, __uint_as_float(rr[2 * i]), -ny);
+          const float u1 = fmaf(2.f, __uint_as_float(rr[2 * i + 1]), -ny);
+          pk[8 * h + i] = tc::pack_bf16(ex2_ftz(u0), ex2_ftz(u1));
         }
-        tc::commit(&bar_mma);
+      };
+      uint32_t ra[16], rb[16];
+      bool ok = wait(&bar_s[n_s % 3u], (n_s / 3u) & 1u);
+      uint32_t d1 = tmem + (n_s % 3u) * 128u + row_lane + c0;
+      if (ok) {
+        tc::fence_after();
+        tc::ld16_issue(d1, ra);
       }
-      if (!tc::wait_bar(&bar_mma, ph_mma)) bad = true;
-      ph_mma ^= 1u;
-      tc::fence_after();
+      for (int j = 0; ok && j < nt; ++j) {
+        uint32_t pk[16];
+        tc::wait_ld16(ra);
+        tc::ld16_issue(d1 + 16, rb);
+        compute_half(0, ra, pk);
+        tc::wait_ld16(rb);
+        ++n_s;                                           // tile j's accumulator read
+        if (j + 1 < nt) {
+          if (!(ok = wait(&bar_s[n_s % 3u], (n_s / 3u) & 1u))) break;
+          tc::fence_after();
+          d1 = tmem + (n_s % 3u) * 128u + row_lane + c0;
+          tc::ld16_issue(d1, ra);
+        }
+        compute_half(1, rb, pk);
+        tc::fence_before();                              // S accumulator reads done
+        // P buffer n_o & 1 was last read by product n_o - 2
+        if (n_o >= 2 && !(ok = wait(&bar_o[(n_o - 2) % 3u], ((n_o - 2) / 3u) & 1u))) break;
+        unsigned char* sPj = sP + (n_o & 1u) * G::kPBytes;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int off = tc::core_index(r_row, c0 + 8 * i, tc::kP) * 2;
+          *reinterpret_cast<uint4*>(sPj + off) =
+              make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc::arrive(&bar_p[n_o % 3u]);
+        ++n_o;                                           // P(j) follows
+      }
+      if (!ok) {
+        tc::wait_ld16(ra);                               // no load left in flight
+        tc::wait_ld16(rb);
+      }
+      n_t += (uint32_t)nt;
+      if (s_abort) break;
+      // partials of this (seed tile, chunk): W and sum w (x - y)
+      {
+        if (!wait(&bar_o[(n_o - 1) % 3u], ((n_o - 1) / 3u) & 1u)) break;  // last P product
+        tc::fence_after();
+        if (cq == 0) {
+          // D2 columns: [0, DPAD) sum w x_hi, [DPAD, 2 DPAD) sum w x_lo, 2 DPAD: sum w
+          float vh[16], vl[16];
+          tc::ld16(tD2 + row_lane + 2 * DPAD, vh);
+          const float W = vh[0];
+          float* o = part + ((int64_t)c * s_total + prow) * DA;
+          if (valid) o[0] = W;
+#pragma unroll
+          for (int k0 = 0; k0 < DPAD; k0 += 16) {
+            tc::ld16(tD2 + row_lane + k0, vh);
+            tc::ld16(tD2 + row_lane + DPAD + k0, vl);
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (valid && k0 + e < DP)
+                o[1 + k0 + e] = (vh[e] + vl[e]) - __ldg(yrow + k0 + e) * W;
+          }
+        }
+        tc::fence_before();                              // D2 reads done (next bar_y)
+      }
     }
-    // partials of this (seed tile, chunk): W and sum w (x - y)
-    if (__syncthreads_or(bad ? 1 : 0)) break;
-    if (t1 > t0) {
-      float acc[G::N2];
-#pragma unroll
-      for (int c0 = 0; c0 < G::N2; c0 += 16) {
-        float v[16];
-        tc::ld16(tD2 + ((uint32_t)(warp * 32) << 16) + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] = v[i];
-      }
-      if (valid) {
-        float* o = part + ((int64_t)c * s_total + prow) * DA;
-        const float W = acc[0];
-        o[0] = W;
-#pragma unroll
-        for (int k = 0; k < DPAD; ++k)
-          if (k < DP) o[1 + k] = (acc[1 + k] + acc[1 + DPAD + k]) - yv[k] * W;
-      }
-    } else if (valid) {
-      float* o = part + ((int64_t)c * s_total + prow) * DA;
-      for (int k = 0; k <= DP; ++k) o[k] = 0.f;
-    }
-    tc::fence_before();
-    const int abort_task = __syncthreads_or(bad ? 1 : 0);
-    tc::fence_after();
-    if (abort_task) break;
   }
-  if (bad) {
-    atomicOr(status, kStTimeout);
-    // give the operations that did not signal one more bounded wait before
-    // the accumulators are released
-    tc::wait_bar(&bar_load, ph_load ^ 1u);
-    tc::wait_bar(&bar_mma, ph_mma ^ 1u);
-  }
+  if (bad) atomicOr(status, kStTimeout);
   tc::fence_before();
   __syncthreads();
-  if (warp == 0)
+  if (warp == kCtl)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(G::kTmemCols)
                  : "memory");
@@ -403,28 +628,24 @@ cudaError_t launch_tc_pack(const float* Xs, int64_t n, int d, int DP, unsigned c
   return cudaGetLastError();
 }
 
+// One persistent CTA per SM: each holds all 512 TMEM columns.
 int tc_grid(int d) {
   static int cache[2] = {0, 0};
   const int i = d <= 16 ? 0 : 1;
   if (cache[i]) return cache[i];
-  int dev = 0, sms = 0, blocks = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (i == 0) {
-    cudaFuncSetAttribute(ms_step_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         tc::Geo<16>::kSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_tc<16>, tc::kThreads,
-                                                  tc::Geo<16>::kSmem);
-  } else {
-    cudaFuncSetAttribute(ms_step_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         tc::Geo<32>::kSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_tc<32>, tc::kThreads,
-                                                  tc::Geo<32>::kSmem);
-  }
-  // at most two CTAs per SM: each holds 256 of the SM's 512 TMEM columns
-  if (blocks > 2) blocks = 2;
-  if (blocks < 1) blocks = 1;
-  cache[i] = sms * blocks;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return 1;
+  cudaError_t e;
+  if (i == 0)
+    e = cudaFuncSetAttribute(ms_step_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::Geo<16>::kSmem);
+  else
+    e = cudaFuncSetAttribute(ms_step_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::Geo<32>::kSmem);
+  if (e != cudaSuccess) return sms;
+  cache[i] = sms;
   return cache[i];
 }
 

@@ -290,8 +290,10 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     const double r_merge = o.merge_radius > 0.0f ? (double)o.merge_radius : (double)h;
     const double r2_s = (r_merge * scale) * (r_merge * scale);
     const bool allow_doubling = !o.all_seeds && !o.seed_indices;
+    // one block per seed (many chunks) or one warp per seed: enough blocks for
+    // either, at most 8 per SM
     auto update_grid = [&](int64_t m) -> int {
-      int64_t g = (m + 7) / 8;
+      int64_t g = m;
       if (g > (int64_t)dv.sms * 8) g = (int64_t)dv.sms * 8;
       return g < 1 ? 1 : (int)g;
     };

@@ -72,7 +72,8 @@ cudaError_t launch_batched_canonical(const SetCtl* sc, int B, const double* ym,
 cudaError_t launch_batched_label(const float* X, const int64_t* pt_off, int B, int d,
                                  const SetCtl* sc, const float* modes_full, int32_t* labels,
                                  float* margins, int64_t total, cudaStream_t st);
-size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P);
+size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P,
+                          int* with_pos);
 }  // namespace fms
 
 using namespace fms;
@@ -393,7 +394,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
       BL(launch_batched_score(part, sc, B, list_off, part_off, totals, DA, score, grid_upd, st));
       {
       int P = 1;
-      if (batched_prune_smem(maxN, d, 4, 4, &P) > 200 * 1024) {
+      if (batched_prune_smem(maxN, d, 4, 4, &P, nullptr) > kBatchedPruneSmem) {
         rc = FMS_ERR_UNSUPPORTED;  // a set's seed count exceeds the on-chip prune
         goto done;
       }
@@ -457,7 +458,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
     for (int b = 0; b < B; ++b) maxM = hsc[b].M > maxM ? hsc[b].M : maxM;
     {
       int P = 1;
-      if (batched_prune_smem(maxM > 0 ? maxM : 1, d, 8, 8, &P) > 200 * 1024) {
+      if (batched_prune_smem(maxM > 0 ? maxM : 1, d, 8, 8, &P, nullptr) > kBatchedPruneSmem) {
         rc = FMS_ERR_UNSUPPORTED;
         goto done;
       }

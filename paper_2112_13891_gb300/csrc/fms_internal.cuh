@@ -73,6 +73,10 @@ struct MergeCtl {
   int64_t evals;          // evaluations of prune scores and refinement
 };
 
+// Chunk count from which the cross-chunk reductions use a whole block (8
+// warps) per seed instead of one warp.
+constexpr int kBlockReduceChunks = 64;
+
 // Smallest point chunk of a warp task (points): below this the per-task work
 // (seed loads, the warp reduction and one store) stops being small next to
 // the evaluations.
@@ -83,6 +87,9 @@ constexpr int kStepMinChunk = 512;
 constexpr int kClusterCtas = 8;
 constexpr int kSeedsPerCluster = 64;
 constexpr int kModesPerCluster = 32;   // refinement: modes one cluster owns
+
+// Shared memory budget of the batched per-set prune (k_batched.cu).
+constexpr size_t kBatchedPruneSmem = 200 * 1024;
 
 // Per-set control block of the batched path (k_batched.cu).
 struct SetCtl {

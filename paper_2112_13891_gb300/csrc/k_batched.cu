@@ -501,7 +501,7 @@ template <typename PT, typename ST>
 __global__ void __launch_bounds__(1024)
     batched_prune(SetCtl* sc, const int32_t* __restrict__ kept, const ST* __restrict__ score,
                   const PT* __restrict__ pos, int DP, int d, PT r2, int32_t* __restrict__ accepted,
-                  int P, int second) {
+                  int P, int second, int pos_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   SetCtl* c = sc + blockIdx.x;
   if (!second && c->final_) return;  // this set's prune result is already final
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(1024)
   // refined modes (rows = mode slots p0 + m)
   greedy_sorted_body<PT, ST>(second ? nullptr : kept + p0, K, score + p0,
                              second ? pos + (int64_t)p0 * DP : pos, DP, d, r2, accepted + p0,
-                             second ? &c->Mr : &c->M, P, smem);
+                             second ? &c->Mr : &c->M, P, smem, pos_in_smem != 0);
 }
 
 __global__ void batched_doubling(SetCtl* sc, int B, float L, int allow, int32_t* any) {
@@ -814,43 +814,52 @@ cudaError_t launch_batched_score(const float* part, const SetCtl* sc, int B,
   return cudaGetLastError();
 }
 
-size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P) {
+// Shared memory of the per-set sorted prune: sort keys and indices, plus the
+// coordinates when they fit in kBatchedPruneSmem (else they are read from
+// global memory; *with_pos tells which).
+size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P,
+                          int* with_pos) {
   int p = 1;
   while (p < maxK) p <<= 1;
   *P = p;
-  return (((size_t)p * (score_bytes + 4) + 15) / 16) * 16 + 2 * (size_t)maxK * d * pos_bytes;
+  const size_t keys = (((size_t)p * (score_bytes + 4) + 15) / 16) * 16 +
+                      (size_t)kPruneMaxDim * kPruneTileStride * pos_bytes;
+  const size_t full = keys + (size_t)maxK * d * pos_bytes;
+  if (with_pos) *with_pos = full <= kBatchedPruneSmem ? 1 : 0;
+  return full <= kBatchedPruneSmem ? full : keys;
 }
 
 cudaError_t launch_batched_prune_f(SetCtl* sc, int B, const int32_t* kept, const float* score,
                                    const float* pos, int DP, int d, float r2, int32_t* accepted,
                                    int maxK, cudaStream_t st) {
-  int P = 1;
-  const size_t sm = batched_prune_smem(maxK, d, 4, 4, &P);
-  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  int P = 1, with_pos = 0;
+  const size_t sm = batched_prune_smem(maxK, d, 4, 4, &P, &with_pos);
+  if (sm > kBatchedPruneSmem) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(batched_prune<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+                         (int)kBatchedPruneSmem);
     attr = true;
   }
-  batched_prune<float, float><<<B, 1024, sm, st>>>(sc, kept, score, pos, DP, d, r2, accepted, P, 0);
+  batched_prune<float, float><<<B, 1024, sm, st>>>(sc, kept, score, pos, DP, d, r2, accepted, P, 0,
+                                                   with_pos);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batched_prune_d(SetCtl* sc, int B, const double* score, const double* pos,
                                    int DP, int d, double r2, int32_t* accepted, int maxK,
                                    cudaStream_t st) {
-  int P = 1;
-  const size_t sm = batched_prune_smem(maxK, d, 8, 8, &P);
-  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  int P = 1, with_pos = 0;
+  const size_t sm = batched_prune_smem(maxK, d, 8, 8, &P, &with_pos);
+  if (sm > kBatchedPruneSmem) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(batched_prune<double, double>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchedPruneSmem);
     attr = true;
   }
   batched_prune<double, double><<<B, 1024, sm, st>>>(sc, nullptr, score, pos, DP, d, r2, accepted,
-                                                     P, 1);
+                                                     P, 1, with_pos);
   return cudaGetLastError();
 }
 

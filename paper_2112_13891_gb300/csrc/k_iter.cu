@@ -139,16 +139,19 @@ cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_se
 }
 
 // Cross-chunk sum of the partials of active position p: lane l sums chunks
-// l, l+32, ... in chunk order for every accumulator (16-byte loads), then a
-// fixed xor tree combines the 32 lane sums.  On return lane k holds
-// accumulator k (W for k = 0, S_{k-1} otherwise) in a[k >> 5], for k <= d.
+// c0 + cs*l, c0 + cs*(l+32), ... in chunk order for every accumulator
+// (16-byte loads), then a fixed xor tree combines the 32 lane sums.  On
+// return lane k holds accumulator k (W for k = 0, S_{k-1} otherwise) in
+// a[k >> 5], for k <= d.  (c0, cs) = (0, 1) sums every chunk; a block whose
+// warp w takes (w, 8) splits them over 8 warps.
 __device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, int s, int p, int C,
-                                              int DA, int d, int lane, float (&a)[3]) {
+                                              int DA, int d, int lane, float (&a)[3], int c0 = 0,
+                                              int cs = 1) {
   for (int k0 = 0; k0 <= d; k0 += 4) {
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
     if ((DA & 3) == 0) {
 #pragma unroll 4
-      for (int c = lane; c < C; c += 32) {
+      for (int c = c0 + cs * lane; c < C; c += 32 * cs) {
         const float4 q = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)c * s + p) * DA + k0));
         v0 += q.x;
         v1 += q.y;
@@ -157,7 +160,7 @@ __device__ __forceinline__ void reduce_chunks(const float* __restrict__ part, in
       }
     } else {  // DA == 2 (d == 1)
 #pragma unroll 4
-      for (int c = lane; c < C; c += 32) {
+      for (int c = c0 + cs * lane; c < C; c += 32 * cs) {
         const float2 q = __ldcg(reinterpret_cast<const float2*>(part + ((int64_t)c * s + p) * DA));
         v0 += q.x;
         v1 += q.y;
@@ -315,15 +318,37 @@ __global__ void __launch_bounds__(256)
                   int32_t R, Tiling tl, int N, int target, int max_iter, float coarse_tol2_s) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
+  __shared__ float red[8][96];
   if (__ldcg(&ctl->done)) return;  // uniform for the whole launch
   const int s = __ldcg(&ctl->s);
   const int C = __ldcg(&ctl->C);
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // many chunks: one block per position, its 8 warps split the chunks and
+  // the warp sums are added in warp order; else one warp per position
+  const bool block_mode = C >= kBlockReduceChunks;
+  const int nw = block_mode ? gridDim.x : gridDim.x * (blockDim.x >> 5);
+  const int p_first = block_mode ? blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wid;
+  for (int p = p_first; p < s; p += nw) {
     const int64_t slot = __ldcg(active + p);
     float a[3] = {0.f, 0.f, 0.f};
-    reduce_chunks(part, s, p, C, DA, d, lane, a);
+    if (block_mode) {
+      reduce_chunks(part, s, p, C, DA, d, lane, a, wid, 8);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) red[wid][lane + 32 * u] = a[u];
+      __syncthreads();
+      if (wid == 0) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          float t = red[0][lane + 32 * u];
+          for (int w = 1; w < 8; ++w) t += red[w][lane + 32 * u];
+          a[u] = t;
+        }
+      }
+      __syncthreads();
+      if (wid != 0) continue;
+    } else {
+      reduce_chunks(part, s, p, C, DA, d, lane, a);
+    }
     const float W = __shfl_sync(kFull, a[0], 0);
     float step2 = 0.0f;
     float delta[3] = {0.f, 0.f, 0.f};

@@ -161,62 +161,67 @@ __global__ void __launch_bounds__(1024)
     greedy_sorted_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
                          const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
                          PT r2, int32_t* __restrict__ accepted, int32_t* __restrict__ M_out,
-                         int P) {
+                         int P, int acc_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
-  greedy_sorted_body<PT, ST>(cand_row, *K_ptr, score, pos, DP, d, r2, accepted, M_out, P, smem);
+  greedy_sorted_body<PT, ST>(cand_row, *K_ptr, score, pos, DP, d, r2, accepted, M_out, P, smem,
+                             acc_in_smem != 0);
 }
 
+// Shared memory of the sorted prune for up to K candidates: sort keys and
+// indices, the batch tile, plus (with_pos) the accepted modes' coordinates.
 template <typename PT, typename ST>
-size_t greedy_sorted_bytes(int K, int d, int* P_out) {
+size_t greedy_sorted_bytes(int K, int d, int* P_out, bool with_pos) {
   int P = 1;
   while (P < K) P <<= 1;
   *P_out = P;
-  return (((size_t)P * (sizeof(ST) + 4) + 15) / 16) * 16 + 2 * (size_t)K * d * sizeof(PT);
+  return greedy_sorted_smem<PT, ST>(K, d, P, with_pos);
 }
 
 constexpr size_t kGreedySmemMax = 200 * 1024;
+
+// The sorted prune (coordinates in shared memory when they fit, else read
+// from global memory); the one-block global greedy only when even the sort
+// keys do not fit.
+template <typename PT, typename ST>
+cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const ST* score,
+                          const PT* pos, int DP, int d, PT r2, int32_t* alive,
+                          int32_t* accepted, int32_t* M_out, int max_K, cudaStream_t st) {
+  int P = 1;
+  size_t sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, true);
+  int with_pos = 1;
+  if (sm > kGreedySmemMax) {
+    sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, false);
+    with_pos = 0;
+  }
+  if (sm <= kGreedySmemMax && d <= kPruneMaxDim) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(greedy_sorted_kernel<PT, ST>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
+      attr = true;
+    }
+    greedy_sorted_kernel<PT, ST><<<1, 1024, sm, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
+                                                      accepted, M_out, P, with_pos);
+    return cudaGetLastError();
+  }
+  greedy_merge_kernel<PT, ST><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2, alive,
+                                                  accepted, M_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
                                   const float* score, const float* pos, int DP, int d, float r2,
                                   int32_t* alive, int32_t* accepted, int32_t* M_out, int max_K,
                                   cudaStream_t st) {
-  int P = 1;
-  const size_t sm = greedy_sorted_bytes<float, float>(max_K, d, &P);
-  if (sm <= kGreedySmemMax) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(greedy_sorted_kernel<float, float>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
-      attr = true;
-    }
-    greedy_sorted_kernel<float, float><<<1, 1024, sm, st>>>(cand_row, K_ptr, score, pos, DP, d,
-                                                            r2, accepted, M_out, P);
-    return cudaGetLastError();
-  }
-  greedy_merge_kernel<float, float><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
-                                                        alive, accepted, M_out);
-  return cudaGetLastError();
+  return launch_greedy<float, float>(cand_row, K_ptr, score, pos, DP, d, r2, alive, accepted,
+                                     M_out, max_K, st);
 }
 
 cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
                                   int DP, int d, double r2, int32_t* alive, int32_t* accepted,
                                   int32_t* M_out, int max_K, cudaStream_t st) {
-  int P = 1;
-  const size_t sm = greedy_sorted_bytes<double, double>(max_K, d, &P);
-  if (sm <= kGreedySmemMax) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(greedy_sorted_kernel<double, double>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
-      attr = true;
-    }
-    greedy_sorted_kernel<double, double><<<1, 1024, sm, st>>>(nullptr, K_ptr, score, pos, DP, d,
-                                                              r2, accepted, M_out, P);
-    return cudaGetLastError();
-  }
-  greedy_merge_kernel<double, double><<<1, 1024, 0, st>>>(nullptr, K_ptr, score, pos, DP, d, r2,
-                                                          alive, accepted, M_out);
-  return cudaGetLastError();
+  return launch_greedy<double, double>(nullptr, K_ptr, score, pos, DP, d, r2, alive, accepted,
+                                       M_out, max_K, st);
 }
 
 // Seed-count control (Sec. II-D): double N while N < L*M (and N < n).
@@ -296,19 +301,24 @@ __global__ void __launch_bounds__(256)
                          int32_t R, Tiling tl) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
+  __shared__ double red[8][96];
   if (__ldcg(&rctl->done)) return;
   const int s = __ldcg(&rctl->s), C = __ldcg(&rctl->C);
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < s; p += nw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // many chunks: one block per mode, its 8 warps split the chunks (warp sums
+  // added in warp order); else one warp per mode
+  const bool block_mode = C >= kBlockReduceChunks;
+  const int nw = block_mode ? gridDim.x : gridDim.x * (blockDim.x >> 5);
+  const int c0 = block_mode ? wid : 0, cs = block_mode ? 8 : 1;
+  for (int p = block_mode ? blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wid; p < s; p += nw) {
     const int m = __ldcg(active + p);
-    // lane l sums chunks l, l+32, ... in FP64; fixed xor tree; lane k keeps
-    // accumulator k (W for k = 0, S_{k-1} otherwise)
+    // lane l sums chunks c0 + cs*l, c0 + cs*(l+32), ... in FP64; fixed xor
+    // tree; lane k keeps accumulator k (W for k = 0, S_{k-1} otherwise)
     double a[3] = {0.0, 0.0, 0.0};
     for (int k0 = 0; k0 <= d; k0 += 4) {
       double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
       if ((DA & 3) == 0) {
-        for (int c = lane; c < C; c += 32) {
+        for (int c = c0 + cs * lane; c < C; c += 32 * cs) {
           const float4 q = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)c * s + p) * DA + k0));
           v0 += (double)q.x;
           v1 += (double)q.y;
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(256)
           v3 += (double)q.w;
         }
       } else {
-        for (int c = lane; c < C; c += 32) {
+        for (int c = c0 + cs * lane; c < C; c += 32 * cs) {
           const float2 q = __ldcg(reinterpret_cast<const float2*>(part + ((int64_t)c * s + p) * DA));
           v0 += (double)q.x;
           v1 += (double)q.y;
@@ -335,6 +345,21 @@ __global__ void __launch_bounds__(256)
         const int k = k0 + e;
         if (k <= d && (k & 31) == lane) a[k >> 5] = vals[e];
       }
+    }
+    if (block_mode) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) red[wid][lane + 32 * u] = a[u];
+      __syncthreads();
+      if (wid == 0) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          double t = red[0][lane + 32 * u];
+          for (int w = 1; w < 8; ++w) t += red[w][lane + 32 * u];
+          a[u] = t;
+        }
+      }
+      __syncthreads();
+      if (wid != 0) continue;
     }
     const double W = __shfl_sync(kFull, a[0], 0);
     if (score_only) {
@@ -406,7 +431,7 @@ cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rc
                                  float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
                                  double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
                                  Tiling tl, int max_M, cudaStream_t st) {
-  int blocks = (max_M + 7) / 8;
+  int blocks = max_M;  // one block per mode (many chunks) or one warp per mode
   if (blocks < 1) blocks = 1;
   if (blocks > 1216) blocks = 1216;
   refine_update_kernel<<<blocks, 256, 0, st>>>(part, active, rctl, ym, yf, mdone, mscore, d, DP,

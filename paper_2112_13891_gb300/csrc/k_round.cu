@@ -8,9 +8,11 @@
 // update every warp evaluates all active seeds of its cluster (groups of R
 // seeds in registers) against its sub-slice; the warp partials are summed in
 // warp order, then the CTA partials are summed in rank order through
-// distributed shared memory.  Every CTA computes the same update from the same
-// sums, so the seed state stays replicated in shared memory; rank 0 writes it
-// back to global memory.  A seed's summation order depends only on n and the
+// distributed shared memory (partials double-buffered by update parity, so one
+// cluster barrier per update suffices).  Every CTA computes the same update
+// from the same sums, so the seed state stays replicated in shared memory;
+// rank 0 writes it back to global memory.  A pass over the points serves a
+// block of R seeds, or a full block plus a last block of at most R/2.  A seed's summation order depends only on n and the
 // slice layout, never on which other seeds are active, so results do not
 // depend on timing.
 //
@@ -23,7 +25,10 @@
 // cannot be kept whatever happens elsewhere.  count only grows, so a stale
 // read only delays a stop; no seed is ever stopped wrongly and the kept set is
 // exactly that of the synchronous rule.  Stopped seeds stay RUNNING with their
-// update count (a later round may resume them).
+// update count (a later round may resume them).  Rank 0 takes the count test
+// and the other ranks apply its decisions one update later (after the next
+// cluster barrier), so a stopped seed may make one extra update; it was
+// already beyond t*, and a resumed seed continues from its count.
 #include <cooperative_groups.h>
 
 #include "fms_internal.cuh"
@@ -156,6 +161,62 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
   return rs32(v, lane);
 }
 
+// One point pass for a full block of RA = 32 / DA seeds (active positions
+// a0 ..) and a partial block of RB seeds (positions a0 + RA ..): the point
+// loads are shared by both blocks.  Returns the block results in res[0]
+// (lane l: accumulator l % DA of seed l / DA) and res[1].  A seed's arithmetic
+// is the same as in group_partial.
+template <int D, int DP, int DA, int RA, int RB>
+__device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0, int w1, int lane,
+                                           const int* alist, int a0, int A, const float (*sy)[D],
+                                           float (&res)[2]) {
+  constexpr int RR = RA + RB;
+  float ys[RR][D];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    const int i = alist[min(a0 + r, A - 1)];
+#pragma unroll
+    for (int k = 0; k < D; ++k) ys[r][k] = sy[i][k];
+  }
+  float acc[RR][DA];
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
+  int j = w0 + lane;
+  RPt<DP> b0 = rload<DP>(Xs, j, w1), b1 = rload<DP>(Xs, j + 32, w1);
+  RPt<DP> b2 = rload<DP>(Xs, j + 64, w1), b3 = rload<DP>(Xs, j + 96, w1);
+  for (; j < w1; j += 128) {
+    const RPt<DP> p0 = b0, p1 = b1, p2 = b2, p3 = b3;
+    b0 = rload<DP>(Xs, j + 128, w1);
+    b1 = rload<DP>(Xs, j + 160, w1);
+    b2 = rload<DP>(Xs, j + 192, w1);
+    b3 = rload<DP>(Xs, j + 224, w1);
+    float x[D];
+    rcoords<D, DP>(p0, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p1, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p2, x);
+    reval<D, RR, DA>(x, ys, acc);
+    rcoords<D, DP>(p3, x);
+    reval<D, RR, DA>(x, ys, acc);
+  }
+  float v[32];
+#pragma unroll
+  for (int r = 0; r < RA; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) v[r * DA + k] = acc[r][k];
+  res[0] = rs32(v, lane);
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) v[r * DA + k] = acc[RA + r][k];
+  res[1] = rs32(v, lane);
+}
+
 template <int D, int DP, int DA>
 __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     ms_round_kernel(const float* __restrict__ Xs, int n, float* __restrict__ y,
@@ -171,9 +232,12 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   __shared__ int sslot[SMAX];
   __shared__ int sact[SMAX];   // 1: takes updates in this round
   __shared__ int alist[SMAX];
-  __shared__ int sstop[SMAX];  // rank 0's stop decisions, read by the other ranks
+  // rank 0's Early-Stopping decisions: sstop[u & 1][i] == u marks seed i as
+  // stopped by the count test of update u (read by every rank after the next
+  // update's cluster barrier)
+  __shared__ int sstop[2][SMAX];
   __shared__ float wb[kRoundWarps][GMAX][32];
-  __shared__ float cpart[SMAX][DA];   // this CTA's sums, read by every rank
+  __shared__ float cpart[2][SMAX][DA];   // this CTA's sums (by update parity), read by every rank
   __shared__ float tot[SMAX][DA];
   __shared__ int sA;
 
@@ -196,6 +260,8 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     sslot[i] = slot;
     sit[i] = it[slot];
     sact[i] = 1;
+    sstop[0][i] = -1;
+    sstop[1][i] = -1;
 #pragma unroll
     for (int k = 0; k < D; ++k) sy[i][k] = y[(int64_t)slot * DP + k];
   }
@@ -224,9 +290,22 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     if (A == 0) break;
     const int G = (A + R - 1) / R;
 
-    // partial sums of every active seed over this warp's points; a group with
-    // fewer than R live seeds keeps only the next power of two in registers
+    // partial sums of every active seed over this warp's points, one point
+    // pass per block of R seeds; a last block of at most R/2 seeds rides in
+    // the previous block's pass; a lone block with fewer than R live seeds
+    // keeps only the next power of two in registers
+    const int last = A - (G - 1) * R;
+    const bool pair = G >= 2 && 2 * last <= R && D < 7;   // (D = 7: registers)
     for (int g = 0; g < G; ++g) {
+      if (pair && g == G - 2) {
+        float res[2];
+        if (last > R / 4 && R >= 4) group_pair<D, DP, DA, R, (R >= 4 ? R / 2 : 1)>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        else if (last > 1 && R >= 8) group_pair<D, DP, DA, R, (R >= 8 ? R / 4 : 1)>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        else group_pair<D, DP, DA, R, 1>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        wb[warp][g][lane] = res[0];
+        wb[warp][g + 1][lane] = res[1];
+        break;
+      }
       const int cnt = min(R, A - g * R);
       float res;
       if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
@@ -238,19 +317,29 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     }
     __syncthreads();
     // this CTA's sums, warps in order
+    const int par = guard & 1;
     for (int t = threadIdx.x; t < G * 32; t += blockDim.x) {
       const int g = t >> 5, l = t & 31;
       float sum = 0.0f;
       for (int w = 0; w < kRoundWarps; ++w) sum += wb[w][g][l];
       const int a = g * R + l / DA;
-      if (a < A) cpart[a][l % DA] = sum;
+      if (a < A) cpart[par][a][l % DA] = sum;
     }
     cluster.sync();
+    // rank 0's count-test stops of the previous update take effect now, in
+    // every rank at the same point: such a seed has made one update more than
+    // the synchronous rule would give it.  That cannot change the outcome:
+    // count(k) >= target already fixes t* <= k, and a later round resumes the
+    // seed from its update count.
+    if (guard > 0)
+      for (int i = threadIdx.x; i < ns; i += blockDim.x)
+        if (cluster.map_shared_rank(&sstop[par ^ 1][0], 0)[i] == guard - 1) sact[i] = 0;
     // cluster sums, ranks in order (every CTA computes the same totals)
     for (int t = threadIdx.x; t < A * DA; t += blockDim.x) {
       const int a = t / DA, k = t - a * DA;
       float sum = 0.0f;
-      for (int rr = 0; rr < ncl; ++rr) sum += cluster.map_shared_rank(&cpart[0][0], rr)[a * DA + k];
+      for (int rr = 0; rr < ncl; ++rr)
+        sum += cluster.map_shared_rank(&cpart[par][0][0], rr)[a * DA + k];
       tot[a][k] = sum;
     }
     __syncthreads();
@@ -276,7 +365,7 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
       if (!ok) st = kFailed;
       else if (step2 <= tol2_s) st = kConverged;
       else if (t >= max_iter) st = kExhausted;
-      int stop = st != kRunning;
+      if (st != kRunning) sact[i] = 0;   // decided identically in every rank
       if (rank == 0) {
         const int64_t slot = sslot[i];
 #pragma unroll
@@ -287,20 +376,15 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
           atomicAdd(hist + t, 1);
         }
         state[slot] = st;
-        if (!stop) {
+        if (st == kRunning) {
           // count(t) >= target: t* <= t, so this seed cannot be kept any more
           int c = 0;
           for (int u = 1; u <= t; ++u) c += *((volatile int32_t*)hist + u);
-          stop = c >= target;
+          if (c >= target) sstop[par][i] = guard;
         }
-        sstop[a] = stop;
       }
     }
     if (rank == 0 && threadIdx.x == 0) atomicAdd(evals, (unsigned long long)A * (unsigned long long)n);
-    cluster.sync();
-    // every rank applies rank 0's decisions
-    for (int a = threadIdx.x; a < A; a += blockDim.x)
-      if (cluster.map_shared_rank(&sstop[0], 0)[a]) sact[alist[a]] = 0;
     __syncthreads();
   }
   // keep this CTA's shared memory alive until no rank can still read it

@@ -60,8 +60,31 @@ def dist_env():
 
 
 def make_input(rank):
+    """Rank r clusters its own seeded point set (independent problems, no data-path collective)."""
     import fms_inputs as fi
     return fi.paper_3d(seed=rank)
+
+
+def reduce_max(x, pg, device):
+    """Max over the ranks of a float (the value itself without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_clustering(t_total_ms, steps, world, pg, device):
+    """Whole-job time per clustering: the slowest rank's timed total over the clusterings that
+    all ranks ran together (each rank runs `steps`); also returns ms per step (max over ranks)."""
+    t = reduce_max(t_total_ms, pg, device)
+    return t / (steps * world), t / steps
+
+
+def reference_runs_on(rank):
+    """The reference (oracle) arm runs on rank 0 only; other ranks exit without work."""
+    return rank == 0
 
 
 class ClockSampler:
@@ -146,7 +169,7 @@ def oracle_threads():
 
 def bench_reference(args):
     rank, world, _ = dist_env()
-    if rank != 0:
+    if not reference_runs_on(rank):
         return
     w = make_input(0)
     import oracle as orc
@@ -219,13 +242,7 @@ def bench_fms(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = float(sum(step_ms))
-    if pg is not None:
-        t = torch.tensor([t_total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = t_total / (args.steps * world)          # ms per clustering, whole job
-    ms_per_step = t_total / args.steps
+    value, ms_per_step = job_ms_per_clustering(float(sum(step_ms)), args.steps, world, pg, dev)
 
     # --- roofline of the dominant kernel: CUDA events around each launch (profile mode) ---
     prof = {"step_ms": 0.0, "step_ev": 0, "step_n": 0, "round_ms": 0.0, "round_ev": 0,
@@ -285,11 +302,7 @@ def bench_fms(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
         d2h_bytes = n * 4 + M * d * 4 + 4
-    e2e = float(np.mean(e2e_ms))
-    if pg is not None:
-        t = torch.tensor([e2e], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e = float(t.item()) / world
+    e2e = reduce_max(float(np.mean(e2e_ms)), pg, dev) / world
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -7,11 +7,11 @@ namespace fms {
 
 // Same prune with the candidates in shared memory, in two parallel stages:
 // (1) the block sorts the candidates by (score descending, rank ascending)
-// with a bitonic sort; (2) one warp walks the sorted list 32 candidates at a
-// time: the batch's coordinates are staged in a transposed, padded tile
-// (one candidate per lane, conflict-free per-lane reads), every lane tests its
-// candidate against the modes accepted so far, and the survivors of a batch
-// are resolved in order (the lowest surviving lane is accepted and removes
+// with a bitonic sort; (2) the sorted list is walked 32 candidates at a time:
+// the batch's coordinates are staged in a transposed, padded tile (one
+// candidate per lane, conflict-free per-lane reads), every warp tests the
+// batch against its share of the modes accepted so far, and one warp resolves
+// the survivors in order (the lowest surviving lane is accepted and removes
 // the later lanes within r).  The accepted set and its order are those of the
 // one-by-one greedy visit.  With acc_in_smem the accepted modes' coordinates
 // are kept in shared memory, else read back from global memory (all lanes
@@ -19,9 +19,15 @@ namespace fms {
 constexpr int kPruneTileStride = 33;   // padded row of the transposed batch tile
 constexpr int kPruneMaxDim = 64;
 
+// Bytes of the sort keys, indices and 64 scratch ints (batch flags, count).
+template <typename ST>
+__host__ __device__ inline size_t greedy_keys_bytes(int P) {
+  return (((size_t)P * (sizeof(ST) + 4) + 64 * 4 + 15) / 16) * 16;
+}
+
 template <typename PT, typename ST>
 __host__ __device__ inline size_t greedy_sorted_smem(int K, int d, int P, bool acc_in_smem) {
-  return (((size_t)P * (sizeof(ST) + 4) + 15) / 16) * 16 +
+  return greedy_keys_bytes<ST>(P) +
          (size_t)kPruneMaxDim * kPruneTileStride * sizeof(PT) +
          (acc_in_smem ? (size_t)K * d * sizeof(PT) : 0);
 }
@@ -32,10 +38,10 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
                                    int DP, int d, PT r2, int32_t* __restrict__ accepted,
                                    int32_t* __restrict__ M_out, int P, unsigned char* smem,
                                    bool acc_in_smem = true) {
-  // layout: keys[P] (ST), idx[P] (int), ctile[64 x 33] (PT), [apos[K*d] (PT)]
+  // layout: keys[P] (ST), idx[P] (int), scratch[64] (int), ctile[64 x 33] (PT), [apos[K*d] (PT)]
   ST* keys = reinterpret_cast<ST*>(smem);
   int* idx = reinterpret_cast<int*>(keys + P);
-  PT* ctile = reinterpret_cast<PT*>(smem + (((size_t)P * (sizeof(ST) + 4) + 15) / 16) * 16);
+  PT* ctile = reinterpret_cast<PT*>(smem + greedy_keys_bytes<ST>(P));
   PT* apos = ctile + kPruneMaxDim * kPruneTileStride;
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     keys[i] = i < K ? score[i] : (ST)-INFINITY;
@@ -63,63 +69,77 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
       __syncthreads();
     }
   }
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto row_of = [&](int q) -> int64_t { return cand_row ? (int64_t)cand_row[q] : (int64_t)q; };
   // coordinates of accepted mode a (a candidate index in accepted[a])
   auto acc_ptr = [&](int a) -> const PT* {
     if (acc_in_smem) return apos + (size_t)a * d;
     return pos + row_of(accepted[a]) * DP;
   };
-  int nacc = 0;
+  int* s_dead = idx + P;                             // scratch: batch suppression flags
+  int* s_nacc = s_dead + 32;                         // scratch: modes accepted so far
+  if (threadIdx.x == 0) *s_nacc = 0;
   for (int base = 0; base < K; base += 32) {
-    // stage the batch: lane c loads sorted candidate base + c (independent
-    // loads in flight across lanes); ctile[k * 33 + c] = its coordinate k
     const int i = base + lane;
-    if (i < K) {
-      const PT* src = pos + row_of(idx[i]) * DP;
-      for (int k = 0; k < d; ++k) ctile[k * kPruneTileStride + lane] = src[k];
+    // stage the batch (warp 0: lane c loads sorted candidate base + c; ctile[k * 33 + c] is
+    // its coordinate k) and clear the suppression flags
+    if (warp == 0) {
+      if (i < K) {
+        const PT* src = pos + row_of(idx[i]) * DP;
+        for (int k = 0; k < d; ++k) ctile[k * kPruneTileStride + lane] = src[k];
+      }
+      s_dead[lane] = 0;
     }
-    __syncwarp();
-    bool alive = i < K;
-    for (int a = 0; a < nacc && __any_sync(kFull, alive); ++a) {
-      if (alive) {
+    __syncthreads();
+    const int nacc = *s_nacc;
+    // every warp tests the batch against its share of the modes accepted so far
+    if (i < K) {
+      bool dead = false;
+      for (int a = warp; a < nacc && !dead; a += nwarps) {
         const PT* ap = acc_ptr(a);
         PT d2 = 0;
         for (int k = 0; k < d; ++k) {
           const PT e = ctile[k * kPruneTileStride + lane] - ap[k];
           d2 += e * e;
         }
-        if (d2 < r2) alive = false;
+        dead = d2 < r2;
       }
+      if (dead) s_dead[lane] = 1;
     }
-    for (;;) {
-      const unsigned m = __ballot_sync(kFull, alive);
-      if (!m) break;
-      const int w = __ffs(m) - 1;
-      if (lane == w) accepted[nacc] = idx[i];
-      if (acc_in_smem)
-        for (int k = lane; k < d; k += 32)
-          apos[(size_t)nacc * d + k] = ctile[k * kPruneTileStride + w];
-      __syncwarp();
-      const PT* wp = acc_ptr(nacc);
-      ++nacc;
-      if (alive) {
-        if (lane == w) {
-          alive = false;
-        } else {
-          PT d2 = 0;
-          for (int k = 0; k < d; ++k) {
-            const PT e = ctile[k * kPruneTileStride + lane] - wp[k];
-            d2 += e * e;
+    __syncthreads();
+    if (warp == 0) {
+      // survivors of the batch, resolved in order by one warp
+      bool alive = i < K && !s_dead[lane];
+      int na = nacc;
+      for (;;) {
+        const unsigned m = __ballot_sync(kFull, alive);
+        if (!m) break;
+        const int w = __ffs(m) - 1;
+        if (lane == w) accepted[na] = idx[i];
+        if (acc_in_smem)
+          for (int k = lane; k < d; k += 32)
+            apos[(size_t)na * d + k] = ctile[k * kPruneTileStride + w];
+        __syncwarp();
+        const PT* wp = acc_ptr(na);
+        ++na;
+        if (alive) {
+          if (lane == w) {
+            alive = false;
+          } else {
+            PT d2 = 0;
+            for (int k = 0; k < d; ++k) {
+              const PT e = ctile[k * kPruneTileStride + lane] - wp[k];
+              d2 += e * e;
+            }
+            if (d2 < r2) alive = false;
           }
-          if (d2 < r2) alive = false;
         }
       }
+      if (lane == 0) *s_nacc = na;
     }
-    __syncwarp();   // the tile is rewritten by the next batch
+    __syncthreads();   // accepted modes visible, the tile is rewritten by the next batch
   }
-  if (lane == 0) *M_out = nacc;
+  if (threadIdx.x == 0) *M_out = *s_nacc;
 }
 
 }  // namespace fms

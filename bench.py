@@ -450,6 +450,32 @@ def bench_extra(args):
                    "phase_ms": st["phase_ms"]}
             line[prec] = rec
         line["value"] = line["tensor"]["ms"]
+    elif args.workload == "pixels_rgb":
+        # N1: RGB image segmentation, 512^2 and 1024^2 pixels (the paper's image workload)
+        line.update({"metric": "ms per RGB image segmentation (labels for every pixel)",
+                     "unit": "ms"})
+        for side in (512, 1024):
+            w = fi.pixels_rgb(seed=side, height=side, width=side)
+            Xh = torch.from_numpy(w.X).pin_memory()
+            X = Xh.cuda()
+            n = X.shape[0]
+            ws = fms.Workspace(fms.workspace_size(n, 3), X.device)
+            lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+            run = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws)
+            r = run()
+            ms, _ = _events_ms(run, max(5, min(50, args.steps)), flush)
+
+            def e2e():
+                X.copy_(Xh, non_blocking=True)
+                rr = fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws)
+                lab_h.copy_(rr.labels, non_blocking=True)
+            e2e_ms, _ = _events_ms(e2e, max(5, min(50, args.steps)), flush)
+            line[f"{side}x{side}"] = {
+                "n": n, "ms": ms, "e2e_ms": e2e_ms, "n_modes": r.stats["n_modes"],
+                "workspace_mb": r.stats["workspace_bytes"] / 2**20,
+                "device_mb_total": (r.stats["workspace_bytes"] + n * 3 * 4 + n * 8) / 2**20,
+                "evals": r.stats["evals"], "rounds": r.stats["rounds"]}
+        line["value"] = line["1024x1024"]["ms"]
     elif args.workload == "step_wide":
         # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
         peaks = measured_peaks()
@@ -493,7 +519,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
-                             "embedding_32d", "step_wide"],
+                             "embedding_32d", "step_wide", "pixels_rgb"],
                     help="paper_3d is the headline line; the others print one line of "
                          "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",

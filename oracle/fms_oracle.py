@@ -12,7 +12,10 @@ cores), the rest is numpy in the order the paper states the steps.
 Readings of the paper used here (where it is silent or garbled):
   * the kernel is the Gaussian exp(-||y-x||^2/(2h^2)); its shadow is itself,
     so the update is the Gaussian-weighted mean over all points (Sec. II-B,
-    Alg. 2 line 6, the prose after Eq. 11; Eq. 11 itself is garbled);
+    Alg. 2 line 6, the prose after Eq. 11; Eq. 11 itself is garbled).  The
+    flat (uniform) kernel of Eq. 12-15 is the alternative (kernel="flat"): the
+    update is the mean of the window ||x_i - y|| <= h and the density is the
+    window count;
   * convergence: ||y_{t+1} - y_t|| <= tol (Alg. 1/2 say only "not converge");
   * Seed Selection (Alg. 2 line 2, Sec. II-D): the seeds are the first N
     entries of a keyed pseudo-random permutation of [0, n) (a 6-round Feistel
@@ -82,10 +85,14 @@ def _core():
             P = ctypes.c_void_p
             I64, I32, F64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
             lib.orc_kde.argtypes = [P, I64, I32, P, I64, F64, P]
+            lib.orc_kde_flat.argtypes = [P, I64, I32, P, I64, F64, P]
             lib.orc_step.argtypes = [P, I64, I32, F64, P, I64, P]
+            lib.orc_step_k.argtypes = [P, I64, I32, F64, P, I64, P, I32]
             lib.orc_trajectories.argtypes = [P, I64, I32, F64, F64, I32, P, I64, P, P]
+            lib.orc_trajectories_k.argtypes = [P, I64, I32, F64, F64, I32, P, I64, P, P, I32]
             lib.orc_label.argtypes = [P, I64, I32, P, I64, P, P]
-            for f in (lib.orc_kde, lib.orc_step, lib.orc_trajectories, lib.orc_label):
+            for f in (lib.orc_kde, lib.orc_kde_flat, lib.orc_step, lib.orc_step_k,
+                      lib.orc_trajectories, lib.orc_trajectories_k, lib.orc_label):
                 f.restype = None
             _lib = lib
     return _lib
@@ -103,34 +110,46 @@ def _ptr(a):
 # Eq. 1, Eq. 6 / 9 / 10: density and one mean-shift update
 # ----------------------------------------------------------------------------
 
-def kde(X, Y, h):
-    """sum_j exp(-||y - x_j||^2 / (2h^2)) for each row y of Y (Eq. 1 without 1/(n h^d)).
+KERNELS = {"gaussian": 0, "flat": 1}
 
-    Pinned by: brute-force Python sums on tiny inputs; closed forms.
+
+def kde(X, Y, h, kernel="gaussian"):
+    """Density at each row y of Y (Eq. 1 without 1/(n h^d)).
+
+    gaussian: sum_j exp(-||y - x_j||^2 / (2h^2)); flat (Eq. 12-13): the window
+    count #{j : ||y - x_j|| <= h}.
+    Pinned by: brute-force Python sums on tiny inputs; closed forms; the flat
+    count against sklearn's window intensities.
     """
     X, Y = _f64(X), _f64(np.atleast_2d(Y))
     out = np.empty(Y.shape[0])
-    _core().orc_kde(_ptr(X), X.shape[0], X.shape[1], _ptr(Y), Y.shape[0], float(h), _ptr(out))
+    fn = _core().orc_kde_flat if KERNELS[kernel] == 1 else _core().orc_kde
+    fn(_ptr(X), X.shape[0], X.shape[1], _ptr(Y), Y.shape[0], float(h), _ptr(out))
     return out
 
 
-def step(X, Y, h):
-    """One Gaussian mean-shift update m(y) = sum w x / sum w for each row of Y (Eq. 6, 9-10).
+def step(X, Y, h, kernel="gaussian"):
+    """One mean-shift update for each row of Y.
 
+    gaussian (Eq. 6, 9-10 with the Gaussian weight): m(y) = sum w x / sum w;
+    flat (Eq. 14-15): the mean of the window S_h(y) (NaN when it is empty).
     Pinned by: the two-point closed form, symmetric-polygon fixed points,
-    monotone KDE ascent, and agreement with a gradient-of-KDE identity.
+    monotone KDE ascent, a gradient-of-KDE identity; the flat update against
+    sklearn's flat mean shift and two-point closed forms.
     """
     X, Y = _f64(X), _f64(np.atleast_2d(Y))
     out = np.empty_like(Y)
-    _core().orc_step(_ptr(X), X.shape[0], X.shape[1], float(h), _ptr(Y), Y.shape[0], _ptr(out))
+    _core().orc_step_k(_ptr(X), X.shape[0], X.shape[1], float(h), _ptr(Y), Y.shape[0],
+                       _ptr(out), KERNELS[kernel])
     return out
 
 
-def trajectories(X, Y0, h, tol, max_iter):
+def trajectories(X, Y0, h, tol, max_iter, kernel="gaussian"):
     """Independent trajectories y <- m(y) until ||step|| <= tol (Alg. 1 / Alg. 2 lines 5-7).
 
     Returns (Y_end, conv_iter, iters): conv_iter[i] is the 1-based update at
-    which ||y_t - y_{t-1}|| <= tol first held, -1 if never within max_iter.
+    which ||y_t - y_{t-1}|| <= tol first held, -1 if never within max_iter,
+    -2 if an update was undefined (flat kernel, empty window).
     Pinned by: closed forms (two points, polygons) and brute-force maxima.
     """
     X = _f64(X)
@@ -140,8 +159,8 @@ def trajectories(X, Y0, h, tol, max_iter):
         raise ValueError("oracle supports d <= 64")
     conv = np.empty(m, dtype=np.int32)
     iters = np.empty(m, dtype=np.int32)
-    _core().orc_trajectories(_ptr(X), X.shape[0], d, float(h), float(tol), int(max_iter),
-                             _ptr(Y), m, _ptr(conv), _ptr(iters))
+    _core().orc_trajectories_k(_ptr(X), X.shape[0], d, float(h), float(tol), int(max_iter),
+                               _ptr(Y), m, _ptr(conv), _ptr(iters), KERNELS[kernel])
     return Y, conv, iters
 
 
@@ -261,7 +280,8 @@ def early_stop(conv_iter: np.ndarray, gamma: float, max_iter: int):
 
     t* is the ceil(gamma*N)-th smallest convergence iteration (max_iter if that
     many seeds never converge).  For gamma < 1, kept = converged by t*; for
-    gamma = 1 every seed is kept (unconverged ones at their last iterate).
+    gamma = 1 every seed is kept (unconverged ones at their last iterate)
+    except failed ones (conv_iter == -2: an undefined update).
     `gamma` is taken as the float32 value the library receives.
     """
     N = conv_iter.shape[0]
@@ -272,24 +292,25 @@ def early_stop(conv_iter: np.ndarray, gamma: float, max_iter: int):
     kth = np.sort(c)[target - 1]
     t_star = int(kth) if kth <= max_iter else int(max_iter)
     if g >= 1.0:
-        kept = np.ones(N, dtype=bool)
-        t_star = int(max_iter) if np.any(conv_iter < 0) else int(np.max(conv_iter))
+        kept = conv_iter != -2
+        t_star = int(max_iter) if np.any(conv_iter == -1) else (
+            int(np.max(conv_iter)) if np.any(conv_iter >= 0) else 0)
     else:
         kept = (conv_iter >= 0) & (conv_iter <= t_star)
     return t_star, kept
 
 
-def merge(X, Y, rank, h, r_merge):
+def merge(X, Y, rank, h, r_merge, kernel="gaussian"):
     """Prune modes (Alg. 1 line 13 / Alg. 2 line 10): greedy radius suppression.
 
-    Candidates are visited in order of (KDE score descending, rank ascending);
-    one is accepted unless an accepted mode lies at distance < r_merge.
-    Returns (accepted row indices into Y, scores of all rows).
+    Candidates are visited in order of (density score descending, rank
+    ascending); one is accepted unless an accepted mode lies at distance
+    < r_merge.  Returns (accepted row indices into Y, scores of all rows).
     """
     Y = _f64(Y)
     if Y.shape[0] == 0:
         return np.zeros(0, dtype=np.int64), np.zeros(0)
-    score = kde(X, Y, h)
+    score = kde(X, Y, h, kernel)
     order = np.lexsort((np.asarray(rank), -score))
     acc = []
     for i in order:
@@ -309,8 +330,11 @@ def canonical_order(modes, scores):
 
 def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gamma=0.95,
             merge_radius=0.0, rng_seed=0, seed_indices=None, refine=True,
-            refine_tol=1e-5, refine_max_iter=50):
+            refine_tol=1e-5, refine_max_iter=50, kernel="gaussian"):
     """Faster Mean-shift (Alg. 2, Sec. II-C/D) or plain mean shift (Alg. 1, all_seeds=True).
+
+    kernel: "gaussian" (the reading used throughout) or "flat" (Eq. 12-15: the
+    window mean, density = window count).
 
     Steps, in the paper's order: select N seeds; iterate every seed to
     convergence (trajectories are independent, so this is done seed by seed);
@@ -332,19 +356,19 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
     else:
         N = min(int(n_initial), n)
         seeds = seed_permutation(n, rng_seed, 0, N)
-    pos, conv, _ = trajectories(X, X[seeds], h, tol, max_iter)
+    pos, conv, _ = trajectories(X, X[seeds], h, tol, max_iter, kernel)
     history, tstars = [N], []
     while True:
         t_star, kept = early_stop(conv, gamma, max_iter)
         tstars.append(t_star)
         kidx = np.nonzero(kept)[0]
-        acc, _ = merge(X, pos[kidx], kidx, h, r_merge)
+        acc, _ = merge(X, pos[kidx], kidx, h, r_merge, kernel)
         M = acc.shape[0]
         if all_seeds or seed_indices is not None or not (N < L * M and N < n):
             break
         N_new = min(2 * N, n)
         new = seed_permutation(n, rng_seed, N, N_new)
-        p2, c2, _ = trajectories(X, X[new], h, tol, max_iter)
+        p2, c2, _ = trajectories(X, X[new], h, tol, max_iter, kernel)
         seeds = np.concatenate([seeds, new])
         pos = np.concatenate([pos, p2])
         conv = np.concatenate([conv, c2])
@@ -352,12 +376,12 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
         history.append(N)
     modes0 = pos[kidx[acc]]
     if refine and M > 0:
-        ref, _, _ = trajectories(X, modes0, h, refine_tol * h, refine_max_iter)
-        acc2, sc2 = merge(X, ref, np.arange(M), h, r_merge)
+        ref, _, _ = trajectories(X, modes0, h, refine_tol * h, refine_max_iter, kernel)
+        acc2, sc2 = merge(X, ref, np.arange(M), h, r_merge, kernel)
         modes, scores = ref[acc2], sc2[acc2]
     else:
         modes = modes0
-        scores = kde(X, modes, h) if M > 0 else np.zeros(0)
+        scores = kde(X, modes, h, kernel) if M > 0 else np.zeros(0)
     o = canonical_order(modes, scores) if modes.shape[0] else np.zeros(0, dtype=np.int64)
     modes, scores = modes[o], scores[o]
     labels, margins = label(X, modes) if modes.shape[0] else (

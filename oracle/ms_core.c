@@ -14,6 +14,12 @@
  * Gaussian, so the mean of Eq. 6 is the Gaussian-weighted mean
  *   m(y) = sum_i w_i x_i / sum_i w_i,  w_i = exp(-||y - x_i||^2 / (2 h^2)),
  * taken over ALL points (Sec. II-B, Alg. 2: no window search).
+ *
+ * The flat (uniform) kernel of Eq. 12-15 is the alternative profile
+ * (kernel = 1): g = 1 where ||x - x_i||^2 <= h^2, else 0, so the update is the
+ * plain mean of the window S_h(y) = {x_i : ||x_i - y|| <= h} (Eq. 13, 15) and
+ * the density is the window's count.  An empty window leaves y undefined
+ * (NaN), which the callers treat as a failed seed.
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,6 +51,18 @@ void orc_kde(const double* X, int64_t n, int d, const double* Y, int64_t m, doub
     }
 }
 
+/* Flat-kernel density: out[i] = |S_h(Y_i)| = #{j : ||Y_i - x_j||^2 <= h^2} (Eq. 12-13). */
+void orc_kde_flat(const double* X, int64_t n, int d, const double* Y, int64_t m, double h,
+                  double* out) {
+    const double h2 = h * h;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < n; ++j) c += sqdist(Y + i * d, X + j * d, d) <= h2;
+        out[i] = (double)c;
+    }
+}
+
 /*
  * One Gaussian mean-shift update y <- m(y) for one point y (Eq. 6 / Eq. 9-10
  * with the Gaussian weight, over all n points).  The weights are taken
@@ -69,17 +87,42 @@ static void ms_update_one(const double* X, int64_t n, int d, double inv2h2, cons
     for (int k = 0; k < d; ++k) ynew[k] /= W;
 }
 
-/* One update for each of m points: Ynew_i = m(Y_i). */
-void orc_step(const double* X, int64_t n, int d, double h, const double* Y, int64_t m,
-              double* Ynew) {
+/*
+ * One flat-kernel update (Eq. 14-15): the mean of the points within distance
+ * h of y (inclusive); NaN when the window is empty.
+ */
+static void ms_update_one_flat(const double* X, int64_t n, int d, double h2, const double* y,
+                               double* ynew) {
+    int64_t m = 0;
+    for (int k = 0; k < d; ++k) ynew[k] = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (sqdist(y, X + j * d, d) <= h2) {
+            ++m;
+            for (int k = 0; k < d; ++k) ynew[k] += X[j * d + k];
+        }
+    }
+    for (int k = 0; k < d; ++k) ynew[k] = m > 0 ? ynew[k] / (double)m : NAN;
+}
+
+/* One update for each of m points: Ynew_i = m(Y_i); kernel 0 Gaussian, 1 flat. */
+void orc_step_k(const double* X, int64_t n, int d, double h, const double* Y, int64_t m,
+                double* Ynew, int kernel) {
     const double inv2h2 = 1.0 / (2.0 * h * h);
 #pragma omp parallel
     {
         double* D = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t i = 0; i < m; ++i) ms_update_one(X, n, d, inv2h2, Y + i * d, Ynew + i * d, D);
+        for (int64_t i = 0; i < m; ++i) {
+            if (kernel == 1) ms_update_one_flat(X, n, d, h * h, Y + i * d, Ynew + i * d);
+            else ms_update_one(X, n, d, inv2h2, Y + i * d, Ynew + i * d, D);
+        }
         free(D);
     }
+}
+
+void orc_step(const double* X, int64_t n, int d, double h, const double* Y, int64_t m,
+              double* Ynew) {
+    orc_step_k(X, n, d, h, Y, m, Ynew, 0);
 }
 
 /*
@@ -87,10 +130,11 @@ void orc_step(const double* X, int64_t n, int d, double h, const double* Y, int6
  * start point Y_i, repeat y <- m(y) until ||m(y) - y|| <= tol or max_iter
  * updates were made.  On return Y_i holds the last iterate, iters[i] the
  * number of updates made and conv_iter[i] the update index t (1-based) at
- * which the test first held, or -1 if it never held.
+ * which the test first held, -1 if it never held, -2 if an update was
+ * undefined (flat kernel, empty window; Y_i keeps the last defined iterate).
  */
-void orc_trajectories(const double* X, int64_t n, int d, double h, double tol, int max_iter,
-                      double* Y, int64_t m, int32_t* conv_iter, int32_t* iters) {
+void orc_trajectories_k(const double* X, int64_t n, int d, double h, double tol, int max_iter,
+                        double* Y, int64_t m, int32_t* conv_iter, int32_t* iters, int kernel) {
     const double inv2h2 = 1.0 / (2.0 * h * h);
 #pragma omp parallel
     {
@@ -102,7 +146,13 @@ void orc_trajectories(const double* X, int64_t n, int d, double h, double tol, i
             conv_iter[i] = -1;
             iters[i] = 0;
             for (int t = 1; t <= max_iter; ++t) {
-                ms_update_one(X, n, d, inv2h2, y, ynew, D);
+                if (kernel == 1) ms_update_one_flat(X, n, d, h * h, y, ynew);
+                else ms_update_one(X, n, d, inv2h2, y, ynew, D);
+                if (ynew[0] != ynew[0]) {   /* empty window: the seed fails (-2) */
+                    iters[i] = t;
+                    conv_iter[i] = -2;
+                    break;
+                }
                 double step2 = 0.0;
                 for (int k = 0; k < d; ++k) {
                     double e = ynew[k] - y[k];
@@ -118,6 +168,11 @@ void orc_trajectories(const double* X, int64_t n, int d, double h, double tol, i
         }
         free(D);
     }
+}
+
+void orc_trajectories(const double* X, int64_t n, int d, double h, double tol, int max_iter,
+                      double* Y, int64_t m, int32_t* conv_iter, int32_t* iters) {
+    orc_trajectories_k(X, n, d, h, tol, max_iter, Y, m, conv_iter, iters, 0);
 }
 
 /*

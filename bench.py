@@ -476,6 +476,25 @@ def bench_extra(args):
                 "device_mb_total": (r.stats["workspace_bytes"] + n * 3 * 4 + n * 8) / 2**20,
                 "evals": r.stats["evals"], "rounds": r.stats["rounds"]}
         line["value"] = line["1024x1024"]["ms"]
+    elif args.workload == "flat_3d":
+        # N2: the flat (uniform) kernel of Eq. 12-15 on the 200K-point 3-D workload
+        w = fi.paper_3d()
+        X = torch.from_numpy(w.X).cuda()
+        n = X.shape[0]
+        line.update({"metric": "ms per 200K-point clustering, flat kernel (Eq. 12-15)",
+                     "unit": "ms"})
+        for kern in ("flat", "gaussian"):
+            ws = fms.Workspace(fms.workspace_size(n, 3, kernel=kern), X.device)
+            run = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, kernel=kern)
+            r = run()
+            ms, _ = _events_ms(run, max(5, min(100, args.steps)), flush)
+            st = fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, kernel=kern,
+                             profile=True).stats
+            line[kern] = {"ms": ms, "n_modes": r.stats["n_modes"], "rounds": r.stats["rounds"],
+                          "evals": r.stats["evals"],
+                          "round_kernel_evals_per_s": st["round_evals"] / max(st["round_kernel_ms"], 1e-9) * 1e3,
+                          "phase_ms": st["phase_ms"]}
+        line["value"] = line["flat"]["ms"]
     elif args.workload == "step_wide":
         # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
         peaks = measured_peaks()
@@ -519,7 +538,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
-                             "embedding_32d", "step_wide", "pixels_rgb"],
+                             "embedding_32d", "step_wide", "pixels_rgb", "flat_3d"],
                     help="paper_3d is the headline line; the others print one line of "
                          "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",

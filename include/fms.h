@@ -86,8 +86,20 @@ typedef struct fms_options {
                                   convergence is always decided by an FP32
                                   update.  Modes agree with FP32 within the
                                   tolerance; a seed's update count may differ. */
-  int32_t reserved[5];      /* must be zero                                       */
+  int32_t kernel;           /* profile of the weights (FMS_KERNEL_*):
+                               GAUSSIAN (0): w = exp(-||y-x||^2 / (2h^2)) over all
+                                  points (the reading of Sec. II-B used throughout).
+                               FLAT (1): the uniform kernel of Eq. 12-15: the
+                                  update is the mean of the points within
+                                  distance h (inclusive), the density of a mode
+                                  the number of such points; a seed whose window
+                                  is empty fails.  FP32 updates only (precision is
+                                  ignored); not available in fms_cluster_batched. */
+  int32_t reserved[4];      /* must be zero                                       */
 } fms_options;
+
+#define FMS_KERNEL_GAUSSIAN 0
+#define FMS_KERNEL_FLAT 1
 
 #define FMS_PRECISION_AUTO 0
 #define FMS_PRECISION_FP32 1

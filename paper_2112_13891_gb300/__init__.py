@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 FMS_OK, FMS_ERR_INVALID_ARG, FMS_ERR_NONFINITE, FMS_ERR_CAPACITY = 0, 1, 2, 3
 FMS_ERR_TIMEOUT, FMS_ERR_CUDA, FMS_ERR_WORKSPACE, FMS_ERR_UNSUPPORTED = 4, 5, 6, 7
 PRECISION = {"auto": 0, "fp32": 1, "tensor": 2}
+KERNEL = {"gaussian": 0, "flat": 1}
 MAX_DIM = 64
 
 
@@ -35,7 +36,8 @@ class FmsOptions(ctypes.Structure):
                 ("merge_radius", ctypes.c_float), ("skip_refine", ctypes.c_int32),
                 ("rng_seed", ctypes.c_uint64), ("seed_indices", ctypes.c_void_p),
                 ("n_seed_indices", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class FmsStats(ctypes.Structure):
@@ -121,7 +123,7 @@ def _points(x: torch.Tensor) -> torch.Tensor:
 
 def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
                  skip_refine=False, rng_seed=0, seed_indices=None, profile=False,
-                 precision="auto") -> FmsOptions:
+                 precision="auto", kernel="gaussian") -> FmsOptions:
     o = FmsOptions()
     _lib.fms_options_default(ctypes.byref(o))
     o.all_seeds = int(bool(all_seeds))
@@ -136,6 +138,7 @@ def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_rad
         o.n_seed_indices = int(seed_indices.numel())
     o.profile = int(bool(profile))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
     return o
 
 
@@ -167,7 +170,7 @@ class Workspace:
 def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 300, *,
             all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
             skip_refine=False, rng_seed=0, seed_indices=None, max_modes=None, margins=True,
-            workspace: Workspace = None, profile=False, precision="auto",
+            workspace: Workspace = None, profile=False, precision="auto", kernel="gaussian",
             out=None) -> ClusterResult:
     """Faster Mean-shift clustering of the rows of `points` (fms_cluster).
 
@@ -179,7 +182,8 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
         seed_indices = seed_indices.to(device=X.device, dtype=torch.int32).contiguous()
     o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
                      merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
-                     seed_indices=seed_indices, profile=profile, precision=precision)
+                     seed_indices=seed_indices, profile=profile, precision=precision,
+                     kernel=kernel)
     if out is not None:
         modes, labels, mar = out
         cap = modes.shape[0]
@@ -370,7 +374,7 @@ class BatchedResult:
 def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, offsets=None,
                     n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0, skip_refine=False,
                     all_seeds=False, rng_seed=0, max_modes=256, margins=True,
-                    workspace: Workspace = None) -> BatchedResult:
+                    workspace: Workspace = None, kernel="gaussian") -> BatchedResult:
     """Cluster many point sets at once.  `points` is a list of [n_b, d] CUDA
     tensors, or one [total, d] tensor with host `offsets` (B+1 ints)."""
     import numpy as np
@@ -384,7 +388,8 @@ def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, 
     B = len(offsets) - 1
     total, d = X.shape
     o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
-                     merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed)
+                     merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
+                     kernel=kernel)
     offs = np.ascontiguousarray(offsets)
     optr = offs.ctypes.data_as(ctypes.c_void_p)
     need = int(_lib.fms_batched_workspace_size(optr, B, d, ctypes.byref(o)))

@@ -132,7 +132,8 @@ void fill_defaults(const fms_options* in, fms_options* o) {
   o->n_seed_indices = in->n_seed_indices;
   o->profile = in->profile;
   o->precision = in->precision;
-  for (int i = 0; i < 5; ++i) o->reserved[i] = in->reserved[i];
+  o->kernel = in->kernel;
+  for (int i = 0; i < 4; ++i) o->reserved[i] = in->reserved[i];
 }
 
 int64_t seed_capacity(int64_t n, const fms_options& o) {
@@ -194,7 +195,9 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt) {
   fill_defaults(opt, &o);
   const int64_t Ncap = seed_capacity(n, o);
   if (Ncap < 1) return 0;
-  return make_layout(n, d, Ncap, device_info().sms, use_tensor_step(d, o.precision)).total;
+  return make_layout(n, d, Ncap, device_info().sms,
+                     o.kernel == FMS_KERNEL_GAUSSIAN && use_tensor_step(d, o.precision))
+      .total;
 }
 
 fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
@@ -213,17 +216,19 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       !(o.gamma > 0.0f && o.gamma <= 1.0f) || !(o.L > 0.0f) || !isfinite(o.merge_radius) ||
       o.merge_radius < 0.0f || (o.seed_indices && o.n_seed_indices < 1))
     return FMS_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i] != 0) return FMS_ERR_INVALID_ARG;
   if (o.precision < FMS_PRECISION_AUTO || o.precision > FMS_PRECISION_TENSOR)
     return FMS_ERR_INVALID_ARG;
+  if (o.kernel != FMS_KERNEL_GAUSSIAN && o.kernel != FMS_KERNEL_FLAT) return FMS_ERR_INVALID_ARG;
+  const int kf = o.kernel == FMS_KERNEL_FLAT ? kKernelFlat : kKernelGaussian;
   if (tol == 0.0f) tol = 1e-3f * h;
   if (o.all_seeds) o.gamma = 1.0f;
 
   const Dev dv = device_info();
   if (dv.sms <= 0) return FMS_ERR_CUDA;
   const int64_t Ncap = seed_capacity(n, o);
-  const bool tensor = use_tensor_step(d, o.precision);
+  const bool tensor = kf == kKernelGaussian && use_tensor_step(d, o.precision);
   const Layout Lo = make_layout(n, d, Ncap, dv.sms, tensor);
   const int DP = Lo.DP, DA = Lo.DA, R = Lo.R;
   bool owns_ws = false;
@@ -310,7 +315,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         cudaEventRecord(a, st);
         lg = slog + n_slog;
         cudaError_t e = launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                                       Lo.tl.target_warps, st, lg, p_lo);
+                                       Lo.tl.target_warps, st, lg, p_lo, kf);
         cudaEventRecord(b, st);
         evs.push_back(a);
         evs.push_back(b);
@@ -318,7 +323,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         return e;
       }
       return launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                            Lo.tl.target_warps, st, nullptr, p_lo);
+                            Lo.tl.target_warps, st, nullptr, p_lo, kf);
     };
     // the coarse step for active positions [0, ctl->s_tc)
     auto tc_launch = [&]() -> cudaError_t {
@@ -396,7 +401,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         }
         FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
                                    target, max_iter, tol2_s,
-                                   reinterpret_cast<unsigned long long*>(&ctl->evals), st));
+                                   reinterpret_cast<unsigned long long*>(&ctl->evals), st, kf));
         if (o.profile) cudaEventRecord(rb, st);
         FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N,
                                        o.gamma >= 1.0f ? 1 : 0, kept, mctl, ctl, n, R, Lo.tl,
@@ -462,7 +467,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       const int clusters = hm.M < qmax ? hm.M : qmax;
       FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
                                   rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
-                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st));
+                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st, kf));
       FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        hm.M, st));
       FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,

@@ -221,6 +221,19 @@ __device__ __forceinline__ float ex2_ftz(float x) {
   return y;
 }
 
+// Profile weight of a seed-point pair from t = -||ys - xs||^2 in scaled
+// coordinates (xs = s x, s = sqrt(log2(e) / (2 h^2))):
+//   KF = 0, Gaussian: exp(-||y - x||^2 / (2 h^2)) = exp2(t);
+//   KF = 1, flat (Eq. 12): 1 inside the window ||y - x|| <= h, i.e.
+//           ||ys - xs||^2 <= s^2 h^2 = log2(e) / 2 for every h, else 0.
+enum : int { kKernelGaussian = 0, kKernelFlat = 1 };
+constexpr float kFlatT = -0.72134752044448170f;   // -log2(e) / 2
+template <int KF>
+__device__ __forceinline__ float kweight(float t) {
+  if constexpr (KF == kKernelFlat) return t >= kFlatT ? 1.0f : 0.0f;
+  else return ex2_ftz(t);
+}
+
 // Block-wide helpers (every thread of the block must call them).
 __device__ inline int block_exclusive_scan(int v, int* total, int* warp_sums) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -304,13 +317,13 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st);
+                            cudaStream_t st, int kf = kKernelGaussian);
 int round_max_clusters(int d);
 cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
                              int clusters, double* ym, float* yf, double* mscore, double tol2_s,
                              int max_iter, int32_t* iters_out, unsigned long long* evals,
-                             cudaStream_t st);
+                             cudaStream_t st, int kf = kKernelGaussian);
 cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
                               cudaStream_t st);
 cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
@@ -340,7 +353,7 @@ cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const floa
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps,
                            cudaStream_t st, int32_t* s_log = nullptr,
-                           const int32_t* p_lo_ptr = nullptr);
+                           const int32_t* p_lo_ptr = nullptr, int kf = kKernelGaussian);
 int step_seeds_per_warp(int d);
 int step_resident_warps_per_sm(int d);
 // smallest chunk (points) of a warp task: the low-d kernel splits a chunk over

@@ -62,8 +62,8 @@ __device__ __forceinline__ void coords(const Pt<DP>& p, float (&x)[D]) {
   for (int k = 0; k < D; ++k) x[k] = t[k];
 }
 
-// R seeds in registers against one point: exact differences, one exp2 each.
-template <int D, int R, int DA>
+// R seeds in registers against one point: exact differences, one weight each.
+template <int D, int R, int DA, int KF = kKernelGaussian>
 __device__ __forceinline__ void eval_point(const float (&x)[D], const float (&ys)[R][D],
                                            float (&acc)[R][DA]) {
 #pragma unroll
@@ -74,7 +74,7 @@ __device__ __forceinline__ void eval_point(const float (&x)[D], const float (&ys
     float t = -dx[0] * dx[0];
 #pragma unroll
     for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
-    const float w = ex2_ftz(t);
+    const float w = kweight<KF>(t);
     acc[r][0] += w;
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
@@ -84,7 +84,7 @@ __device__ __forceinline__ void eval_point(const float (&x)[D], const float (&ys
 // One low-d warp task: R seeds (active positions g*R.., clamped to s-1) of a
 // set against the points [j0, j1) of that set; writes 32 partials to
 // part_task (index (c * s + p) * DA + k relative to the set's partial block).
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF = kKernelGaussian>
 __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, int j1,
                                           const float* __restrict__ y,
                                           const int32_t* __restrict__ active, int s, int g, int c,
@@ -115,13 +115,13 @@ __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, 
     b3 = load_pt<DP>(Xs, j + 224, j1);
     float x[D];
     coords<D, DP>(p0, x);
-    eval_point<D, R, DA>(x, ys, acc);
+    eval_point<D, R, DA, KF>(x, ys, acc);
     coords<D, DP>(p1, x);
-    eval_point<D, R, DA>(x, ys, acc);
+    eval_point<D, R, DA, KF>(x, ys, acc);
     coords<D, DP>(p2, x);
-    eval_point<D, R, DA>(x, ys, acc);
+    eval_point<D, R, DA, KF>(x, ys, acc);
     coords<D, DP>(p3, x);
-    eval_point<D, R, DA>(x, ys, acc);
+    eval_point<D, R, DA, KF>(x, ys, acc);
   }
   float v[32];
 #pragma unroll
@@ -137,7 +137,7 @@ __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, 
 // points [j0, j1) read with warp-uniform loads; DA = DPAD + 4.  Group g covers
 // active positions p_lo + g*32*RG ... (positions below p_lo belong to the
 // tensor-core step).
-template <int DPAD, int RG>
+template <int DPAD, int RG, int KF = kKernelGaussian>
 __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, int j0, int j1,
                                           const float* __restrict__ y,
                                           const int32_t* __restrict__ active, int s, int g, int c,
@@ -175,7 +175,7 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
       float t = -dx[0] * dx[0];
 #pragma unroll
       for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
-      const float w = ex2_ftz(t);
+      const float w = kweight<KF>(t);
       acc[r][0] += w;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);

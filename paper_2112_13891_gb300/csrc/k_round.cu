@@ -94,7 +94,7 @@ __device__ __forceinline__ void rcoords(const RPt<DP>& p, float (&x)[D]) {
   for (int k = 0; k < D; ++k) x[k] = t[k];
 }
 
-template <int D, int R, int DA>
+template <int D, int R, int DA, int KF>
 __device__ __forceinline__ void reval(const float (&x)[D], const float (&ys)[R][D],
                                       float (&acc)[R][DA]) {
 #pragma unroll
@@ -105,7 +105,7 @@ __device__ __forceinline__ void reval(const float (&x)[D], const float (&ys)[R][
     float t = -dx[0] * dx[0];
 #pragma unroll
     for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
-    const float w = ex2_ftz(t);
+    const float w = kweight<KF>(t);
     acc[r][0] += w;
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
@@ -116,7 +116,7 @@ __device__ __forceinline__ void reval(const float (&x)[D], const float (&ys)[R][
 // over the points [w0, w1) handled by this warp: lane l returns accumulator
 // l % DA of seed l / DA (zero for seed slots beyond RR).  The arithmetic of a
 // seed does not depend on RR.
-template <int D, int DP, int DA, int RR>
+template <int D, int DP, int DA, int RR, int KF>
 __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int w0, int w1,
                                                int lane, const int* alist, int a0, int A,
                                                const float (*sy)[D]) {
@@ -143,13 +143,13 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
     b3 = rload<DP>(Xs, j + 224, w1);
     float x[D];
     rcoords<D, DP>(p0, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p1, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p2, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p3, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
   }
   float v[32];
 #pragma unroll
@@ -166,7 +166,7 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
 // loads are shared by both blocks.  Returns the block results in res[0]
 // (lane l: accumulator l % DA of seed l / DA) and res[1].  A seed's arithmetic
 // is the same as in group_partial.
-template <int D, int DP, int DA, int RA, int RB>
+template <int D, int DP, int DA, int RA, int RB, int KF>
 __device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0, int w1, int lane,
                                            const int* alist, int a0, int A, const float (*sy)[D],
                                            float (&res)[2]) {
@@ -194,13 +194,13 @@ __device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0,
     b3 = rload<DP>(Xs, j + 224, w1);
     float x[D];
     rcoords<D, DP>(p0, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p1, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p2, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
     rcoords<D, DP>(p3, x);
-    reval<D, RR, DA>(x, ys, acc);
+    reval<D, RR, DA, KF>(x, ys, acc);
   }
   float v[32];
 #pragma unroll
@@ -217,7 +217,7 @@ __device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0,
   res[1] = rs32(v, lane);
 }
 
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF>
 __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     ms_round_kernel(const float* __restrict__ Xs, int n, float* __restrict__ y,
                     int32_t* __restrict__ it, int32_t* __restrict__ conv,
@@ -299,20 +299,20 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     for (int g = 0; g < G; ++g) {
       if (pair && g == G - 2) {
         float res[2];
-        if (last > R / 4 && R >= 4) group_pair<D, DP, DA, R, (R >= 4 ? R / 2 : 1)>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
-        else if (last > 1 && R >= 8) group_pair<D, DP, DA, R, (R >= 8 ? R / 4 : 1)>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
-        else group_pair<D, DP, DA, R, 1>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        if (last > R / 4 && R >= 4) group_pair<D, DP, DA, R, (R >= 4 ? R / 2 : 1), KF>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        else if (last > 1 && R >= 8) group_pair<D, DP, DA, R, (R >= 8 ? R / 4 : 1), KF>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
+        else group_pair<D, DP, DA, R, 1, KF>(Xs, w0, w1, lane, alist, g * R, A, sy, res);
         wb[warp][g][lane] = res[0];
         wb[warp][g + 1][lane] = res[1];
         break;
       }
       const int cnt = min(R, A - g * R);
       float res;
-      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 1) res = group_partial<D, DP, DA, 2>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else res = group_partial<D, DP, DA, 1>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 1) res = group_partial<D, DP, DA, 2, KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else res = group_partial<D, DP, DA, 1, KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
       wb[warp][g][lane] = res;
     }
     __syncthreads();
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   cluster.sync();
 }
 
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF>
 static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it, int32_t* conv,
                                   int32_t* state, const int32_t* list, const int32_t* S_ptr,
                                   int clusters, int32_t* hist, int target, int max_iter,
@@ -408,7 +408,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA>, Xs, n, y, it, conv, state, list,
+  return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA, KF>, Xs, n, y, it, conv, state, list,
                             S_ptr, hist, target, max_iter, tol2_s, evals);
 }
 
@@ -425,7 +425,9 @@ static int max_clusters_t() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int c = 0;
-  if (cudaOccupancyMaxActiveClusters(&c, ms_round_kernel<D, DP, DA>, &cfg) != cudaSuccess) c = 0;
+  if (cudaOccupancyMaxActiveClusters(&c, ms_round_kernel<D, DP, DA, kKernelGaussian>, &cfg) !=
+      cudaSuccess)
+    c = 0;
   return c;
 }
 
@@ -451,15 +453,22 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st) {
+                            cudaStream_t st, int kf) {
   switch (d) {
-    case 1: return launch_round_t<1, 4, 2>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 2: return launch_round_t<2, 4, 4>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 3: return launch_round_t<3, 4, 4>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 4: return launch_round_t<4, 4, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 5: return launch_round_t<5, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 6: return launch_round_t<6, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 7: return launch_round_t<7, 8, 8>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 1: return kf ? launch_round_t<1, 4, 2, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<1, 4, 2, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 2: return kf ? launch_round_t<2, 4, 4, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<2, 4, 4, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 3: return kf ? launch_round_t<3, 4, 4, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<3, 4, 4, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 4: return kf ? launch_round_t<4, 4, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<4, 4, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 5: return kf ? launch_round_t<5, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<5, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 6: return kf ? launch_round_t<6, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<6, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 7: return kf ? launch_round_t<7, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
+                 : launch_round_t<7, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -476,7 +485,7 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
 // order the second prune).  Partial buffers are double-buffered, so one
 // cluster barrier per update suffices.
 // ---------------------------------------------------------------------------
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF>
 __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     ms_refine_kernel(const float* __restrict__ Xs, int n, const float* __restrict__ y,
                      const int32_t* __restrict__ kept, const int32_t* __restrict__ accepted,
@@ -548,11 +557,11 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     for (int g = 0; g < G; ++g) {
       const int cnt = min(R, A - g * R);
       float res;
-      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R)>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else if (cnt > 1) res = group_partial<D, DP, DA, 2>(Xs, w0, w1, lane, alist, g * R, A, sy);
-      else res = group_partial<D, DP, DA, 1>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      if (cnt > 8 && R >= 16) res = group_partial<D, DP, DA, (R >= 16 ? 16 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 4 && R >= 8) res = group_partial<D, DP, DA, (R >= 8 ? 8 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 2 && R >= 4) res = group_partial<D, DP, DA, (R >= 4 ? 4 : R), KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else if (cnt > 1) res = group_partial<D, DP, DA, 2, KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
+      else res = group_partial<D, DP, DA, 1, KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
       wb[warp][g][lane] = res;
     }
     __syncthreads();
@@ -613,7 +622,7 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   cluster.sync();
 }
 
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF>
 static cudaError_t launch_refine_t(const float* Xs, int n, const float* y, const int32_t* kept,
                                    const int32_t* accepted, const int32_t* M_ptr, int clusters,
                                    double* ym, float* yf, double* mscore, double tol2_s,
@@ -630,7 +639,7 @@ static cudaError_t launch_refine_t(const float* Xs, int n, const float* y, const
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, ms_refine_kernel<D, DP, DA>, Xs, n, y, kept, accepted, M_ptr,
+  return cudaLaunchKernelEx(&cfg, ms_refine_kernel<D, DP, DA, KF>, Xs, n, y, kept, accepted, M_ptr,
                             ym, yf, mscore, tol2_s, max_iter, iters_out, evals);
 }
 
@@ -638,15 +647,22 @@ cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
                              int clusters, double* ym, float* yf, double* mscore, double tol2_s,
                              int max_iter, int32_t* iters_out, unsigned long long* evals,
-                             cudaStream_t st) {
+                             cudaStream_t st, int kf) {
   switch (d) {
-    case 1: return launch_refine_t<1, 4, 2>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 2: return launch_refine_t<2, 4, 4>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 3: return launch_refine_t<3, 4, 4>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 4: return launch_refine_t<4, 4, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 5: return launch_refine_t<5, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 6: return launch_refine_t<6, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 7: return launch_refine_t<7, 8, 8>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 1: return kf ? launch_refine_t<1, 4, 2, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<1, 4, 2, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 2: return kf ? launch_refine_t<2, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<2, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 3: return kf ? launch_refine_t<3, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<3, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 4: return kf ? launch_refine_t<4, 4, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<4, 4, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 5: return kf ? launch_refine_t<5, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<5, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 6: return kf ? launch_refine_t<6, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<6, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 7: return kf ? launch_refine_t<7, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
+                 : launch_refine_t<7, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -24,7 +24,7 @@ namespace fms {
 // R = 32 / DA seeds per warp task.  Each lane keeps a ring of four points in
 // flight (the loads for points i+4..i+7 are issued before points i..i+3 are
 // evaluated), which hides the L1/L2 latency of the point stream.
-template <int D, int DP, int DA>
+template <int D, int DP, int DA, int KF>
 __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs, int64_t n,
                                                     const float* __restrict__ y,
                                                     const int32_t* __restrict__ active,
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
     const int c = (int)(task / G);
     const int j0 = c * Lc;
     const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
-    lowd_task<D, DP, DA>(Xs, j0, j1, y, active, s, g, c, part, lane);
+    lowd_task<D, DP, DA, KF>(Xs, j0, j1, y, active, s, g, c, part, lane);
   }
 }
 
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
 // are read with warp-uniform (broadcast) loads, so no cross-lane reduction is
 // needed.  DPAD is the padded dimension (pad coordinates are zero on both
 // sides and contribute nothing); DA = DPAD + 4 accumulators per seed in part.
-template <int DPAD, int RG>
+template <int DPAD, int RG, int KF>
 __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs, int64_t n,
                                                     int DP, const float* __restrict__ y,
                                                     const int32_t* __restrict__ active,
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
     const int c = (int)(task / G);
     const int j0 = c * Lc;
     const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
-    wide_task<DPAD, RG>(Xs, DP, j0, j1, y, active, s, g, c, part, lane, p_lo);
+    wide_task<DPAD, RG, KF>(Xs, DP, j0, j1, y, active, s, g, c, part, lane, p_lo);
   }
 }
 
@@ -119,19 +119,19 @@ int step_resident_warps_per_sm(int d) {
   int blocks = 0, threads = 256;
   cudaError_t e = cudaSuccess;
   switch (d) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<1, 4, 2>, 256, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<2, 4, 4>, 256, 0); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<3, 4, 4>, 256, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<4, 4, 8>, 256, 0); break;
-    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<5, 8, 8>, 256, 0); break;
-    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<6, 8, 8>, 256, 0); break;
-    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<7, 8, 8>, 256, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<1, 4, 2, 0>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<2, 4, 4, 0>, 256, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<3, 4, 4, 0>, 256, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<4, 4, 8, 0>, 256, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<5, 8, 8, 0>, 256, 0); break;
+    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<6, 8, 8, 0>, 256, 0); break;
+    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<7, 8, 8, 0>, 256, 0); break;
     default:
       threads = 128;
-      if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<8, 4>, 128, 0);
-      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<16, 2>, 128, 0);
-      else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1>, 128, 0);
-      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1>, 128, 0);
+      if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<8, 4, 0>, 128, 0);
+      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<16, 2, 0>, 128, 0);
+      else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1, 0>, 128, 0);
+      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1, 0>, 128, 0);
       break;
   }
   if (e != cudaSuccess || blocks < 1) blocks = 1;
@@ -139,32 +139,45 @@ int step_resident_warps_per_sm(int d) {
   return cache[d];
 }
 
-cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
-                           const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
-                           const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
-                           int32_t* s_log, const int32_t* p_lo_ptr) {
+template <int KF>
+static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, const float* y,
+                                   const int32_t* active, const int32_t* s_ptr,
+                                   const int32_t* C_ptr, const int32_t* Lc_ptr, float* part,
+                                   int target_warps, cudaStream_t st, int32_t* s_log,
+                                   const int32_t* p_lo_ptr) {
   const dim3 g((target_warps + 7) / 8);
   const int grid_ctas = (int)g.x;
   switch (d) {
-    case 1: ms_step_lowd<1, 4, 2><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 2: ms_step_lowd<2, 4, 4><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 3: ms_step_lowd<3, 4, 4><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 4: ms_step_lowd<4, 4, 8><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 5: ms_step_lowd<5, 8, 8><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 6: ms_step_lowd<6, 8, 8><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
-    case 7: ms_step_lowd<7, 8, 8><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 1: ms_step_lowd<1, 4, 2, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 2: ms_step_lowd<2, 4, 4, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 3: ms_step_lowd<3, 4, 4, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 4: ms_step_lowd<4, 4, 8, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 5: ms_step_lowd<5, 8, 8, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 6: ms_step_lowd<6, 8, 8, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
+    case 7: ms_step_lowd<7, 8, 8, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
     default:
       if (d <= 8)
-        ms_step_wide<8, 4><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<8, 4, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 16)
-        ms_step_wide<16, 2><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<16, 2, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 32)
-        ms_step_wide<32, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<32, 1, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else
-        ms_step_wide<64, 1><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<64, 1, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
+                           const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
+                           const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
+                           int32_t* s_log, const int32_t* p_lo_ptr, int kf) {
+  if (kf == kKernelFlat)
+    return launch_ms_step_t<kKernelFlat>(Xs, n, d, DP, y, active, s_ptr, C_ptr, Lc_ptr, part,
+                                         target_warps, st, s_log, p_lo_ptr);
+  return launch_ms_step_t<kKernelGaussian>(Xs, n, d, DP, y, active, s_ptr, C_ptr, Lc_ptr, part,
+                                           target_warps, st, s_log, p_lo_ptr);
 }
 
 }  // namespace fms

@@ -495,6 +495,31 @@ def bench_extra(args):
                           "round_kernel_evals_per_s": st["round_evals"] / max(st["round_kernel_ms"], 1e-9) * 1e3,
                           "phase_ms": st["phase_ms"]}
         line["value"] = line["flat"]["ms"]
+    elif args.workload == "frames_3d":
+        # N3: a frame sequence (8 frames x 200K points, 20 drifting blobs) with the
+        # paper's seed-count carry-over (H = 32) against starting every frame afresh
+        frames = fi.drifting_frames(seed=0, frames=8, n=200_000, k=10, sigma=2.0, box=200.0)
+        Fx = torch.from_numpy(np.stack(frames)).cuda()
+        line.update({"metric": "ms per frame, 8 frames x 200K points (3-D, 10 drifting blobs), "
+                               "768 initial seeds, seed-count carry-over",
+                     "unit": "ms"})
+        for label, kw in (("carry_H32", dict(H=32.0, n_initial=768)),
+                          ("fresh_each_frame", dict(H=32.0, n_initial=768, fresh=True))):
+            fresh = kw.pop("fresh", False)
+            ws = fms.Workspace(fms.workspace_size(Fx.shape[1], 3), Fx.device)
+            if fresh:
+                run = lambda: [fms.cluster(Fx[f], 5.0, 5e-3, 300, n_initial=768, workspace=ws)
+                               for f in range(Fx.shape[0])]
+            else:
+                run = lambda: fms.cluster_frames(Fx, 5.0, 5e-3, 300, workspace=ws, **kw)
+            r = run()
+            ms, _ = _events_ms(run, max(3, min(20, args.steps)), flush)
+            rec = {"ms_per_frame": ms / Fx.shape[0]}
+            if not fresh:
+                rec["seed_counts"] = r.seed_counts
+                rec["n_modes"] = [int(m.shape[0]) for m in r.modes]
+            line[label] = rec
+        line["value"] = line["carry_H32"]["ms_per_frame"]
     elif args.workload == "step_wide":
         # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
         peaks = measured_peaks()
@@ -538,7 +563,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
-                             "embedding_32d", "step_wide", "pixels_rgb", "flat_3d"],
+                             "embedding_32d", "step_wide", "pixels_rgb", "flat_3d", "frames_3d"],
                     help="paper_3d is the headline line; the others print one line of "
                          "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",

@@ -235,6 +235,24 @@ def pixels_rgb(seed: int = 0, height: int = 512, width: int = 512, k: int = 12,
                     gamma=0.95)
 
 
+def drifting_frames(seed: int = 0, frames: int = 8, n: int = 65_536, k: int = 10, d: int = 3,
+                    sigma: float = 2.0, box: float = 200.0, drift: float = 0.5):
+    """A synthetic frame sequence: k Gaussian blobs whose centres move by a
+    small random step (|step| ~ drift) from frame to frame; each frame draws n
+    fresh points (equal blob proportions).  Stands in for the paper's video
+    tracking use, for which it gives no data."""
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(0.0, box, size=(k, d))
+    out = []
+    sizes = np.full(k, n // k, dtype=np.int64)
+    sizes[: n % k] += 1
+    for _ in range(frames):
+        X, lab = blobs(rng, centers, sigma, sizes)
+        out.append(_as_points(X))
+        centers = centers + rng.standard_normal((k, d)) * drift
+    return out
+
+
 WORKLOADS = {
     "plain_2d": plain_2d,
     "paper_3d": paper_3d,

@@ -209,6 +209,34 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
                                size_t workspace_bytes, fms_stats* stats, void* stream);
 
 /*
+ * Faster Mean-shift over a sequence of F frames of n points each (Sec. II-D,
+ * the video / tracking use).  Frame f is clustered exactly as fms_cluster with
+ * opt->n_initial = N_f (doubling inside the frame while N < L*M as usual),
+ * N_0 = opt->n_initial (0 -> 128).  When frame f ends with N seeds and M
+ * modes, the next frame starts with N_{f+1} = N - M if N > H*M, else N (the
+ * paper's seed reduction for nearly identical consecutive frames).
+ *   frames          [F][n][d] float32, device.
+ *   H               seed-reduction factor; <= 0 -> 32 (the paper's value).
+ *   out_modes       [F][max_modes][d] device; out_n_modes [F] host;
+ *   out_labels      [F][n] device; out_margins [F][n] device, nullable;
+ *   out_seed_counts [F] host, nullable: N_f, the seed count frame f started with.
+ *   workspace       >= fms_workspace_size(n, d, opt) bytes (reused by every
+ *                   frame) or NULL (allocated once on `stream`).
+ *   stats           nullable: iterations, rounds, evaluations and launches
+ *                   summed over the frames; the other fields of the last frame.
+ * opt->all_seeds and opt->seed_indices fix N and are rejected.  The call
+ * synchronises once per frame: the next frame's seed count is decided on the
+ * host, as in the paper's flowchart.  FMS_ERR_CAPACITY if any frame had more
+ * than max_modes modes (all frames are still processed).
+ */
+fms_status fms_cluster_frames(const float* frames, int32_t F, int64_t n, int32_t d, float h,
+                              float tol, int32_t max_iter, const fms_options* opt, float H,
+                              float* out_modes, int32_t max_modes, int32_t* out_n_modes,
+                              int32_t* out_labels, float* out_margins, int32_t* out_seed_counts,
+                              void* workspace, size_t workspace_bytes, fms_stats* stats,
+                              void* stream);
+
+/*
  * Seed Selection (Alg. 2 line 2): writes entries [start, start+count) of a
  * keyed pseudo-random permutation pi of [0, n) to out_indices (device int32).
  * pi(i) applies a balanced 6-round Feistel network on 2*hb bits (4^hb the

@@ -391,6 +391,29 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
                         seed_pos=pos, kept=kept, premerge_modes=modes0, iters=max(tstars))
 
 
+def next_frame_seed_count(N, M, H=32.0):
+    """Seed count carried to the next frame (Sec. II-D, video use): when the
+    frame ended with N seeds and M modes and N > H*M, the next frame starts
+    with N - M seeds; otherwise with N."""
+    return int(N - M) if N > H * M else int(N)
+
+
+def cluster_frames(frames, h, tol, max_iter, *, n_initial=128, L=8.0, H=32.0, **kw):
+    """Faster Mean-shift over a sequence of frames (Sec. II-D): each frame is
+    clustered by `cluster` starting from the seed count carried over from the
+    previous frame (doubling inside a frame while N < L*M as usual); the count
+    carried on is reduced by M when N > H*M.  Returns (per-frame results,
+    starting seed counts)."""
+    out, starts = [], []
+    N = int(n_initial)
+    for X in frames:
+        starts.append(N)
+        r = cluster(X, h, tol, max_iter, n_initial=N, L=L, **kw)
+        out.append(r)
+        N = max(1, next_frame_seed_count(r.n_seeds, r.modes.shape[0], H))
+    return out, starts
+
+
 # ----------------------------------------------------------------------------
 # Unrolled steps and their adjoint (north-star pattern; no paper counterpart)
 # ----------------------------------------------------------------------------

@@ -76,6 +76,10 @@ _lib.fms_cluster.restype = ctypes.c_int
 _lib.fms_cluster.argtypes = [_P, _I64, _I32, _F32, _F32, _I32, ctypes.POINTER(FmsOptions), _P,
                              _I32, ctypes.POINTER(_I32), _P, _P, _P, _SZ,
                              ctypes.POINTER(FmsStats), _P]
+_lib.fms_cluster_frames.restype = ctypes.c_int
+_lib.fms_cluster_frames.argtypes = [_P, _I32, _I64, _I32, _F32, _F32, _I32,
+                                    ctypes.POINTER(FmsOptions), _F32, _P, _I32, _P, _P, _P, _P,
+                                    _P, _SZ, ctypes.POINTER(FmsStats), _P]
 _lib.fms_select_seeds.restype = ctypes.c_int
 _lib.fms_select_seeds.argtypes = [_I64, ctypes.c_uint64, _I64, _I64, _P, _P]
 _lib.fms_step_workspace_size.restype = _SZ
@@ -205,6 +209,49 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
     M = nm.value
     return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar,
                          stats=st.as_dict(), status=code)
+
+
+@dataclass
+class FramesResult:
+    modes: list          # per frame: [M_f, d] tensor
+    labels: torch.Tensor  # [F, n]
+    margins: torch.Tensor
+    seed_counts: list    # N_f, the seed count frame f started with
+    stats: dict
+    status: int
+
+
+def cluster_frames(frames, h: float, tol: float = 0.0, max_iter: int = 300, *, H=32.0,
+                   n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0, skip_refine=False,
+                   rng_seed=0, max_modes=256, precision="auto", kernel="gaussian",
+                   workspace: Workspace = None) -> FramesResult:
+    """Faster Mean-shift over a frame sequence (fms_cluster_frames): `frames`
+    is a [F, n, d] CUDA tensor or a list of F [n, d] tensors."""
+    if isinstance(frames, (list, tuple)):
+        frames = torch.stack([_points(f) for f in frames])
+    frames = frames.contiguous().float()
+    F, n, d = frames.shape
+    o = make_options(n_initial=n_initial, L=L, gamma=gamma, merge_radius=merge_radius,
+                     skip_refine=skip_refine, rng_seed=rng_seed, precision=precision,
+                     kernel=kernel)
+    cap = max(int(max_modes), 1)
+    modes = torch.empty((F, cap, d), dtype=torch.float32, device=frames.device)
+    labels = torch.empty((F, n), dtype=torch.int32, device=frames.device)
+    mar = torch.empty((F, n), dtype=torch.float32, device=frames.device)
+    nm = (_I32 * F)()
+    starts = (_I32 * F)()
+    need = int(_lib.fms_workspace_size(n, d, ctypes.byref(o)))
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, frames.device)
+    st = FmsStats()
+    code = _lib.fms_cluster_frames(_ptr(frames), F, n, d, float(h), float(tol), int(max_iter),
+                                   ctypes.byref(o), float(H), _ptr(modes), cap, nm, _ptr(labels),
+                                   _ptr(mar), starts, _ptr(workspace.buf), workspace.nbytes,
+                                   ctypes.byref(st), _stream())
+    if code not in (FMS_OK, FMS_ERR_CAPACITY):
+        raise FmsError(code, "fms_cluster_frames")
+    return FramesResult(modes=[modes[f, : min(nm[f], cap)] for f in range(F)], labels=labels,
+                        margins=mar, seed_counts=list(starts), stats=st.as_dict(), status=code)
 
 
 def select_seeds(n: int, rng_seed: int, start: int, count: int, device="cuda") -> torch.Tensor:

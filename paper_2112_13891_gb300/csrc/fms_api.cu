@@ -606,6 +606,70 @@ done:
   return rc;
 }
 
+fms_status fms_cluster_frames(const float* frames, int32_t F, int64_t n, int32_t d, float h,
+                              float tol, int32_t max_iter, const fms_options* opt_in, float H,
+                              float* out_modes, int32_t max_modes, int32_t* out_n_modes,
+                              int32_t* out_labels, float* out_margins, int32_t* out_seed_counts,
+                              void* workspace, size_t workspace_bytes, fms_stats* stats,
+                              void* stream_) {
+  fms_options o;
+  fill_defaults(opt_in, &o);
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!frames || F < 1 || !out_n_modes || !out_labels || n < 1 || n > INT32_MAX || d < 1 ||
+      d > FMS_MAX_DIM || o.all_seeds || o.seed_indices || max_modes < 0 ||
+      (max_modes > 0 && !out_modes))
+    return FMS_ERR_INVALID_ARG;
+  if (!(H > 0.0f)) H = 32.0f;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const size_t need = fms_workspace_size(n, d, &o);
+  if (need == 0) return FMS_ERR_INVALID_ARG;
+  void* ws = workspace;
+  bool owns = false;
+  if (ws) {
+    if (workspace_bytes < need) return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns = true;
+    workspace_bytes = need;
+  }
+  fms_status rc = FMS_OK;
+  int64_t N = o.n_initial;
+  for (int32_t f = 0; f < F; ++f) {
+    fms_options of = o;
+    of.n_initial = (int32_t)(N < n ? N : n);
+    if (out_seed_counts) out_seed_counts[f] = of.n_initial;
+    fms_stats sf;
+    const fms_status r = fms_cluster(
+        frames + (size_t)f * (size_t)n * d, n, d, h, tol, max_iter, &of,
+        out_modes ? out_modes + (size_t)f * max_modes * d : nullptr, max_modes, out_n_modes + f,
+        out_labels + (size_t)f * n, out_margins ? out_margins + (size_t)f * n : nullptr, ws,
+        workspace_bytes, &sf, stream_);
+    if (r != FMS_OK && r != FMS_ERR_CAPACITY) {
+      rc = r;
+      break;
+    }
+    if (r == FMS_ERR_CAPACITY) rc = FMS_ERR_CAPACITY;
+    if (stats) {
+      const fms_stats acc = *stats;
+      *stats = sf;
+      stats->iterations += acc.iterations;
+      stats->rounds += acc.rounds;
+      stats->kernel_launches += acc.kernel_launches;
+      stats->evals += acc.evals;
+      stats->score_evals += acc.score_evals;
+    }
+    // Sec. II-D: N > H*M -> the next frame starts with N - M seeds
+    const int64_t Nf = sf.n_seeds_final, M = *(out_n_modes + f);
+    N = (double)Nf > (double)H * (double)M ? Nf - M : Nf;
+    if (N < 1) N = 1;
+  }
+  if (owns) {
+    cudaFreeAsync(ws, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == FMS_OK) rc = FMS_ERR_CUDA;
+  }
+  return rc;
+}
+
 fms_status fms_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
                             int32_t* out_indices, void* stream) {
   if (n < 1 || n > INT32_MAX || start < 0 || count < 0 || start + count > n ||

@@ -89,3 +89,29 @@ def test_plain_2d_planted_count():
     w = fi.plain_2d()
     res = orc.cluster(w.X, w.h, w.tol, w.max_iter, all_seeds=True)
     assert res.modes.shape[0] == 5
+
+
+def test_frame_seed_count_rule():
+    """Sec. II-D: N > H*M reduces the next frame's seed count by M."""
+    assert orc.next_frame_seed_count(512, 12, 32.0) == 500     # 512 > 384
+    assert orc.next_frame_seed_count(384, 12, 32.0) == 384     # not strictly larger
+    assert orc.next_frame_seed_count(128, 2, 32.0) == 126
+    assert orc.next_frame_seed_count(256, 20, 32.0) == 256
+
+
+def test_frames_equal_single_calls_with_carried_counts():
+    """Each frame's result is exactly cluster() started from the carried count."""
+    import fms_inputs as fi
+    frames = fi.drifting_frames(seed=3, frames=4, n=3000, k=3)
+    res, starts = orc.cluster_frames(frames, 5.0, 5e-3, 300, n_initial=256, H=32.0)
+    assert starts[0] == 256
+    for f, X in enumerate(frames):
+        one = orc.cluster(X, 5.0, 5e-3, 300, n_initial=starts[f])
+        assert np.array_equal(one.modes, res[f].modes)
+        assert np.array_equal(one.labels, res[f].labels)
+        if f + 1 < len(frames):
+            M = res[f].modes.shape[0]
+            N = res[f].n_seeds
+            assert starts[f + 1] == (N - M if N > 32.0 * M else N)
+    # few modes, many seeds: the count shrinks from frame to frame
+    assert starts[-1] < starts[0]

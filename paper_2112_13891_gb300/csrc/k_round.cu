@@ -112,6 +112,98 @@ __device__ __forceinline__ void reval(const float (&x)[D], const float (&ys)[R][
   }
 }
 
+// RR seeds in registers, evaluated two at a time with packed f32x2 arithmetic
+// (one FADD2/FMUL2/FFMA2 serves a pair of seeds against the same point).  For
+// a pair, nd = y - x = -(x - y) exactly (an FFMA with -1), the squared
+// distance, the weight and sum w are bit-identical to the scalar
+// exact-difference evaluation of reval, and the pair accumulates sum w (y - x)
+// = -sum w (x - y) exactly at every step (round-to-nearest is sign-symmetric),
+// so every seed's sums are the same bits as reval's.  An odd last seed takes
+// the scalar path.
+template <int D, int RR, int KF>
+struct SeedPack {
+  static constexpr int NP = RR / 2;
+  static constexpr int NPA = NP > 0 ? NP : 1;
+  float2 yp[NPA][D];
+  float2 Wp[NPA];
+  float2 Sp[NPA][D];   // sum w (y - x) of the pair
+  float y1[D], W1, S1[D];
+
+  __device__ __forceinline__ void load(const float (&ys)[RR][D]) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      Wp[p] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        yp[p][k] = make_float2(ys[2 * p][k], ys[2 * p + 1][k]);
+        Sp[p][k] = make_float2(0.f, 0.f);
+      }
+    }
+    W1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      y1[k] = (RR & 1) ? ys[RR - 1][k] : 0.f;
+      S1[k] = 0.f;
+    }
+  }
+
+  __device__ __forceinline__ void eval(const float (&x)[D]) {
+    float2 xx[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xx[k] = make_float2(x[k], x[k]);
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      float2 nd[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) nd[k] = __ffma2_rn(xx[k], m1, yp[p][k]);
+      float2 dd = __fmul2_rn(nd[0], nd[0]);
+#pragma unroll
+      for (int k = 1; k < D; ++k) dd = __ffma2_rn(nd[k], nd[k], dd);
+      const float2 w = make_float2(kweight<KF>(-dd.x), kweight<KF>(-dd.y));
+      Wp[p] = __fadd2_rn(Wp[p], w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) Sp[p][k] = __ffma2_rn(w, nd[k], Sp[p][k]);
+    }
+    if constexpr ((RR & 1) != 0) {
+      float dx[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) dx[k] = x[k] - y1[k];
+      float t = -dx[0] * dx[0];
+#pragma unroll
+      for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
+      const float w = kweight<KF>(t);
+      W1 += w;
+#pragma unroll
+      for (int k = 0; k < D; ++k) S1[k] = fmaf(w, dx[k], S1[k]);
+    }
+  }
+
+  // accumulators of seed r: acc[r][0] = sum w, acc[r][1 + k] = sum w (x - y)_k
+  template <int DA>
+  __device__ __forceinline__ void store(float (&acc)[RR][DA]) const {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      acc[2 * p][0] = Wp[p].x;
+      acc[2 * p + 1][0] = Wp[p].y;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        acc[2 * p][1 + k] = -Sp[p][k].x;
+        acc[2 * p + 1][1 + k] = -Sp[p][k].y;
+      }
+#pragma unroll
+      for (int k = D + 1; k < DA; ++k) acc[2 * p][k] = acc[2 * p + 1][k] = 0.f;
+    }
+    if constexpr ((RR & 1) != 0) {
+      acc[RR - 1][0] = W1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[RR - 1][1 + k] = S1[k];
+#pragma unroll
+      for (int k = D + 1; k < DA; ++k) acc[RR - 1][k] = 0.f;
+    }
+  }
+};
+
 // Partial sums of RR seeds (active positions a0..a0+RR-1, clamped to A-1)
 // over the points [w0, w1) handled by this warp: lane l returns accumulator
 // l % DA of seed l / DA (zero for seed slots beyond RR).  The arithmetic of a
@@ -127,11 +219,8 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
 #pragma unroll
     for (int k = 0; k < D; ++k) ys[r][k] = sy[i][k];
   }
-  float acc[RR][DA];
-#pragma unroll
-  for (int r = 0; r < RR; ++r)
-#pragma unroll
-    for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
+  SeedPack<D, RR, KF> sp;
+  sp.load(ys);
   int j = w0 + lane;
   RPt<DP> b0 = rload<DP>(Xs, j, w1), b1 = rload<DP>(Xs, j + 32, w1);
   RPt<DP> b2 = rload<DP>(Xs, j + 64, w1), b3 = rload<DP>(Xs, j + 96, w1);
@@ -143,14 +232,16 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
     b3 = rload<DP>(Xs, j + 224, w1);
     float x[D];
     rcoords<D, DP>(p0, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p1, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p2, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p3, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
   }
+  float acc[RR][DA];
+  sp.store(acc);
   float v[32];
 #pragma unroll
   for (int e = 0; e < 32; ++e) v[e] = 0.0f;
@@ -178,11 +269,8 @@ __device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0,
 #pragma unroll
     for (int k = 0; k < D; ++k) ys[r][k] = sy[i][k];
   }
-  float acc[RR][DA];
-#pragma unroll
-  for (int r = 0; r < RR; ++r)
-#pragma unroll
-    for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
+  SeedPack<D, RR, KF> sp;
+  sp.load(ys);
   int j = w0 + lane;
   RPt<DP> b0 = rload<DP>(Xs, j, w1), b1 = rload<DP>(Xs, j + 32, w1);
   RPt<DP> b2 = rload<DP>(Xs, j + 64, w1), b3 = rload<DP>(Xs, j + 96, w1);
@@ -194,14 +282,16 @@ __device__ __forceinline__ void group_pair(const float* __restrict__ Xs, int w0,
     b3 = rload<DP>(Xs, j + 224, w1);
     float x[D];
     rcoords<D, DP>(p0, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p1, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p2, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
     rcoords<D, DP>(p3, x);
-    reval<D, RR, DA, KF>(x, ys, acc);
+    sp.eval(x);
   }
+  float acc[RR][DA];
+  sp.store(acc);
   float v[32];
 #pragma unroll
   for (int r = 0; r < RA; ++r)

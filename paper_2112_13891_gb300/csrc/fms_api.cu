@@ -53,6 +53,24 @@ struct Layout {
 
 constexpr int kSlogCap = 4096;
 
+// Control region of a clustering call: IterCtl, MergeCtl, the refinement's
+// IterCtl and the status word at fixed offsets, so that one device -> host
+// copy into pinned memory reads all of them.
+constexpr size_t kCtlMergeOff = 256, kCtlRefineOff = 512, kCtlStatusOff = 768;
+constexpr size_t kCtlBlockBytes = 1024;
+static_assert(sizeof(IterCtl) <= kCtlMergeOff && sizeof(MergeCtl) <= 256 &&
+                  sizeof(IterCtl) <= 256,
+              "control region");
+
+// Pinned staging of the control region (one per host thread, kept for the
+// life of the thread): pageable destinations would make every readback a
+// staged, host-blocking copy.
+unsigned char* pinned_ctl() {
+  thread_local unsigned char* buf = nullptr;
+  if (!buf && cudaMallocHost(&buf, kCtlBlockBytes) != cudaSuccess) buf = nullptr;
+  return buf;
+}
+
 // Whether a call's seed updates start on the tensor-core step.
 bool use_tensor_step(int d, int32_t precision) {
   if (precision == FMS_PRECISION_TENSOR) return d >= 8 && d <= kTcMaxDim;
@@ -104,13 +122,14 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms, bool tensor) {
   L.off_modes_full = take((size_t)Ncap * d * 4);
   L.off_part = take(part_floats * 4);
   L.off_part64 = take(part64_doubles * 8);
-  L.off_ctl = take(sizeof(IterCtl));
-  L.off_mctl = take(sizeof(MergeCtl));
-  L.off_status = take(64);
+  // control blocks and the status word in one region, read back with one copy
+  L.off_ctl = take(kCtlBlockBytes);
+  L.off_mctl = L.off_ctl + kCtlMergeOff;
+  L.off_rctl = L.off_ctl + kCtlRefineOff;
+  L.off_status = L.off_ctl + kCtlStatusOff;
   L.off_slog = take((size_t)kSlogCap * 2 * 4);   // ms_step log, coarse step log
   L.off_yf = take((size_t)Ncap * L.DP * 4);
   L.off_ract = take((size_t)Ncap * 4);
-  L.off_rctl = take(sizeof(IterCtl));
   L.off_hist = take((size_t)(kHistCap + 2) * 4);
   L.off_S = take(64);
   L.off_img = take(tensor ? tc_image_bytes(n, d) : 0);
@@ -282,6 +301,27 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     int32_t* hist = at<int32_t>(ws, Lo.off_hist);
     int32_t* S_dev = at<int32_t>(ws, Lo.off_S);
     unsigned char* img = at<unsigned char>(ws, Lo.off_img);
+    unsigned char* hbuf = pinned_ctl();
+    // read the control region (pinned staging when available), then sync
+    auto readback = [&]() -> cudaError_t {
+      cudaError_t e;
+      if (hbuf) {
+        e = cudaMemcpyAsync(hbuf, ctl, kCtlBlockBytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        memcpy(&hctl, hbuf, sizeof(IterCtl));
+        memcpy(&hm, hbuf + kCtlMergeOff, sizeof(MergeCtl));
+        memcpy(&hrctl, hbuf + kCtlRefineOff, sizeof(IterCtl));
+        memcpy(&hstatus, hbuf + kCtlStatusOff, sizeof(uint32_t));
+        return cudaSuccess;
+      }
+      e = cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      return e;
+    };
     int32_t* tclog = slog + kSlogCap;
     Tiling tl_iter = Lo.tl;   // the seed-update loop (tensor-core chunking when on)
     tl_iter.tc_ctas = Lo.tc_ctas;
@@ -346,11 +386,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       return e;
     };
 
-    FMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IterCtl), st));
-    FMS_CUDA(cudaMemsetAsync(mctl, 0, sizeof(MergeCtl), st));
-    FMS_CUDA(cudaMemsetAsync(rctl, 0, sizeof(IterCtl), st));
+    FMS_CUDA(cudaMemsetAsync(ctl, 0, kCtlBlockBytes, st));   // ctl, mctl, rctl, status
     FMS_CUDA(cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, st));
-    FMS_CUDA(cudaMemsetAsync(status, 0, 64, st));
     if (o.profile)
       for (int i = 0; i < 5; ++i)
         if (cudaEventCreate(&phase_ev[i]) != cudaSuccess) {
@@ -422,9 +459,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                      max_iter, n, R, tl_iter, N, target, st, update_grid(N),
                                      coarse_tol2_s));
           }
-          FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
-          FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
-          FMS_CUDA(cudaStreamSynchronize(st));
+          FMS_CUDA(readback());
           if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
           if (hstatus & kStTimeout) {
             rc = FMS_ERR_TIMEOUT;
@@ -444,8 +479,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       // --- seed-count control (Sec. II-D) ---
       FMS_LAUNCH(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
       mark(2);
-      FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
-      FMS_CUDA(cudaStreamSynchronize(st));
+      FMS_CUDA(readback());
       phase_add(0, 0, 1);
       phase_add(1, 1, 2);
       K_last = hm.K;
@@ -484,8 +518,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                           rtol_s * rtol_s, kRefineMaxIter, 0, n, R, Lo.tl, hm.M,
                                           st));
         }
-        FMS_CUDA(cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
-        FMS_CUDA(cudaStreamSynchronize(st));
+        FMS_CUDA(readback());
         if (hrctl.done) break;
       }
       // density at the refined modes (FP64 sums over chunks), for the second prune
@@ -508,17 +541,13 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     mark(3);
     FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
     mark(4);
-    FMS_CUDA(cudaMemcpyAsync(&hm, mctl, sizeof(MergeCtl), cudaMemcpyDeviceToHost, st));
-    FMS_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
-    FMS_CUDA(cudaMemcpyAsync(&hrctl, rctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
-    FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> hslog(n_slog), htclog(n_tclog);
     if (n_slog > 0)
       FMS_CUDA(cudaMemcpyAsync(hslog.data(), slog, (size_t)n_slog * 4, cudaMemcpyDeviceToHost, st));
     if (n_tclog > 0)
       FMS_CUDA(cudaMemcpyAsync(htclog.data(), tclog, (size_t)n_tclog * 4, cudaMemcpyDeviceToHost,
                                st));
-    FMS_CUDA(cudaStreamSynchronize(st));
+    FMS_CUDA(readback());
     Mfinal = hm.Mr;
     *out_n_modes = Mfinal;
     if (hstatus & kStNonFinite) goto device_error;

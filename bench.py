@@ -148,6 +148,43 @@ def measured_peaks():
         return {}
 
 
+# Source files whose contents fix each profiled kernel's code: a stored DRAM
+# traffic figure counts only while their digest matches the one it was taken at.
+KERNEL_SOURCES = {
+    "ms_round": ["paper_2112_13891_gb300/csrc/k_round.cu",
+                 "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
+    "ms_step": ["paper_2112_13891_gb300/csrc/k_step.cu",
+                "paper_2112_13891_gb300/csrc/fms_step_body.cuh",
+                "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
+    "ms_step_tc": ["paper_2112_13891_gb300/csrc/k_step_tc.cu",
+                   "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
+}
+
+
+def source_digest(kname):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kname]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kname):
+    """DRAM bytes per launch from profiles/<kernel>_traffic.json, or None when
+    the file is missing or the kernel's sources changed since the capture."""
+    tfile = os.path.join(ROOT, "profiles", f"{kname}_traffic.json")
+    if not os.path.exists(tfile):
+        return None
+    try:
+        rec = json.load(open(tfile))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_digest") != source_digest(kname):
+        return None
+    return rec.get("bytes_per_launch")
+
+
 def run_oracle_sample(w, seconds=12.0):
     """Time the FP64 oracle's full clustering of the workload on the host cores."""
     import oracle as orc
@@ -270,13 +307,7 @@ def bench_fms(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ops_per_eval / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"{kname}_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = stored_traffic(kname)
     phases = {k: v / args.steps for k, v in zip(("rounds", "prunes", "refine", "labels"),
                                                prof["phase"])}
 

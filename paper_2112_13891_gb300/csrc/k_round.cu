@@ -26,9 +26,9 @@
 // read only delays a stop; no seed is ever stopped wrongly and the kept set is
 // exactly that of the synchronous rule.  Stopped seeds stay RUNNING with their
 // update count (a later round may resume them).  Rank 0 takes the count test
-// and the other ranks apply its decisions one update later (after the next
-// cluster barrier), so a stopped seed may make one extra update; it was
-// already beyond t*, and a resumed seed continues from its count.
+// during the update's point pass, with the counts read at the start of the
+// update, and every rank applies its decisions in the same update, after the
+// cluster barrier.
 #include <cooperative_groups.h>
 
 #include "fms_internal.cuh"
@@ -323,8 +323,9 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   __shared__ int sact[SMAX];   // 1: takes updates in this round
   __shared__ int alist[SMAX];
   // rank 0's Early-Stopping decisions: sstop[u & 1][i] == u marks seed i as
-  // stopped by the count test of update u (read by every rank after the next
-  // update's cluster barrier)
+  // stopped by the count test of update u, unless it converges or fails in
+  // that update (written before the update's cluster barrier, read by every
+  // rank after it)
   __shared__ int sstop[2][SMAX];
   __shared__ float wb[kRoundWarps][GMAX][32];
   __shared__ float cpart[2][SMAX][DA];   // this CTA's sums (by update parity), read by every rank
@@ -363,6 +364,10 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   __syncthreads();
 
   for (int guard = 0; guard <= max_iter; ++guard) {
+    // rank 0, warp 1: the convergence counts hist[1..32], read now and used
+    // after the pass (the load latency hides behind it)
+    int hv = 0;
+    if (rank == 0 && warp == 1 && lane < max_iter) hv = *((volatile int32_t*)hist + 1 + lane);
     // active list (identical in every CTA: built from replicated state)
     if (warp == 0) {
       int base = 0;
@@ -405,9 +410,32 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
       else res = group_partial<D, DP, DA, 1, KF>(Xs, w0, w1, lane, alist, g * R, A, sy);
       wb[warp][g][lane] = res;
     }
+    const int par = guard & 1;
+    if (rank == 0 && warp == 1) {
+      // count test of this update: a seed that will have made t updates and
+      // has not converged by then is past t* once count(t) = sum_{u <= t}
+      // hist[u] >= target.  count from the values read above (a count read
+      // earlier can only be smaller, so a stop can come late, never early)
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y2 = __shfl_up_sync(kFull, hv, o);
+        if (lane >= o) hv += y2;
+      }
+      const int c32 = __shfl_sync(kFull, hv, 31);
+      for (int a0 = 0; a0 < A; a0 += 32) {
+        const int a = a0 + lane;
+        const int i = alist[min(a, A - 1)];
+        const int t = sit[i] + 1;
+        int c = __shfl_sync(kFull, hv, min(t, 32) - 1);
+        if (a < A && t > 32) {
+          c = c32;
+          for (int u = 33; u <= min(t, max_iter); ++u) c += *((volatile int32_t*)hist + u);
+        }
+        if (a < A && c >= target) sstop[par][i] = guard;
+      }
+    }
     __syncthreads();
     // this CTA's sums, warps in order
-    const int par = guard & 1;
     for (int t = threadIdx.x; t < G * 32; t += blockDim.x) {
       const int g = t >> 5, l = t & 31;
       float sum = 0.0f;
@@ -416,20 +444,18 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
       if (a < A) cpart[par][a][l % DA] = sum;
     }
     cluster.sync();
-    // rank 0's count-test stops of the previous update take effect now, in
-    // every rank at the same point: such a seed has made one update more than
-    // the synchronous rule would give it.  That cannot change the outcome:
-    // count(k) >= target already fixes t* <= k, and a later round resumes the
-    // seed from its update count.
-    if (guard > 0)
-      for (int i = threadIdx.x; i < ns; i += blockDim.x)
-        if (cluster.map_shared_rank(&sstop[par ^ 1][0], 0)[i] == guard - 1) sact[i] = 0;
-    // cluster sums, ranks in order (every CTA computes the same totals)
+    // cluster sums, ranks in order (every CTA computes the same totals); the
+    // launch's cluster size is kClusterCtas, so all remote loads are issued
+    // before the adds
     for (int t = threadIdx.x; t < A * DA; t += blockDim.x) {
       const int a = t / DA, k = t - a * DA;
+      float part[kClusterCtas];
+#pragma unroll
+      for (int rr = 0; rr < kClusterCtas; ++rr)
+        part[rr] = cluster.map_shared_rank(&cpart[par][0][0], rr)[a * DA + k];
       float sum = 0.0f;
-      for (int rr = 0; rr < ncl; ++rr)
-        sum += cluster.map_shared_rank(&cpart[par][0][0], rr)[a * DA + k];
+#pragma unroll
+      for (int rr = 0; rr < kClusterCtas; ++rr) sum += part[rr];
       tot[a][k] = sum;
     }
     __syncthreads();
@@ -455,7 +481,12 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
       if (!ok) st = kFailed;
       else if (step2 <= tol2_s) st = kConverged;
       else if (t >= max_iter) st = kExhausted;
-      if (st != kRunning) sact[i] = 0;   // decided identically in every rank
+      // rank 0's count test of this update stops a seed that is still
+      // RUNNING; every rank reads the same decision after the barrier.  A
+      // stopped seed stays RUNNING with its update count (a later round may
+      // resume it)
+      const bool stop = cluster.map_shared_rank(&sstop[par][0], 0)[i] == guard;
+      if (st != kRunning || stop) sact[i] = 0;   // decided identically in every rank
       if (rank == 0) {
         const int64_t slot = sslot[i];
 #pragma unroll
@@ -466,12 +497,6 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
           atomicAdd(hist + t, 1);
         }
         state[slot] = st;
-        if (st == kRunning) {
-          // count(t) >= target: t* <= t, so this seed cannot be kept any more
-          int c = 0;
-          for (int u = 1; u <= t; ++u) c += *((volatile int32_t*)hist + u);
-          if (c >= target) sstop[par][i] = guard;
-        }
       }
     }
     if (rank == 0 && threadIdx.x == 0) atomicAdd(evals, (unsigned long long)A * (unsigned long long)n);
@@ -666,9 +691,13 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     cluster.sync();
     for (int t = threadIdx.x; t < A * DA; t += blockDim.x) {
       const int a = t / DA, k = t - a * DA;
+      double part[kClusterCtas];
+#pragma unroll
+      for (int rr = 0; rr < kClusterCtas; ++rr)
+        part[rr] = cluster.map_shared_rank(&cpart[buf][0][0], rr)[a * DA + k];
       double sum = 0.0;
-      for (int rr = 0; rr < ncl; ++rr)
-        sum += cluster.map_shared_rank(&cpart[buf][0][0], rr)[a * DA + k];
+#pragma unroll
+      for (int rr = 0; rr < kClusterCtas; ++rr) sum += part[rr];
       tot[a][k] = sum;
     }
     __syncthreads();

@@ -221,24 +221,25 @@ __device__ __forceinline__ float group_partial(const float* __restrict__ Xs, int
   }
   SeedPack<D, RR, KF> sp;
   sp.load(ys);
+  // NB point loads per lane in flight: with few seeds a point costs few
+  // instructions, so more loads must be in flight to cover the L2 latency.
+  // The lane's points are evaluated in increasing order whatever NB is (and
+  // points past w1 are far away, weight exactly 0), so a seed's sums have
+  // the same bits in every pass shape.
+  constexpr int NB = DP == 4 ? (RR <= 2 ? 12 : (RR <= 4 ? 6 : 4)) : (RR <= 1 ? 8 : 4);
   int j = w0 + lane;
-  RPt<DP> b0 = rload<DP>(Xs, j, w1), b1 = rload<DP>(Xs, j + 32, w1);
-  RPt<DP> b2 = rload<DP>(Xs, j + 64, w1), b3 = rload<DP>(Xs, j + 96, w1);
-  for (; j < w1; j += 128) {
-    const RPt<DP> p0 = b0, p1 = b1, p2 = b2, p3 = b3;
-    b0 = rload<DP>(Xs, j + 128, w1);
-    b1 = rload<DP>(Xs, j + 160, w1);
-    b2 = rload<DP>(Xs, j + 192, w1);
-    b3 = rload<DP>(Xs, j + 224, w1);
-    float x[D];
-    rcoords<D, DP>(p0, x);
-    sp.eval(x);
-    rcoords<D, DP>(p1, x);
-    sp.eval(x);
-    rcoords<D, DP>(p2, x);
-    sp.eval(x);
-    rcoords<D, DP>(p3, x);
-    sp.eval(x);
+  RPt<DP> b[NB];
+#pragma unroll
+  for (int u = 0; u < NB; ++u) b[u] = rload<DP>(Xs, j + 32 * u, w1);
+  for (; j < w1; j += 32 * NB) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const RPt<DP> p = b[u];
+      b[u] = rload<DP>(Xs, j + 32 * (NB + u), w1);
+      float x[D];
+      rcoords<D, DP>(p, x);
+      sp.eval(x);
+    }
   }
   float acc[RR][DA];
   sp.store(acc);

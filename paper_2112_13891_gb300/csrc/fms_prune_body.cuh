@@ -9,7 +9,8 @@ namespace fms {
 // (1) the block sorts the candidates by (score descending, rank ascending)
 // with a bitonic sort; (2) the sorted list is walked 32 candidates at a time:
 // the batch's coordinates are staged in a transposed, padded tile (one
-// candidate per lane, conflict-free per-lane reads), every warp tests the
+// candidate per lane, conflict-free per-lane reads; two tiles, warp 1 stages
+// the next batch while the current one is tested), every warp tests the
 // batch against its share of the modes accepted so far, and one warp resolves
 // the survivors in order (the lowest surviving lane is accepted and removes
 // the later lanes within r).  The accepted set and its order are those of the
@@ -28,7 +29,7 @@ __host__ __device__ inline size_t greedy_keys_bytes(int P) {
 template <typename PT, typename ST>
 __host__ __device__ inline size_t greedy_sorted_smem(int K, int d, int P, bool acc_in_smem) {
   return greedy_keys_bytes<ST>(P) +
-         (size_t)kPruneMaxDim * kPruneTileStride * sizeof(PT) +
+         2 * (size_t)kPruneMaxDim * kPruneTileStride * sizeof(PT) +
          (acc_in_smem ? (size_t)K * d * sizeof(PT) : 0);
 }
 
@@ -38,11 +39,13 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
                                    int DP, int d, PT r2, int32_t* __restrict__ accepted,
                                    int32_t* __restrict__ M_out, int P, unsigned char* smem,
                                    bool acc_in_smem = true) {
-  // layout: keys[P] (ST), idx[P] (int), scratch[64] (int), ctile[64 x 33] (PT), [apos[K*d] (PT)]
+  // layout: keys[P] (ST), idx[P] (int), scratch[64] (int), ctile[2][64 x 33] (PT),
+  // [apos[K*d] (PT)]
   ST* keys = reinterpret_cast<ST*>(smem);
   int* idx = reinterpret_cast<int*>(keys + P);
-  PT* ctile = reinterpret_cast<PT*>(smem + greedy_keys_bytes<ST>(P));
-  PT* apos = ctile + kPruneMaxDim * kPruneTileStride;
+  PT* ctile2 = reinterpret_cast<PT*>(smem + greedy_keys_bytes<ST>(P));
+  constexpr int kTile = kPruneMaxDim * kPruneTileStride;
+  PT* apos = ctile2 + 2 * kTile;
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     keys[i] = i < K ? score[i] : (ST)-INFINITY;
     idx[i] = i < K ? i : INT32_MAX;
@@ -78,19 +81,24 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
   };
   int* s_dead = idx + P;                             // scratch: batch suppression flags
   int* s_nacc = s_dead + 32;                         // scratch: modes accepted so far
-  if (threadIdx.x == 0) *s_nacc = 0;
-  for (int base = 0; base < K; base += 32) {
+  // warp w stages batch `base` (lane c: sorted candidate base + c; tile[k * 33 + c] is
+  // its coordinate k)
+  auto stage = [&](int base, PT* tile) {
     const int i = base + lane;
-    // stage the batch (warp 0: lane c loads sorted candidate base + c; ctile[k * 33 + c] is
-    // its coordinate k) and clear the suppression flags
-    if (warp == 0) {
-      if (i < K) {
-        const PT* src = pos + row_of(idx[i]) * DP;
-        for (int k = 0; k < d; ++k) ctile[k * kPruneTileStride + lane] = src[k];
-      }
-      s_dead[lane] = 0;
+    if (i < K) {
+      const PT* src = pos + row_of(idx[i]) * DP;
+      for (int k = 0; k < d; ++k) tile[k * kPruneTileStride + lane] = src[k];
     }
-    __syncthreads();
+  };
+  if (threadIdx.x == 0) *s_nacc = 0;
+  if (warp == 0) {
+    stage(0, ctile2);
+    s_dead[lane] = 0;
+  }
+  for (int base = 0, b = 0; base < K; base += 32, ++b) {
+    const int i = base + lane;
+    PT* ctile = ctile2 + (b & 1) * kTile;
+    __syncthreads();   // this batch's tile and cleared flags are visible
     const int nacc = *s_nacc;
     // every warp tests the batch against its share of the modes accepted so far
     if (i < K) {
@@ -106,6 +114,8 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
       }
       if (dead) s_dead[lane] = 1;
     }
+    // the next batch's tile (its last readers finished before this batch's barrier)
+    if (warp == (nwarps > 1 ? 1 : 0) && base + 32 < K) stage(base + 32, ctile2 + ((b + 1) & 1) * kTile);
     __syncthreads();
     if (warp == 0) {
       // survivors of the batch, resolved in order by one warp
@@ -135,10 +145,11 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
           }
         }
       }
+      s_dead[lane] = 0;
       if (lane == 0) *s_nacc = na;
     }
-    __syncthreads();   // accepted modes visible, the tile is rewritten by the next batch
   }
+  __syncthreads();
   if (threadIdx.x == 0) *M_out = *s_nacc;
 }
 

@@ -596,10 +596,12 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
 // against yf over their fixed sub-slices (exactly as in ms_round); the warp
 // sums are combined in FP64 across warps and across ranks; then
 //   ym <- ym + S/W - (ym - yf)   (= m(yf))
-// and a mode stops once ||step|| <= tol (FP64) or after max_iter updates.  A
-// final pass records W = sum_j w_j at each refined mode (its density, used to
-// order the second prune).  Partial buffers are double-buffered, so one
-// cluster barrier per update suffices.
+// and a mode stops once ||step|| <= tol (FP64) or after max_iter updates.
+// The density that orders the second prune is W = sum_j w_j of the mode's
+// last update, i.e. at the position one step (<= tol) before the refined
+// mode; the density is stationary there, so the difference is O(tol^2)
+// relative, far below the FP32 weights' rounding.  Partial buffers are
+// double-buffered, so one cluster barrier per update suffices.
 // ---------------------------------------------------------------------------
 template <int D, int DP, int DA, int KF>
 __global__ void __launch_bounds__(kRoundWarps * 32, 1)
@@ -647,14 +649,12 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
   __syncthreads();
 
   int iters = 0;
-  // pass 0..max_iter-1: updates; the pass after the loop: densities only
-  for (int pass = 0;; ++pass) {
-    const bool score_pass = (pass >= max_iter);
+  for (int pass = 0; pass < max_iter; ++pass) {
     if (warp == 0) {
       int base = 0;
       for (int b0 = 0; b0 < ns; b0 += 32) {
         const int i = b0 + lane;
-        const int take = (i < ns) && (score_pass || sact[i]);
+        const int take = (i < ns) && sact[i];
         const unsigned m = __ballot_sync(kFull, take);
         if (take) alist[base + __popc(m & ((1u << lane) - 1))] = i;
         base += __popc(m);
@@ -662,13 +662,8 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
       if (lane == 0) sA = base;
     }
     __syncthreads();
-    int A = sA;
-    if (A == 0 && !score_pass) {
-      // every mode has converged: go to the density pass
-      pass = max_iter - 1;
-      __syncthreads();
-      continue;
-    }
+    const int A = sA;
+    if (A == 0) break;   // every mode has stopped
     const int G = (A + R - 1) / R;
     for (int g = 0; g < G; ++g) {
       const int cnt = min(R, A - g * R);
@@ -704,15 +699,14 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     __syncthreads();
     if (rank == 0 && threadIdx.x == 0 && A > 0)
       atomicAdd(evals, (unsigned long long)A * (unsigned long long)n);
-    if (score_pass) {
-      if (rank == 0)
-        for (int a = threadIdx.x; a < A; a += blockDim.x) mscore[s0 + alist[a]] = tot[a][0];
-      break;
-    }
     ++iters;
     for (int a = threadIdx.x; a < A; a += blockDim.x) {
       const int i = alist[a];
       const double W = tot[a][0];
+      // the density recorded for the mode: sum w at the position of its last
+      // update (the step from there is <= the refinement tolerance, and at a
+      // stationary point of the density that moves it by O(step^2))
+      if (rank == 0) mscore[s0 + i] = W;
       bool ok = W > 0.0 && isfinite(W);
       double step2 = 0.0, dl[D];
 #pragma unroll

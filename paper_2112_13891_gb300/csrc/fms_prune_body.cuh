@@ -6,24 +6,29 @@
 namespace fms {
 
 // Same prune with the candidates in shared memory, in two parallel stages:
-// (1) the block sorts the candidates by (score descending, rank ascending)
-// with a bitonic sort; (2) the sorted list is walked 32 candidates at a time:
-// the batch's coordinates are staged in a transposed, padded tile (one
-// candidate per lane, conflict-free per-lane reads; two tiles, warp 1 stages
-// the next batch while the current one is tested), every warp tests the
-// batch against its share of the modes accepted so far, and one warp resolves
-// the survivors in order (the lowest surviving lane is accepted and removes
-// the later lanes within r).  The accepted set and its order are those of the
+// (1) the block sorts the candidates by (score descending, rank ascending):
+// up to 512 candidates by counting, for each, the candidates ordered before
+// it (one pass, no barriers between stages), else with a bitonic sort; (2) the
+// sorted list is walked 32 candidates at a time: the batch's coordinates are
+// staged in a transposed, padded tile (one candidate per lane, conflict-free
+// per-lane reads; two tiles, warp 1 stages the next batch while the current
+// one is tested), every warp tests the batch against its share of the modes
+// accepted so far, warp v also records which batch members lie within r of
+// member v (a 32-bit mask), and one warp resolves the survivors in order with
+// those masks (the lowest surviving lane is accepted and removes the lanes
+// within r of it).  The accepted set and its order are those of the
 // one-by-one greedy visit.  With acc_in_smem the accepted modes' coordinates
 // are kept in shared memory, else read back from global memory (all lanes
 // read the same row).
 constexpr int kPruneTileStride = 33;   // padded row of the transposed batch tile
 constexpr int kPruneMaxDim = 64;
 
-// Bytes of the sort keys, indices and 64 scratch ints (batch flags, count).
+// Bytes of the sort keys, indices and 96 scratch ints (batch flags, count,
+// the batch's neighbour masks).
+constexpr int kPruneScratchInts = 96;
 template <typename ST>
 __host__ __device__ inline size_t greedy_keys_bytes(int P) {
-  return (((size_t)P * (sizeof(ST) + 4) + 64 * 4 + 15) / 16) * 16;
+  return (((size_t)P * (sizeof(ST) + 4) + kPruneScratchInts * 4 + 15) / 16) * 16;
 }
 
 template <typename PT, typename ST>
@@ -46,12 +51,36 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
   PT* ctile2 = reinterpret_cast<PT*>(smem + greedy_keys_bytes<ST>(P));
   constexpr int kTile = kPruneMaxDim * kPruneTileStride;
   PT* apos = ctile2 + 2 * kTile;
+  // order: "a before b" iff a.key > b.key, or equal keys and a.idx < b.idx
+  if (K <= 512 && K <= (int)blockDim.x) {
+    // rank of candidate t = number of candidates before it (a permutation:
+    // the order is total; a NaN score counts as -inf)
+    const int t = threadIdx.x;
+    ST mk = (ST)-INFINITY;
+    if (t < K) {
+      mk = score[t];
+      if (!(mk == mk)) mk = (ST)-INFINITY;
+      keys[t] = mk;
+    }
+    __syncthreads();
+    int rank = 0;
+    if (t < K)
+      for (int j = 0; j < K; ++j) {
+        const ST kj = keys[j];
+        rank += (kj > mk || (kj == mk && j < t)) ? 1 : 0;
+      }
+    __syncthreads();
+    if (t < K) {
+      keys[rank] = mk;
+      idx[rank] = t;
+    }
+  } else {
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     keys[i] = i < K ? score[i] : (ST)-INFINITY;
     idx[i] = i < K ? i : INT32_MAX;
   }
   __syncthreads();
-  // bitonic sort: "a before b" iff a.key > b.key, or equal keys and a.idx < b.idx
+  // bitonic sort
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -72,6 +101,7 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
       __syncthreads();
     }
   }
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto row_of = [&](int q) -> int64_t { return cand_row ? (int64_t)cand_row[q] : (int64_t)q; };
   // coordinates of accepted mode a (a candidate index in accepted[a])
@@ -81,6 +111,7 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
   };
   int* s_dead = idx + P;                             // scratch: batch suppression flags
   int* s_nacc = s_dead + 32;                         // scratch: modes accepted so far
+  unsigned* s_near = reinterpret_cast<unsigned*>(s_dead + 64);   // scratch: batch masks
   // warp w stages batch `base` (lane c: sorted candidate base + c; tile[k * 33 + c] is
   // its coordinate k)
   auto stage = [&](int base, PT* tile) {
@@ -114,36 +145,37 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
       }
       if (dead) s_dead[lane] = 1;
     }
+    // masks: bit l of s_near[v] <=> batch members l and v lie within r (the
+    // same FP arithmetic as the test against an accepted mode: the coordinate
+    // differences are exact negations of each other)
+    for (int v = warp; v < 32; v += nwarps) {
+      bool nb = false;
+      if (i < K && base + v < K) {
+        PT d2 = 0;
+        for (int k = 0; k < d; ++k) {
+          const PT e = ctile[k * kPruneTileStride + lane] - ctile[k * kPruneTileStride + v];
+          d2 += e * e;
+        }
+        nb = d2 < r2;
+      }
+      const unsigned m = __ballot_sync(kFull, nb);
+      if (lane == 0) s_near[v] = m;
+    }
     // the next batch's tile (its last readers finished before this batch's barrier)
     if (warp == (nwarps > 1 ? 1 : 0) && base + 32 < K) stage(base + 32, ctile2 + ((b + 1) & 1) * kTile);
     __syncthreads();
     if (warp == 0) {
       // survivors of the batch, resolved in order by one warp
-      bool alive = i < K && !s_dead[lane];
+      unsigned alive = __ballot_sync(kFull, i < K && !s_dead[lane]);
       int na = nacc;
-      for (;;) {
-        const unsigned m = __ballot_sync(kFull, alive);
-        if (!m) break;
-        const int w = __ffs(m) - 1;
+      while (alive) {
+        const int w = __ffs(alive) - 1;
         if (lane == w) accepted[na] = idx[i];
         if (acc_in_smem)
           for (int k = lane; k < d; k += 32)
             apos[(size_t)na * d + k] = ctile[k * kPruneTileStride + w];
-        __syncwarp();
-        const PT* wp = acc_ptr(na);
+        alive &= ~(s_near[w] | (1u << w));
         ++na;
-        if (alive) {
-          if (lane == w) {
-            alive = false;
-          } else {
-            PT d2 = 0;
-            for (int k = 0; k < d; ++k) {
-              const PT e = ctile[k * kPruneTileStride + lane] - wp[k];
-              d2 += e * e;
-            }
-            if (d2 < r2) alive = false;
-          }
-        }
       }
       s_dead[lane] = 0;
       if (lane == 0) *s_nacc = na;

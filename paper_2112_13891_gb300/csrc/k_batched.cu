@@ -823,7 +823,7 @@ size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* 
   while (p < maxK) p <<= 1;
   *P = p;
   // keys and indices, scratch, the two batch tiles (as greedy_sorted_smem)
-  const size_t keys = (((size_t)p * (score_bytes + 4) + 64 * 4 + 15) / 16) * 16 +
+  const size_t keys = (((size_t)p * (score_bytes + 4) + kPruneScratchInts * 4 + 15) / 16) * 16 +
                       2 * (size_t)kPruneMaxDim * kPruneTileStride * pos_bytes;
   const size_t full = keys + (size_t)maxK * d * pos_bytes;
   if (with_pos) *with_pos = full <= kBatchedPruneSmem ? 1 : 0;

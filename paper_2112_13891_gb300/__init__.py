@@ -146,18 +146,45 @@ def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_rad
     return o
 
 
+_NEED_CACHE: dict = {}
+
+
+def _workspace_need(n: int, d: int, o: FmsOptions) -> int:
+    """fms_workspace_size, remembered per (device, n, d, options)."""
+    key = (torch.cuda.current_device(), n, d, bytes(o))
+    need = _NEED_CACHE.get(key)
+    if need is None:
+        need = int(_lib.fms_workspace_size(n, d, ctypes.byref(o)))
+        if len(_NEED_CACHE) > 256:
+            _NEED_CACHE.clear()
+        _NEED_CACHE[key] = need
+    return need
+
+
 def workspace_size(n: int, d: int, **opts) -> int:
     o = make_options(**opts)
     return int(_lib.fms_workspace_size(int(n), int(d), ctypes.byref(o)))
 
 
-@dataclass
 class ClusterResult:
-    modes: torch.Tensor        # [M, d] float32, canonical order
-    labels: torch.Tensor       # [n] int32
-    margins: torch.Tensor      # [n] float32 or None
-    stats: dict
-    status: int
+    """modes [M, d] float32 (canonical order), labels [n] int32, margins [n]
+    float32 or None, stats (dict, converted from fms_stats on first use),
+    status."""
+
+    __slots__ = ("modes", "labels", "margins", "_stats", "status")
+
+    def __init__(self, modes, labels, margins, stats, status):
+        self.modes = modes
+        self.labels = labels
+        self.margins = margins
+        self._stats = stats
+        self.status = status
+
+    @property
+    def stats(self) -> dict:
+        if not isinstance(self._stats, dict):
+            self._stats = self._stats.as_dict()
+        return self._stats
 
 
 class Workspace:
@@ -196,7 +223,7 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
         modes = torch.empty((max(cap, 1), d), dtype=torch.float32, device=X.device)
         labels = torch.empty(n, dtype=torch.int32, device=X.device)
         mar = torch.empty(n, dtype=torch.float32, device=X.device) if margins else None
-    need = int(_lib.fms_workspace_size(n, d, ctypes.byref(o)))
+    need = _workspace_need(n, d, o)
     if workspace is None or workspace.nbytes < need:
         workspace = Workspace(need, X.device)
     nm = _I32(0)
@@ -207,8 +234,8 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
     if code not in (FMS_OK, FMS_ERR_CAPACITY):
         raise FmsError(code, "fms_cluster")
     M = nm.value
-    return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar,
-                         stats=st.as_dict(), status=code)
+    return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar, stats=st,
+                         status=code)
 
 
 @dataclass

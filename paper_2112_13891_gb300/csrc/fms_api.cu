@@ -23,11 +23,19 @@ struct Dev {
   int sms = 0;
 };
 
+// SM count of the current device (queried once per device)
 Dev device_info() {
+  constexpr int kMaxDevices = 64;
+  static int sms_cache[kMaxDevices] = {0};
   Dev d;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return d;
+  if (dev >= 0 && dev < kMaxDevices && sms_cache[dev] > 0) {
+    d.sms = sms_cache[dev];
+    return d;
+  }
   if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) d.sms = 0;
+  if (dev >= 0 && dev < kMaxDevices && d.sms > 0) sms_cache[dev] = d.sms;
   return d;
 }
 

@@ -74,6 +74,7 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
       keys[rank] = mk;
       idx[rank] = t;
     }
+    __syncthreads();   // the sorted order is read by other threads below
   } else {
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     keys[i] = i < K ? score[i] : (ST)-INFINITY;

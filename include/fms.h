@@ -128,7 +128,8 @@ typedef struct fms_stats {
   double round_kernel_ms;   /* summed device time of the cluster round launches   */
   int64_t round_evals;      /* evaluations of those launches                      */
   int32_t round_launches;
-  int32_t reserved2;
+  int32_t graph;            /* 1: the call ran as one cached CUDA graph (the same
+                               kernels as the host-driven path, one host sync) */
   double phase_ms[4];       /* device time of: seed rounds (selection, updates,
                                stop), prunes + doubling, refinement + ordering,
                                labels                                            */

@@ -51,7 +51,7 @@ class FmsStats(ctypes.Structure):
                 ("step_launches", ctypes.c_int32), ("coarse_launches", ctypes.c_int32),
                 ("step_evals", ctypes.c_int64), ("round_kernel_ms", ctypes.c_double),
                 ("round_evals", ctypes.c_int64), ("round_launches", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32), ("phase_ms", ctypes.c_double * 4),
+                ("graph", ctypes.c_int32), ("phase_ms", ctypes.c_double * 4),
                 ("coarse_kernel_ms", ctypes.c_double), ("coarse_evals", ctypes.c_int64)]
 
     def as_dict(self):

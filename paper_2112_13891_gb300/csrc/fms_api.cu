@@ -79,6 +79,93 @@ unsigned char* pinned_ctl() {
   return buf;
 }
 
+constexpr size_t kCtlRoundOff = 896;   // RoundCtl of the device-driven rounds
+static_assert(kCtlRoundOff + sizeof(RoundCtl) <= kCtlBlockBytes, "control region");
+
+// ---------------------------------------------------------------------------
+// CUDA-graph form of fms_cluster.  When every round fits the cluster kernels,
+// the whole call (packing, Seed Selection, the rounds with their prunes and
+// seed-count decisions, refinement, labels) is one graph: a conditional WHILE
+// node repeats the round body while round_advance asks for another round, and
+// an IF node runs the post-round work; the host synchronises once, to read
+// the control region.  A graph bakes in its pointers and scalars, so it is
+// kept per (arguments, options, device) and built the second time the same
+// call is seen (a one-off call takes the host-driven path at no build cost).
+// ---------------------------------------------------------------------------
+struct GraphKey {
+  const void* points;
+  const void* modes;
+  const void* labels;
+  const void* margins;
+  const void* ws;
+  size_t ws_bytes;
+  int64_t n;
+  int32_t d, max_iter, max_modes, dev;
+  float h, tol;
+  unsigned char opts[sizeof(fms_options)];
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  int kernels_pre = 0, kernels_round = 0, kernels_post = 0;
+  bool failed = false;
+};
+
+struct GraphCache {
+  static constexpr int kEntries = 4, kSeen = 8;
+  GraphEntry entries[kEntries];
+  int used = 0, next = 0;
+  GraphKey seen[kSeen];
+  int n_seen = 0, next_seen = 0;
+  ~GraphCache() {
+    for (int i = 0; i < used; ++i)
+      if (entries[i].exec) cudaGraphExecDestroy(entries[i].exec);
+  }
+};
+
+bool same_key(const GraphKey& a, const GraphKey& b) { return memcmp(&a, &b, sizeof(GraphKey)) == 0; }
+
+GraphCache& graph_cache() {
+  thread_local GraphCache c;
+  return c;
+}
+
+// Private capture streams (per device and purpose), kept for the thread's life.
+cudaStream_t capture_stream(int dev, int which) {
+  constexpr int kMaxDevices = 64;
+  thread_local cudaStream_t s[kMaxDevices][2] = {};
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  if (!s[dev][which] &&
+      cudaStreamCreateWithFlags(&s[dev][which], cudaStreamNonBlocking) != cudaSuccess)
+    s[dev][which] = nullptr;
+  return s[dev][which];
+}
+
+// During capture on `cs`: add a conditional node after the captured work and
+// return its body graph; further capture on `cs` depends on the node.
+cudaError_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies);
+}
+
 // Whether a call's seed updates start on the tensor-core step.
 bool use_tensor_step(int d, int32_t precision) {
   if (precision == FMS_PRECISION_TENSOR) return d >= 8 && d <= kTcMaxDim;
@@ -394,8 +481,178 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       return e;
     };
 
-    FMS_CUDA(cudaMemsetAsync(ctl, 0, kCtlBlockBytes, st));   // ctl, mctl, rctl, status
-    FMS_CUDA(cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, st));
+    // --- Seed Selection (Alg. 2 line 2): initial seed count ---
+    int32_t N0;
+    if (o.all_seeds) N0 = (int32_t)n;
+    else if (o.seed_indices) N0 = o.n_seed_indices;
+    else N0 = (int32_t)(o.n_initial < n ? o.n_initial : n);
+    RoundCtl* rctl_round = at<RoundCtl>(ws, Lo.off_ctl + kCtlRoundOff);
+    const int cap_seeds = qmax * kSeedsPerCluster, cap_modes = qmax * kModesPerCluster;
+    const int keep_exhausted = o.gamma >= 1.0f ? 1 : 0;
+    const double rtol_s = kRefineTolFactor * (double)h * scale;
+
+    // --- the CUDA-graph form (see GraphKey) ---
+    // resume: 0 host path from the start, 1 host rounds from the graph's state,
+    // 2 host refinement and labels, 3 the graph did everything
+    int resume = 0;
+    const bool graph_ok = !o.profile && !owns_ws && hbuf && qmax > 0 && !tensor &&
+                          !o.all_seeds && !o.seed_indices && !o.skip_refine &&
+                          max_iter <= kHistCap && N0 <= cap_seeds;
+    if (graph_ok) {
+      GraphKey key;
+      memset(&key, 0, sizeof(key));
+      key.points = points;
+      key.modes = out_modes;
+      key.labels = out_labels;
+      key.margins = out_margins;
+      key.ws = ws;
+      key.ws_bytes = workspace_bytes;
+      key.n = n;
+      key.d = d;
+      key.max_iter = max_iter;
+      key.max_modes = max_modes;
+      cudaGetDevice(&key.dev);
+      key.h = h;
+      key.tol = tol;
+      memcpy(key.opts, &o, sizeof(fms_options));
+      GraphCache& gc = graph_cache();
+      GraphEntry* ge = nullptr;
+      for (int i = 0; i < gc.used; ++i)
+        if (same_key(gc.entries[i].key, key)) ge = &gc.entries[i];
+      bool seen = false;
+      for (int i = 0; i < gc.n_seen; ++i)
+        if (same_key(gc.seen[i], key)) seen = true;
+      if (!ge && !seen) {
+        gc.seen[gc.next_seen] = key;
+        gc.next_seen = (gc.next_seen + 1) % GraphCache::kSeen;
+        if (gc.n_seen < GraphCache::kSeen) ++gc.n_seen;
+      } else if (!ge) {
+        // build: the same sequence of launches as the host path, captured on
+        // private streams, with the round's N and target read from RoundCtl
+        GraphEntry* slot = &gc.entries[gc.next];
+        if (gc.used == GraphCache::kEntries && slot->exec) cudaGraphExecDestroy(slot->exec);
+        gc.next = (gc.next + 1) % GraphCache::kEntries;
+        if (gc.used < GraphCache::kEntries) ++gc.used;
+        *slot = GraphEntry();
+        slot->key = key;
+        cudaStream_t cs = capture_stream(key.dev, 0), cs2 = capture_stream(key.dev, 1);
+        cudaGraph_t g = nullptr;
+        bool capturing = false;
+        cudaError_t e = (cs && cs2) ? cudaGraphCreate(&g, 0) : cudaErrorNotSupported;
+        cudaGraphConditionalHandle h_loop = 0, h_post = 0;
+        if (e == cudaSuccess)
+          e = cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+          e = cudaGraphConditionalHandleCreate(&h_post, g, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+          e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        capturing = e == cudaSuccess;
+        // before the rounds
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, kCtlBlockBytes, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, cs);
+        if (e == cudaSuccess)
+          e = launch_pack_points(points, n, d, DP, (float)scale, Xs, status, cs);
+        if (e == cudaSuccess)
+          e = launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, 0, 0, N0, seed_idx, y, it, conv,
+                               state, status, cs, init_state);
+        if (e == cudaSuccess) e = launch_round_begin(rctl_round, N0, o.gamma, cs);
+        slot->kernels_pre = 3;
+        // the rounds
+        cudaGraph_t body = nullptr;
+        if (e == cudaSuccess) e = add_conditional(cs, h_loop, cudaGraphCondTypeWhile, &body);
+        if (e == cudaSuccess)
+          e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaError_t e2 = launch_round_list(state, 0, active, S_dev, cs2, rctl_round);
+          if (e2 == cudaSuccess)
+            e2 = launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, qmax, hist, 0,
+                                 max_iter, tol2_s,
+                                 reinterpret_cast<unsigned long long*>(&ctl->evals), cs2, kf,
+                                 rctl_round);
+          if (e2 == cudaSuccess)
+            e2 = launch_round_finish(hist, 0, max_iter, state, conv, 0, keep_exhausted, kept,
+                                     mctl, ctl, n, R, Lo.tl, cs2, rctl_round);
+          if (e2 == cudaSuccess)
+            e2 = launch_ms_step(Xs, n, d, DP, y, kept, &mctl->K, &mctl->C, &mctl->Lc, part,
+                                Lo.tl.target_warps, cs2, nullptr, nullptr, kf);
+          if (e2 == cudaSuccess) e2 = launch_score_reduce(part, mctl, DA, score, cap_seeds, cs2);
+          if (e2 == cudaSuccess)
+            e2 = launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
+                                       &mctl->M, cap_seeds, cs2);
+          if (e2 == cudaSuccess)
+            e2 = launch_round_advance(rctl_round, mctl, n, o.L, allow_doubling ? 1 : 0, o.gamma,
+                                      cap_seeds, cap_modes, o.rng_seed, Xs, DP, seed_idx, y, it,
+                                      conv, state, init_state, h_loop, h_post, cs2);
+          cudaGraph_t gb = body;
+          const cudaError_t e3 = cudaStreamEndCapture(cs2, &gb);
+          e = e2 != cudaSuccess ? e2 : e3;
+        }
+        slot->kernels_round = 7;
+        // after the rounds: refinement, second prune, order, labels
+        cudaGraph_t post = nullptr;
+        if (e == cudaSuccess) e = add_conditional(cs, h_post, cudaGraphCondTypeIf, &post);
+        if (e == cudaSuccess)
+          e = cudaStreamBeginCaptureToGraph(cs2, post, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaError_t e2 = launch_ms_refine(
+              Xs, n, d, y, kept, acc1, &mctl->M, qmax, ym, yf, mscore, rtol_s * rtol_s,
+              kRefineMaxIter, &rctl->steps, reinterpret_cast<unsigned long long*>(&rctl->evals),
+              cs2, kf);
+          if (e2 == cudaSuccess)
+            e2 = launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
+                                       cap_modes, cs2);
+          if (e2 == cudaSuccess)
+            e2 = launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,
+                                        out_modes, max_modes, modes_full, nullptr, cap_modes,
+                                        cs2);
+          if (e2 == cudaSuccess)
+            e2 = launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins,
+                              cs2);
+          cudaGraph_t gp = post;
+          const cudaError_t e3 = cudaStreamEndCapture(cs2, &gp);
+          e = e2 != cudaSuccess ? e2 : e3;
+        }
+        slot->kernels_post = 4;
+        if (capturing) {
+          cudaGraph_t gout = g;
+          const cudaError_t e3 = cudaStreamEndCapture(cs, &gout);
+          if (e == cudaSuccess) e = e3;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&slot->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          if (slot->exec) cudaGraphExecDestroy(slot->exec);
+          slot->exec = nullptr;
+          slot->failed = true;
+          cudaGetLastError();   // clear the error the failed build left
+        }
+        ge = slot;
+      }
+      if (ge && ge->exec) {
+        FMS_CUDA(cudaGraphLaunch(ge->exec, st));
+        FMS_CUDA(readback());
+        RoundCtl rcv;
+        memcpy(&rcv, hbuf + kCtlRoundOff, sizeof(RoundCtl));
+        rounds = rcv.rounds;
+        N = rcv.N;
+        K_last = rcv.K_last;
+        n_launches = ge->kernels_pre + ge->kernels_round * rcv.rounds +
+                     (rcv.leave == 0 ? ge->kernels_post : 0);
+        if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
+        if (hstatus & kStTimeout) {
+          rc = FMS_ERR_TIMEOUT;
+          goto done;
+        }
+        resume = rcv.leave == 0 ? 3 : (rcv.leave == 1 ? 1 : 2);
+      }
+    }
+    if (resume == 0) {
+      FMS_CUDA(cudaMemsetAsync(ctl, 0, kCtlBlockBytes, st));   // ctl, mctl, rctl, status, round
+      FMS_CUDA(cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, st));
+    }
     if (o.profile)
       for (int i = 0; i < 5; ++i)
         if (cudaEventCreate(&phase_ev[i]) != cudaSuccess) {
@@ -412,18 +669,16 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       cudaEventSynchronize(phase_ev[b]);
       if (cudaEventElapsedTime(&t, phase_ev[a], phase_ev[b]) == cudaSuccess) phase_acc[slot] += t;
     };
-    mark(0);
-    FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
-    if (tensor) FMS_LAUNCH(launch_tc_pack(Xs, n, d, DP, img, st));
+    if (resume == 0) {
+      mark(0);
+      FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
+      if (tensor) FMS_LAUNCH(launch_tc_pack(Xs, n, d, DP, img, st));
+      N = N0;
+      FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y,
+                                  it, conv, state, status, st, init_state));
+    }
 
-    // --- Seed Selection (Alg. 2 line 2) ---
-    if (o.all_seeds) N = (int32_t)n;
-    else if (o.seed_indices) N = o.n_seed_indices;
-    else N = (int32_t)(o.n_initial < n ? o.n_initial : n);
-    FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y, it,
-                              conv, state, status, st, init_state));
-
-    for (;;) {
+    for (; resume <= 1;) {
       ++rounds;
       int target = (int)ceil((double)o.gamma * (double)N);
       if (target < 1) target = 1;
@@ -448,9 +703,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                    target, max_iter, tol2_s,
                                    reinterpret_cast<unsigned long long*>(&ctl->evals), st, kf));
         if (o.profile) cudaEventRecord(rb, st);
-        FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N,
-                                       o.gamma >= 1.0f ? 1 : 0, kept, mctl, ctl, n, R, Lo.tl,
-                                       st));
+        FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N, keep_exhausted,
+                                       kept, mctl, ctl, n, R, Lo.tl, st));
         mark(1);
       } else {
         FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, tl_iter, N, target,
@@ -501,6 +755,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       break;
     }
 
+    std::vector<int32_t> hslog(n_slog), htclog(n_tclog);
+    if (resume <= 2) {
     mark(2);
     // --- refinement and second prune ---
     if (!o.skip_refine && hm.M > 0 && qmax > 0 && hm.M <= qmax * kModesPerCluster) {
@@ -549,13 +805,15 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     mark(3);
     FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
     mark(4);
-    std::vector<int32_t> hslog(n_slog), htclog(n_tclog);
+    hslog.assign(n_slog, 0);
+    htclog.assign(n_tclog, 0);
     if (n_slog > 0)
       FMS_CUDA(cudaMemcpyAsync(hslog.data(), slog, (size_t)n_slog * 4, cudaMemcpyDeviceToHost, st));
     if (n_tclog > 0)
       FMS_CUDA(cudaMemcpyAsync(htclog.data(), tclog, (size_t)n_tclog * 4, cudaMemcpyDeviceToHost,
                                st));
     FMS_CUDA(readback());
+    }
     Mfinal = hm.Mr;
     *out_n_modes = Mfinal;
     if (hstatus & kStNonFinite) goto device_error;
@@ -579,6 +837,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       stats->evals = hctl.evals;
       stats->score_evals = hm.evals + hrctl.evals + (int64_t)hm.M * n;
       stats->workspace_bytes = Lo.total;
+      stats->graph = resume != 0 ? 1 : 0;
       if (o.profile) {
         phase_add(2, 2, 3);
         phase_add(3, 3, 4);

@@ -56,6 +56,24 @@ struct IterCtl {
   int64_t evals;      // seed-point evaluations issued
 };
 
+// Seed count and stop target of the device-driven rounds (CUDA-graph form).
+struct RoundCtl {
+  int32_t N;        // seeds in play
+  int32_t target;   // ceil(gamma * N), clamped to [1, N]
+  int32_t rounds;   // rounds completed
+  int32_t leave;    // != 0: the host continues (1: next round, 2: refinement)
+  int32_t K_last;   // prune candidates of the last round
+  int32_t pad[3];
+};
+
+// ceil(gamma * N) clamped to [1, N] (the Early-Stopping count of Sec. II-C)
+__host__ __device__ inline int32_t stop_target(float gamma, int32_t N) {
+  int t = (int)ceil((double)gamma * (double)N);
+  if (t < 1) t = 1;
+  if (t > N) t = N;
+  return t;
+}
+
 // Control block of the prune / refine phase.
 struct MergeCtl {
   int32_t K;              // candidates of the prune (kept seeds)
@@ -299,6 +317,13 @@ cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_se
                              int32_t init_state = kRunning);
 cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t count,
                                 int32_t* out, cudaStream_t st);
+cudaError_t launch_round_begin(RoundCtl* rc, int32_t N, float gamma, cudaStream_t st);
+cudaError_t launch_round_advance(RoundCtl* rc, MergeCtl* mctl, int64_t n, float L, int allow,
+                                 float gamma, int cap_seeds, int cap_modes, uint64_t rng_seed,
+                                 const float* Xs, int DP, int32_t* seed_idx, float* y,
+                                 int32_t* it, int32_t* conv, int32_t* state, int32_t init_state,
+                                 cudaGraphConditionalHandle h_loop,
+                                 cudaGraphConditionalHandle h_post, cudaStream_t st);
 cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t* it,
                               const int32_t* conv, int32_t* active, int64_t n, int32_t R,
                               Tiling tl, int N, int target, int max_iter, cudaStream_t st);
@@ -317,7 +342,8 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st, int kf = kKernelGaussian);
+                            cudaStream_t st, int kf = kKernelGaussian,
+                            const RoundCtl* rc = nullptr);   // rc: target from the device
 int round_max_clusters(int d);
 cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
@@ -325,11 +351,12 @@ cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              int max_iter, int32_t* iters_out, unsigned long long* evals,
                              cudaStream_t st, int kf = kKernelGaussian);
 cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
-                              cudaStream_t st);
+                              cudaStream_t st, const RoundCtl* rc = nullptr);   // rc: N
 cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 const int32_t* state, const int32_t* conv, int N,
                                 int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
-                                int64_t n, int32_t R, Tiling tl, cudaStream_t st);
+                                int64_t n, int32_t R, Tiling tl, cudaStream_t st,
+                                const RoundCtl* rc = nullptr);   // rc: N and target
 
 // k_unroll.cu: unrolled steps and their adjoint
 struct UGeom {

@@ -96,6 +96,19 @@ cudaError_t launch_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int
   return cudaGetLastError();
 }
 
+// Slot `slot` takes point idx: position Xs[idx], no updates yet, state init_state.
+__device__ __forceinline__ void init_seed_slot(const float* __restrict__ Xs, int DP, int64_t idx,
+                                               int64_t slot, int32_t* __restrict__ seed_idx,
+                                               float* __restrict__ y, int32_t* __restrict__ it,
+                                               int32_t* __restrict__ conv,
+                                               int32_t* __restrict__ state, int32_t init_state) {
+  seed_idx[slot] = (int32_t)idx;
+  for (int k = 0; k < DP; ++k) y[slot * DP + k] = Xs[idx * DP + k];
+  it[slot] = 0;
+  conv[slot] = -1;
+  state[slot] = init_state;
+}
+
 // Initialise seed slots [slot0, slot0+count): point index from the explicit
 // list or the permutation (rank0 + t), position Xs[idx], state RUNNING.
 __global__ void seed_init_kernel(const float* __restrict__ Xs, int64_t n, int DP, FeistelKey f,
@@ -115,13 +128,81 @@ __global__ void seed_init_kernel(const float* __restrict__ Xs, int64_t n, int DP
     } else {
       idx = permute(rank0 + t, n, f);
     }
-    const int64_t slot = slot0 + t;
-    seed_idx[slot] = (int32_t)idx;
-    for (int k = 0; k < DP; ++k) y[slot * DP + k] = Xs[idx * DP + k];
-    it[slot] = 0;
-    conv[slot] = -1;
-    state[slot] = init_state;
+    init_seed_slot(Xs, DP, idx, slot0 + t, seed_idx, y, it, conv, state, init_state);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven rounds (the CUDA-graph form of fms_cluster): the round's seed
+// count and stop target live in RoundCtl, and round_advance takes the
+// seed-count decision of Sec. II-D on the device: N <- min(2N, n) while
+// N < L*M (and doubling is allowed), the new slots N..2N-1 taking the next
+// entries of the same keyed permutation.  It sets the graph's loop condition
+// (another round) and the condition of the post-round work (refinement,
+// labels), and leaves the rest to the host (leave != 0) when the next round
+// or the refinement would not fit the cluster kernels.
+// ---------------------------------------------------------------------------
+__global__ void round_begin_kernel(RoundCtl* rc, int32_t N, float gamma) {
+  rc->N = N;
+  rc->target = stop_target(gamma, N);
+  rc->rounds = 0;
+  rc->leave = 0;
+  rc->K_last = 0;
+}
+
+cudaError_t launch_round_begin(RoundCtl* rc, int32_t N, float gamma, cudaStream_t st) {
+  round_begin_kernel<<<1, 1, 0, st>>>(rc, N, gamma);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(1024)
+    round_advance_kernel(RoundCtl* rc, MergeCtl* mctl, int64_t n, float L, int allow,
+                         float gamma, int cap_seeds, int cap_modes, FeistelKey f,
+                         const float* __restrict__ Xs, int DP, int32_t* __restrict__ seed_idx,
+                         float* __restrict__ y, int32_t* __restrict__ it,
+                         int32_t* __restrict__ conv, int32_t* __restrict__ state,
+                         int32_t init_state, cudaGraphConditionalHandle h_loop,
+                         cudaGraphConditionalHandle h_post) {
+  const int N = rc->N, M = mctl->M;
+  int next = N;
+  if (allow && (float)N < L * (float)M && (int64_t)N < n) {
+    const int64_t t2 = 2LL * N;
+    next = (int32_t)(t2 < n ? t2 : n);
+  }
+  for (int t = threadIdx.x; t < next - N; t += blockDim.x)
+    init_seed_slot(Xs, DP, permute((int64_t)N + t, n, f), (int64_t)N + t, seed_idx, y, it, conv,
+                   state, init_state);
+  __syncthreads();   // every thread has read rc->N
+  if (threadIdx.x == 0) {
+    mctl->next_N = next;
+    rc->rounds += 1;
+    rc->K_last = mctl->K;
+    int more = 0, leave = 0;
+    if (next > N) {
+      rc->N = next;
+      rc->target = stop_target(gamma, next);
+      if (next <= cap_seeds) more = 1;
+      else leave = 1;   // the next round needs the host-driven path
+    } else if (M > cap_modes) {
+      leave = 2;        // the refinement needs the host-driven path
+    }
+    rc->leave = leave;
+    cudaGraphSetConditional(h_loop, more ? 1u : 0u);
+    cudaGraphSetConditional(h_post, (!more && !leave) ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_round_advance(RoundCtl* rc, MergeCtl* mctl, int64_t n, float L, int allow,
+                                 float gamma, int cap_seeds, int cap_modes, uint64_t rng_seed,
+                                 const float* Xs, int DP, int32_t* seed_idx, float* y,
+                                 int32_t* it, int32_t* conv, int32_t* state, int32_t init_state,
+                                 cudaGraphConditionalHandle h_loop,
+                                 cudaGraphConditionalHandle h_post, cudaStream_t st) {
+  const FeistelKey f = make_key(n, rng_seed);
+  round_advance_kernel<<<1, 1024, 0, st>>>(rc, mctl, n, L, allow, gamma, cap_seeds, cap_modes, f,
+                                           Xs, DP, seed_idx, y, it, conv, state, init_state,
+                                           h_loop, h_post);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,

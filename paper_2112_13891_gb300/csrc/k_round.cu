@@ -313,8 +313,10 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
     ms_round_kernel(const float* __restrict__ Xs, int n, float* __restrict__ y,
                     int32_t* __restrict__ it, int32_t* __restrict__ conv,
                     int32_t* __restrict__ state, const int32_t* __restrict__ list,
-                    const int32_t* __restrict__ S_ptr, int32_t* hist, int target, int max_iter,
-                    float tol2_s, unsigned long long* evals) {
+                    const int32_t* __restrict__ S_ptr, int32_t* hist, int target_arg,
+                    int max_iter, float tol2_s, unsigned long long* evals,
+                    const RoundCtl* __restrict__ rc) {
+  const int target = rc ? rc->target : target_arg;
   constexpr int R = 32 / DA;
   constexpr int SMAX = kSeedsPerCluster;
   constexpr int GMAX = (SMAX + R - 1) / R;
@@ -511,7 +513,8 @@ template <int D, int DP, int DA, int KF>
 static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it, int32_t* conv,
                                   int32_t* state, const int32_t* list, const int32_t* S_ptr,
                                   int clusters, int32_t* hist, int target, int max_iter,
-                                  float tol2_s, unsigned long long* evals, cudaStream_t st) {
+                                  float tol2_s, unsigned long long* evals, const RoundCtl* rc,
+                                  cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(clusters * kClusterCtas);
   cfg.blockDim = dim3(kRoundWarps * 32);
@@ -525,7 +528,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA, KF>, Xs, n, y, it, conv, state, list,
-                            S_ptr, hist, target, max_iter, tol2_s, evals);
+                            S_ptr, hist, target, max_iter, tol2_s, evals, rc);
 }
 
 template <int D, int DP, int DA>
@@ -569,23 +572,24 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st, int kf) {
+                            cudaStream_t st, int kf, const RoundCtl* rc) {
+#define FMS_ROUND(D_, DP_, DA_)                                                                \
+  return kf ? launch_round_t<D_, DP_, DA_, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
+                                              clusters, hist, target, max_iter, tol2_s, evals, \
+                                              rc, st)                                          \
+            : launch_round_t<D_, DP_, DA_, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
+                                              clusters, hist, target, max_iter, tol2_s, evals, \
+                                              rc, st)
   switch (d) {
-    case 1: return kf ? launch_round_t<1, 4, 2, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<1, 4, 2, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 2: return kf ? launch_round_t<2, 4, 4, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<2, 4, 4, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 3: return kf ? launch_round_t<3, 4, 4, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<3, 4, 4, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 4: return kf ? launch_round_t<4, 4, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<4, 4, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 5: return kf ? launch_round_t<5, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<5, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 6: return kf ? launch_round_t<6, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<6, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
-    case 7: return kf ? launch_round_t<7, 8, 8, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st)
-                 : launch_round_t<7, 8, 8, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr, clusters, hist, target, max_iter, tol2_s, evals, st);
+    case 1: FMS_ROUND(1, 4, 2);
+    case 2: FMS_ROUND(2, 4, 4);
+    case 3: FMS_ROUND(3, 4, 4);
+    case 4: FMS_ROUND(4, 4, 8);
+    case 5: FMS_ROUND(5, 8, 8);
+    case 6: FMS_ROUND(6, 8, 8);
+    case 7: FMS_ROUND(7, 8, 8);
   }
+#undef FMS_ROUND
   return cudaErrorInvalidValue;
 }
 
@@ -787,9 +791,10 @@ cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
 // (converged by t*), counters for the prune.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-    round_list_kernel(const int32_t* __restrict__ state, int N, int32_t* __restrict__ list,
-                      int32_t* S_out) {
+    round_list_kernel(const int32_t* __restrict__ state, int N_arg, int32_t* __restrict__ list,
+                      int32_t* S_out, const RoundCtl* __restrict__ rc) {
   __shared__ int scratch[64];
+  const int N = rc ? rc->N : N_arg;
   int base = 0;
   for (int b = 0; b < N; b += blockDim.x) {
     const int i = b + threadIdx.x;
@@ -803,17 +808,20 @@ __global__ void __launch_bounds__(1024)
 }
 
 cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
-                              cudaStream_t st) {
-  round_list_kernel<<<1, 1024, 0, st>>>(state, N, list, S_out);
+                              cudaStream_t st, const RoundCtl* rc) {
+  round_list_kernel<<<1, 1024, 0, st>>>(state, N, list, S_out, rc);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(1024)
-    round_finish_kernel(const int32_t* __restrict__ hist, int target, int max_iter,
-                        const int32_t* __restrict__ state, const int32_t* __restrict__ conv, int N,
-                        int keep_exhausted, int32_t* __restrict__ kept, MergeCtl* mctl,
-                        IterCtl* ctl, int64_t n, int32_t R, Tiling tl) {
+    round_finish_kernel(const int32_t* __restrict__ hist, int target_arg, int max_iter,
+                        const int32_t* __restrict__ state, const int32_t* __restrict__ conv,
+                        int N_arg, int keep_exhausted, int32_t* __restrict__ kept, MergeCtl* mctl,
+                        IterCtl* ctl, int64_t n, int32_t R, Tiling tl,
+                        const RoundCtl* __restrict__ rc) {
   __shared__ int scratch[64];
+  const int target = rc ? rc->target : target_arg;
+  const int N = rc ? rc->N : N_arg;
   __shared__ int sh_t;
   if (threadIdx.x == 0) {
     int c = 0, t = max_iter;
@@ -864,9 +872,10 @@ __global__ void __launch_bounds__(1024)
 cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 const int32_t* state, const int32_t* conv, int N,
                                 int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
-                                int64_t n, int32_t R, Tiling tl, cudaStream_t st) {
+                                int64_t n, int32_t R, Tiling tl, cudaStream_t st,
+                                const RoundCtl* rc) {
   round_finish_kernel<<<1, 1024, 0, st>>>(hist, target, max_iter, state, conv, N, keep_exhausted,
-                                          kept, mctl, ctl, n, R, tl);
+                                          kept, mctl, ctl, n, R, tl, rc);
   return cudaGetLastError();
 }
 

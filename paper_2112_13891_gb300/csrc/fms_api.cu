@@ -52,7 +52,7 @@ struct Layout {
   size_t off_Xs, off_y, off_seed_idx, off_it, off_conv, off_state, off_active, off_kept,
       off_alive, off_acc1, off_acc2, off_score, off_ym, off_mdone, off_mscore, off_modes_full,
       off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, off_yf, off_ract, off_rctl,
-      off_hist, off_S, off_img, total;
+      off_hist, off_S, off_img, off_wlast, total;
   int DP, DA, R, grid_ctas;
   int64_t Ncap;
   Tiling tl;
@@ -228,6 +228,7 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms, bool tensor) {
   L.off_hist = take((size_t)(kHistCap + 2) * 4);
   L.off_S = take(64);
   L.off_img = take(tensor ? tc_image_bytes(n, d) : 0);
+  L.off_wlast = take((size_t)Ncap * 4);   // sum w of each seed's latest cluster-round update
   L.total = o;
   return L;
 }
@@ -396,6 +397,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     int32_t* hist = at<int32_t>(ws, Lo.off_hist);
     int32_t* S_dev = at<int32_t>(ws, Lo.off_S);
     unsigned char* img = at<unsigned char>(ws, Lo.off_img);
+    float* wlast = at<float>(ws, Lo.off_wlast);
     unsigned char* hbuf = pinned_ctl();
     // read the control region (pinned staging when available), then sync
     auto readback = [&]() -> cudaError_t {
@@ -569,15 +571,11 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           if (e2 == cudaSuccess)
             e2 = launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, qmax, hist, 0,
                                  max_iter, tol2_s,
-                                 reinterpret_cast<unsigned long long*>(&ctl->evals), cs2, kf,
-                                 rctl_round);
+                                 reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, cs2,
+                                 kf, rctl_round);
           if (e2 == cudaSuccess)
             e2 = launch_round_finish(hist, 0, max_iter, state, conv, 0, keep_exhausted, kept,
-                                     mctl, ctl, n, R, Lo.tl, cs2, rctl_round);
-          if (e2 == cudaSuccess)
-            e2 = launch_ms_step(Xs, n, d, DP, y, kept, &mctl->K, &mctl->C, &mctl->Lc, part,
-                                Lo.tl.target_warps, cs2, nullptr, nullptr, kf);
-          if (e2 == cudaSuccess) e2 = launch_score_reduce(part, mctl, DA, score, cap_seeds, cs2);
+                                     mctl, ctl, n, R, Lo.tl, cs2, rctl_round, wlast, score);
           if (e2 == cudaSuccess)
             e2 = launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
                                        &mctl->M, cap_seeds, cs2);
@@ -589,7 +587,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           const cudaError_t e3 = cudaStreamEndCapture(cs2, &gb);
           e = e2 != cudaSuccess ? e2 : e3;
         }
-        slot->kernels_round = 7;
+        slot->kernels_round = 5;
         // after the rounds: refinement, second prune, order, labels
         cudaGraph_t post = nullptr;
         if (e == cudaSuccess) e = add_conditional(cs, h_post, cudaGraphCondTypeIf, &post);
@@ -701,10 +699,12 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         }
         FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
                                    target, max_iter, tol2_s,
-                                   reinterpret_cast<unsigned long long*>(&ctl->evals), st, kf));
+                                   reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, st,
+                                   kf));
         if (o.profile) cudaEventRecord(rb, st);
+        // the prune's densities: sum w of each kept seed's last update (ms_round)
         FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N, keep_exhausted,
-                                       kept, mctl, ctl, n, R, Lo.tl, st));
+                                       kept, mctl, ctl, n, R, Lo.tl, st, nullptr, wlast, score));
         mark(1);
       } else {
         FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, tl_iter, N, target,
@@ -729,13 +729,13 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           }
           if (hctl.done) break;
         }
-        // --- prune candidates (Alg. 2 line 10) ---
+        // --- prune candidates (Alg. 2 line 10) and their densities ---
         FMS_LAUNCH(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
                                     Lo.tl, st));
         mark(1);
+        FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
+        FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
       }
-      FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
-      FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
       FMS_LAUNCH(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
                                        &mctl->M, N, st));
       // --- seed-count control (Sec. II-D) ---

@@ -342,8 +342,9 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st, int kf = kKernelGaussian,
+                            float* wlast, cudaStream_t st, int kf = kKernelGaussian,
                             const RoundCtl* rc = nullptr);   // rc: target from the device
+// (wlast[slot]: sum w of the seed's latest update, at the position before it)
 int round_max_clusters(int d);
 cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
@@ -356,7 +357,9 @@ cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 const int32_t* state, const int32_t* conv, int N,
                                 int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
                                 int64_t n, int32_t R, Tiling tl, cudaStream_t st,
-                                const RoundCtl* rc = nullptr);   // rc: N and target
+                                const RoundCtl* rc = nullptr,   // rc: N and target
+                                const float* wlast = nullptr,   // with score: the prune
+                                float* score = nullptr);        // densities from wlast
 
 // k_unroll.cu: unrolled steps and their adjoint
 struct UGeom {

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
                     int32_t* __restrict__ state, const int32_t* __restrict__ list,
                     const int32_t* __restrict__ S_ptr, int32_t* hist, int target_arg,
                     int max_iter, float tol2_s, unsigned long long* evals,
-                    const RoundCtl* __restrict__ rc) {
+                    const RoundCtl* __restrict__ rc, float* __restrict__ wlast) {
   const int target = rc ? rc->target : target_arg;
   constexpr int R = 32 / DA;
   constexpr int SMAX = kSeedsPerCluster;
@@ -494,6 +494,9 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
         const int64_t slot = sslot[i];
 #pragma unroll
         for (int k = 0; k < D; ++k) y[slot * DP + k] = sy[i][k];
+        // sum w of this update, at the position before its step: the prune's
+        // density of a seed whose last update this is
+        wlast[slot] = W;
         it[slot] = t;
         if (st == kConverged) {
           conv[slot] = t;
@@ -514,7 +517,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
                                   int32_t* state, const int32_t* list, const int32_t* S_ptr,
                                   int clusters, int32_t* hist, int target, int max_iter,
                                   float tol2_s, unsigned long long* evals, const RoundCtl* rc,
-                                  cudaStream_t st) {
+                                  float* wlast, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(clusters * kClusterCtas);
   cfg.blockDim = dim3(kRoundWarps * 32);
@@ -528,7 +531,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA, KF>, Xs, n, y, it, conv, state, list,
-                            S_ptr, hist, target, max_iter, tol2_s, evals, rc);
+                            S_ptr, hist, target, max_iter, tol2_s, evals, rc, wlast);
 }
 
 template <int D, int DP, int DA>
@@ -572,14 +575,14 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            cudaStream_t st, int kf, const RoundCtl* rc) {
+                            float* wlast, cudaStream_t st, int kf, const RoundCtl* rc) {
 #define FMS_ROUND(D_, DP_, DA_)                                                                \
   return kf ? launch_round_t<D_, DP_, DA_, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
                                               clusters, hist, target, max_iter, tol2_s, evals, \
-                                              rc, st)                                          \
+                                              rc, wlast, st)                                          \
             : launch_round_t<D_, DP_, DA_, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
                                               clusters, hist, target, max_iter, tol2_s, evals, \
-                                              rc, st)
+                                              rc, wlast, st)
   switch (d) {
     case 1: FMS_ROUND(1, 4, 2);
     case 2: FMS_ROUND(2, 4, 4);
@@ -818,7 +821,8 @@ __global__ void __launch_bounds__(1024)
                         const int32_t* __restrict__ state, const int32_t* __restrict__ conv,
                         int N_arg, int keep_exhausted, int32_t* __restrict__ kept, MergeCtl* mctl,
                         IterCtl* ctl, int64_t n, int32_t R, Tiling tl,
-                        const RoundCtl* __restrict__ rc) {
+                        const RoundCtl* __restrict__ rc, const float* __restrict__ wlast,
+                        float* __restrict__ score) {
   __shared__ int scratch[64];
   const int target = rc ? rc->target : target_arg;
   const int N = rc ? rc->N : N_arg;
@@ -848,7 +852,10 @@ __global__ void __launch_bounds__(1024)
     }
     int tot;
     const int off = block_exclusive_scan(take, &tot, scratch);
-    if (take) kept[base + off] = i;
+    if (take) {
+      kept[base + off] = i;
+      if (wlast) score[base + off] = wlast[i];
+    }
     base += tot;
   }
   convd = block_sum(convd, scratch);
@@ -859,7 +866,7 @@ __global__ void __launch_bounds__(1024)
     choose_chunks(n, base, R, tl, &C, &Lc);
     mctl->C = C;
     mctl->Lc = Lc;
-    mctl->evals += (int64_t)base * n;
+    if (!wlast) mctl->evals += (int64_t)base * n;   // the density pass the host then runs
     ctl->N = N;
     ctl->r = t_star;
     ctl->n_converged = convd;
@@ -873,9 +880,9 @@ cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 const int32_t* state, const int32_t* conv, int N,
                                 int keep_exhausted, int32_t* kept, MergeCtl* mctl, IterCtl* ctl,
                                 int64_t n, int32_t R, Tiling tl, cudaStream_t st,
-                                const RoundCtl* rc) {
+                                const RoundCtl* rc, const float* wlast, float* score) {
   round_finish_kernel<<<1, 1024, 0, st>>>(hist, target, max_iter, state, conv, N, keep_exhausted,
-                                          kept, mctl, ctl, n, R, tl, rc);
+                                          kept, mctl, ctl, n, R, tl, rc, wlast, score);
   return cudaGetLastError();
 }
 

@@ -59,8 +59,8 @@ def test_graph_matches_host_path_paper_3d():
     out = _three_calls(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
     _identical(out)
     st = out[1][3]
-    # the graph: packing, seed init, round start; 7 launches per round; 4 after
-    assert st["kernel_launches"] == 3 + 7 * st["rounds"] + 4
+    # the graph: packing, seed init, round start; 5 launches per round; 4 after
+    assert st["kernel_launches"] == 3 + 5 * st["rounds"] + 4
     assert out[0][3]["graph"] == 0 and out[1][3]["graph"] == 1 and out[2][3]["graph"] == 1
     ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
     cmp = compare_clustering(out[2][0].cpu().numpy(), out[2][1].cpu().numpy(), ref, w.h)

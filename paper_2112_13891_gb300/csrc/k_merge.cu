@@ -523,18 +523,26 @@ cudaError_t launch_unrefined_modes(const float* y, const int32_t* kept, const in
 // ---------------------------------------------------------------------------
 constexpr int kLabelTileFloats = 8192;
 
+// DT > 0: the dimension at compile time (coordinates in registers); DT = 0:
+// any d <= FMS_MAX_DIM_PAD, read at run time.
+template <int DT>
 __global__ void __launch_bounds__(256)
-    label_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ modes,
+    label_kernel(const float* __restrict__ X, int64_t n, int d_arg, const float* __restrict__ modes,
                  const int32_t* __restrict__ M_ptr, int M_host, int32_t* __restrict__ labels,
                  float* __restrict__ margins) {
+  constexpr int DX = DT > 0 ? DT : FMS_MAX_DIM_PAD;
+  const int d = DT > 0 ? DT : d_arg;
   __shared__ float sm[kLabelTileFloats];
   const int M = M_ptr ? *M_ptr : M_host;
   const int tile = kLabelTileFloats / d;
   for (int64_t jb = (int64_t)blockIdx.x * blockDim.x; jb < n; jb += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = jb + threadIdx.x;
-    float x[FMS_MAX_DIM_PAD];
-    if (j < n)
-      for (int k = 0; k < d; ++k) x[k] = X[j * d + k];
+    float x[DX];
+    if (j < n) {
+#pragma unroll
+      for (int k = 0; k < DX; ++k)
+        if (k < d) x[k] = X[j * d + k];
+    }
     float b1 = INFINITY, b2 = INFINITY;
     int arg = -1;
     for (int m0 = 0; m0 < M; m0 += tile) {
@@ -545,10 +553,12 @@ __global__ void __launch_bounds__(256)
       if (j < n) {
         for (int m = 0; m < mt; ++m) {
           float d2 = 0.0f;
-          for (int k = 0; k < d; ++k) {
-            const float e = x[k] - sm[m * d + k];
-            d2 = fmaf(e, e, d2);
-          }
+#pragma unroll
+          for (int k = 0; k < DX; ++k)
+            if (k < d) {
+              const float e = x[k] - sm[m * d + k];
+              d2 = fmaf(e, e, d2);
+            }
           if (d2 < b1) {
             b2 = b1;
             b1 = d2;
@@ -572,7 +582,23 @@ cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  label_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins);
+  switch (d) {
+#define FMS_LABEL(D_)                                                                           \
+  case D_:                                                                                      \
+    label_kernel<D_><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins); \
+    break;
+    FMS_LABEL(1)
+    FMS_LABEL(2)
+    FMS_LABEL(3)
+    FMS_LABEL(4)
+    FMS_LABEL(5)
+    FMS_LABEL(6)
+    FMS_LABEL(7)
+    FMS_LABEL(8)
+#undef FMS_LABEL
+    default:
+      label_kernel<0><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins);
+  }
   return cudaGetLastError();
 }
 

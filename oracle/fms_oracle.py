@@ -32,7 +32,13 @@ Readings of the paper used here (where it is silent or garbled):
     1e-5*h, at most 50 updates) and merged again with the same rule; modes are
     reported in canonical order (score descending, ties by coordinates);
   * every point is labelled by its nearest mode (Alg. 2 lines 11-13), ties to
-    the lowest mode index; the margin is the gap to the second-nearest mode.
+    the lowest mode index; the margin is the gap to the second-nearest mode;
+  * the cosine metric (the sibling method the paper cites, whose formulation
+    it does not print; metric="cosine"): points are normalised to the unit
+    sphere, the weight is exp((x.y - 1)/h^2) = exp(-||x - y||^2/(2h^2)) for
+    unit x, y (the Gaussian kernel of the chord distance), and every update
+    is projected back onto the sphere, y <- m(y)/||m(y)||; prune radius,
+    tolerances and margins are chord distances; modes are unit vectors.
 
 Parity status of each function is stated in its docstring ("pinned by ...").
 """
@@ -90,9 +96,12 @@ def _core():
             lib.orc_step_k.argtypes = [P, I64, I32, F64, P, I64, P, I32]
             lib.orc_trajectories.argtypes = [P, I64, I32, F64, F64, I32, P, I64, P, P]
             lib.orc_trajectories_k.argtypes = [P, I64, I32, F64, F64, I32, P, I64, P, P, I32]
+            lib.orc_trajectories_m.argtypes = [P, I64, I32, F64, F64, I32, P, I64, P, P, I32,
+                                               I32]
             lib.orc_label.argtypes = [P, I64, I32, P, I64, P, P]
             for f in (lib.orc_kde, lib.orc_kde_flat, lib.orc_step, lib.orc_step_k,
-                      lib.orc_trajectories, lib.orc_trajectories_k, lib.orc_label):
+                      lib.orc_trajectories, lib.orc_trajectories_k, lib.orc_trajectories_m,
+                      lib.orc_label):
                 f.restype = None
             _lib = lib
     return _lib
@@ -144,13 +153,18 @@ def step(X, Y, h, kernel="gaussian"):
     return out
 
 
-def trajectories(X, Y0, h, tol, max_iter, kernel="gaussian"):
+def trajectories(X, Y0, h, tol, max_iter, kernel="gaussian", sphere=False):
     """Independent trajectories y <- m(y) until ||step|| <= tol (Alg. 1 / Alg. 2 lines 5-7).
 
     Returns (Y_end, conv_iter, iters): conv_iter[i] is the 1-based update at
     which ||y_t - y_{t-1}|| <= tol first held, -1 if never within max_iter,
-    -2 if an update was undefined (flat kernel, empty window).
-    Pinned by: closed forms (two points, polygons) and brute-force maxima.
+    -2 if an update was undefined (flat kernel, empty window; on the sphere,
+    a mean at the origin).  sphere=True (cosine metric; X and Y0 on the unit
+    sphere): every update is projected back, y <- m(y)/||m(y)||.
+    Pinned by: closed forms (two points, polygons) and brute-force maxima; on
+    the sphere, the circular closed form (update angle = atan2(sum w sin,
+    sum w cos) with w = exp((cos(theta - phi) - 1)/h^2)), rotation
+    equivariance and invariance to the points' norms.
     """
     X = _f64(X)
     Y = _f64(np.atleast_2d(Y0)).copy()
@@ -159,9 +173,23 @@ def trajectories(X, Y0, h, tol, max_iter, kernel="gaussian"):
         raise ValueError("oracle supports d <= 64")
     conv = np.empty(m, dtype=np.int32)
     iters = np.empty(m, dtype=np.int32)
-    _core().orc_trajectories_k(_ptr(X), X.shape[0], d, float(h), float(tol), int(max_iter),
-                               _ptr(Y), m, _ptr(conv), _ptr(iters), KERNELS[kernel])
+    _core().orc_trajectories_m(_ptr(X), X.shape[0], d, float(h), float(tol), int(max_iter),
+                               _ptr(Y), m, _ptr(conv), _ptr(iters), KERNELS[kernel],
+                               1 if sphere else 0)
     return Y, conv, iters
+
+
+METRICS = ("euclidean", "cosine")
+
+
+def normalize_rows(X):
+    """Rows scaled to unit length (the cosine metric's points); a zero row is
+    an error (it has no direction)."""
+    X = _f64(X)
+    nrm = np.sqrt((X * X).sum(axis=1))
+    if np.any(nrm == 0.0):
+        raise ValueError("cosine metric: a point has zero norm")
+    return X / nrm[:, None]
 
 
 def label(X, modes, return_margins=True):
@@ -330,18 +358,23 @@ def canonical_order(modes, scores):
 
 def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gamma=0.95,
             merge_radius=0.0, rng_seed=0, seed_indices=None, refine=True,
-            refine_tol=1e-5, refine_max_iter=50, kernel="gaussian"):
+            refine_tol=1e-5, refine_max_iter=50, kernel="gaussian", metric="euclidean"):
     """Faster Mean-shift (Alg. 2, Sec. II-C/D) or plain mean shift (Alg. 1, all_seeds=True).
 
     kernel: "gaussian" (the reading used throughout) or "flat" (Eq. 12-15: the
-    window mean, density = window count).
+    window mean, density = window count).  metric: "euclidean" or "cosine"
+    (points normalised, updates projected onto the unit sphere; see the
+    module notes).
 
     Steps, in the paper's order: select N seeds; iterate every seed to
     convergence (trajectories are independent, so this is done seed by seed);
     Early Stopping decides t* and the kept seeds; prune; if N < L*M and N < n
     double N and repeat for the new seeds; refine and re-merge; label.
     """
-    X = _f64(X32)
+    if metric not in METRICS:
+        raise ValueError(f"metric must be one of {METRICS}")
+    sphere = metric == "cosine"
+    X = normalize_rows(X32) if sphere else _f64(X32)
     n, d = X.shape
     r_merge = float(merge_radius) if merge_radius and merge_radius > 0 else float(h)
     if all_seeds:
@@ -356,7 +389,7 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
     else:
         N = min(int(n_initial), n)
         seeds = seed_permutation(n, rng_seed, 0, N)
-    pos, conv, _ = trajectories(X, X[seeds], h, tol, max_iter, kernel)
+    pos, conv, _ = trajectories(X, X[seeds], h, tol, max_iter, kernel, sphere)
     history, tstars = [N], []
     while True:
         t_star, kept = early_stop(conv, gamma, max_iter)
@@ -368,7 +401,7 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
             break
         N_new = min(2 * N, n)
         new = seed_permutation(n, rng_seed, N, N_new)
-        p2, c2, _ = trajectories(X, X[new], h, tol, max_iter, kernel)
+        p2, c2, _ = trajectories(X, X[new], h, tol, max_iter, kernel, sphere)
         seeds = np.concatenate([seeds, new])
         pos = np.concatenate([pos, p2])
         conv = np.concatenate([conv, c2])
@@ -376,7 +409,7 @@ def cluster(X32, h, tol, max_iter, *, all_seeds=False, n_initial=128, L=8.0, gam
         history.append(N)
     modes0 = pos[kidx[acc]]
     if refine and M > 0:
-        ref, _, _ = trajectories(X, modes0, h, refine_tol * h, refine_max_iter, kernel)
+        ref, _, _ = trajectories(X, modes0, h, refine_tol * h, refine_max_iter, kernel, sphere)
         acc2, sc2 = merge(X, ref, np.arange(M), h, r_merge, kernel)
         modes, scores = ref[acc2], sc2[acc2]
     else:

@@ -133,8 +133,23 @@ void orc_step(const double* X, int64_t n, int d, double h, const double* Y, int6
  * which the test first held, -1 if it never held, -2 if an update was
  * undefined (flat kernel, empty window; Y_i keeps the last defined iterate).
  */
+/*
+ * Same, with sphere != 0 for the cosine metric: X and the start points lie on
+ * the unit sphere and every update is projected back onto it,
+ * y <- m(y) / ||m(y)||, so the step tested against tol is the projected one.
+ */
+void orc_trajectories_m(const double* X, int64_t n, int d, double h, double tol, int max_iter,
+                        double* Y, int64_t m, int32_t* conv_iter, int32_t* iters, int kernel,
+                        int sphere);
+
 void orc_trajectories_k(const double* X, int64_t n, int d, double h, double tol, int max_iter,
                         double* Y, int64_t m, int32_t* conv_iter, int32_t* iters, int kernel) {
+    orc_trajectories_m(X, n, d, h, tol, max_iter, Y, m, conv_iter, iters, kernel, 0);
+}
+
+void orc_trajectories_m(const double* X, int64_t n, int d, double h, double tol, int max_iter,
+                        double* Y, int64_t m, int32_t* conv_iter, int32_t* iters, int kernel,
+                        int sphere) {
     const double inv2h2 = 1.0 / (2.0 * h * h);
 #pragma omp parallel
     {
@@ -152,6 +167,17 @@ void orc_trajectories_k(const double* X, int64_t n, int d, double h, double tol,
                     iters[i] = t;
                     conv_iter[i] = -2;
                     break;
+                }
+                if (sphere) {
+                    double nn = 0.0;
+                    for (int k = 0; k < d; ++k) nn += ynew[k] * ynew[k];
+                    nn = sqrt(nn);
+                    if (!(nn > 0.0)) {     /* the mean is the origin: undefined direction */
+                        iters[i] = t;
+                        conv_iter[i] = -2;
+                        break;
+                    }
+                    for (int k = 0; k < d; ++k) ynew[k] /= nn;
                 }
                 double step2 = 0.0;
                 for (int k = 0; k < d; ++k) {

@@ -258,3 +258,30 @@ WORKLOADS = {
     "paper_3d": paper_3d,
     "embedding_32d": embedding_32d,
 }
+
+
+def directional_blobs(seed: int, k: int, d: int, per: int, spread: float, h: float,
+                      min_angle: float = 0.9, radius=(0.5, 20.0)) -> Workload:
+    """Unit directions (pairwise angles >= min_angle radians, rejection-sampled)
+    with Gaussian spread `spread` around each, then every point scaled by a
+    random positive length in `radius` (the cosine metric ignores it): the
+    embedding-style workload of the cosine-metric variant."""
+    rng = np.random.default_rng(seed)
+    dirs = []
+    tries = 0
+    while len(dirs) < k:
+        u = rng.standard_normal(d)
+        u /= np.linalg.norm(u)
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place separated directions")
+        if all(math.acos(max(-1.0, min(1.0, float(u @ e)))) >= min_angle for e in dirs):
+            dirs.append(u)
+    dirs = np.array(dirs)
+    lab = np.repeat(np.arange(k), per)
+    P = dirs[lab] + spread * rng.standard_normal((k * per, d))
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    P *= rng.uniform(radius[0], radius[1], (k * per, 1))
+    perm = rng.permutation(k * per)
+    return Workload(name=f"directional_{k}x{d}", X=_as_points(P[perm]), planted=lab[perm],
+                    centers=dirs, h=h, tol=1e-3 * h, max_iter=300, all_seeds=False, gamma=0.95)

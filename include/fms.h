@@ -95,11 +95,26 @@ typedef struct fms_options {
                                   the number of such points; a seed whose window
                                   is empty fails.  FP32 updates only (precision is
                                   ignored); not available in fms_cluster_batched. */
-  int32_t reserved[4];      /* must be zero                                       */
+  int32_t metric;           /* distance (FMS_METRIC_*):
+                               EUCLIDEAN (0): the paper's metric.
+                               COSINE (1): the sibling method the paper cites
+                                  (its formulation is not printed there): the
+                                  points are normalised to the unit sphere (a
+                                  zero point is an invalid argument), the weight
+                                  is the kernel of the chord distance ||x - y||
+                                  between unit vectors (Gaussian: exp((x.y - 1)
+                                  / h^2)), and every update is projected back
+                                  onto the sphere.  h, tol, merge_radius and the
+                                  margins are chord distances; modes are unit
+                                  vectors.  FP32 updates only; not available in
+                                  fms_cluster_batched.                          */
+  int32_t reserved[3];      /* must be zero                                       */
 } fms_options;
 
 #define FMS_KERNEL_GAUSSIAN 0
 #define FMS_KERNEL_FLAT 1
+#define FMS_METRIC_EUCLIDEAN 0
+#define FMS_METRIC_COSINE 1
 
 #define FMS_PRECISION_AUTO 0
 #define FMS_PRECISION_FP32 1

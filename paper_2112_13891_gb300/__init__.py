@@ -27,6 +27,7 @@ FMS_OK, FMS_ERR_INVALID_ARG, FMS_ERR_NONFINITE, FMS_ERR_CAPACITY = 0, 1, 2, 3
 FMS_ERR_TIMEOUT, FMS_ERR_CUDA, FMS_ERR_WORKSPACE, FMS_ERR_UNSUPPORTED = 4, 5, 6, 7
 PRECISION = {"auto": 0, "fp32": 1, "tensor": 2}
 KERNEL = {"gaussian": 0, "flat": 1}
+METRIC = {"euclidean": 0, "cosine": 1}
 MAX_DIM = 64
 
 
@@ -37,7 +38,7 @@ class FmsOptions(ctypes.Structure):
                 ("rng_seed", ctypes.c_uint64), ("seed_indices", ctypes.c_void_p),
                 ("n_seed_indices", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("metric", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class FmsStats(ctypes.Structure):
@@ -127,7 +128,7 @@ def _points(x: torch.Tensor) -> torch.Tensor:
 
 def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
                  skip_refine=False, rng_seed=0, seed_indices=None, profile=False,
-                 precision="auto", kernel="gaussian") -> FmsOptions:
+                 precision="auto", kernel="gaussian", metric="euclidean") -> FmsOptions:
     o = FmsOptions()
     _lib.fms_options_default(ctypes.byref(o))
     o.all_seeds = int(bool(all_seeds))
@@ -143,6 +144,7 @@ def make_options(*, all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_rad
     o.profile = int(bool(profile))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+    o.metric = METRIC[metric] if isinstance(metric, str) else int(metric)
     return o
 
 
@@ -202,7 +204,7 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
             all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
             skip_refine=False, rng_seed=0, seed_indices=None, max_modes=None, margins=True,
             workspace: Workspace = None, profile=False, precision="auto", kernel="gaussian",
-            out=None) -> ClusterResult:
+            metric="euclidean", out=None) -> ClusterResult:
     """Faster Mean-shift clustering of the rows of `points` (fms_cluster).
 
     `out` may pass preallocated (modes [max_modes, d], labels [n], margins [n]).
@@ -214,7 +216,7 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
     o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
                      merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
                      seed_indices=seed_indices, profile=profile, precision=precision,
-                     kernel=kernel)
+                     kernel=kernel, metric=metric)
     if out is not None:
         modes, labels, mar = out
         cap = modes.shape[0]
@@ -251,6 +253,7 @@ class FramesResult:
 def cluster_frames(frames, h: float, tol: float = 0.0, max_iter: int = 300, *, H=32.0,
                    n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0, skip_refine=False,
                    rng_seed=0, max_modes=256, precision="auto", kernel="gaussian",
+                   metric="euclidean",
                    workspace: Workspace = None) -> FramesResult:
     """Faster Mean-shift over a frame sequence (fms_cluster_frames): `frames`
     is a [F, n, d] CUDA tensor or a list of F [n, d] tensors."""
@@ -260,7 +263,7 @@ def cluster_frames(frames, h: float, tol: float = 0.0, max_iter: int = 300, *, H
     F, n, d = frames.shape
     o = make_options(n_initial=n_initial, L=L, gamma=gamma, merge_radius=merge_radius,
                      skip_refine=skip_refine, rng_seed=rng_seed, precision=precision,
-                     kernel=kernel)
+                     kernel=kernel, metric=metric)
     cap = max(int(max_modes), 1)
     modes = torch.empty((F, cap, d), dtype=torch.float32, device=frames.device)
     labels = torch.empty((F, n), dtype=torch.int32, device=frames.device)
@@ -448,7 +451,8 @@ class BatchedResult:
 def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, offsets=None,
                     n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0, skip_refine=False,
                     all_seeds=False, rng_seed=0, max_modes=256, margins=True,
-                    workspace: Workspace = None, kernel="gaussian") -> BatchedResult:
+                    workspace: Workspace = None, kernel="gaussian",
+                    metric="euclidean") -> BatchedResult:
     """Cluster many point sets at once.  `points` is a list of [n_b, d] CUDA
     tensors, or one [total, d] tensor with host `offsets` (B+1 ints)."""
     import numpy as np
@@ -463,7 +467,7 @@ def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, 
     total, d = X.shape
     o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
                      merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
-                     kernel=kernel)
+                     kernel=kernel, metric=metric)
     offs = np.ascontiguousarray(offsets)
     optr = offs.ctypes.data_as(ctypes.c_void_p)
     need = int(_lib.fms_batched_workspace_size(optr, B, d, ctypes.byref(o)))

@@ -118,6 +118,10 @@ struct GraphCache {
   int used = 0, next = 0;
   GraphKey seen[kSeen];
   int n_seen = 0, next_seen = 0;
+  // builds stop when they outrun the reuse (a working set larger than the
+  // cache would rebuild on every call)
+  int64_t builds = 0, hits = 0;
+  bool disabled = false;   // set while fms_cluster_frames runs its frames
   ~GraphCache() {
     for (int i = 0; i < used; ++i)
       if (entries[i].exec) cudaGraphExecDestroy(entries[i].exec);
@@ -248,7 +252,8 @@ void fill_defaults(const fms_options* in, fms_options* o) {
   o->profile = in->profile;
   o->precision = in->precision;
   o->kernel = in->kernel;
-  for (int i = 0; i < 4; ++i) o->reserved[i] = in->reserved[i];
+  o->metric = in->metric;
+  for (int i = 0; i < 3; ++i) o->reserved[i] = in->reserved[i];
 }
 
 int64_t seed_capacity(int64_t n, const fms_options& o) {
@@ -331,11 +336,13 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       !(o.gamma > 0.0f && o.gamma <= 1.0f) || !(o.L > 0.0f) || !isfinite(o.merge_radius) ||
       o.merge_radius < 0.0f || (o.seed_indices && o.n_seed_indices < 1))
     return FMS_ERR_INVALID_ARG;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return FMS_ERR_INVALID_ARG;
   if (o.precision < FMS_PRECISION_AUTO || o.precision > FMS_PRECISION_TENSOR)
     return FMS_ERR_INVALID_ARG;
   if (o.kernel != FMS_KERNEL_GAUSSIAN && o.kernel != FMS_KERNEL_FLAT) return FMS_ERR_INVALID_ARG;
+  if (o.metric != FMS_METRIC_EUCLIDEAN && o.metric != FMS_METRIC_COSINE) return FMS_ERR_INVALID_ARG;
+  const bool cosine = o.metric == FMS_METRIC_COSINE;
   const int kf = o.kernel == FMS_KERNEL_FLAT ? kKernelFlat : kKernelGaussian;
   if (tol == 0.0f) tol = 1e-3f * h;
   if (o.all_seeds) o.gamma = 1.0f;
@@ -343,7 +350,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
   const Dev dv = device_info();
   if (dv.sms <= 0) return FMS_ERR_CUDA;
   const int64_t Ncap = seed_capacity(n, o);
-  const bool tensor = kf == kKernelGaussian && use_tensor_step(d, o.precision);
+  const bool tensor = kf == kKernelGaussian && !cosine && use_tensor_step(d, o.precision);
   const Layout Lo = make_layout(n, d, Ncap, dv.sms, tensor);
   const int DP = Lo.DP, DA = Lo.DA, R = Lo.R;
   bool owns_ws = false;
@@ -426,6 +433,10 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     const int qmax = d <= 7 ? round_max_clusters(d) : 0;
 
     const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
+    // cosine metric: the packed points lie on the sphere of radius scale, and
+    // every update is projected back onto it
+    const float sphere_r = cosine ? (float)scale : 0.0f;
+    const double sphere_rd = cosine ? scale : 0.0;
     const double tol_s = (double)tol * scale;
     const float tol2_s = (float)(tol_s * tol_s);
     const float coarse_tol2_s = (float)(100.0 * tol_s * tol_s);   // (10 tol)^2
@@ -497,7 +508,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     // resume: 0 host path from the start, 1 host rounds from the graph's state,
     // 2 host refinement and labels, 3 the graph did everything
     int resume = 0;
-    const bool graph_ok = !o.profile && !owns_ws && hbuf && qmax > 0 && !tensor &&
+    const bool graph_ok = !graph_cache().disabled && !o.profile && !owns_ws && hbuf &&
+                          qmax > 0 && !tensor &&
                           !o.all_seeds && !o.seed_indices && !o.skip_refine &&
                           max_iter <= kHistCap && N0 <= cap_seeds;
     if (graph_ok) {
@@ -528,7 +540,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         gc.seen[gc.next_seen] = key;
         gc.next_seen = (gc.next_seen + 1) % GraphCache::kSeen;
         if (gc.n_seen < GraphCache::kSeen) ++gc.n_seen;
-      } else if (!ge) {
+      } else if (!ge && gc.builds < 8 + 2 * gc.hits) {
+        ++gc.builds;
         // build: the same sequence of launches as the host path, captured on
         // private streams, with the round's N and target read from RoundCtl
         GraphEntry* slot = &gc.entries[gc.next];
@@ -554,7 +567,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, kCtlBlockBytes, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, cs);
         if (e == cudaSuccess)
-          e = launch_pack_points(points, n, d, DP, (float)scale, Xs, status, cs);
+          e = launch_pack_points(points, n, d, DP, (float)scale, Xs, status, cs, cosine ? 1 : 0);
         if (e == cudaSuccess)
           e = launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, 0, 0, N0, seed_idx, y, it, conv,
                                state, status, cs, init_state);
@@ -572,7 +585,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
             e2 = launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, qmax, hist, 0,
                                  max_iter, tol2_s,
                                  reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, cs2,
-                                 kf, rctl_round);
+                                 kf, rctl_round, sphere_r);
           if (e2 == cudaSuccess)
             e2 = launch_round_finish(hist, 0, max_iter, state, conv, 0, keep_exhausted, kept,
                                      mctl, ctl, n, R, Lo.tl, cs2, rctl_round, wlast, score);
@@ -598,7 +611,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           cudaError_t e2 = launch_ms_refine(
               Xs, n, d, y, kept, acc1, &mctl->M, qmax, ym, yf, mscore, rtol_s * rtol_s,
               kRefineMaxIter, &rctl->steps, reinterpret_cast<unsigned long long*>(&rctl->evals),
-              cs2, kf);
+              cs2, kf, sphere_rd);
           if (e2 == cudaSuccess)
             e2 = launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        cap_modes, cs2);
@@ -608,7 +621,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                                         cs2);
           if (e2 == cudaSuccess)
             e2 = launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins,
-                              cs2);
+                              cs2, cosine ? 1 : 0);
           cudaGraph_t gp = post;
           const cudaError_t e3 = cudaStreamEndCapture(cs2, &gp);
           e = e2 != cudaSuccess ? e2 : e3;
@@ -630,6 +643,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         ge = slot;
       }
       if (ge && ge->exec) {
+        ++gc.hits;
         FMS_CUDA(cudaGraphLaunch(ge->exec, st));
         FMS_CUDA(readback());
         RoundCtl rcv;
@@ -669,7 +683,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     };
     if (resume == 0) {
       mark(0);
-      FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st));
+      FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st,
+                                    cosine ? 1 : 0));
       if (tensor) FMS_LAUNCH(launch_tc_pack(Xs, n, d, DP, img, st));
       N = N0;
       FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y,
@@ -700,7 +715,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
                                    target, max_iter, tol2_s,
                                    reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, st,
-                                   kf));
+                                   kf, nullptr, sphere_r));
         if (o.profile) cudaEventRecord(rb, st);
         // the prune's densities: sum w of each kept seed's last update (ms_round)
         FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N, keep_exhausted,
@@ -719,7 +734,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
             }
             FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
                                      max_iter, n, R, tl_iter, N, target, st, update_grid(N),
-                                     coarse_tol2_s));
+                                     coarse_tol2_s, sphere_r));
           }
           FMS_CUDA(readback());
           if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
@@ -765,7 +780,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       const int clusters = hm.M < qmax ? hm.M : qmax;
       FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
                                   rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
-                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st, kf));
+                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st, kf,
+                                  sphere_rd));
       FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        hm.M, st));
       FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,
@@ -780,7 +796,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           FMS_LAUNCH(step_launch(yf, ract, &rctl->s, &rctl->C, &rctl->Lc));
           FMS_LAUNCH(launch_refine_update(part, ract, rctl, ym, yf, mdone, mscore, d, DP, DA,
                                           rtol_s * rtol_s, kRefineMaxIter, 0, n, R, Lo.tl, hm.M,
-                                          st));
+                                          st, sphere_rd));
         }
         FMS_CUDA(readback());
         if (hrctl.done) break;
@@ -803,7 +819,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     }
     // --- labels (Alg. 2 lines 11-13) ---
     mark(3);
-    FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st));
+    FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st,
+                            cosine ? 1 : 0));
     mark(4);
     hslog.assign(n_slog, 0);
     htclog.assign(n_tclog, 0);
@@ -930,6 +947,13 @@ fms_status fms_cluster_frames(const float* frames, int32_t F, int64_t n, int32_t
   }
   fms_status rc = FMS_OK;
   int64_t N = o.n_initial;
+  // frames have their own pointers, so the per-call graph cache would only
+  // churn: the frames run on the host-driven path
+  struct NoGraph {
+    bool prev;
+    NoGraph() : prev(graph_cache().disabled) { graph_cache().disabled = true; }
+    ~NoGraph() { graph_cache().disabled = prev; }
+  } no_graph;
   for (int32_t f = 0; f < F; ++f) {
     fms_options of = o;
     of.n_initial = (int32_t)(N < n ? N : n);

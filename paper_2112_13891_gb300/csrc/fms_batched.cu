@@ -211,9 +211,11 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
     o.seed_indices = opt_in->seed_indices;
     o.profile = opt_in->profile;
     o.kernel = opt_in->kernel;
+    o.metric = opt_in->metric;
   }
   if (stats) memset(stats, 0, sizeof(*stats));
   if (o.kernel != FMS_KERNEL_GAUSSIAN) return FMS_ERR_UNSUPPORTED;   // (flat: fms_cluster only)
+  if (o.metric != FMS_METRIC_EUCLIDEAN) return FMS_ERR_UNSUPPORTED;   // (cosine: fms_cluster only)
   if (!points || !offsets || B < 1 || d < 1 || d > FMS_MAX_DIM || !(h > 0.f) || !isfinite(h) ||
       !(tol >= 0.f) || max_iter < 1 || !out_labels || !out_n_modes || max_modes < 0 ||
       (max_modes > 0 && !out_modes) || o.seed_indices || !(o.gamma > 0.f && o.gamma <= 1.f))

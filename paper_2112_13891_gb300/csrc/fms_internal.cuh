@@ -308,8 +308,9 @@ __device__ inline int block_min(int v, int* red) {
 // ---------------------------------------------------------------------------
 
 // k_iter.cu
+// unit != 0 (cosine metric): each row normalised to unit length first
 cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
-                               uint32_t* status, cudaStream_t st);
+                               uint32_t* status, cudaStream_t st, int unit = 0);
 cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
                              const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
                              int32_t count, int32_t* seed_idx, float* y, int32_t* it,
@@ -330,7 +331,8 @@ cudaError_t launch_iter_begin(IterCtl* ctl, const int32_t* state, const int32_t*
 cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
-                          cudaStream_t st, int grid, float coarse_tol2_s = 0.0f);
+                          cudaStream_t st, int grid, float coarse_tol2_s = 0.0f,
+                          float sphere_r = 0.0f);   // > 0: project onto that sphere
 cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
                               cudaStream_t st);
 cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
@@ -343,14 +345,16 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
                             float* wlast, cudaStream_t st, int kf = kKernelGaussian,
-                            const RoundCtl* rc = nullptr);   // rc: target from the device
+                            const RoundCtl* rc = nullptr,   // rc: target from the device
+                            float sphere_r = 0.0f);         // > 0: project onto that sphere
 // (wlast[slot]: sum w of the seed's latest update, at the position before it)
 int round_max_clusters(int d);
 cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
                              int clusters, double* ym, float* yf, double* mscore, double tol2_s,
                              int max_iter, int32_t* iters_out, unsigned long long* evals,
-                             cudaStream_t st, int kf = kKernelGaussian);
+                             cudaStream_t st, int kf = kKernelGaussian,
+                             double sphere_r = 0.0);
 cudaError_t launch_round_list(const int32_t* state, int N, int32_t* list, int32_t* S_out,
                               cudaStream_t st, const RoundCtl* rc = nullptr);   // rc: N
 cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
@@ -428,7 +432,8 @@ cudaError_t launch_refine_setup(const float* y, const int32_t* kept, const int32
 cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
                                  float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
                                  double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
-                                 Tiling tl, int max_M, cudaStream_t st);
+                                 Tiling tl, int max_M, cudaStream_t st,
+                                 double sphere_r = 0.0);
 cudaError_t launch_canonical_order(const double* ym, const double* mscore,
                                    const int32_t* accepted, const int32_t* M_ptr, int d, int DP,
                                    double inv_scale, float* out_modes, int32_t max_modes,
@@ -439,6 +444,7 @@ cudaError_t launch_unrefined_modes(const float* y, const int32_t* kept, const in
                                    double* mscore, int max_M, cudaStream_t st);
 cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
                          const int32_t* M_dev, int32_t M_host, int32_t* labels, float* margins,
-                         cudaStream_t st);
+                         cudaStream_t st,
+                         int unit = 0);   // unit: compare the points' directions
 
 }  // namespace fms

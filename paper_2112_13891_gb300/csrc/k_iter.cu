@@ -26,8 +26,35 @@ __global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStNonFinite);
 }
 
+// Cosine metric: row j scaled to unit length, then by s; a zero row flags
+// kStBadArg (it has no direction), a non-finite one kStNonFinite.
+__global__ void pack_unit_rows_kernel(const float* __restrict__ X, int64_t n, int d, int DP,
+                                      float scale, float* __restrict__ Xs, uint32_t* status) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double nn = 0.0;
+    bool bad = false;
+    for (int k = 0; k < d; ++k) {
+      const float v = X[j * d + k];
+      if (!isfinite(v)) bad = true;
+      nn += (double)v * (double)v;
+    }
+    if (bad) atomicOr(status, kStNonFinite);
+    else if (!(nn > 0.0)) atomicOr(status, kStBadArg);
+    const double f = nn > 0.0 ? (double)scale / sqrt(nn) : 0.0;
+    for (int k = 0; k < DP; ++k) Xs[j * DP + k] = k < d ? (float)((double)X[j * d + k] * f) : 0.0f;
+  }
+}
+
 cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
-                               uint32_t* status, cudaStream_t st) {
+                               uint32_t* status, cudaStream_t st, int unit) {
+  if (unit) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    pack_unit_rows_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status);
+    return cudaGetLastError();
+  }
   int64_t total = n * DP;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
@@ -396,7 +423,8 @@ __global__ void __launch_bounds__(256)
     update_kernel(const float* __restrict__ part, int32_t* __restrict__ active, IterCtl* ctl,
                   float* __restrict__ y, int32_t* __restrict__ it, int32_t* __restrict__ conv,
                   int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s, int64_t n,
-                  int32_t R, Tiling tl, int N, int target, int max_iter, float coarse_tol2_s) {
+                  int32_t R, Tiling tl, int N, int target, int max_iter, float coarse_tol2_s,
+                  float sphere_r) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
   __shared__ float red[8][96];
@@ -444,8 +472,45 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
-    const bool finite = ok && isfinite(step2);
-    if (finite) {
+    bool finite = ok && isfinite(step2);
+    if (finite && sphere_r > 0.0f) {
+      // cosine metric: the new position is the mean scaled back onto the
+      // sphere of radius sphere_r; the step is the projected one
+      float pv[3] = {0.f, 0.f, 0.f};
+      float nn = 0.0f;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) {
+          pv[u] = y[slot * DP + (k - 1)] + delta[u];
+          nn = fmaf(pv[u], pv[u], nn);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFull, nn, o);
+      const float f = sphere_r / sqrtf(nn);
+      step2 = 0.0f;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) {
+          const float q = pv[u] * f;
+          const float e = q - y[slot * DP + (k - 1)];
+          step2 = fmaf(e, e, step2);
+          pv[u] = q;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
+      finite = nn > 0.0f && isfinite(step2);
+      if (finite) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int k = lane + 32 * u;
+          if (k >= 1 && k <= d) y[slot * DP + (k - 1)] = pv[u];
+        }
+      }
+    } else if (finite) {
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int k = lane + 32 * u;
@@ -482,9 +547,9 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
-                          cudaStream_t st, int grid, float coarse_tol2_s) {
+                          cudaStream_t st, int grid, float coarse_tol2_s, float sphere_r) {
   update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s, n,
-                                      R, tl, N, target, max_iter, coarse_tol2_s);
+                                      R, tl, N, target, max_iter, coarse_tol2_s, sphere_r);
   return cudaGetLastError();
 }
 

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256)
                          IterCtl* rctl, double* __restrict__ ym, float* __restrict__ yf,
                          int32_t* __restrict__ mdone, double* __restrict__ mscore, int d, int DP,
                          int DA, double tol2_s, int max_iter, int score_only, int64_t n,
-                         int32_t R, Tiling tl) {
+                         int32_t R, Tiling tl, double sphere_r) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
   __shared__ double red[8][96];
@@ -379,7 +379,47 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
-    if (ok) {
+    bool good = ok;
+    if (ok && sphere_r > 0.0) {
+      // cosine metric: the FP64 position scaled back onto the sphere
+      double pv[3] = {0.0, 0.0, 0.0}, nn = 0.0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) {
+          pv[u] = ym[(int64_t)m * DP + (k - 1)] + delta[u];
+          nn += pv[u] * pv[u];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFull, nn, o);
+      const double f = sphere_r / sqrt(nn);
+      step2 = 0.0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= 1 && k <= d) {
+          const int64_t e = (int64_t)m * DP + (k - 1);
+          pv[u] *= f;
+          const double dd = pv[u] - ym[e];
+          step2 += dd * dd;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) step2 += __shfl_xor_sync(kFull, step2, o);
+      good = nn > 0.0 && isfinite(step2);
+      if (good) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int k = lane + 32 * u;
+          if (k >= 1 && k <= d) {
+            const int64_t e = (int64_t)m * DP + (k - 1);
+            ym[e] = pv[u];
+            yf[e] = (float)pv[u];
+          }
+        }
+      }
+    } else if (ok) {
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int k = lane + 32 * u;
@@ -391,7 +431,7 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    if (lane == 0 && (!ok || step2 <= tol2_s)) mdone[m] = 1;
+    if (lane == 0 && (!good || step2 <= tol2_s)) mdone[m] = 1;
   }
   if (score_only) return;
   // last block: the modes still moving take the next update
@@ -430,12 +470,13 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
                                  float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
                                  double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
-                                 Tiling tl, int max_M, cudaStream_t st) {
+                                 Tiling tl, int max_M, cudaStream_t st, double sphere_r) {
   int blocks = max_M;  // one block per mode (many chunks) or one warp per mode
   if (blocks < 1) blocks = 1;
   if (blocks > 1216) blocks = 1216;
   refine_update_kernel<<<blocks, 256, 0, st>>>(part, active, rctl, ym, yf, mdone, mscore, d, DP,
-                                               DA, tol2_s, max_iter, score_only, n, R, tl);
+                                               DA, tol2_s, max_iter, score_only, n, R, tl,
+                                               sphere_r);
   return cudaGetLastError();
 }
 
@@ -529,7 +570,7 @@ template <int DT>
 __global__ void __launch_bounds__(256)
     label_kernel(const float* __restrict__ X, int64_t n, int d_arg, const float* __restrict__ modes,
                  const int32_t* __restrict__ M_ptr, int M_host, int32_t* __restrict__ labels,
-                 float* __restrict__ margins) {
+                 float* __restrict__ margins, int unit) {
   constexpr int DX = DT > 0 ? DT : FMS_MAX_DIM_PAD;
   const int d = DT > 0 ? DT : d_arg;
   __shared__ float sm[kLabelTileFloats];
@@ -542,6 +583,17 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int k = 0; k < DX; ++k)
         if (k < d) x[k] = X[j * d + k];
+      if (unit) {
+        // cosine metric: the point's direction (in FP64, as the packing)
+        double nn = 0.0;
+#pragma unroll
+        for (int k = 0; k < DX; ++k)
+          if (k < d) nn += (double)x[k] * (double)x[k];
+        const double f = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+#pragma unroll
+        for (int k = 0; k < DX; ++k)
+          if (k < d) x[k] = (float)((double)x[k] * f);
+      }
     }
     float b1 = INFINITY, b2 = INFINITY;
     int arg = -1;
@@ -578,14 +630,14 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
                          const int32_t* M_dev, int32_t M_host, int32_t* labels, float* margins,
-                         cudaStream_t st) {
+                         cudaStream_t st, int unit) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   switch (d) {
 #define FMS_LABEL(D_)                                                                           \
   case D_:                                                                                      \
-    label_kernel<D_><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins); \
+    label_kernel<D_><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins, unit); \
     break;
     FMS_LABEL(1)
     FMS_LABEL(2)
@@ -597,7 +649,8 @@ cudaError_t launch_label(const float* X, int64_t n, int d, const float* modes,
     FMS_LABEL(8)
 #undef FMS_LABEL
     default:
-      label_kernel<0><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins);
+      label_kernel<0><<<(int)blocks, 256, 0, st>>>(X, n, d, modes, M_dev, M_host, labels, margins,
+                                                  unit);
   }
   return cudaGetLastError();
 }

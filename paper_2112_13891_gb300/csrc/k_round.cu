@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
                     int32_t* __restrict__ state, const int32_t* __restrict__ list,
                     const int32_t* __restrict__ S_ptr, int32_t* hist, int target_arg,
                     int max_iter, float tol2_s, unsigned long long* evals,
-                    const RoundCtl* __restrict__ rc, float* __restrict__ wlast) {
+                    const RoundCtl* __restrict__ rc, float* __restrict__ wlast, float sphere_r) {
   const int target = rc ? rc->target : target_arg;
   constexpr int R = 32 / DA;
   constexpr int SMAX = kSeedsPerCluster;
@@ -474,7 +474,29 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
         step2 = fmaf(dl[k], dl[k], step2);
       }
       ok = ok && isfinite(step2);
-      if (ok) {
+      if (ok && sphere_r > 0.0f) {
+        // cosine metric: the mean scaled back onto the sphere of radius
+        // sphere_r; the step is the projected one
+        float p[D], nn = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          p[k] = sy[i][k] + dl[k];
+          nn = fmaf(p[k], p[k], nn);
+        }
+        const float f = sphere_r / sqrtf(nn);
+        step2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          p[k] *= f;
+          const float e = p[k] - sy[i][k];
+          step2 = fmaf(e, e, step2);
+        }
+        ok = nn > 0.0f && isfinite(step2);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sy[i][k] = p[k];
+        }
+      } else if (ok) {
 #pragma unroll
         for (int k = 0; k < D; ++k) sy[i][k] += dl[k];
       }
@@ -517,7 +539,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
                                   int32_t* state, const int32_t* list, const int32_t* S_ptr,
                                   int clusters, int32_t* hist, int target, int max_iter,
                                   float tol2_s, unsigned long long* evals, const RoundCtl* rc,
-                                  float* wlast, cudaStream_t st) {
+                                  float* wlast, float sphere_r, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(clusters * kClusterCtas);
   cfg.blockDim = dim3(kRoundWarps * 32);
@@ -531,7 +553,7 @@ static cudaError_t launch_round_t(const float* Xs, int n, float* y, int32_t* it,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ms_round_kernel<D, DP, DA, KF>, Xs, n, y, it, conv, state, list,
-                            S_ptr, hist, target, max_iter, tol2_s, evals, rc, wlast);
+                            S_ptr, hist, target, max_iter, tol2_s, evals, rc, wlast, sphere_r);
 }
 
 template <int D, int DP, int DA>
@@ -575,14 +597,15 @@ cudaError_t launch_ms_round(const float* Xs, int64_t n, int d, float* y, int32_t
                             int32_t* conv, int32_t* state, const int32_t* list,
                             const int32_t* S_ptr, int clusters, int32_t* hist, int target,
                             int max_iter, float tol2_s, unsigned long long* evals,
-                            float* wlast, cudaStream_t st, int kf, const RoundCtl* rc) {
+                            float* wlast, cudaStream_t st, int kf, const RoundCtl* rc,
+                            float sphere_r) {
 #define FMS_ROUND(D_, DP_, DA_)                                                                \
   return kf ? launch_round_t<D_, DP_, DA_, 1>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
                                               clusters, hist, target, max_iter, tol2_s, evals, \
-                                              rc, wlast, st)                                          \
+                                              rc, wlast, sphere_r, st)                                          \
             : launch_round_t<D_, DP_, DA_, 0>(Xs, (int)n, y, it, conv, state, list, S_ptr,     \
                                               clusters, hist, target, max_iter, tol2_s, evals, \
-                                              rc, wlast, st)
+                                              rc, wlast, sphere_r, st)
   switch (d) {
     case 1: FMS_ROUND(1, 4, 2);
     case 2: FMS_ROUND(2, 4, 4);
@@ -616,7 +639,8 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
                      const int32_t* __restrict__ kept, const int32_t* __restrict__ accepted,
                      const int32_t* __restrict__ M_ptr, double* __restrict__ ym,
                      float* __restrict__ yf, double* __restrict__ mscore, double tol2_s,
-                     int max_iter, int32_t* iters_out, unsigned long long* evals) {
+                     int max_iter, int32_t* iters_out, unsigned long long* evals,
+                     double sphere_r) {
   constexpr int R = 32 / DA;
   constexpr int SMAX = kModesPerCluster;
   constexpr int GMAX = (SMAX + R - 1) / R;
@@ -721,7 +745,31 @@ __global__ void __launch_bounds__(kRoundWarps * 32, 1)
         dl[k] = ok ? tot[a][1 + k] / W - (sym[i][k] - (double)sy[i][k]) : 0.0;
         step2 += dl[k] * dl[k];
       }
-      if (ok) {
+      if (ok && sphere_r > 0.0) {
+        // cosine metric: project the FP64 position onto the sphere
+        double p[D], nn = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          p[k] = sym[i][k] + dl[k];
+          nn += p[k] * p[k];
+        }
+        const double f = sphere_r / sqrt(nn);
+        step2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          p[k] *= f;
+          dl[k] = p[k] - sym[i][k];
+          step2 += dl[k] * dl[k];
+        }
+        ok = nn > 0.0 && isfinite(step2);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            sym[i][k] = p[k];
+            sy[i][k] = (float)p[k];
+          }
+        }
+      } else if (ok) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           sym[i][k] += dl[k];
@@ -748,7 +796,7 @@ static cudaError_t launch_refine_t(const float* Xs, int n, const float* y, const
                                    const int32_t* accepted, const int32_t* M_ptr, int clusters,
                                    double* ym, float* yf, double* mscore, double tol2_s,
                                    int max_iter, int32_t* iters_out, unsigned long long* evals,
-                                   cudaStream_t st) {
+                                   double sphere_r, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(clusters * kClusterCtas);
   cfg.blockDim = dim3(kRoundWarps * 32);
@@ -761,29 +809,29 @@ static cudaError_t launch_refine_t(const float* Xs, int n, const float* y, const
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ms_refine_kernel<D, DP, DA, KF>, Xs, n, y, kept, accepted, M_ptr,
-                            ym, yf, mscore, tol2_s, max_iter, iters_out, evals);
+                            ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r);
 }
 
 cudaError_t launch_ms_refine(const float* Xs, int64_t n, int d, const float* y,
                              const int32_t* kept, const int32_t* accepted, const int32_t* M_ptr,
                              int clusters, double* ym, float* yf, double* mscore, double tol2_s,
                              int max_iter, int32_t* iters_out, unsigned long long* evals,
-                             cudaStream_t st, int kf) {
+                             cudaStream_t st, int kf, double sphere_r) {
   switch (d) {
-    case 1: return kf ? launch_refine_t<1, 4, 2, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<1, 4, 2, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 2: return kf ? launch_refine_t<2, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<2, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 3: return kf ? launch_refine_t<3, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<3, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 4: return kf ? launch_refine_t<4, 4, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<4, 4, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 5: return kf ? launch_refine_t<5, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<5, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 6: return kf ? launch_refine_t<6, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<6, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
-    case 7: return kf ? launch_refine_t<7, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st)
-                 : launch_refine_t<7, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, st);
+    case 1: return kf ? launch_refine_t<1, 4, 2, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<1, 4, 2, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 2: return kf ? launch_refine_t<2, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<2, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 3: return kf ? launch_refine_t<3, 4, 4, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<3, 4, 4, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 4: return kf ? launch_refine_t<4, 4, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<4, 4, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 5: return kf ? launch_refine_t<5, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<5, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 6: return kf ? launch_refine_t<6, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<6, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
+    case 7: return kf ? launch_refine_t<7, 8, 8, 1>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st)
+                 : launch_refine_t<7, 8, 8, 0>(Xs, (int)n, y, kept, accepted, M_ptr, clusters, ym, yf, mscore, tol2_s, max_iter, iters_out, evals, sphere_r, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -551,6 +551,34 @@ def bench_extra(args):
                 rec["n_modes"] = [int(m.shape[0]) for m in r.modes]
             line[label] = rec
         line["value"] = line["carry_H32"]["ms_per_frame"]
+    elif args.workload == "cosine_embed":
+        # N4: the cosine metric on direction data (200K unit-normal-like points
+        # in 3-D, 200K embedding-like points in 16-D), against the Euclidean
+        # metric on the same points normalised beforehand
+        line.update({"metric": "ms per 200K-point clustering, cosine metric", "unit": "ms"})
+        for d, k, spread, h, ang in ((3, 20, 0.04, 0.12, 0.5), (16, 32, 0.04, 0.25, 0.9)):
+            w = fi.directional_blobs(seed=100 + d, k=k, d=d, per=200_000 // k, spread=spread,
+                                     h=h, min_angle=ang)
+            X = torch.from_numpy(w.X).cuda()
+            U = X / X.norm(dim=1, keepdim=True)
+            n = X.shape[0]
+            rec = {"n": n, "k": k, "h_chord": h}
+            for metric, pts in (("cosine", X), ("euclidean_on_normalised", U)):
+                mname = "cosine" if metric == "cosine" else "euclidean"
+                ws = fms.Workspace(fms.workspace_size(n, d, metric=mname), X.device)
+                outs = (torch.empty((n, d), device="cuda"),
+                        torch.empty(n, dtype=torch.int32, device="cuda"),
+                        torch.empty(n, device="cuda"))
+                run = lambda: fms.cluster(pts, w.h, w.tol, w.max_iter, workspace=ws, metric=mname,
+                                          out=outs)
+                r = run()
+                ms, _ = _events_ms(run, max(5, min(50, args.steps)), flush)
+                rec[metric] = {"ms": ms, "n_modes": r.stats["n_modes"], "rounds": r.stats["rounds"],
+                               "evals": r.stats["evals"],
+                               "evals_per_s": r.stats["evals"] / (ms * 1e-3),
+                               "graph": r.stats["graph"]}
+            line[f"d{d}"] = rec
+        line["value"] = line["d3"]["cosine"]["ms"]
     elif args.workload == "step_wide":
         # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
         peaks = measured_peaks()
@@ -594,7 +622,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
-                             "embedding_32d", "step_wide", "pixels_rgb", "flat_3d", "frames_3d"],
+                             "embedding_32d", "step_wide", "pixels_rgb", "flat_3d", "frames_3d",
+                             "cosine_embed"],
                     help="paper_3d is the headline line; the others print one line of "
                          "their own measurements")
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",

@@ -316,7 +316,8 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt) {
   const int64_t Ncap = seed_capacity(n, o);
   if (Ncap < 1) return 0;
   return make_layout(n, d, Ncap, device_info().sms,
-                     o.kernel == FMS_KERNEL_GAUSSIAN && use_tensor_step(d, o.precision))
+                     o.kernel == FMS_KERNEL_GAUSSIAN && o.metric != FMS_METRIC_COSINE &&
+                         use_tensor_step(d, o.precision))
       .total;
 }
 

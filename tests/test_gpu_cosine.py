@@ -82,3 +82,13 @@ def test_cosine_rejects_zero_points_and_batched():
     Y = torch.randn((200, 3), device="cuda")
     with pytest.raises(fms.FmsError):
         fms.cluster_batched([Y, Y], 0.2, metric="cosine")
+
+
+@pytest.mark.parametrize("d,k,spread,h,ang", [(3, 20, 0.04, 0.12, 0.5), (16, 32, 0.04, 0.25, 0.9)])
+def test_cosine_at_the_200k_size(d, k, spread, h, ang):
+    # the configurations the cosine line of bench.py times: every label and
+    # mode against the oracle at full size
+    w = fi.directional_blobs(seed=100 + d, k=k, d=d, per=200_000 // k, spread=spread, h=h,
+                             min_angle=ang)
+    res, ref = _check(w)
+    assert res.stats["n_modes"] == k

@@ -31,28 +31,73 @@ __host__ __device__ inline size_t greedy_keys_bytes(int P) {
   return (((size_t)P * (sizeof(ST) + 4) + kPruneScratchInts * 4 + 15) / 16) * 16;
 }
 
+// preload: every candidate's coordinates are copied to shared memory once,
+// before the sort (P x d values, transposed), so that staging a batch reads
+// shared memory instead of two dependent global loads per batch.
 template <typename PT, typename ST>
-__host__ __device__ inline size_t greedy_sorted_smem(int K, int d, int P, bool acc_in_smem) {
+__host__ __device__ inline size_t greedy_sorted_smem(int K, int d, int P, bool acc_in_smem,
+                                                     bool preload = false) {
   return greedy_keys_bytes<ST>(P) +
          2 * (size_t)kPruneMaxDim * kPruneTileStride * sizeof(PT) +
+         (preload ? (size_t)P * d * sizeof(PT) : 0) +
          (acc_in_smem ? (size_t)K * d * sizeof(PT) : 0);
 }
 
-template <typename PT, typename ST>
+template <typename PT, typename ST, int DT = 0>
 __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const int K,
                                    const ST* __restrict__ score, const PT* __restrict__ pos,
                                    int DP, int d, PT r2, int32_t* __restrict__ accepted,
                                    int32_t* __restrict__ M_out, int P, unsigned char* smem,
-                                   bool acc_in_smem = true) {
-  // layout: keys[P] (ST), idx[P] (int), scratch[64] (int), ctile[2][64 x 33] (PT),
-  // [apos[K*d] (PT)]
+                                   bool acc_in_smem = true, bool preload = false) {
+  // layout: keys[P] (ST), idx[P] (int), scratch[96] (int), ctile[2][64 x 33] (PT),
+  // [cpre[d][P] (PT)], [apos[K*d] (PT)]
   ST* keys = reinterpret_cast<ST*>(smem);
   int* idx = reinterpret_cast<int*>(keys + P);
   PT* ctile2 = reinterpret_cast<PT*>(smem + greedy_keys_bytes<ST>(P));
   constexpr int kTile = kPruneMaxDim * kPruneTileStride;
-  PT* apos = ctile2 + 2 * kTile;
+  PT* cpre = ctile2 + 2 * kTile;
+  PT* apos = cpre + (preload ? (size_t)P * d : 0);
+  auto row_of = [&](int q) -> int64_t { return cand_row ? (int64_t)cand_row[q] : (int64_t)q; };
+  if (preload)   // read by stage() after the sort's barriers
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+      const PT* src = pos + row_of(t) * DP;
+      for (int k = 0; k < d; ++k) cpre[(size_t)k * P + t] = src[k];
+    }
   // order: "a before b" iff a.key > b.key, or equal keys and a.idx < b.idx
-  if (K <= 512 && K <= (int)blockDim.x) {
+  if (sizeof(ST) == 4 && K <= 512 && K <= (int)blockDim.x) {
+    // FP32 scores: (score, index) packed into one 64-bit key whose unsigned
+    // order is the visit order (score bits mapped to an unsigned order, the
+    // complemented index below them), so the rank count is one comparison
+    // per pair; the keys occupy the keys + idx region until the ranks are known
+    unsigned long long* vk = reinterpret_cast<unsigned long long*>(smem);
+    const int t = threadIdx.x;
+    unsigned long long mv = 0;
+    if (t < K) {
+      float f = (float)score[t];
+      if (!(f == f)) f = -INFINITY;   // a NaN score counts as -inf
+      if (f == 0.0f) f = 0.0f;        // -0 and +0 are equal scores
+      unsigned u = __float_as_uint(f);
+      u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+      mv = ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)t);
+      vk[t] = mv;
+    }
+    __syncthreads();
+    int rank = 0;
+    if (t < K) {
+      int j = 0;
+      for (; j + 8 <= K; j += 8) {
+        unsigned long long kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) kk[u] = vk[j + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rank += kk[u] > mv ? 1 : 0;
+      }
+      for (; j < K; ++j) rank += vk[j] > mv ? 1 : 0;
+    }
+    __syncthreads();
+    if (t < K) idx[rank] = t;
+    __syncthreads();   // the sorted order is read by other threads below
+  } else if (K <= 512 && K <= (int)blockDim.x) {
     // rank of candidate t = number of candidates before it (a permutation:
     // the order is total; a NaN score counts as -inf)
     const int t = threadIdx.x;
@@ -64,11 +109,21 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
     }
     __syncthreads();
     int rank = 0;
-    if (t < K)
-      for (int j = 0; j < K; ++j) {
+    if (t < K) {
+      // eight independent (broadcast) loads in flight per step
+      int j = 0;
+      for (; j + 8 <= K; j += 8) {
+        ST kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) kk[u] = keys[j + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rank += (kk[u] > mk || (kk[u] == mk && j + u < t)) ? 1 : 0;
+      }
+      for (; j < K; ++j) {
         const ST kj = keys[j];
         rank += (kj > mk || (kj == mk && j < t)) ? 1 : 0;
       }
+    }
     __syncthreads();
     if (t < K) {
       keys[rank] = mk;
@@ -104,7 +159,6 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
   }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  auto row_of = [&](int q) -> int64_t { return cand_row ? (int64_t)cand_row[q] : (int64_t)q; };
   // coordinates of accepted mode a (a candidate index in accepted[a])
   auto acc_ptr = [&](int a) -> const PT* {
     if (acc_in_smem) return apos + (size_t)a * d;
@@ -118,10 +172,76 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
   auto stage = [&](int base, PT* tile) {
     const int i = base + lane;
     if (i < K) {
-      const PT* src = pos + row_of(idx[i]) * DP;
-      for (int k = 0; k < d; ++k) tile[k * kPruneTileStride + lane] = src[k];
+      const int c = idx[i];
+      if (preload) {
+        for (int k = 0; k < d; ++k) tile[k * kPruneTileStride + lane] = cpre[(size_t)k * P + c];
+      } else {
+        const PT* src = pos + row_of(c) * DP;
+        for (int k = 0; k < d; ++k) tile[k * kPruneTileStride + lane] = src[k];
+      }
     }
   };
+  if constexpr (DT > 0) {
+    if (preload && acc_in_smem) {
+      // Register visit (d = DT known at compile time): every warp holds the
+      // batch's coordinates in registers (lane c: sorted candidate base + c),
+      // tests them against its share of the modes accepted so far, and warp 0
+      // accepts the survivors lowest lane first; each accepted candidate is
+      // broadcast by shuffles and removes the survivors within r of it (a
+      // ballot).  The distances are those of the test against an accepted
+      // mode, so the accepted set and its order are the greedy visit's.
+      if (threadIdx.x == 0) *s_nacc = 0;
+      if (warp == 0) s_dead[lane] = 0;
+      for (int base = 0; base < K; base += 32) {
+        const int i = base + lane;
+        const int c = i < K ? idx[i] : 0;
+        PT x[DT];
+#pragma unroll
+        for (int k = 0; k < DT; ++k) x[k] = i < K ? cpre[(size_t)k * P + c] : (PT)0;
+        __syncthreads();   // accepted rows, their count and cleared flags are visible
+        const int nacc = *s_nacc;
+        bool dead = false;
+        if (i < K)
+          for (int a = warp; a < nacc && !dead; a += nwarps) {
+            const PT* ap = apos + (size_t)a * DT;
+            PT d2 = 0;
+#pragma unroll
+            for (int k = 0; k < DT; ++k) {
+              const PT e = x[k] - ap[k];
+              d2 += e * e;
+            }
+            dead = d2 < r2;
+          }
+        if (dead) s_dead[lane] = 1;
+        __syncthreads();
+        if (warp == 0) {
+          unsigned alive = __ballot_sync(kFull, i < K && !s_dead[lane]);
+          int na = nacc;
+          while (alive) {
+            const int w = __ffs(alive) - 1;
+            PT d2 = 0;
+#pragma unroll
+            for (int k = 0; k < DT; ++k) {
+              const PT e = x[k] - __shfl_sync(kFull, x[k], w);
+              d2 += e * e;
+            }
+            if (lane == w) {
+              accepted[na] = c;
+#pragma unroll
+              for (int k = 0; k < DT; ++k) apos[(size_t)na * DT + k] = x[k];
+            }
+            ++na;
+            alive &= ~(__ballot_sync(kFull, d2 < r2) | (1u << w));
+          }
+          s_dead[lane] = 0;
+          if (lane == 0) *s_nacc = na;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) *M_out = *s_nacc;
+      return;
+    }
+  }
   if (threadIdx.x == 0) *s_nacc = 0;
   if (warp == 0) {
     stage(0, ctile2);

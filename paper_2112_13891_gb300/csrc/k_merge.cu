@@ -156,25 +156,43 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) *M_out = M;
 }
 
-template <typename PT, typename ST>
+// DT > 0: d = DT at compile time (candidates in registers during the visit)
+template <typename PT, typename ST, int DT>
 __global__ void __launch_bounds__(1024)
     greedy_sorted_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
                          const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
                          PT r2, int32_t* __restrict__ accepted, int32_t* __restrict__ M_out,
-                         int P, int acc_in_smem) {
+                         int P, int acc_in_smem, int preload) {
   extern __shared__ __align__(16) unsigned char smem[];
-  greedy_sorted_body<PT, ST>(cand_row, *K_ptr, score, pos, DP, d, r2, accepted, M_out, P, smem,
-                             acc_in_smem != 0);
+  greedy_sorted_body<PT, ST, DT>(cand_row, *K_ptr, score, pos, DP, DT > 0 ? DT : d, r2, accepted,
+                                 M_out, P, smem, acc_in_smem != 0, preload != 0);
+}
+
+template <typename PT, typename ST, int DT>
+static cudaError_t launch_sorted_t(const int32_t* cand_row, const int32_t* K_ptr, const ST* score,
+                                   const PT* pos, int DP, int d, PT r2, int32_t* accepted,
+                                   int32_t* M_out, int P, int with_pos, int preload, size_t sm,
+                                   int smem_max, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(greedy_sorted_kernel<PT, ST, DT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    attr = true;
+  }
+  greedy_sorted_kernel<PT, ST, DT><<<1, 1024, sm, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
+                                                        accepted, M_out, P, with_pos, preload);
+  return cudaGetLastError();
 }
 
 // Shared memory of the sorted prune for up to K candidates: sort keys and
-// indices, the batch tile, plus (with_pos) the accepted modes' coordinates.
+// indices, the batch tiles, plus (preload) every candidate's coordinates and
+// (with_pos) the accepted modes' coordinates.
 template <typename PT, typename ST>
-size_t greedy_sorted_bytes(int K, int d, int* P_out, bool with_pos) {
+size_t greedy_sorted_bytes(int K, int d, int* P_out, bool with_pos, bool preload) {
   int P = 1;
   while (P < K) P <<= 1;
   *P_out = P;
-  return greedy_sorted_smem<PT, ST>(K, d, P, with_pos);
+  return greedy_sorted_smem<PT, ST>(K, d, P, with_pos, preload);
 }
 
 constexpr size_t kGreedySmemMax = 200 * 1024;
@@ -186,23 +204,36 @@ template <typename PT, typename ST>
 cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const ST* score,
                           const PT* pos, int DP, int d, PT r2, int32_t* alive,
                           int32_t* accepted, int32_t* M_out, int max_K, cudaStream_t st) {
+  // largest layout that fits: preloaded candidates and accepted modes in
+  // shared memory, then accepted modes only, then neither
   int P = 1;
-  size_t sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, true);
-  int with_pos = 1;
+  int with_pos = 1, preload = 1;
+  size_t sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, true, true);
   if (sm > kGreedySmemMax) {
-    sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, false);
+    preload = 0;
+    sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, true, false);
+  }
+  if (sm > kGreedySmemMax) {
+    sm = greedy_sorted_bytes<PT, ST>(max_K, d, &P, false, false);
     with_pos = 0;
   }
   if (sm <= kGreedySmemMax && d <= kPruneMaxDim) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(greedy_sorted_kernel<PT, ST>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmemMax);
-      attr = true;
-    }
-    greedy_sorted_kernel<PT, ST><<<1, 1024, sm, st>>>(cand_row, K_ptr, score, pos, DP, d, r2,
-                                                      accepted, M_out, P, with_pos);
-    return cudaGetLastError();
+    const int mx = (int)kGreedySmemMax;
+#define FMS_SORTED(DT_)                                                                      \
+  return launch_sorted_t<PT, ST, DT_>(cand_row, K_ptr, score, pos, DP, d, r2, accepted, M_out, \
+                                      P, with_pos, preload, sm, mx, st)
+    if (preload && with_pos) switch (d) {
+        case 1: FMS_SORTED(1);
+        case 2: FMS_SORTED(2);
+        case 3: FMS_SORTED(3);
+        case 4: FMS_SORTED(4);
+        case 5: FMS_SORTED(5);
+        case 6: FMS_SORTED(6);
+        case 7: FMS_SORTED(7);
+        case 8: FMS_SORTED(8);
+      }
+    FMS_SORTED(0);
+#undef FMS_SORTED
   }
   greedy_merge_kernel<PT, ST><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2, alive,
                                                   accepted, M_out);
@@ -499,15 +530,30 @@ __global__ void canonical_order_kernel(const double* __restrict__ ym,
                                        double inv_scale, float* __restrict__ out_modes,
                                        int32_t max_modes, float* __restrict__ modes_full,
                                        float* __restrict__ out_scores) {
+  // the modes' scores are staged in shared memory (one load each instead of a
+  // dependent load per comparison); coordinates are read only on equal scores
+  constexpr int kStage = 1024;
+  __shared__ double s_sc[kStage];
   const int M = *M_ptr;
+  const bool staged = M <= kStage;
+  if (staged) {
+    for (int j = threadIdx.x; j < M; j += blockDim.x) s_sc[j] = mscore[accepted ? accepted[j] : j];
+    __syncthreads();
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     const int ai = accepted ? accepted[i] : i;
     const double* pa = ym + (int64_t)ai * DP;
     const double sa = mscore[ai];
     int rank = 0;
     for (int j = 0; j < M; ++j) {
-      const int aj = accepted ? accepted[j] : j;
-      if (j != i && key_less(mscore[aj], ym + (int64_t)aj * DP, sa, pa, d)) ++rank;
+      if (j == i) continue;
+      const double sj = staged ? s_sc[j] : mscore[accepted ? accepted[j] : j];
+      if (sj != sa) {
+        rank += sj > sa ? 1 : 0;
+      } else {
+        const int aj = accepted ? accepted[j] : j;
+        if (key_less(sj, ym + (int64_t)aj * DP, sa, pa, d)) ++rank;
+      }
     }
     for (int k = 0; k < d; ++k) {
       const float v = (float)(pa[k] * inv_scale);

@@ -874,19 +874,26 @@ __global__ void __launch_bounds__(1024)
   __shared__ int scratch[64];
   const int target = rc ? rc->target : target_arg;
   const int N = rc ? rc->N : N_arg;
+  // t* = the first update r whose cumulative convergence count reaches the
+  // target (max_iter if none does): the histogram is read by the whole block
+  // and scanned, so its entries are loaded in parallel
   __shared__ int sh_t;
-  if (threadIdx.x == 0) {
-    int c = 0, t = max_iter;
-    for (int r = 1; r <= max_iter; ++r) {
-      c += hist[r];
-      if (c >= target) {
-        t = r;
-        break;
-      }
-    }
-    sh_t = t;
-  }
+  if (threadIdx.x == 0) sh_t = target <= 0 ? 1 : max_iter;
   __syncthreads();
+  if (target > 0) {
+    int carry = 0;
+    for (int b0 = 1; b0 <= max_iter; b0 += blockDim.x) {
+      const int r = b0 + threadIdx.x;
+      const int v = r <= max_iter ? hist[r] : 0;
+      int tot;
+      const int inc = carry + block_exclusive_scan(v, &tot, scratch) + v;
+      // counts are non-negative, so exactly one r crosses the target
+      if (r <= max_iter && inc >= target && inc - v < target) sh_t = r;
+      carry += tot;
+      if (carry >= target) break;   // block-uniform
+    }
+    __syncthreads();
+  }
   const int t_star = sh_t;
   int base = 0, convd = 0;
   for (int b = 0; b < N; b += blockDim.x) {

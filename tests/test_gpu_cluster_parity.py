@@ -72,6 +72,20 @@ def test_separated_blobs(k, d):
     assert res.stats["n_modes"] == k
 
 
+@pytest.mark.parametrize("k,d", [(300, 2), (200, 3)])
+def test_many_modes(k, d):
+    # hundreds of modes: the first prunes accept most candidates (the one-warp
+    # visit with a long accepted list), later rounds exceed 512 candidates
+    # (the block-wide visit); the seed count doubles several times
+    w = fi.separated_blobs(seed=k + d, k=k, d=d, per=15, sigma=0.3, h=1.0)
+    res = _run(w, gamma=0.95, rng_seed=5)
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=5)
+    _check(w, res, ref)
+    assert res.stats["n_modes"] == k
+    assert res.stats["n_seeds_final"] == ref.n_seeds
+    assert res.stats["rounds"] == len(ref.n_history)
+
+
 def test_embedding_32d_faster():
     w = fi.embedding_32d()
     res = _run(w, gamma=0.95, rng_seed=0)

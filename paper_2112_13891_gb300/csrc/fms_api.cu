@@ -735,7 +735,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
             }
             FMS_LAUNCH(launch_update(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s,
                                      max_iter, n, R, tl_iter, N, target, st, update_grid(N),
-                                     coarse_tol2_s, sphere_r));
+                                     coarse_tol2_s, sphere_r, wlast));
           }
           FMS_CUDA(readback());
           if (hstatus & (kStNonFinite | kStBadArg)) goto device_error;
@@ -745,12 +745,20 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
           }
           if (hctl.done) break;
         }
-        // --- prune candidates (Alg. 2 line 10) and their densities ---
-        FMS_LAUNCH(launch_kept_list(ctl, state, conv, o.gamma >= 1.0f ? 1 : 0, kept, mctl, n, R,
-                                    Lo.tl, st));
-        mark(1);
-        FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
-        FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
+        // --- prune candidates (Alg. 2 line 10) and their densities: with
+        // gamma < 1 every candidate converged, and its density is sum w of its
+        // last update (one step <= tol before it); kept seeds that did not
+        // converge (gamma = 1) get a density pass at their positions ---
+        if (keep_exhausted) {
+          FMS_LAUNCH(launch_kept_list(ctl, state, conv, 1, kept, mctl, n, R, Lo.tl, st));
+          mark(1);
+          FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
+          FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
+        } else {
+          FMS_LAUNCH(launch_kept_list(ctl, state, conv, 0, kept, mctl, n, R, Lo.tl, st, wlast,
+                                      score));
+          mark(1);
+        }
       }
       FMS_LAUNCH(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
                                        &mctl->M, N, st));
@@ -802,12 +810,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         FMS_CUDA(readback());
         if (hrctl.done) break;
       }
-      // density at the refined modes (FP64 sums over chunks), for the second prune
-      FMS_LAUNCH(launch_refine_setup(y, kept, acc1, &mctl->M, DP, ym, yf, ract, mdone, rctl, 0, n,
-                                     R, Lo.tl, hm.M, st));
-      FMS_LAUNCH(step_launch(yf, ract, &rctl->s, &rctl->C, &rctl->Lc));
-      FMS_LAUNCH(launch_refine_update(part, ract, rctl, ym, yf, mdone, mscore, d, DP, DA, 0.0,
-                                      kRefineMaxIter, 1, n, R, Lo.tl, hm.M, st));
+      // the second prune's densities: sum w (FP64 over chunks) of each mode's
+      // last refinement update, recorded by refine_update (as in ms_refine)
       FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        hm.M, st));
       FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,
@@ -853,7 +857,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       stats->t_star_last = hm.t_star;
       stats->kernel_launches = n_launches;
       stats->evals = hctl.evals;
-      stats->score_evals = hm.evals + hrctl.evals + (int64_t)hm.M * n;
+      stats->score_evals = hm.evals + hrctl.evals;
       stats->workspace_bytes = Lo.total;
       stats->graph = resume != 0 ? 1 : 0;
       if (o.profile) {

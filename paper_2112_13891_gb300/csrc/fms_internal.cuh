@@ -332,7 +332,8 @@ cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, floa
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
                           cudaStream_t st, int grid, float coarse_tol2_s = 0.0f,
-                          float sphere_r = 0.0f);   // > 0: project onto that sphere
+                          float sphere_r = 0.0f,    // > 0: project onto that sphere
+                          float* wlast = nullptr);  // sum w of each seed's last update
 cudaError_t launch_step_setup(int32_t* active, int32_t m, IterCtl* ctl, int32_t C, int32_t Lc,
                               cudaStream_t st);
 cudaError_t launch_step_finish(const float* part, const IterCtl* ctl, const float* seeds, int d,
@@ -413,7 +414,9 @@ cudaError_t launch_ms_step_tc(const unsigned char* img, int64_t n, int d, int DP
 // k_merge.cu
 cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int32_t* conv,
                              int keep_exhausted, int32_t* kept, MergeCtl* mctl, int64_t n,
-                             int32_t R, Tiling tl, cudaStream_t st);
+                             int32_t R, Tiling tl, cudaStream_t st,
+                             const float* wlast = nullptr,   // gather the prune's scores from
+                             float* score = nullptr);        // each kept seed's last update
 cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA, float* score,
                                 int max_K, cudaStream_t st);
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,

@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256)
                   float* __restrict__ y, int32_t* __restrict__ it, int32_t* __restrict__ conv,
                   int32_t* __restrict__ state, int d, int DP, int DA, float tol2_s, int64_t n,
                   int32_t R, Tiling tl, int N, int target, int max_iter, float coarse_tol2_s,
-                  float sphere_r) {
+                  float sphere_r, float* __restrict__ wlast) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
   __shared__ float red[8][96];
@@ -518,6 +518,9 @@ __global__ void __launch_bounds__(256)
       }
     }
     if (lane == 0) {
+      // sum w of this update (at the position before it): the prune's density
+      // of a seed that converges here
+      if (wlast) wlast[slot] = W;
       const int t = it[slot] + 1;
       it[slot] = t;
       const bool coarse = state[slot] == kCoarse;
@@ -547,9 +550,10 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_update(const float* part, int32_t* active, IterCtl* ctl, float* y, int32_t* it,
                           int32_t* conv, int32_t* state, int d, int DP, int DA, float tol2_s,
                           int max_iter, int64_t n, int32_t R, Tiling tl, int N, int target,
-                          cudaStream_t st, int grid, float coarse_tol2_s, float sphere_r) {
+                          cudaStream_t st, int grid, float coarse_tol2_s, float sphere_r,
+                          float* wlast) {
   update_kernel<<<grid, 256, 0, st>>>(part, active, ctl, y, it, conv, state, d, DP, DA, tol2_s, n,
-                                      R, tl, N, target, max_iter, coarse_tol2_s, sphere_r);
+                                      R, tl, N, target, max_iter, coarse_tol2_s, sphere_r, wlast);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@ namespace fms {
 __global__ void __launch_bounds__(1024)
     kept_list_kernel(const IterCtl* __restrict__ ctl, const int32_t* __restrict__ state,
                      const int32_t* __restrict__ conv, int keep_exhausted,
-                     int32_t* __restrict__ kept, MergeCtl* mctl, int64_t n, int32_t R, Tiling tl) {
+                     int32_t* __restrict__ kept, MergeCtl* mctl, int64_t n, int32_t R, Tiling tl,
+                     const float* __restrict__ wlast, float* __restrict__ score) {
   __shared__ int scratch[64];
   const int N = ctl->N;
   const int t_star = ctl->r;
@@ -29,7 +30,10 @@ __global__ void __launch_bounds__(1024)
     }
     int tot;
     const int off = block_exclusive_scan(take, &tot, scratch);
-    if (take) kept[base + off] = i;
+    if (take) {
+      kept[base + off] = i;
+      if (wlast) score[base + off] = wlast[i];
+    }
     base += tot;
   }
   if (threadIdx.x == 0) {
@@ -39,14 +43,16 @@ __global__ void __launch_bounds__(1024)
     choose_chunks(n, base, R, tl, &C, &Lc);
     mctl->C = C;
     mctl->Lc = Lc;
-    mctl->evals += (int64_t)base * n;
+    if (!wlast) mctl->evals += (int64_t)base * n;   // the density pass the host then runs
   }
 }
 
 cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int32_t* conv,
                              int keep_exhausted, int32_t* kept, MergeCtl* mctl, int64_t n,
-                             int32_t R, Tiling tl, cudaStream_t st) {
-  kept_list_kernel<<<1, 1024, 0, st>>>(ctl, state, conv, keep_exhausted, kept, mctl, n, R, tl);
+                             int32_t R, Tiling tl, cudaStream_t st, const float* wlast,
+                             float* score) {
+  kept_list_kernel<<<1, 1024, 0, st>>>(ctl, state, conv, keep_exhausted, kept, mctl, n, R, tl,
+                                       wlast, score);
   return cudaGetLastError();
 }
 
@@ -393,10 +399,10 @@ __global__ void __launch_bounds__(256)
       if (wid != 0) continue;
     }
     const double W = __shfl_sync(kFull, a[0], 0);
-    if (score_only) {
-      if (lane == 0) mscore[m] = W;
-      continue;
-    }
+    // the mode's density: sum w of its latest update (the last one is at most
+    // the refinement tolerance before the refined mode), or the density pass
+    if (lane == 0) mscore[m] = W;
+    if (score_only) continue;
     const bool ok = W > 0.0 && isfinite(W);
     double step2 = 0.0, delta[3] = {0.0, 0.0, 0.0};
 #pragma unroll

@@ -113,7 +113,7 @@ BLayout make_blayout(int64_t total, int B, int d, int sms, int tw_mult, int min_
   BLayout L{};
   L.DP = padded(d);
   L.DA = step_accumulators(d);
-  L.R = step_seeds_per_warp(d);
+  L.R = batched_seeds_per_warp(d);
   L.TW = (sms > 0 ? sms : 1) * step_resident_warps_per_sm(d);
   // every set gets a share of the GPU's warps for its chunking (all sets run
   // in the same launches)

@@ -390,10 +390,12 @@ cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const floa
                            cudaStream_t st, int32_t* s_log = nullptr,
                            const int32_t* p_lo_ptr = nullptr, int kf = kKernelGaussian);
 int step_seeds_per_warp(int d);
+int batched_seeds_per_warp(int d);   // the batched step's wide tasks (32 lanes x RG seeds)
 int step_resident_warps_per_sm(int d);
 // smallest chunk (points) of a warp task: the low-d kernel splits a chunk over
-// 32 lanes, the wide kernel gives every point to all 32 lanes
-inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : 64; }
+// 32 lanes, the quad kernel (8 <= d <= 16) over 4 point lanes, the wide kernel
+// (d > 16) gives every point to all 32 lanes
+inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : (d <= 16 ? 256 : 64); }
 int step_accumulators(int d);
 
 // k_step_tc.cu: the coarse step on the tensor cores (1 <= d <= 32).  The

@@ -192,4 +192,91 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
   }
 }
 
+// One quad warp task (8 <= d <= 16): the warp's lanes are 8 seed slots x 4
+// point lanes (lane = 4 * slot + point lane); a slot holds RG seeds (8 * RG
+// seeds per task), point lane q walks the chunk's points j0 + q, j0 + q + 4,
+// ... in increasing order, and the four point lanes of a slot are combined by
+// a fixed two-level xor tree.  Each point load feeds 8 * RG evaluations, and a
+// task needs only 8 * RG seeds, so chunks stay long when few seeds are active
+// (partials are C x s x DA floats).  The partial of a seed depends only on
+// the chunk, not on the seed's slot or on the other seeds.
+template <int DPAD, int RG, int KF = kKernelGaussian>
+__device__ __forceinline__ void quad_task(const float* __restrict__ Xs, int DP, int j0, int j1,
+                                          const float* __restrict__ y,
+                                          const int32_t* __restrict__ active, int s, int g, int c,
+                                          float* __restrict__ part, int lane, int p_lo = 0) {
+  constexpr int DA = DPAD + 4;
+  constexpr int SPT = 8 * RG;
+  const int slot_l = lane >> 2, q = lane & 3;
+  float ys[RG][DPAD];
+  float acc[RG][DPAD + 1];
+#pragma unroll
+  for (int r = 0; r < RG; ++r) {
+    int p = p_lo + g * SPT + r * 8 + slot_l;
+    p = p < s ? p : s - 1;
+    const int64_t slot = __ldg(active + p);
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) ys[r][k] = k < DP ? __ldg(y + slot * DP + k) : 0.0f;
+#pragma unroll
+    for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
+  }
+  auto load_point = [&](int j, float (&x)[DPAD]) {
+    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DP);
+#pragma unroll
+    for (int u = 0; u < DPAD / 4; ++u) {
+      const float4 v = (4 * u < DP) ? __ldg(xp + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[4 * u] = v.x;
+      x[4 * u + 1] = v.y;
+      x[4 * u + 2] = v.z;
+      x[4 * u + 3] = v.w;
+    }
+  };
+  auto eval = [&](const float (&x)[DPAD]) {
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      float dx[DPAD];
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
+      float t = -dx[0] * dx[0];
+#pragma unroll
+      for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
+      const float w = kweight<KF>(t);
+      acc[r][0] += w;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
+    }
+  };
+  // two points per step, both loads issued before either is evaluated
+  int j = j0 + q;
+  for (; j + 4 < j1; j += 8) {
+    float xa[DPAD], xb[DPAD];
+    load_point(j, xa);
+    load_point(j + 4, xb);
+    eval(xa);
+    eval(xb);
+  }
+  if (j < j1) {
+    float xa[DPAD];
+    load_point(j, xa);
+    eval(xa);
+  }
+#pragma unroll
+  for (int r = 0; r < RG; ++r) {
+#pragma unroll
+    for (int k = 0; k <= DPAD; ++k) {
+      float v = acc[r][k];
+      v += __shfl_xor_sync(kFull, v, 1);
+      v += __shfl_xor_sync(kFull, v, 2);
+      acc[r][k] = v;
+    }
+    const int p = p_lo + g * SPT + r * 8 + slot_l;
+    if (p < s) {
+      float* o = part + ((int64_t)c * s + p) * DA;
+#pragma unroll
+      for (int k = 0; k <= DPAD; ++k)
+        if ((k & 3) == q) o[k] = acc[r][k];
+    }
+  }
+}
+
 }  // namespace fms

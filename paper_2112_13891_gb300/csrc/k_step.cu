@@ -90,11 +90,53 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
   }
 }
 
+// 8 <= d <= 16: the quad kernel (8 seed slots x 4 point lanes per warp).  At
+// d = 32 (one seed per slot) its four distinct point rows per load cost more
+// L1 wavefronts per evaluation than the arithmetic can cover (measured: 73 vs
+// 170 Geval/s with 65,536 seeds), so d > 16 keeps the wide kernel.
+template <int DPAD, int RG, int KF>
+__global__ void __launch_bounds__(128) ms_step_quad(const float* __restrict__ Xs, int64_t n,
+                                                    int DP, const float* __restrict__ y,
+                                                    const int32_t* __restrict__ active,
+                                                    const int32_t* __restrict__ s_ptr,
+                                                    const int32_t* __restrict__ C_ptr,
+                                                    const int32_t* __restrict__ Lc_ptr,
+                                                    float* __restrict__ part,
+                                                    int32_t* __restrict__ s_log,
+                                                    const int32_t* __restrict__ p_lo_ptr) {
+  constexpr int SPT = 8 * RG;  // seeds per warp task
+  const int s = *s_ptr;
+  const int p_lo = p_lo_ptr ? *p_lo_ptr : 0;
+  if (s_log && blockIdx.x == 0 && threadIdx.x == 0) *s_log = s - p_lo;
+  if (s - p_lo <= 0) return;
+  const int C = *C_ptr;
+  const int Lc = *Lc_ptr;
+  const int G = (s - p_lo + SPT - 1) / SPT;
+  const int64_t T = (int64_t)G * C;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+       task += nw) {
+    const int g = (int)(task % G);
+    const int c = (int)(task / G);
+    const int j0 = c * Lc;
+    const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
+    quad_task<DPAD, RG, KF>(Xs, DP, j0, j1, y, active, s, g, c, part, lane, p_lo);
+  }
+}
+
 int step_seeds_per_warp(int d) {
   if (d <= 1) return 16;
   if (d <= 3) return 8;
   if (d <= 7) return 4;
-  if (d <= 8) return 32 * 4;
+  if (d <= 8) return 8 * 4;    // quad kernel: 8 slots x RG seeds
+  if (d <= 16) return 8 * 2;
+  return 32;                   // wide kernel: 32 lanes x 1 seed
+}
+
+int batched_seeds_per_warp(int d) {
+  if (d <= 7) return step_seeds_per_warp(d);
+  if (d <= 8) return 32 * 4;   // wide tasks: 32 lanes x RG seeds
   if (d <= 16) return 32 * 2;
   return 32;
 }
@@ -128,8 +170,8 @@ int step_resident_warps_per_sm(int d) {
     case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_lowd<7, 8, 8, 0>, 256, 0); break;
     default:
       threads = 128;
-      if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<8, 4, 0>, 128, 0);
-      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<16, 2, 0>, 128, 0);
+      if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<8, 4, 0>, 128, 0);
+      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<16, 2, 0>, 128, 0);
       else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1, 0>, 128, 0);
       else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1, 0>, 128, 0);
       break;
@@ -157,9 +199,9 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
     case 7: ms_step_lowd<7, 8, 8, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
     default:
       if (d <= 8)
-        ms_step_wide<8, 4, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_quad<8, 4, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 16)
-        ms_step_wide<16, 2, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_quad<16, 2, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 32)
         ms_step_wide<32, 1, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else

@@ -26,6 +26,29 @@ __global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStNonFinite);
 }
 
+// DP = 4 or 8: one thread per point, the padded row written with vector stores
+template <int DP>
+__global__ void pack_rows_kernel(const float* __restrict__ X, int n, int d, float scale,
+                                 float* __restrict__ Xs, uint32_t* status) {
+  bool bad = false;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    float v[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      v[k] = 0.0f;
+      if (k < d) {
+        const float x = X[(int64_t)j * d + k];
+        if (!isfinite(x)) bad = true;
+        v[k] = x * scale;
+      }
+    }
+    float4* o = reinterpret_cast<float4*>(Xs + (int64_t)j * DP);
+#pragma unroll
+    for (int q = 0; q < DP / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStNonFinite);
+}
+
 // Cosine metric: row j scaled to unit length, then by s; a zero row flags
 // kStBadArg (it has no direction), a non-finite one kStNonFinite.
 __global__ void pack_unit_rows_kernel(const float* __restrict__ X, int64_t n, int d, int DP,
@@ -53,6 +76,15 @@ cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float s
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     pack_unit_rows_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status);
+    return cudaGetLastError();
+  }
+  if ((DP == 4 || DP == 8) && n <= INT32_MAX && (reinterpret_cast<uintptr_t>(Xs) & 15) == 0) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (DP == 4)
+      pack_rows_kernel<4><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status);
+    else
+      pack_rows_kernel<8><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status);
     return cudaGetLastError();
   }
   int64_t total = n * DP;

@@ -784,7 +784,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     mark(2);
     // --- refinement and second prune ---
     if (!o.skip_refine && hm.M > 0 && qmax > 0 && hm.M <= qmax * kModesPerCluster) {
-      // cluster-persistent refinement (updates and the density pass in one launch)
+      // cluster-persistent refinement (all updates, and each mode's density, in one launch)
       const double rtol_s = kRefineTolFactor * (double)h * scale;
       const int clusters = hm.M < qmax ? hm.M : qmax;
       FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
@@ -804,8 +804,8 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
         for (int i = 0; i < kUpdatesPerBatch && batch * kUpdatesPerBatch + i < kRefineMaxIter; ++i) {
           FMS_LAUNCH(step_launch(yf, ract, &rctl->s, &rctl->C, &rctl->Lc));
           FMS_LAUNCH(launch_refine_update(part, ract, rctl, ym, yf, mdone, mscore, d, DP, DA,
-                                          rtol_s * rtol_s, kRefineMaxIter, 0, n, R, Lo.tl, hm.M,
-                                          st, sphere_rd));
+                                          rtol_s * rtol_s, kRefineMaxIter, n, R, Lo.tl, hm.M, st,
+                                          sphere_rd));
         }
         FMS_CUDA(readback());
         if (hrctl.done) break;

@@ -436,7 +436,7 @@ cudaError_t launch_refine_setup(const float* y, const int32_t* kept, const int32
                                 int64_t n, int32_t R, Tiling tl, int max_M, cudaStream_t st);
 cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
                                  float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
-                                 double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
+                                 double tol2_s, int max_iter, int64_t n, int32_t R,
                                  Tiling tl, int max_M, cudaStream_t st,
                                  double sphere_r = 0.0);
 cudaError_t launch_canonical_order(const double* ym, const double* mscore,

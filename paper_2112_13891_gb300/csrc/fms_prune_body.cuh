@@ -8,18 +8,23 @@ namespace fms {
 // Same prune with the candidates in shared memory, in two parallel stages:
 // (1) the block sorts the candidates by (score descending, rank ascending):
 // up to 512 candidates by counting, for each, the candidates ordered before
-// it (one pass, no barriers between stages), else with a bitonic sort; (2) the
-// sorted list is walked 32 candidates at a time: the batch's coordinates are
-// staged in a transposed, padded tile (one candidate per lane, conflict-free
+// it (FP32 scores as one packed 64-bit key comparison per pair), else with a
+// bitonic sort; (2) the sorted list is walked 32 candidates at a time, one
+// candidate per lane.  Register visit (d = DT known at compile time, the
+// candidates' coordinates preloaded into shared memory): every warp holds the
+// batch in registers and tests it against its share of the modes accepted so
+// far; warp 0 accepts the survivors lowest lane first, each broadcast by
+// shuffles and removing the survivors within r of it (a ballot).  Block visit
+// (any d): the batch is staged in a transposed, padded tile (conflict-free
 // per-lane reads; two tiles, warp 1 stages the next batch while the current
-// one is tested), every warp tests the batch against its share of the modes
-// accepted so far, warp v also records which batch members lie within r of
-// member v (a 32-bit mask), and one warp resolves the survivors in order with
-// those masks (the lowest surviving lane is accepted and removes the lanes
-// within r of it).  The accepted set and its order are those of the
-// one-by-one greedy visit.  With acc_in_smem the accepted modes' coordinates
-// are kept in shared memory, else read back from global memory (all lanes
-// read the same row).
+// one is tested), every warp tests it against its share of the accepted
+// modes, warp v records which batch members lie within r of member v (a
+// 32-bit mask), and warp 0 resolves the survivors in order with those masks.
+// Both use the distance of the test against an accepted mode for every
+// suppression, so the accepted set and its order are those of the one-by-one
+// greedy visit.  With acc_in_smem the accepted modes' coordinates are kept in
+// shared memory, else read back from global memory (all lanes read the same
+// row).
 constexpr int kPruneTileStride = 33;   // padded row of the transposed batch tile
 constexpr int kPruneMaxDim = 64;
 

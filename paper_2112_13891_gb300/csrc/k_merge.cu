@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256)
     refine_update_kernel(const float* __restrict__ part, int32_t* __restrict__ active,
                          IterCtl* rctl, double* __restrict__ ym, float* __restrict__ yf,
                          int32_t* __restrict__ mdone, double* __restrict__ mscore, int d, int DP,
-                         int DA, double tol2_s, int max_iter, int score_only, int64_t n,
+                         int DA, double tol2_s, int max_iter, int64_t n,
                          int32_t R, Tiling tl, double sphere_r) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
@@ -400,9 +400,8 @@ __global__ void __launch_bounds__(256)
     }
     const double W = __shfl_sync(kFull, a[0], 0);
     // the mode's density: sum w of its latest update (the last one is at most
-    // the refinement tolerance before the refined mode), or the density pass
+    // the refinement tolerance before the refined mode)
     if (lane == 0) mscore[m] = W;
-    if (score_only) continue;
     const bool ok = W > 0.0 && isfinite(W);
     double step2 = 0.0, delta[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -470,7 +469,6 @@ __global__ void __launch_bounds__(256)
     }
     if (lane == 0 && (!good || step2 <= tol2_s)) mdone[m] = 1;
   }
-  if (score_only) return;
   // last block: the modes still moving take the next update
   __threadfence();
   __syncthreads();
@@ -506,13 +504,13 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_refine_update(const float* part, int32_t* active, IterCtl* rctl, double* ym,
                                  float* yf, int32_t* mdone, double* mscore, int d, int DP, int DA,
-                                 double tol2_s, int max_iter, int score_only, int64_t n, int32_t R,
+                                 double tol2_s, int max_iter, int64_t n, int32_t R,
                                  Tiling tl, int max_M, cudaStream_t st, double sphere_r) {
   int blocks = max_M;  // one block per mode (many chunks) or one warp per mode
   if (blocks < 1) blocks = 1;
   if (blocks > 1216) blocks = 1216;
   refine_update_kernel<<<blocks, 256, 0, st>>>(part, active, rctl, ym, yf, mdone, mscore, d, DP,
-                                               DA, tol2_s, max_iter, score_only, n, R, tl,
+                                               DA, tol2_s, max_iter, n, R, tl,
                                                sphere_r);
   return cudaGetLastError();
 }

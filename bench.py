@@ -199,6 +199,19 @@ def run_oracle_sample(w, seconds=12.0):
     return el / runs * 1e3, runs
 
 
+def oracle_one_core_ms(seconds):
+    """The same oracle sample on one host core: a child process started with
+    OMP_NUM_THREADS=1 (OpenMP fixes its thread count when the library loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample-only",
+                        str(seconds)], env=env, capture_output=True, text=True,
+                       timeout=max(120.0, 20 * seconds))
+    if r.returncode != 0:
+        return None, 0
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["ms"], out["runs"]
+
+
 def oracle_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else (os.cpu_count() or 1)
@@ -341,6 +354,10 @@ def bench_fms(args):
         cpu = {"value": ms_cpu, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"full FP64 oracle clustering of the same 200K-point workload, "
                          f"{runs} run(s), OpenMP over seeds"}
+        ms_one, runs_one = oracle_one_core_ms(args.cpu_seconds)
+        if ms_one is not None:
+            cpu["value_1_core"] = ms_one
+            cpu["sample_1_core"] = f"the same clustering on one host core, {runs_one} run(s)"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -630,7 +647,13 @@ def main():
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="M",
                     help="only run fms_mean_shift_step with M seeds on the workload's points "
                          "(a small case for ncu captures of ms_step), then exit")
+    ap.add_argument("--oracle-sample-only", type=float, default=0.0, metavar="SECONDS",
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample_only > 0:
+        ms, runs = run_oracle_sample(make_input(0), seconds=args.oracle_sample_only)
+        print(json.dumps({"ms": ms, "runs": runs}))
+        return
     if args.kernel_probe:
         kernel_probe(args.kernel_probe)
         return

@@ -63,6 +63,32 @@ def test_paper_3d_all_seeds_small():
     _check(w, res, ref)
 
 
+def test_paper_3d_all_seeds_full_size_sampled():
+    # Alg. 1 at the 200K size the all-seeds bench line runs: every point is a
+    # seed, too many for the oracle to cluster whole.  Trajectories are
+    # independent, so sampled seeds' FP64 trajectories are exact references:
+    # each one's end point was a prune candidate, so a first-prune mode lies
+    # within r_merge = h of it and moves by a few tol in the refinement; the
+    # second prune can drop that mode for one within h of it (rare), hence the
+    # 2h bound for every sample.  The sampled points' labels are the FP64
+    # nearest modes away from ties.
+    w = fi.paper_3d()
+    res = _run(w, all_seeds=True)
+    modes = res.modes.cpu().numpy().astype(np.float64)
+    labels = res.labels.cpu().numpy()
+    assert res.stats["n_seeds_final"] == w.X.shape[0]
+    rng = np.random.default_rng(11)
+    sample = rng.choice(w.X.shape[0], 48, replace=False)
+    y_end, conv, _ = orc.trajectories(w.X, w.X[sample], w.h, w.tol, w.max_iter)
+    assert np.all(conv > 0)
+    dist = np.linalg.norm(y_end[:, None, :] - modes[None, :, :], axis=2).min(axis=1)
+    assert np.mean(dist < 1.01 * w.h) >= 0.95, np.sort(dist)[-4:]
+    assert np.all(dist < 2.02 * w.h), dist.max()
+    lab, marg = orc.label(w.X[sample], modes)
+    clear = marg > 1e-2 * w.h
+    assert np.array_equal(lab[clear], labels[sample][clear])
+
+
 @pytest.mark.parametrize("k,d", [(6, 2), (10, 5), (12, 8), (9, 16)])
 def test_separated_blobs(k, d):
     w = fi.separated_blobs(seed=k + d, k=k, d=d, per=300, sigma=1.0, h=1.5)

@@ -13,7 +13,9 @@
  *   - Early Stopping: iteration ends once ceil(gamma*N) seeds have converged;
  *     seeds not converged by then are discarded (Sec. II-C);
  *   - modes are pruned (Alg. 2 line 10) and every point is labelled by its
- *     nearest mode (Alg. 2 lines 11-13).
+ *     nearest mode (Alg. 2 lines 11-13);
+ *   - options select the flat kernel of Eq. 12-15 instead of the Gaussian,
+ *     and the cosine metric of the sibling method the paper cites.
  *
  * Conventions (all entry points):
  *   - Array arguments are DEVICE pointers unless marked "host".  Points are
@@ -174,7 +176,10 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt);
  *                moves it by at most tol (in point units); 0 -> 1e-3*h.
  *   max_iter     cap on updates per seed (> 0).
  *   out_modes    [max_modes x d] float32, device: the modes, in canonical
- *                order (KDE value at the mode descending, ties by coordinates).
+ *                order: density descending (sum w of the mode's last
+ *                refinement update, one step of at most 1e-5*h before the
+ *                mode, so within O(1e-10) relative of the KDE value at the
+ *                mode), ties by coordinates.
  *   out_n_modes  host int32: M.  If M > max_modes, FMS_ERR_CAPACITY is
  *                returned, *out_n_modes = M and out_modes holds the first
  *                max_modes modes; labels are still written.
@@ -185,7 +190,10 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt);
  *                256-byte aligned; NULL -> the call allocates one with
  *                cudaMallocAsync on `stream` and frees it before returning.
  *   stats        host, nullable.
- * Synchronises `stream` once per seed round and once at the end.
+ * Synchronises `stream` once per seed round and once at the end; a call
+ * repeated with the same pointers, sizes, scalars and options and a caller
+ * workspace runs as one cached CUDA graph and synchronises once
+ * (stats->graph = 1).
  */
 fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
                        int32_t max_iter, const fms_options* opt, float* out_modes,

@@ -98,6 +98,18 @@ def test_separated_blobs(k, d):
     assert res.stats["n_modes"] == k
 
 
+@pytest.mark.parametrize("d", [1, 4, 6, 7])
+def test_every_low_dimension(d):
+    # the cluster rounds, the prune's register visit and the labels are
+    # compiled per dimension for d <= 8; the other values run elsewhere
+    w = fi.separated_blobs(seed=40 + d, k=5, d=d, per=300, sigma=0.8, h=1.2)
+    res = _run(w, gamma=0.95, rng_seed=6)
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=6)
+    _check(w, res, ref)
+    assert res.stats["n_modes"] == 5
+    assert res.stats["t_star_last"] == ref.t_star[-1]
+
+
 @pytest.mark.parametrize("k,d", [(300, 2), (200, 3)])
 def test_many_modes(k, d):
     # hundreds of modes: the first prunes accept most candidates (the one-warp

@@ -202,6 +202,35 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
                        fms_stats* stats, void* stream);
 
 /*
+ * fms_cluster with HOST input and output buffers (the same clustering, Alg. 2
+ * or Alg. 1): the call copies the points to the device, clusters them and
+ * copies the labels, margins and modes back, with the copy-backs queued on
+ * `stream` before the call's final synchronisation (one synchronisation in
+ * the CUDA-graph form).  Page-locked host buffers make the copies
+ * asynchronous; pageable ones work but are staged by the driver.
+ *
+ *   points       HOST [n x d] float32.
+ *   out_modes    HOST [max_modes x d] float32 (the first min(M, max_modes)
+ *                rows are the modes in canonical order); nullable when
+ *                max_modes = 0.
+ *   out_n_modes  host int32: M (FMS_ERR_CAPACITY as in fms_cluster).
+ *   out_labels   HOST [n] int32; out_margins HOST [n] float32, nullable.
+ *   workspace    DEVICE buffer of >= fms_cluster_host_workspace_size(n, d,
+ *                max_modes, opt) bytes, 256-byte aligned (it holds the
+ *                clustering workspace and device copies of the inputs and
+ *                outputs); NULL -> allocated with cudaMallocAsync and freed.
+ * The host output buffers are written when the call returns FMS_OK or
+ * FMS_ERR_CAPACITY.
+ */
+size_t fms_cluster_host_workspace_size(int64_t n, int32_t d, int32_t max_modes,
+                                       const fms_options* opt);
+fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, float tol,
+                            int32_t max_iter, const fms_options* opt, float* out_modes,
+                            int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                            float* out_margins, void* workspace, size_t workspace_bytes,
+                            fms_stats* stats, void* stream);
+
+/*
  * Batched Faster Mean-shift: B independent point sets of uneven size
  * clustered together, every phase of Alg. 2 (Sec. II-C/D) one launch for all
  * sets (the sets share h, tol, max_iter and the options).  The paper clusters

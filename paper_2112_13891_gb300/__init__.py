@@ -77,6 +77,12 @@ _lib.fms_cluster.restype = ctypes.c_int
 _lib.fms_cluster.argtypes = [_P, _I64, _I32, _F32, _F32, _I32, ctypes.POINTER(FmsOptions), _P,
                              _I32, ctypes.POINTER(_I32), _P, _P, _P, _SZ,
                              ctypes.POINTER(FmsStats), _P]
+_lib.fms_cluster_host_workspace_size.restype = _SZ
+_lib.fms_cluster_host_workspace_size.argtypes = [_I64, _I32, _I32, ctypes.POINTER(FmsOptions)]
+_lib.fms_cluster_host.restype = ctypes.c_int
+_lib.fms_cluster_host.argtypes = [_P, _I64, _I32, _F32, _F32, _I32, ctypes.POINTER(FmsOptions),
+                                  _P, _I32, ctypes.POINTER(_I32), _P, _P, _P, _SZ,
+                                  ctypes.POINTER(FmsStats), _P]
 _lib.fms_cluster_frames.restype = ctypes.c_int
 _lib.fms_cluster_frames.argtypes = [_P, _I32, _I64, _I32, _F32, _F32, _I32,
                                     ctypes.POINTER(FmsOptions), _F32, _P, _I32, _P, _P, _P, _P,
@@ -235,6 +241,50 @@ def cluster(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 30
                             _ptr(workspace.buf), workspace.nbytes, ctypes.byref(st), _stream())
     if code not in (FMS_OK, FMS_ERR_CAPACITY):
         raise FmsError(code, "fms_cluster")
+    M = nm.value
+    return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar, stats=st,
+                         status=code)
+
+
+def cluster_host(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int = 300, *,
+                 all_seeds=False, n_initial=128, L=8.0, gamma=0.95, merge_radius=0.0,
+                 skip_refine=False, rng_seed=0, max_modes=256, margins=False,
+                 workspace: Workspace = None, precision="auto", kernel="gaussian",
+                 metric="euclidean", out=None, device=None) -> ClusterResult:
+    """fms_cluster_host: `points` is a CPU float32 [n, d] tensor (page-locked
+    for asynchronous copies); the results come back in CPU tensors, copied
+    under the call's own synchronisation.  `out` may pass preallocated CPU
+    tensors (modes [max_modes, d], labels [n], margins [n] or None)."""
+    if points.is_cuda:
+        raise ValueError("cluster_host takes host (CPU) points; use cluster() for device tensors")
+    X = points.contiguous().float()
+    if X.dim() != 2:
+        raise ValueError("points must be [n, d]")
+    n, d = X.shape
+    o = make_options(all_seeds=all_seeds, n_initial=n_initial, L=L, gamma=gamma,
+                     merge_radius=merge_radius, skip_refine=skip_refine, rng_seed=rng_seed,
+                     precision=precision, kernel=kernel, metric=metric)
+    if out is not None:
+        modes, labels, mar = out
+        cap = modes.shape[0]
+    else:
+        cap = int(max_modes)
+        modes = torch.empty((max(cap, 1), d), dtype=torch.float32).pin_memory()
+        labels = torch.empty(n, dtype=torch.int32).pin_memory()
+        mar = torch.empty(n, dtype=torch.float32).pin_memory() if margins else None
+    need = int(_lib.fms_cluster_host_workspace_size(n, d, cap, ctypes.byref(o)))
+    if need == 0:
+        raise FmsError(FMS_ERR_INVALID_ARG, "fms_cluster_host_workspace_size")
+    if workspace is None or workspace.nbytes < need:
+        workspace = Workspace(need, device)
+    nm = _I32(0)
+    st = FmsStats()
+    code = _lib.fms_cluster_host(_ptr(X), n, d, float(h), float(tol), int(max_iter),
+                                 ctypes.byref(o), _ptr(modes), cap, ctypes.byref(nm),
+                                 _ptr(labels), _ptr(mar), _ptr(workspace.buf), workspace.nbytes,
+                                 ctypes.byref(st), _stream())
+    if code not in (FMS_OK, FMS_ERR_CAPACITY):
+        raise FmsError(code, "fms_cluster_host")
     M = nm.value
     return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar, stats=st,
                          status=code)

@@ -321,11 +321,37 @@ size_t fms_workspace_size(int64_t n, int32_t d, const fms_options* opt) {
       .total;
 }
 
+// Device-to-host copies of the results that fms_cluster_host queues on the
+// stream before the call's last readback, so they complete under its one
+// synchronisation (copying again is harmless if the graph hands back).
+struct HostCopies {
+  int count;
+  void* dst[3];
+  const void* src[3];
+  size_t bytes[3];
+};
+
+static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float h, float tol,
+                               int32_t max_iter, const fms_options* opt_in, float* out_modes,
+                               int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                               float* out_margins, void* workspace, size_t workspace_bytes,
+                               fms_stats* stats, void* stream_, const HostCopies* hc);
+
 fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float tol,
                        int32_t max_iter, const fms_options* opt_in, float* out_modes,
                        int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
                        float* out_margins, void* workspace, size_t workspace_bytes,
                        fms_stats* stats, void* stream_) {
+  return cluster_impl(points, n, d, h, tol, max_iter, opt_in, out_modes, max_modes, out_n_modes,
+                      out_labels, out_margins, workspace, workspace_bytes, stats, stream_,
+                      nullptr);
+}
+
+static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float h, float tol,
+                               int32_t max_iter, const fms_options* opt_in, float* out_modes,
+                               int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                               float* out_margins, void* workspace, size_t workspace_bytes,
+                               fms_stats* stats, void* stream_, const HostCopies* hc) {
   fms_status rc = FMS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   fms_options o;
@@ -426,6 +452,17 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       return e;
+    };
+    // the caller's host copies of the results (fms_cluster_host), queued
+    // before the readback that ends the call
+    auto host_copies = [&]() -> cudaError_t {
+      for (int i = 0; hc && i < hc->count; ++i) {
+        if (hc->bytes[i] == 0) continue;
+        const cudaError_t e = cudaMemcpyAsync(hc->dst[i], hc->src[i], hc->bytes[i],
+                                              cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
     };
     int32_t* tclog = slog + kSlogCap;
     Tiling tl_iter = Lo.tl;   // the seed-update loop (tensor-core chunking when on)
@@ -646,6 +683,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
       if (ge && ge->exec) {
         ++gc.hits;
         FMS_CUDA(cudaGraphLaunch(ge->exec, st));
+        FMS_CUDA(host_copies());
         FMS_CUDA(readback());
         RoundCtl rcv;
         memcpy(&rcv, hbuf + kCtlRoundOff, sizeof(RoundCtl));
@@ -834,6 +872,7 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
     if (n_tclog > 0)
       FMS_CUDA(cudaMemcpyAsync(htclog.data(), tclog, (size_t)n_tclog * 4, cudaMemcpyDeviceToHost,
                                st));
+    FMS_CUDA(host_copies());
     FMS_CUDA(readback());
     }
     Mfinal = hm.Mr;
@@ -920,6 +959,92 @@ done:
     if (rc == FMS_OK || rc == FMS_ERR_CAPACITY) {
       if (cudaStreamSynchronize(st) != cudaSuccess) rc = FMS_ERR_CUDA;
     }
+  }
+  return rc;
+}
+
+// fms_cluster_host: the clustering workspace, then the device copies of the
+// points, labels, margins and modes (256-byte aligned regions).
+struct HostLayout {
+  size_t cluster, off_points, off_labels, off_margins, off_modes, total;
+};
+
+static HostLayout host_layout(int64_t n, int32_t d, int32_t max_modes, const fms_options* opt) {
+  HostLayout L{};
+  L.cluster = fms_workspace_size(n, d, opt);
+  if (L.cluster == 0) return L;
+  size_t o = align256(L.cluster);
+  L.off_points = o;
+  o += align256((size_t)n * d * 4);
+  L.off_labels = o;
+  o += align256((size_t)n * 4);
+  L.off_margins = o;
+  o += align256((size_t)n * 4);
+  L.off_modes = o;
+  o += align256((size_t)(max_modes > 0 ? max_modes : 1) * d * 4);
+  L.total = o;
+  return L;
+}
+
+size_t fms_cluster_host_workspace_size(int64_t n, int32_t d, int32_t max_modes,
+                                       const fms_options* opt) {
+  if (max_modes < 0) return 0;
+  const HostLayout L = host_layout(n, d, max_modes, opt);
+  return L.cluster == 0 ? 0 : L.total;
+}
+
+fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, float tol,
+                            int32_t max_iter, const fms_options* opt, float* out_modes,
+                            int32_t max_modes, int32_t* out_n_modes, int32_t* out_labels,
+                            float* out_margins, void* workspace, size_t workspace_bytes,
+                            fms_stats* stats, void* stream_) {
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!points || !out_labels || !out_n_modes || n < 1 || n > INT32_MAX || d < 1 ||
+      d > FMS_MAX_DIM || max_modes < 0 || (max_modes > 0 && !out_modes))
+    return FMS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const HostLayout L = host_layout(n, d, max_modes, opt);
+  if (L.cluster == 0) return FMS_ERR_INVALID_ARG;
+  void* ws = workspace;
+  bool owns = false;
+  if (ws) {
+    if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+      return FMS_ERR_WORKSPACE;
+  } else {
+    if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) return FMS_ERR_CUDA;
+    owns = true;
+  }
+  float* dpoints = at<float>(ws, L.off_points);
+  int32_t* dlabels = at<int32_t>(ws, L.off_labels);
+  float* dmargins = out_margins ? at<float>(ws, L.off_margins) : nullptr;
+  float* dmodes = at<float>(ws, L.off_modes);
+  fms_status rc = FMS_OK;
+  if (cudaMemcpyAsync(dpoints, points, (size_t)n * d * 4, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess) {
+    rc = FMS_ERR_CUDA;
+  } else {
+    HostCopies hc{};
+    hc.dst[hc.count] = out_labels;
+    hc.src[hc.count] = dlabels;
+    hc.bytes[hc.count++] = (size_t)n * 4;
+    if (out_margins) {
+      hc.dst[hc.count] = out_margins;
+      hc.src[hc.count] = dmargins;
+      hc.bytes[hc.count++] = (size_t)n * 4;
+    }
+    if (max_modes > 0) {
+      hc.dst[hc.count] = out_modes;
+      hc.src[hc.count] = dmodes;
+      hc.bytes[hc.count++] = (size_t)max_modes * d * 4;
+    }
+    rc = cluster_impl(dpoints, n, d, h, tol, max_iter, opt, max_modes > 0 ? dmodes : nullptr,
+                      max_modes, out_n_modes, dlabels, dmargins, ws, L.cluster, stats, stream_,
+                      &hc);
+  }
+  if (owns) {
+    cudaFreeAsync(ws, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && (rc == FMS_OK || rc == FMS_ERR_CAPACITY))
+      rc = FMS_ERR_CUDA;
   }
   return rc;
 }

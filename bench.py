@@ -25,6 +25,7 @@ data-path collective ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -331,7 +332,7 @@ def bench_fms(args):
     lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
     modes_h = torch.empty((cap_h, d), dtype=torch.float32).pin_memory()
     ws_h = fms.Workspace(int(fms._lib.fms_cluster_host_workspace_size(
-        n, d, cap_h, __import__("ctypes").byref(fms.make_options(gamma=0.95, rng_seed=0)))),
+        n, d, cap_h, ctypes.byref(fms.make_options(gamma=0.95, rng_seed=0)))),
         X.device)
     run_h = lambda: fms.cluster_host(Xh, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0,
                                      workspace=ws_h, out=(modes_h, lab_h, None))
@@ -450,8 +451,8 @@ def bench_extra(args):
         Xc = torch.cat(X)
         offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in X])]).astype(np.int64)
         ws = fms.Workspace(fms._lib.fms_batched_workspace_size(
-            offs.ctypes.data_as(__import__("ctypes").c_void_p), len(X), 16,
-            __import__("ctypes").byref(fms.make_options())), Xc.device)
+            offs.ctypes.data_as(ctypes.c_void_p), len(X), 16,
+            ctypes.byref(fms.make_options())), Xc.device)
         run = lambda: fms.cluster_batched(Xc, 2.5, 2.5e-3, 300, offsets=offs, max_modes=128,
                                           workspace=ws)
         r = run()   # first call tunes the tiling
@@ -517,7 +518,7 @@ def bench_extra(args):
             ms, _ = _events_ms(run, max(5, min(50, args.steps)), flush)
 
             ws_h = fms.Workspace(int(fms._lib.fms_cluster_host_workspace_size(
-                n, 3, 256, __import__("ctypes").byref(fms.make_options()))), X.device)
+                n, 3, 256, ctypes.byref(fms.make_options()))), X.device)
             modes_h = torch.empty((256, 3), dtype=torch.float32).pin_memory()
 
             def e2e():   # host buffers through fms_cluster_host

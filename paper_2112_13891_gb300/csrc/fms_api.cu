@@ -548,8 +548,8 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     int resume = 0;
     const bool graph_ok = !graph_cache().disabled && !o.profile && !owns_ws && hbuf &&
                           qmax > 0 && !tensor &&
-                          !o.all_seeds && !o.seed_indices && !o.skip_refine &&
-                          max_iter <= kHistCap && N0 <= cap_seeds;
+                          !o.all_seeds && !keep_exhausted && !o.seed_indices &&
+                          !o.skip_refine && max_iter <= kHistCap && N0 <= cap_seeds;
     if (graph_ok) {
       GraphKey key;
       memset(&key, 0, sizeof(key));
@@ -756,10 +756,17 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
                                    reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, st,
                                    kf, nullptr, sphere_r));
         if (o.profile) cudaEventRecord(rb, st);
-        // the prune's densities: sum w of each kept seed's last update (ms_round)
+        // the prune's densities: sum w of each kept seed's last update (ms_round);
+        // with gamma = 1 kept seeds need not have converged, so a density pass
+        // at their positions instead
         FMS_LAUNCH(launch_round_finish(hist, target, max_iter, state, conv, N, keep_exhausted,
-                                       kept, mctl, ctl, n, R, Lo.tl, st, nullptr, wlast, score));
+                                       kept, mctl, ctl, n, R, Lo.tl, st, nullptr,
+                                       keep_exhausted ? nullptr : wlast, score));
         mark(1);
+        if (keep_exhausted) {
+          FMS_LAUNCH(step_launch(y, kept, &mctl->K, &mctl->C, &mctl->Lc));
+          FMS_LAUNCH(launch_score_reduce(part, mctl, DA, score, N, st));
+        }
       } else {
         FMS_LAUNCH(launch_iter_begin(ctl, state, it, conv, active, n, R, tl_iter, N, target,
                                      max_iter, st));

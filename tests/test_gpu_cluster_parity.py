@@ -175,6 +175,40 @@ def test_tiny_inputs(n):
     _check(w, res, ref)
 
 
+def test_maximum_dimension():
+    # d = FMS_MAX_DIM = 64: the wide FP32 step, the block-wide prune and the
+    # generic label kernel
+    w = fi.separated_blobs(seed=64, k=6, d=64, per=250, sigma=0.7, h=2.0)
+    res = _run(w, gamma=0.95, rng_seed=7, precision="fp32")
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=7)
+    _check(w, res, ref)
+    assert res.stats["n_modes"] == 6
+
+
+@pytest.mark.parametrize("d", [3, 16])
+def test_one_update_only(d):
+    # max_iter = 1: every seed makes one update; with gamma = 1 the seeds
+    # that do not converge in it are kept where the update left them
+    w = fi.separated_blobs(seed=90 + d, k=4, d=d, per=200, sigma=0.6, h=1.5)
+    w1 = fi.Workload(name=w.name, X=w.X, h=w.h, tol=w.tol, max_iter=1)
+    res = _run(w1, gamma=1.0, rng_seed=8, precision="fp32")
+    ref = orc.cluster(w.X, w.h, w.tol, 1, gamma=1.0, rng_seed=8)
+    _check(w1, res, ref)
+    assert res.stats["iterations"] <= 1
+
+
+def test_gamma_one_keeps_exhausted_seeds_on_the_host_path():
+    # d = 16 runs the host-driven path; gamma = 1 with a small max_iter keeps
+    # seeds that did not converge, whose prune densities come from a density
+    # pass at their positions (not from their last update)
+    w = fi.separated_blobs(seed=33, k=5, d=16, per=300, sigma=0.8, h=2.0)
+    w6 = fi.Workload(name=w.name, X=w.X, h=w.h, tol=w.tol, max_iter=4)
+    res = _run(w6, gamma=1.0, rng_seed=9, precision="fp32")
+    ref = orc.cluster(w.X, w.h, w.tol, 4, gamma=1.0, rng_seed=9)
+    _check(w6, res, ref)
+    assert res.stats["n_kept"] == res.stats["n_seeds_final"]
+
+
 def test_identical_points():
     X = np.full((500, 3), 2.5, dtype=np.float32)
     w = fi.Workload(name="same", X=X, h=1.0, tol=1e-3, max_iter=300)

@@ -12,9 +12,9 @@ namespace fms {
 // bitonic sort; (2) the sorted list is walked 32 candidates at a time, one
 // candidate per lane.  Register visit (d = DT known at compile time, the
 // candidates' coordinates preloaded into shared memory): every warp holds the
-// batch in registers and tests it against its share of the modes accepted so
-// far; warp 0 accepts the survivors lowest lane first, each broadcast by
-// shuffles and removing the survivors within r of it (a ballot).  Block visit
+// batch in registers, tests it against its share of the modes accepted so
+// far and computes one member's neighbour mask by shuffles; warp 0 accepts
+// the survivors lowest lane first with those masks.  Block visit
 // (any d): the batch is staged in a transposed, padded tile (conflict-free
 // per-lane reads; two tiles, warp 1 stages the next batch while the current
 // one is tested), every warp tests it against its share of the accepted
@@ -190,11 +190,13 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
     if (preload && acc_in_smem) {
       // Register visit (d = DT known at compile time): every warp holds the
       // batch's coordinates in registers (lane c: sorted candidate base + c),
-      // tests them against its share of the modes accepted so far, and warp 0
-      // accepts the survivors lowest lane first; each accepted candidate is
-      // broadcast by shuffles and removes the survivors within r of it (a
-      // ballot).  The distances are those of the test against an accepted
-      // mode, so the accepted set and its order are the greedy visit's.
+      // tests them against its share of the modes accepted so far, and warp v
+      // records which members lie within r of member v (shuffles and a
+      // ballot); warp 0 then accepts the survivors lowest lane first, each
+      // removing its neighbours by mask, and the accepted lanes write their
+      // rows in parallel.  The distances are those of the test against an
+      // accepted mode, so the accepted set and its order are the greedy
+      // visit's.
       if (threadIdx.x == 0) *s_nacc = 0;
       if (warp == 0) s_dead[lane] = 0;
       for (int base = 0; base < K; base += 32) {
@@ -218,28 +220,36 @@ __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const i
             dead = d2 < r2;
           }
         if (dead) s_dead[lane] = 1;
+        // warp v: the batch members within r of member v (bit l of s_near[v])
+        for (int v = warp; v < 32; v += nwarps) {
+          PT d2 = 0;
+#pragma unroll
+          for (int k = 0; k < DT; ++k) {
+            const PT e = x[k] - __shfl_sync(kFull, x[k], v);
+            d2 += e * e;
+          }
+          const unsigned m = __ballot_sync(kFull, i < K && d2 < r2);
+          if (lane == 0) s_near[v] = m;
+        }
         __syncthreads();
         if (warp == 0) {
+          // survivors accepted lowest lane first, each removing its neighbours;
+          // then every accepted lane writes its own row
           unsigned alive = __ballot_sync(kFull, i < K && !s_dead[lane]);
-          int na = nacc;
+          unsigned acc = 0;
           while (alive) {
             const int w = __ffs(alive) - 1;
-            PT d2 = 0;
+            acc |= 1u << w;
+            alive &= ~(s_near[w] | (1u << w));
+          }
+          if ((acc >> lane) & 1u) {
+            const int at = nacc + __popc(acc & ((1u << lane) - 1u));
+            accepted[at] = c;
 #pragma unroll
-            for (int k = 0; k < DT; ++k) {
-              const PT e = x[k] - __shfl_sync(kFull, x[k], w);
-              d2 += e * e;
-            }
-            if (lane == w) {
-              accepted[na] = c;
-#pragma unroll
-              for (int k = 0; k < DT; ++k) apos[(size_t)na * DT + k] = x[k];
-            }
-            ++na;
-            alive &= ~(__ballot_sync(kFull, d2 < r2) | (1u << w));
+            for (int k = 0; k < DT; ++k) apos[(size_t)at * DT + k] = x[k];
           }
           s_dead[lane] = 0;
-          if (lane == 0) *s_nacc = na;
+          if (lane == 0) *s_nacc = nacc + __popc(acc);
         }
       }
       __syncthreads();

@@ -107,3 +107,46 @@ def test_graph_hands_back_a_refinement_too_large_for_the_clusters():
     _identical(out)
     assert out[0][3]["n_modes"] > 480
     assert out[2][3]["graph"] == 1
+
+
+def test_concurrent_host_threads():
+    # the graph cache, the pinned readback buffer and the capture streams are
+    # per host thread: two threads clustering repeatedly on their own streams
+    # and workspaces get the serial call's bits (graph form from the second
+    # call on)
+    import threading
+    w = fi.separated_blobs(seed=21, k=6, d=3, per=500, sigma=0.6, h=1.5)
+    X = torch.from_numpy(w.X).cuda()
+    n, d = X.shape
+    ref = fms.cluster(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=5)
+    torch.cuda.synchronize()
+    results, errors = {}, []
+
+    def worker(tid):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                ws = fms.Workspace(fms.workspace_size(n, d), X.device)
+                modes = torch.empty((n, d), device="cuda")
+                labels = torch.empty(n, dtype=torch.int32, device="cuda")
+                margins = torch.empty(n, device="cuda")
+                out = []
+                for _ in range(4):
+                    r = fms.cluster(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=5,
+                                    workspace=ws, out=(modes, labels, margins))
+                    out.append((r.modes.clone(), labels.clone(), r.stats["graph"]))
+                s.synchronize()
+            results[tid] = out
+        except Exception as e:   # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for tid in range(2):
+        assert [o[2] for o in results[tid]] == [0, 1, 1, 1]
+        for m, lab, _ in results[tid]:
+            assert torch.equal(m, ref.modes) and torch.equal(lab, ref.labels)

@@ -157,6 +157,21 @@ typedef struct fms_stats {
 /* Human-readable name of a status code (static storage). */
 const char* fms_strerror(fms_status status);
 
+/*
+ * Self-test of the bounded waits the tensor-core step uses on its mbarriers
+ * (failure detection without a GPU fault; no counterpart in the paper): one
+ * CTA waits on a phase that nothing completes, polling at most `spins` times
+ * through the wait helper `variant` selects (0: try_wait, 1: polling
+ * test_wait with an abort flag, 2: suspending try_wait with an abort flag).
+ * A wait that gives up sets the FMS_ERR_TIMEOUT bit of the status word and
+ * returns, as in the step kernel; the phase is then completed and the same
+ * wait must succeed.  *out_status (host) receives the status word: 2 =
+ * timed out as expected, 8 = the completed phase was not seen.  Returns
+ * FMS_ERR_TIMEOUT when the first wait gave up.  Synchronises `stream`.
+ */
+fms_status fms_selftest_bounded_wait(int32_t variant, int64_t spins, uint32_t* out_status,
+                                     void* stream);
+
 /* Fill *opt with the explicit default values listed in fms_options. */
 void fms_options_default(fms_options* opt);
 

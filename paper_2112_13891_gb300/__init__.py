@@ -83,6 +83,8 @@ _lib.fms_cluster_host.restype = ctypes.c_int
 _lib.fms_cluster_host.argtypes = [_P, _I64, _I32, _F32, _F32, _I32, ctypes.POINTER(FmsOptions),
                                   _P, _I32, ctypes.POINTER(_I32), _P, _P, _P, _SZ,
                                   ctypes.POINTER(FmsStats), _P]
+_lib.fms_selftest_bounded_wait.restype = ctypes.c_int
+_lib.fms_selftest_bounded_wait.argtypes = [_I32, _I64, ctypes.POINTER(ctypes.c_uint32), _P]
 _lib.fms_cluster_frames.restype = ctypes.c_int
 _lib.fms_cluster_frames.argtypes = [_P, _I32, _I64, _I32, _F32, _F32, _I32,
                                     ctypes.POINTER(FmsOptions), _F32, _P, _I32, _P, _P, _P, _P,
@@ -288,6 +290,13 @@ def cluster_host(points: torch.Tensor, h: float, tol: float = 0.0, max_iter: int
     M = nm.value
     return ClusterResult(modes=modes[: min(M, cap)], labels=labels, margins=mar, stats=st,
                          status=code)
+
+
+def selftest_bounded_wait(variant: int = 0, spins: int = 1000):
+    """Run fms_selftest_bounded_wait: returns (status code, status word)."""
+    word = ctypes.c_uint32(0)
+    code = _lib.fms_selftest_bounded_wait(int(variant), int(spins), ctypes.byref(word), _stream())
+    return code, word.value
 
 
 @dataclass

@@ -1056,6 +1056,31 @@ fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, 
   return rc;
 }
 
+extern "C++" {
+namespace fms {
+// k_step_tc.cu: the bounded-wait self-test kernel
+cudaError_t launch_wait_selftest(uint32_t* status, long spins, int variant, cudaStream_t st);
+}  // namespace fms
+}
+
+fms_status fms_selftest_bounded_wait(int32_t variant, int64_t spins, uint32_t* out_status,
+                                     void* stream_) {
+  if (variant < 0 || variant > 2 || spins < 1 || !out_status) return FMS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  uint32_t* dstatus = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dstatus), 4, st) != cudaSuccess)
+    return FMS_ERR_CUDA;
+  fms_status rc = FMS_OK;
+  if (cudaMemsetAsync(dstatus, 0, 4, st) != cudaSuccess ||
+      fms::launch_wait_selftest(dstatus, (long)spins, variant, st) != cudaSuccess ||
+      cudaMemcpyAsync(out_status, dstatus, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = FMS_ERR_CUDA;
+  cudaFreeAsync(dstatus, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = FMS_ERR_CUDA;
+  if (rc == FMS_OK && (*out_status & kStTimeout)) rc = FMS_ERR_TIMEOUT;
+  return rc;
+}
+
 fms_status fms_cluster_frames(const float* frames, int32_t F, int64_t n, int32_t d, float h,
                               float tol, int32_t max_iter, const fms_options* opt_in, float H,
                               float* out_modes, int32_t max_modes, int32_t* out_n_modes,

@@ -98,8 +98,8 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
 }
 
 // bounded wait on an mbarrier phase; false when the bound ran out
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {
-  for (long it = 0; it < kSpin; ++it) {
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase, long spins = kSpin) {
+  for (long it = 0; it < spins; ++it) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -117,8 +117,8 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t phase) {
 // may suspend the warp and leaves its issue slots to the other warps.
 template <bool kPoll>
 __device__ __forceinline__ bool wait_bar_abort(uint64_t* bar, uint32_t phase,
-                                               volatile int* abort_flag) {
-  for (long it = 0; it < kSpin; ++it) {
+                                               volatile int* abort_flag, long spins = kSpin) {
+  for (long it = 0; it < spins; ++it) {
     uint32_t ok;
     if (kPoll)
       asm volatile(
@@ -664,6 +664,39 @@ cudaError_t launch_ms_step_tc(const unsigned char* img, int64_t n, int d, int DP
     ms_step_tc<32><<<grid, tc::kThreads, tc::Geo<32>::kSmem, st>>>(
         img, (int)n, y, DP, DA, active, s_total_ptr, count_ptr, C_ptr, Lc_ptr, part, status,
         s_log);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded waits ms_step_tc uses: one CTA waits on phase 0
+// of a fresh mbarrier that nothing completes, with `spins` polls, through the
+// helper `variant` selects (0: wait_bar, 1: polling wait_bar_abort, 2:
+// suspending wait_bar_abort); a wait that gives up sets kStTimeout, as in
+// the step kernel.  Then one arrival completes the phase and the same wait
+// must succeed (kStBadArg if it does not).
+__global__ void wait_selftest_kernel(uint32_t* status, long spins, int variant) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  bool ok;
+  if (variant == 1) ok = tc::wait_bar_abort<true>(&bar, 0, &abort_flag, spins);
+  else if (variant == 2) ok = tc::wait_bar_abort<false>(&bar, 0, &abort_flag, spins);
+  else ok = tc::wait_bar(&bar, 0, spins);
+  if (!ok) atomicOr(status, kStTimeout);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(tc::su32(&bar))
+                 : "memory");
+  __syncthreads();
+  if (!tc::wait_bar(&bar, 0, spins)) atomicOr(status, kStBadArg);
+}
+
+cudaError_t launch_wait_selftest(uint32_t* status, long spins, int variant, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 64, 0, st>>>(status, spins, variant);
   return cudaGetLastError();
 }
 

@@ -344,25 +344,50 @@ __device__ void scan_clock(int r, int N, const int32_t* __restrict__ state,
                            const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
                            int32_t* __restrict__ active, int want, int* s_out, int* conv_out,
                            int* next_event_out, int* scratch) {
+  // each thread takes V consecutive seeds per block-wide step (one block scan
+  // per blockDim * V seeds; V = 16 once N is large), its V state loads issued
+  // together, then its V update-count loads; the list stays in slot order
+  constexpr int kScanRun = 16;
+  const int V = N > (int)blockDim.x * 2 ? kScanRun : 1;
   int base = 0, convd = 0, nxt = INT32_MAX;
-  for (int b = 0; b < N; b += blockDim.x) {
-    const int i = b + threadIdx.x;
-    int take = 0;
-    if (i < N) {
-      const int stt = __ldcg(state + i);
-      if (stt == kRunning || stt == kCoarse) {
-        const int ti = __ldcg(it + i);
-        if (ti == r) take = (want < 0 || stt == want) ? 1 : 0;
-        else if (ti > r) nxt = min(nxt, ti);
-      } else if (stt == kConverged) {
-        const int ci = __ldcg(conv + i);
+  for (int64_t b = 0; b < N; b += (int64_t)blockDim.x * V) {
+    const int64_t i0 = b + (int64_t)threadIdx.x * V;
+    int stt[kScanRun], cnt_v[kScanRun];
+#pragma unroll
+    for (int v = 0; v < kScanRun; ++v)
+      stt[v] = (v < V && i0 + v < N) ? __ldcg(state + i0 + v) : -1;
+#pragma unroll
+    for (int v = 0; v < kScanRun; ++v) {
+      const int64_t i = i0 + v;
+      cnt_v[v] = 0;
+      if (stt[v] == kRunning || stt[v] == kCoarse) cnt_v[v] = __ldcg(it + i);
+      else if (stt[v] == kConverged) cnt_v[v] = __ldcg(conv + i);
+    }
+    unsigned takes = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int v = 0; v < kScanRun; ++v) {
+      if (stt[v] == kRunning || stt[v] == kCoarse) {
+        const int ti = cnt_v[v];
+        if (ti == r) {
+          if (want < 0 || stt[v] == want) {
+            takes |= 1u << v;
+            ++cnt;
+          }
+        } else if (ti > r) {
+          nxt = min(nxt, ti);
+        }
+      } else if (stt[v] == kConverged) {
+        const int ci = cnt_v[v];
         if (ci <= r) ++convd;
         else nxt = min(nxt, ci);
       }
     }
     int tot;
-    const int off = block_exclusive_scan(take, &tot, scratch);
-    if (take) active[base + off] = i;
+    int off = block_exclusive_scan(cnt, &tot, scratch);
+#pragma unroll
+    for (int v = 0; v < kScanRun; ++v)
+      if ((takes >> v) & 1u) active[base + off++] = (int32_t)(i0 + v);
     base += tot;
   }
   convd = block_sum(convd, scratch);

@@ -63,6 +63,17 @@ def test_paper_3d_all_seeds_small():
     _check(w, res, ref)
 
 
+def test_paper_3d_all_seeds_30k():
+    # 30,000 seeds: more candidates than the sorted prune's keys can hold in
+    # shared memory, so the one-block global greedy runs; checked whole
+    # against the oracle
+    w = fi.paper_3d(n=30_000)
+    res = _run(w, all_seeds=True)
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, all_seeds=True)
+    _check(w, res, ref)
+    assert res.stats["n_kept"] == 30_000
+
+
 def test_paper_3d_all_seeds_full_size_sampled():
     # Alg. 1 at the 200K size the all-seeds bench line runs: every point is a
     # seed, too many for the oracle to cluster whole.  Trajectories are

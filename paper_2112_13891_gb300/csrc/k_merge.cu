@@ -88,76 +88,134 @@ cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA,
 // than r" -- the same accepted set as visiting the sorted list once.
 // One CTA of 1024 threads; candidate q has rank q.
 // ---------------------------------------------------------------------------
+template <typename ST>
+__device__ __forceinline__ void argmax_merge(ST& best, int& bq, ST os, int oq) {
+  if (os > best || (os == best && oq < bq)) {
+    best = os;
+    bq = oq;
+  }
+}
+
+// Block-wide (score desc, index asc) winner; INT32_MAX when no candidate
+// has a comparable score.  Every thread returns the same value.
+template <typename ST>
+__device__ int block_argmax(ST best, int bq, ST* sh_s, int* sh_q, int* sh_best) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const ST os = __shfl_xor_sync(kFull, best, o);
+    const int oq = __shfl_xor_sync(kFull, bq, o);
+    argmax_merge<ST>(best, bq, os, oq);
+  }
+  if (lane == 0) {
+    sh_s[wid] = best;
+    sh_q[wid] = bq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ST b = sh_s[0];
+    int bb = sh_q[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge<ST>(b, bb, sh_s[w], sh_q[w]);
+    *sh_best = bb;
+  }
+  __syncthreads();
+  const int win = *sh_best;
+  __syncthreads();   // sh_best and sh_s / sh_q are reused by the next call
+  return win;
+}
+
+// The greedy visit for candidate sets too large for the sorted prune's
+// shared memory: repeatedly accept the remaining candidate of highest
+// (score, lowest index) and drop every candidate within r of it.  The
+// remaining candidates are kept as a compacted list (in `list`); one pass per
+// accepted mode drops the new mode's neighbours and finds the next winner,
+// each thread taking kRun list entries per step with their loads issued
+// together.  The winner and every suppression are decided exactly as in the
+// one-by-one visit, so the accepted set and order are the same.
 template <typename PT, typename ST>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
     greedy_merge_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
                         const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
-                        PT r2, int32_t* __restrict__ alive, int32_t* __restrict__ accepted,
+                        PT r2, int32_t* __restrict__ list, int32_t* __restrict__ accepted,
                         int32_t* __restrict__ M_out) {
+  constexpr int kRun = 8;
   __shared__ ST sh_s[32];
   __shared__ int sh_q[32];
   __shared__ PT sh_pos[FMS_MAX_DIM_PAD];
   __shared__ int sh_best;
+  __shared__ int scratch[64];
   const int K = *K_ptr;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = threadIdx.x; q < K; q += blockDim.x) alive[q] = 1;
-  __syncthreads();
-  int M = 0;
-  for (int round = 0; round < K; ++round) {
-    ST best = -INFINITY;
-    int bq = INT32_MAX;
-    for (int q = threadIdx.x; q < K; q += blockDim.x) {
-      if (!alive[q]) continue;
-      const ST sc = score[q];
-      if (sc > best || (sc == best && q < bq)) {
-        best = sc;
-        bq = q;
-      }
-    }
+  const int T = blockDim.x;
+  ST best = (ST)-INFINITY;
+  int bq = INT32_MAX;
+  for (int b = 0; b < K; b += T * kRun) {
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const ST os = __shfl_xor_sync(kFull, best, o);
-      const int oq = __shfl_xor_sync(kFull, bq, o);
-      if (os > best || (os == best && oq < bq)) {
-        best = os;
-        bq = oq;
+    for (int v = 0; v < kRun; ++v) {
+      const int q = b + v * T + threadIdx.x;
+      if (q < K) {
+        list[q] = q;
+        argmax_merge<ST>(best, bq, score[q], q);
       }
     }
-    if (lane == 0) {
-      sh_s[wid] = best;
-      sh_q[wid] = bq;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      ST b = sh_s[0];
-      int bb = sh_q[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        if (sh_s[w] > b || (sh_s[w] == b && sh_q[w] < bb)) {
-          b = sh_s[w];
-          bb = sh_q[w];
-        }
-      }
-      sh_best = bb;
-      if (bb != INT32_MAX) accepted[M] = bb;
-    }
-    __syncthreads();
-    const int win = sh_best;
-    if (win == INT32_MAX) break;
+  }
+  int win = block_argmax<ST>(best, bq, sh_s, sh_q, &sh_best);
+  int len = K, M = 0;
+  while (win != INT32_MAX) {
+    if (threadIdx.x == 0) accepted[M] = win;
     ++M;
     const int64_t wrow = cand_row ? cand_row[win] : win;
-    for (int k = threadIdx.x; k < d; k += blockDim.x) sh_pos[k] = pos[wrow * DP + k];
+    for (int k = threadIdx.x; k < d; k += T) sh_pos[k] = pos[wrow * DP + k];
     __syncthreads();
-    for (int q = threadIdx.x; q < K; q += blockDim.x) {
-      if (!alive[q]) continue;
-      const int64_t row = cand_row ? cand_row[q] : q;
-      PT d2 = 0;
-      for (int k = 0; k < d; ++k) {
-        const PT e = pos[row * DP + k] - sh_pos[k];
-        d2 += e * e;
+    best = (ST)-INFINITY;
+    bq = INT32_MAX;
+    int newlen = 0;
+    for (int b = 0; b < len; b += T * kRun) {
+      int q[kRun];
+      int64_t row[kRun];
+      ST sc[kRun];
+      PT d2[kRun];
+#pragma unroll
+      for (int v = 0; v < kRun; ++v) {
+        const int idx = b + v * T + threadIdx.x;
+        q[v] = idx < len ? list[idx] : -1;
       }
-      if (d2 < r2) alive[q] = 0;
+#pragma unroll
+      for (int v = 0; v < kRun; ++v) {
+        sc[v] = q[v] >= 0 ? score[q[v]] : (ST)0;
+        row[v] = q[v] >= 0 ? (cand_row ? (int64_t)cand_row[q[v]] : (int64_t)q[v]) : 0;
+        d2[v] = 0;
+      }
+      for (int k = 0; k < d; ++k) {
+        const PT pk = sh_pos[k];
+#pragma unroll
+        for (int v = 0; v < kRun; ++v) {
+          if (q[v] >= 0) {
+            const PT e = pos[row[v] * DP + k] - pk;
+            d2[v] += e * e;
+          }
+        }
+      }
+      unsigned keep = 0;
+      int cnt = 0;
+#pragma unroll
+      for (int v = 0; v < kRun; ++v) {
+        if (q[v] >= 0 && q[v] != win && !(d2[v] < r2)) {
+          keep |= 1u << v;
+          ++cnt;
+          argmax_merge<ST>(best, bq, sc[v], q[v]);
+        }
+      }
+      // in-place compaction: this step writes only below the end of what it
+      // read, and every read precedes the scan's barriers
+      int tot;
+      int off = block_exclusive_scan(cnt, &tot, scratch);
+#pragma unroll
+      for (int v = 0; v < kRun; ++v)
+        if ((keep >> v) & 1u) list[newlen + off++] = q[v];
+      newlen += tot;
     }
-    __syncthreads();
+    len = newlen;
+    win = block_argmax<ST>(best, bq, sh_s, sh_q, &sh_best);
   }
   if (threadIdx.x == 0) *M_out = M;
 }
@@ -241,7 +299,7 @@ cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const S
     FMS_SORTED(0);
 #undef FMS_SORTED
   }
-  greedy_merge_kernel<PT, ST><<<1, 1024, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2, alive,
+  greedy_merge_kernel<PT, ST><<<1, 512, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2, alive,
                                                   accepted, M_out);
   return cudaGetLastError();
 }

@@ -372,8 +372,10 @@ fms_status fms_mean_shift_step_coarse(const float* points, int64_t n, int32_t d,
  * holds that much device memory until the process exits.  A request whose
  * scratch would not fit -- fms_step_workspace_size(n, d, m) larger than
  * FMS_NOALLOC_SCRATCH_BYTES -- is refused with FMS_ERR_WORKSPACE before any
- * device work.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
+ * device work.  Every call looks up the array's device address in the
+ * current device's context (cudaGetSymbolAddress, which enqueues no work), so
+ * the call stays valid after that context has been reset or recreated.  The
+ * first call on a device may load the library's device code; make that first
  * call before capturing the stream into a graph.
  *
  * All calls share the one array and it keeps the previous call's contents:

@@ -39,20 +39,12 @@ Dev device_info() {
   return d;
 }
 
-int padded_dim(int d) {
-  if (d <= 4) return 4;
-  if (d <= 8) return 8;
-  return (d + 3) / 4 * 4;
-}
-
-size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-
 // Workspace carving.  All sizes in bytes, every region 256-byte aligned.
 struct Layout {
   size_t off_Xs, off_y, off_seed_idx, off_it, off_conv, off_state, off_active, off_kept,
       off_alive, off_acc1, off_acc2, off_score, off_ym, off_mdone, off_mscore, off_modes_full,
       off_part, off_part64, off_ctl, off_mctl, off_status, off_slog, off_yf, off_ract, off_rctl,
-      off_hist, off_S, off_img, off_wlast, total;
+      off_hist, off_S, off_img, off_wlast, off_grid, total;
   int DP, DA, R, grid_ctas;
   int64_t Ncap;
   Tiling tl;
@@ -233,8 +225,34 @@ Layout make_layout(int64_t n, int d, int64_t Ncap, int sms, bool tensor) {
   L.off_S = take(64);
   L.off_img = take(tensor ? tc_image_bytes(n, d) : 0);
   L.off_wlast = take((size_t)Ncap * 4);   // sum w of each seed's latest cluster-round update
+  L.off_grid = take(d <= 7 ? grid_scratch_bytes(d) : 0);   // grid rounds: barrier + accumulators
   L.total = o;
   return L;
+}
+
+// Grid-round launch plan (occupancy and shared-memory checks), cached per
+// host thread for the last few (device, n, d, max_iter class) seen.
+GridPlan cached_grid_plan(int64_t n, int d, int sms, int max_iter) {
+  struct Entry {
+    int dev;
+    int64_t n;
+    int d, sms, hist_ok;
+    GridPlan p;
+  };
+  thread_local Entry cache[8];
+  thread_local int used = 0, next = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GridPlan{};
+  const int hist_ok = max_iter < kGridHist ? 1 : 0;
+  for (int i = 0; i < used; ++i)
+    if (cache[i].dev == dev && cache[i].n == n && cache[i].d == d && cache[i].sms == sms &&
+        cache[i].hist_ok == hist_ok)
+      return cache[i].p;
+  Entry e{dev, n, d, sms, hist_ok, grid_round_plan(n, d, sms, max_iter)};
+  cache[next] = e;
+  next = (next + 1) % 8;
+  if (used < 8) ++used;
+  return e.p;
 }
 
 void fill_defaults(const fms_options* in, fms_options* o) {
@@ -469,6 +487,9 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     tl_iter.tc_ctas = Lo.tc_ctas;
     const int32_t init_state = tensor ? kCoarse : kRunning;
     const int qmax = d <= 7 ? round_max_clusters(d) : 0;
+    // persistent grid rounds (one CTA per SM) for d <= 7 when they fit
+    const GridPlan gp = d <= 7 ? cached_grid_plan(n, d, dv.sms, max_iter) : GridPlan{};
+    void* grid_scratch = at<void>(ws, Lo.off_grid);
 
     const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
     // cosine metric: the packed points lie on the sphere of radius scale, and
@@ -538,7 +559,30 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     else if (o.seed_indices) N0 = o.n_seed_indices;
     else N0 = (int32_t)(o.n_initial < n ? o.n_initial : n);
     RoundCtl* rctl_round = at<RoundCtl>(ws, Lo.off_ctl + kCtlRoundOff);
-    const int cap_seeds = qmax * kSeedsPerCluster, cap_modes = qmax * kModesPerCluster;
+    const int cap_seeds = gp.ok ? kGridMaxSeeds : qmax * kSeedsPerCluster;
+    const int cap_modes = qmax * kModesPerCluster;
+    // one grid round over the RUNNING seeds of [0, N) (N and target from rcp
+    // when non-null)
+    auto grid_launch = [&](const RoundCtl* rcp, int N_, int target_, cudaStream_t s_) {
+      GridRoundArgs ga{};
+      ga.Xs = Xs;
+      ga.n = (int)n;
+      ga.y = y;
+      ga.it = it;
+      ga.conv = conv;
+      ga.state = state;
+      ga.wlast = wlast;
+      ga.hist = hist;
+      ga.rc = rcp;
+      ga.N_arg = N_;
+      ga.target_arg = target_;
+      ga.max_iter = max_iter;
+      ga.tol2_s = tol2_s;
+      ga.sphere_r = sphere_r;
+      ga.evals = reinterpret_cast<unsigned long long*>(&ctl->evals);
+      ga.status = status;
+      return launch_ms_grid_round(gp, d, kf, ga, grid_scratch, s_);
+    };
     const int keep_exhausted = o.gamma >= 1.0f ? 1 : 0;
     const double rtol_s = kRefineTolFactor * (double)h * scale;
 
@@ -618,12 +662,17 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
           e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cudaError_t e2 = launch_round_list(state, 0, active, S_dev, cs2, rctl_round);
-          if (e2 == cudaSuccess)
-            e2 = launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, qmax, hist, 0,
-                                 max_iter, tol2_s,
-                                 reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, cs2,
-                                 kf, rctl_round, sphere_r);
+          cudaError_t e2 = cudaSuccess;
+          if (gp.ok) {
+            e2 = grid_launch(rctl_round, 0, 0, cs2);
+          } else {
+            e2 = launch_round_list(state, 0, active, S_dev, cs2, rctl_round);
+            if (e2 == cudaSuccess)
+              e2 = launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, qmax, hist, 0,
+                                   max_iter, tol2_s,
+                                   reinterpret_cast<unsigned long long*>(&ctl->evals), wlast,
+                                   cs2, kf, rctl_round, sphere_r);
+          }
           if (e2 == cudaSuccess)
             e2 = launch_round_finish(hist, 0, max_iter, state, conv, 0, keep_exhausted, kept,
                                      mctl, ctl, n, R, Lo.tl, cs2, rctl_round, wlast, score);
@@ -638,7 +687,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
           const cudaError_t e3 = cudaStreamEndCapture(cs2, &gb);
           e = e2 != cudaSuccess ? e2 : e3;
         }
-        slot->kernels_round = 5;
+        slot->kernels_round = gp.ok ? 4 : 5;
         // after the rounds: refinement, second prune, order, labels
         cudaGraph_t post = nullptr;
         if (e == cudaSuccess) e = add_conditional(cs, h_post, cudaGraphCondTypeIf, &post);
@@ -736,14 +785,14 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       if (target < 1) target = 1;
       if (target > N) target = N;
       // --- mean-shift iterations under Early Stopping (Sec. II-C) ---
+      const bool use_grid = gp.ok && N <= kGridMaxSeeds;
       const bool use_clusters =
-          qmax > 0 && N <= qmax * kSeedsPerCluster && max_iter <= kHistCap;
+          use_grid || (qmax > 0 && N <= qmax * kSeedsPerCluster && max_iter <= kHistCap);
       if (use_clusters) {
-        // cluster-persistent round: ~8 seeds per cluster, no host round trips
-        int clusters = (N + 7) / 8;
-        if (clusters > qmax) clusters = qmax;
-        FMS_LAUNCH(launch_round_list(state, N, active, S_dev, st));
+        // persistent round (grid of one CTA per SM, or thread-block clusters
+        // when the grid plan does not fit): no host round trips
         cudaEvent_t ra = nullptr, rb = nullptr;
+        if (!use_grid) FMS_LAUNCH(launch_round_list(state, N, active, S_dev, st));
         if (o.profile) {
           cudaEventCreate(&ra);
           cudaEventCreate(&rb);
@@ -751,10 +800,16 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
           round_evs.push_back(ra);
           round_evs.push_back(rb);
         }
-        FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
-                                   target, max_iter, tol2_s,
-                                   reinterpret_cast<unsigned long long*>(&ctl->evals), wlast, st,
-                                   kf, nullptr, sphere_r));
+        if (use_grid) {
+          FMS_LAUNCH(grid_launch(nullptr, N, target, st));
+        } else {
+          int clusters = (N + 7) / 8;
+          if (clusters > qmax) clusters = qmax;
+          FMS_LAUNCH(launch_ms_round(Xs, n, d, y, it, conv, state, active, S_dev, clusters, hist,
+                                     target, max_iter, tol2_s,
+                                     reinterpret_cast<unsigned long long*>(&ctl->evals), wlast,
+                                     st, kf, nullptr, sphere_r));
+        }
         if (o.profile) cudaEventRecord(rb, st);
         // the prune's densities: sum w of each kept seed's last update (ms_round);
         // with gamma = 1 kept seeds need not have converged, so a density pass
@@ -1163,36 +1218,6 @@ fms_status fms_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t
   return FMS_OK;
 }
 
-namespace {
-struct StepLayout {
-  size_t off_Xs, off_Ys, off_active, off_part, off_ctl, off_status, total;
-  int DP, DA, R, grid_ctas, C, Lc;
-};
-
-StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
-  StepLayout L{};
-  L.DP = padded_dim(d);
-  L.DA = step_accumulators(d);
-  L.R = step_seeds_per_warp(d);
-  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), step_min_chunk(d)};
-  L.grid_ctas = (tl.target_warps + 7) / 8;
-  choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    const size_t at_ = o;
-    o += align256(bytes > 0 ? bytes : 1);
-    return at_;
-  };
-  L.off_Xs = take((size_t)n * L.DP * 4);
-  L.off_Ys = take((size_t)m * L.DP * 4);
-  L.off_active = take((size_t)m * 4);
-  L.off_part = take((size_t)L.C * (size_t)m * L.DA * 4);
-  L.off_ctl = take(sizeof(IterCtl));
-  L.off_status = take(64);
-  L.total = o;
-  return L;
-}
-}  // namespace
 
 size_t fms_step_workspace_size(int64_t n, int32_t d, int64_t m) {
   if (n < 1 || n > INT32_MAX || d < 1 || d > FMS_MAX_DIM || m < 1 || m > INT32_MAX) return 0;

@@ -366,6 +366,54 @@ cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 const float* wlast = nullptr,   // with score: the prune
                                 float* score = nullptr);        // densities from wlast
 
+// k_grid.cu: persistent grid rounds (one CTA per SM, cooperative launch).
+// Most seeds one round launch holds, and the convergence histogram entries
+// every CTA keeps (max_iter must be below kGridHist).
+constexpr int kGridMaxSeeds = 1024;
+constexpr int kGridHist = 2048;
+
+// Launch plan of the grid round for (n, d) on this device.
+struct GridPlan {
+  int ok;         // 1: the grid round can run
+  int G;          // CTAs (one per SM)
+  int per_cta;    // points per CTA slice
+  int n_sub;      // sub-slices per CTA slice
+  int sub_len;    // points per sub-slice (multiple of 32)
+  int resident;   // 1: the slice is staged in shared memory
+  int smem;       // dynamic shared memory per CTA (bytes)
+  int fx_bits;    // fixed-point scale of the cross-CTA sums: 2^fx_bits
+};
+
+struct GridRoundArgs {
+  const float* Xs;             // packed points [n][DP]
+  int n;
+  int per_cta, n_sub, sub_len; // filled by launch_ms_grid_round
+  float* y;                    // seed state (slots [0, N))
+  int32_t* it;
+  int32_t* conv;
+  int32_t* state;
+  float* wlast;
+  int32_t* hist;               // global convergence histogram [max_iter + 2]
+  const RoundCtl* rc;          // non-null: N and target from the device
+  int N_arg, target_arg;
+  int max_iter;
+  float tol2_s;                // squared tolerance in scaled coordinates
+  float sphere_r;              // > 0: cosine metric, project onto this sphere
+  unsigned long long* evals;
+  unsigned long long* gacc;    // filled by launch_ms_grid_round
+  unsigned* gbar;
+  uint32_t* status;
+  float fx_scale;              // 2^fx_bits
+  float inv_fx_scale;          // 2^-fx_bits
+};
+
+GridPlan grid_round_plan(int64_t n, int d, int sms, int max_iter);
+size_t grid_scratch_bytes(int d);
+size_t grid_scratch_clear_bytes(int d);
+// Clears the scratch's counter and first accumulator, then launches the round.
+cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs a,
+                                 void* scratch, cudaStream_t st);
+
 // k_unroll.cu: unrolled steps and their adjoint
 struct UGeom {
   int B, n, m, d, DP;  // DP: padded row length (multiple of 4) of the packed copies
@@ -397,6 +445,47 @@ int step_resident_warps_per_sm(int d);
 // (d > 16) gives every point to all 32 lanes
 inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : (d <= 16 ? 256 : 64); }
 int step_accumulators(int d);
+
+// Scratch layout of one stand-alone update (fms_mean_shift_step and its
+// allocation-free variant): packed points, packed seeds, active list,
+// per-chunk partial sums, control block, status word; every region 256-byte
+// aligned.
+struct StepLayout {
+  size_t off_Xs, off_Ys, off_active, off_part, off_ctl, off_status, total;
+  int DP, DA, R, grid_ctas, C, Lc;
+};
+
+inline int padded_dim(int d) {
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  return (d + 3) / 4 * 4;
+}
+
+inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+inline StepLayout step_layout(int64_t n, int d, int64_t m, int sms) {
+  StepLayout L{};
+  L.DP = padded_dim(d);
+  L.DA = step_accumulators(d);
+  L.R = step_seeds_per_warp(d);
+  Tiling tl{(sms > 0 ? sms : 1) * step_resident_warps_per_sm(d), step_min_chunk(d)};
+  L.grid_ctas = (tl.target_warps + 7) / 8;
+  choose_chunks(n, (int32_t)m, L.R, tl, &L.C, &L.Lc);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = o;
+    o += align256(bytes > 0 ? bytes : 1);
+    return at_;
+  };
+  L.off_Xs = take((size_t)n * L.DP * 4);
+  L.off_Ys = take((size_t)m * L.DP * 4);
+  L.off_active = take((size_t)m * 4);
+  L.off_part = take((size_t)L.C * (size_t)m * L.DA * 4);
+  L.off_ctl = take(sizeof(IterCtl));
+  L.off_status = take(64);
+  L.total = o;
+  return L;
+}
 
 // k_step_tc.cu: the coarse step on the tensor cores (1 <= d <= 32).  The
 // point tile images are built once per call by launch_tc_pack; the step

@@ -11,11 +11,11 @@
 // The array below is a static __device__ buffer: every GPU that loads the
 // library reserves FMS_NOALLOC_SCRATCH_BYTES for it until the process exits.
 // In host code its name only stands for the buffer; the device address that
-// kernels need is fetched once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on that device.
+// kernels need is looked up with cudaGetSymbolAddress, with the calling device
+// current, on every call.  The lookup enqueues no work, and looking it up each
+// time (instead of caching it per device) keeps the call correct after the
+// device's context has been reset or recreated, when the array may have moved.
 #include <math.h>
-
-#include <mutex>
 
 #include "../../include/fms.h"
 #include "fms_internal.cuh"
@@ -26,33 +26,13 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FMS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current device's context.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
-}
-
-size_t round256(size_t x) { return (x + 255) / 256 * 256; }
-
-int padded_dim_of(int d) {
-  if (d <= 4) return 4;
-  if (d <= 8) return 8;
-  return (d + 3) / 4 * 4;
 }
 
 }  // namespace
@@ -70,43 +50,32 @@ extern "C" fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return FMS_ERR_CUDA;
 
-  // the same scratch layout the workspace form uses: packed points, packed
-  // seeds, active list, per-chunk partial sums, control block, status word
-  const int DP = padded_dim_of(d);
-  const int DA = step_accumulators(d);
-  const int R = step_seeds_per_warp(d);
-  Tiling tl{sms * step_resident_warps_per_sm(d), step_min_chunk(d)};
-  int32_t C = 0, Lc = 0;
-  choose_chunks(n, (int32_t)m, R, tl, &C, &Lc);
-  const size_t off_Xs = 0;
-  const size_t off_Ys = off_Xs + round256((size_t)n * DP * 4);
-  const size_t off_active = off_Ys + round256((size_t)m * DP * 4);
-  const size_t off_part = off_active + round256((size_t)m * 4);
-  const size_t off_ctl = off_part + round256((size_t)C * (size_t)m * DA * 4);
-  const size_t off_status = off_ctl + round256(sizeof(IterCtl));
-  const size_t total = off_status + 256;
-  if (total > (size_t)FMS_NOALLOC_SCRATCH_BYTES) return FMS_ERR_WORKSPACE;
+  // the same scratch layout the workspace form uses (step_layout): packed
+  // points, packed seeds, active list, per-chunk partial sums, control block,
+  // status word
+  const StepLayout L = step_layout(n, d, m, sms);
+  if (L.total > (size_t)FMS_NOALLOC_SCRATCH_BYTES) return FMS_ERR_WORKSPACE;
 
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return FMS_ERR_CUDA;
   char* b = static_cast<char*>(base);
-  float* Xs = reinterpret_cast<float*>(b + off_Xs);
-  float* Ys = reinterpret_cast<float*>(b + off_Ys);
-  int32_t* active = reinterpret_cast<int32_t*>(b + off_active);
-  float* part = reinterpret_cast<float*>(b + off_part);
-  IterCtl* ctl = reinterpret_cast<IterCtl*>(b + off_ctl);
-  uint32_t* status = reinterpret_cast<uint32_t*>(b + off_status);
+  float* Xs = reinterpret_cast<float*>(b + L.off_Xs);
+  float* Ys = reinterpret_cast<float*>(b + L.off_Ys);
+  int32_t* active = reinterpret_cast<int32_t*>(b + L.off_active);
+  float* part = reinterpret_cast<float*>(b + L.off_part);
+  IterCtl* ctl = reinterpret_cast<IterCtl*>(b + L.off_ctl);
+  uint32_t* status = reinterpret_cast<uint32_t*>(b + L.off_status);
 
   const double scale = sqrt(1.4426950408889634 / (2.0 * (double)h * (double)h));
   // the status word is OR-ed into by the packing kernel: it must start at zero
   // (every other region is fully written before it is read)
   if (cudaMemsetAsync(status, 0, 4, st) != cudaSuccess) return FMS_ERR_CUDA;
-  if (launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st) != cudaSuccess ||
-      launch_pack_points(seeds, m, d, DP, (float)scale, Ys, status, st) != cudaSuccess ||
-      launch_step_setup(active, (int32_t)m, ctl, C, Lc, st) != cudaSuccess ||
-      launch_ms_step(Xs, n, d, DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
-                     ((tl.target_warps + 7) / 8) * 8, st, nullptr) != cudaSuccess ||
-      launch_step_finish(part, ctl, seeds, d, DA, 1.0 / scale, out_seeds, out_wsum, (int)m,
+  if (launch_pack_points(points, n, d, L.DP, (float)scale, Xs, status, st) != cudaSuccess ||
+      launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st) != cudaSuccess ||
+      launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st) != cudaSuccess ||
+      launch_ms_step(Xs, n, d, L.DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
+                     L.grid_ctas * 8, st, nullptr) != cudaSuccess ||
+      launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum, (int)m,
                          st) != cudaSuccess)
     return FMS_ERR_CUDA;
   return FMS_OK;

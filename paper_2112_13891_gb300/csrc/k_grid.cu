@@ -1,0 +1,623 @@
+// ms_grid_round: one Seed-Selection round of Gaussian mean-shift updates
+// (Eq. 6 / Alg. 2 line 6 under the Early Stopping of Sec. II-C) on a
+// persistent grid of one CTA per SM.
+//
+// Decomposition.  CTA c owns a fixed, contiguous slice of the points (n / G
+// points for G CTAs), staged once into shared memory by TMA bulk copies when
+// it fits (else read from L2).  The slice is cut into fixed sub-slices.  In
+// every update each CTA evaluates every active seed of the round against its
+// slice: a warp task is (a group of R seeds, one sub-slice); lane l takes the
+// sub-slice points l, l + 32, ...; the 32 lane sums are combined by a fixed
+// xor tree.  That FP32 value -- the partial of one seed over one sub-slice --
+// is a leaf.  Leaves are converted to 64-bit fixed point (2^F units, F chosen
+// so that no sum over all n points can overflow) and added exactly: first in
+// shared memory, then across CTAs with red.global.add.u64 into a triple-
+// buffered accumulator.  Integer addition is associative, so the totals (and
+// every seed's trajectory) do not depend on which warp took which task, on the
+// group size R, on the order of the atomics or on which other seeds are
+// active; the only rounding is that of the leaves and of one conversion to
+// FP64 per total.
+//
+// One grid barrier per update (a release-add on a counter, an acquire poll,
+// both bounded): after it every CTA reads the same totals and applies the same
+// update to its replicated copy of the round's seed state, so no second
+// exchange is needed.  CTA 0 writes the seed state back to global memory.
+//
+// Early Stopping.  Every CTA keeps the convergence histogram of all seeds of
+// all rounds; after each update it finds t_stop, the first update count whose
+// cumulative convergence count reaches ceil(gamma N), and deactivates every
+// RUNNING seed that has made t_stop or more updates without converging: such
+// a seed converges (if ever) after t* <= t_stop and cannot be kept.  Counts
+// only grow, so the kept set is that of the synchronous rule; a stopped seed
+// stays RUNNING with its update count (a later round may resume it).
+#include "fms_internal.cuh"
+
+namespace fms {
+
+namespace {
+
+constexpr int kGridWarps = 16;
+constexpr int kGridThreads = kGridWarps * 32;
+constexpr int kGridSubLen = 2048;                // longest sub-slice (points)
+constexpr long long kGridSpinCycles = 4000000000LL;   // bound of one wait (~2 s)
+
+// Shared memory carving (bytes), identical on host and device.
+struct GridSmem {
+  int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_list, off_hist, off_pts;
+  int total;
+};
+
+__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline GridSmem grid_smem(int D, int DA, int DP, int pts) {
+  GridSmem s{};
+  int o = 0;
+  s.off_bar = o;
+  o += 16;
+  s.off_misc = o;
+  o += 128;
+  s.off_y = o;
+  o = al16(o + kGridMaxSeeds * D * 4);
+  s.off_it = o;
+  o += kGridMaxSeeds * 4;
+  s.off_slot = o;
+  o += kGridMaxSeeds * 4;
+  s.off_act = o;
+  o += kGridMaxSeeds * 4;
+  s.off_list = o;
+  o += kGridMaxSeeds * 4;
+  s.off_hist = o;
+  o += kGridHist * 4;
+  s.off_pts = o;
+  o += pts * DP * 4;
+  s.total = o;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Reduce-scatter of 32 values across the warp: lane l returns sum over lanes
+// of v[l] (fixed xor tree, the same for every slot).
+__device__ __forceinline__ float grid_rs32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0];
+}
+
+// Leaf partials of RR seeds (active positions a0 .. a0 + cnt - 1) over the
+// points [j0, j1) of this CTA's slice (pts: shared or global memory, DP floats
+// per point): exact-difference form, acc[r][0] = sum w, acc[r][1 + k] =
+// sum w (x - y)_k.  The RR x DA sums are reduce-scattered over the warp in
+// blocks of 32 (lane l of block q holds accumulator 32 q + l), converted to
+// fixed point and added into the update's global accumulator gacc.
+template <int D, int DP, int DA, int RR, int KF, bool RES>
+__device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0, int j1, int lane,
+                                          const int* __restrict__ alist, int a0, int cnt,
+                                          const float* __restrict__ sy,
+                                          unsigned long long* gacc, float fx) {
+  constexpr int NV = (RR * DA + 31) / 32;
+  float ys[RR][D];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    const int i = alist[a0 + (r < cnt ? r : cnt - 1)];
+#pragma unroll
+    for (int k = 0; k < D; ++k) ys[r][k] = sy[i * D + k];
+  }
+  float acc[RR][DA];
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+#pragma unroll
+    for (int k = 0; k < DA; ++k) acc[r][k] = 0.0f;
+#pragma unroll 4
+  for (int j = j0 + lane; j < j1; j += 32) {
+    float x[D];
+    const float4 p0 = RES ? *reinterpret_cast<const float4*>(pts + (size_t)j * DP)
+                          : __ldg(reinterpret_cast<const float4*>(pts + (size_t)j * DP));
+    float t8[8];
+    t8[0] = p0.x;
+    t8[1] = p0.y;
+    t8[2] = p0.z;
+    t8[3] = p0.w;
+    if constexpr (DP == 8) {
+      const float4 p1 = RES ? *reinterpret_cast<const float4*>(pts + (size_t)j * DP + 4)
+                            : __ldg(reinterpret_cast<const float4*>(pts + (size_t)j * DP + 4));
+      t8[4] = p1.x;
+      t8[5] = p1.y;
+      t8[6] = p1.z;
+      t8[7] = p1.w;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = t8[k];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      float dx[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) dx[k] = x[k] - ys[r][k];
+      float t = -dx[0] * dx[0];
+#pragma unroll
+      for (int k = 1; k < D; ++k) t = fmaf(-dx[k], dx[k], t);
+      const float w = kweight<KF>(t);
+      acc[r][0] += w;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    float v[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int f = 32 * q + e;
+      v[e] = f < RR * DA ? acc[f / DA][f % DA] : 0.0f;
+    }
+    const float s = grid_rs32(v, lane);
+    const int f = 32 * q + lane;
+    if (f < cnt * DA) {
+      const long long qv = __float2ll_rn(s * fx);
+      red_add_u64(gacc + (size_t)a0 * DA + f, (unsigned long long)qv);
+    }
+  }
+}
+
+template <int D, int DP, int DA, int KF, bool RES, int RR>
+__device__ __forceinline__ void grid_task_r(int R, const float* pts, int j0, int j1, int lane,
+                                            const int* alist, int a0, int cnt, const float* sy,
+                                            unsigned long long* gacc, float fx) {
+  if constexpr (RR >= 1) {
+    if (R == RR) {
+      grid_task<D, DP, DA, RR, KF, RES>(pts, j0, j1, lane, alist, a0, cnt, sy, gacc, fx);
+      return;
+    }
+    grid_task_r<D, DP, DA, KF, RES, RR - 1>(R, pts, j0, j1, lane, alist, a0, cnt, sy, gacc, fx);
+  }
+}
+
+// Largest seed group a warp task takes (two reduce-scatters at most).
+template <int D, int DA>
+constexpr int grid_rmax() {
+  return DA == 2 ? 24 : (DA == 4 ? 12 : 6);
+}
+
+}  // namespace
+
+template <int D, int DP, int DA, int KF, bool RES>
+__global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const GridRoundArgs a) {
+  constexpr int RMAX = grid_rmax<D, DA>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GridSmem L = grid_smem(D, DA, DP, RES ? a.per_cta : 0);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  // misc: [0] A, [1] abort, [2] t_stop, [3] S, [4] converged seeds, [16..31] scan scratch
+  int* misc = reinterpret_cast<int*>(smem + L.off_misc);
+  float* sy = reinterpret_cast<float*>(smem + L.off_y);
+  int* sit = reinterpret_cast<int*>(smem + L.off_it);
+  int* sslot = reinterpret_cast<int*>(smem + L.off_slot);
+  int* sact = reinterpret_cast<int*>(smem + L.off_act);
+  int* alist = reinterpret_cast<int*>(smem + L.off_list);
+  int* hist_s = reinterpret_cast<int*>(smem + L.off_hist);
+  float* spts = reinterpret_cast<float*>(smem + L.off_pts);
+
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int N = a.rc ? a.rc->N : a.N_arg;
+  const int target = a.rc ? a.rc->target : a.target_arg;
+  const int cb = min(a.n, cta * a.per_cta), ce = min(a.n, cb + a.per_cta);
+  const int nc = ce - cb;
+  const float fx = a.fx_scale, inv_fx = a.inv_fx_scale;
+
+  // --- stage this CTA's point slice (TMA bulk copies into shared memory) ---
+  if (RES && tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t bytes = (uint32_t)nc * DP * 4;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes)
+                 : "memory");
+    const char* src = reinterpret_cast<const char*>(a.Xs + (size_t)cb * DP);
+    for (uint32_t off = 0; off < bytes; off += 32768u) {
+      const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(spts) + off),
+          "l"(src + off), "r"(len), "r"(smem_u32(mbar))
+          : "memory");
+    }
+  }
+  if (tid == 0) {
+    misc[1] = 0;
+    misc[4] = 0;
+  }
+  // --- the round's seeds: RUNNING slots of [0, N) in slot order (the same
+  // list in every CTA) ---
+  {
+    int base = 0;
+    for (int b = 0; b < N; b += kGridThreads) {
+      const int i = b + tid;
+      const int take = (i < N) && a.state[i] == kRunning;
+      int tot;
+      const int off = block_exclusive_scan(take, &tot, misc + 16);
+      if (take && base + off < kGridMaxSeeds) {
+        const int p = base + off;
+        sslot[p] = i;
+        sit[p] = a.it[i];
+        sact[p] = 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sy[p * D + k] = a.y[(size_t)i * DP + k];
+      }
+      base += tot;
+    }
+    if (tid == 0) misc[3] = base;
+  }
+  {
+    int conv_total = 0;
+    for (int c = tid; c < kGridHist; c += kGridThreads) {
+      const int v = (c >= 1 && c <= a.max_iter) ? __ldcg(a.hist + c) : 0;
+      hist_s[c] = v;
+      conv_total += v;
+    }
+    if (conv_total) atomicAdd(misc + 4, conv_total);
+  }
+  __syncthreads();
+  const int S = misc[3];
+  if (S > kGridMaxSeeds) {
+    // the host keeps N within the capacity; a larger list is an error (all
+    // CTAs see the same S and return before the first barrier), once the
+    // slice copy has landed
+    if (cta == 0 && tid == 0) atomicOr(a.status, kStCapacity);
+    if (RES) {
+      for (long long it = 0; it < (1LL << 30); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(smem_u32(mbar)), "r"(0u)
+            : "memory");
+        if (ok) break;
+      }
+    }
+    return;
+  }
+
+  // Early Stopping and the next active list (warp 0): t_stop = the first
+  // update count whose cumulative convergence count reaches the target
+  // (none while fewer seeds than the target have converged); seeds that have
+  // made t_stop or more updates leave the active set
+  auto next_list = [&]() {
+    if (warp != 0) return;
+    int ts = INT32_MAX;
+    if (misc[4] >= target) {
+      int carry = 0;
+      for (int b0 = 1; b0 <= a.max_iter && ts == INT32_MAX; b0 += 32) {
+        const int t = b0 + lane;
+        int v = t <= a.max_iter ? hist_s[t] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(kFull, v, o);
+          if (lane >= o) v += u;
+        }
+        const unsigned hit = __ballot_sync(kFull, t <= a.max_iter && carry + v >= target);
+        if (hit) ts = b0 + __ffs(hit) - 1;
+        carry += __shfl_sync(kFull, v, 31);
+      }
+    }
+    int base = 0;
+    for (int b0 = 0; b0 < S; b0 += 32) {
+      const int p = b0 + lane;
+      int take = 0;
+      if (p < S && sact[p]) {
+        if (sit[p] >= ts) sact[p] = 0;
+        else take = 1;
+      }
+      const unsigned m = __ballot_sync(kFull, take);
+      if (take) alist[base + __popc(m & ((1u << lane) - 1))] = p;
+      base += __popc(m);
+    }
+    if (lane == 0) misc[0] = base;
+  };
+
+  const float* pts = RES ? spts : a.Xs + (size_t)cb * DP;
+  if (RES) {
+    bool ok = false;
+    const long long t0 = clock64();
+    for (;;) {
+      uint32_t r;
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(r)
+          : "r"(smem_u32(mbar)), "r"(0u)
+          : "memory");
+      if (r) {
+        ok = true;
+        break;
+      }
+      if (clock64() - t0 > kGridSpinCycles) break;
+    }
+    // a copy that did not land is flagged; the first barrier sees the flag
+    // and every CTA leaves the round
+    if (!ok) atomicOr(a.status, kStTimeout);
+  }
+  next_list();
+  __syncthreads();
+
+  const int n_sub = a.n_sub, sub_len = a.sub_len;
+  const size_t stride = (size_t)kGridMaxSeeds * DA;
+  for (int k = 0; k <= a.max_iter + 1; ++k) {
+    const int A = misc[0];
+    if (A == 0) break;
+    unsigned long long* gcur = a.gacc + (size_t)(k % 3) * stride;
+    // CTA 0 clears the next update's accumulator (last read two barriers ago)
+    if (cta == 0) {
+      unsigned long long* gnext = a.gacc + (size_t)((k + 1) % 3) * stride;
+      for (int e = tid; e < A * DA; e += kGridThreads) gnext[e] = 0ull;
+    }
+    // this CTA's leaves of every active seed: tasks (seed group, sub-slice),
+    // groups of R <= RMAX seeds, a multiple of the warp count when possible
+    int m = (A + kGridWarps * RMAX - 1) / (kGridWarps * RMAX);
+    int R = (A + kGridWarps * m - 1) / (kGridWarps * m);
+    if (R < 1) R = 1;
+    const int groups = (A + R - 1) / R;
+    const int tasks = groups * n_sub;
+    for (int t = warp; t < tasks; t += kGridWarps) {
+      const int g = t / n_sub, sb = t - g * n_sub;
+      const int j0 = min(nc, sb * sub_len), j1 = min(nc, j0 + sub_len);
+      const int a0 = g * R;
+      const int cnt = min(R, A - a0);
+      grid_task_r<D, DP, DA, KF, RES, RMAX>(R, pts, j0, j1, lane, alist, a0, cnt, sy, gcur, fx);
+    }
+    __syncthreads();
+    // grid barrier: every CTA's leaves of this update are in gcur
+    if (tid == 0) {
+      __threadfence();
+      red_release_add(a.gbar, 1u);
+      const unsigned want = (unsigned)G * (unsigned)(k + 1);
+      const long long t0 = clock64();
+      for (int it = 0;; ++it) {
+        if (ld_acquire(a.gbar) >= want) break;
+        if ((it & 31) == 31) {
+          if (*(volatile uint32_t*)a.status & kStTimeout) {
+            misc[1] = 1;
+            break;
+          }
+          if (clock64() - t0 > kGridSpinCycles) {
+            atomicOr(a.status, kStTimeout);
+            misc[1] = 1;
+            break;
+          }
+        }
+      }
+      if (*(volatile uint32_t*)a.status & kStTimeout) misc[1] = 1;
+    }
+    __syncthreads();
+    if (misc[1]) break;
+
+    // update of every active seed from the exact totals (identical in every
+    // CTA): m(y) = y + S / W with S = sum w (x - y)
+    for (int ap = tid; ap < A; ap += kGridThreads) {
+      const int p = alist[ap];
+      float tot[DA];
+#pragma unroll
+      for (int j = 0; j < DA; ++j)
+        tot[j] = __ll2float_rn((long long)__ldcg(gcur + (size_t)ap * DA + j)) * inv_fx;
+      const float W = tot[0];
+      bool ok = W > 0.0f && isfinite(W);
+      float dl[D], step2 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        dl[q] = ok ? tot[1 + q] / W : 0.0f;
+        step2 = fmaf(dl[q], dl[q], step2);
+      }
+      ok = ok && isfinite(step2);
+      if (ok && a.sphere_r > 0.0f) {
+        // cosine metric: the mean scaled back onto the sphere of radius
+        // sphere_r; the step is the projected one
+        float pp[D], nn = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          pp[q] = sy[p * D + q] + dl[q];
+          nn = fmaf(pp[q], pp[q], nn);
+        }
+        const float f = a.sphere_r / sqrtf(nn);
+        step2 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          pp[q] *= f;
+          const float e = pp[q] - sy[p * D + q];
+          step2 = fmaf(e, e, step2);
+        }
+        ok = nn > 0.0f && isfinite(step2);
+        if (ok) {
+#pragma unroll
+          for (int q = 0; q < D; ++q) sy[p * D + q] = pp[q];
+        }
+      } else if (ok) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) sy[p * D + q] += dl[q];
+      }
+      const int t = sit[p] + 1;
+      sit[p] = t;
+      int st = kRunning;
+      if (!ok) st = kFailed;
+      else if (step2 <= a.tol2_s) st = kConverged;
+      else if (t >= a.max_iter) st = kExhausted;
+      if (st != kRunning) sact[p] = 0;
+      if (st == kConverged) {
+        if (t < kGridHist) atomicAdd(hist_s + t, 1);
+        atomicAdd(misc + 4, 1);
+      }
+      if (cta == 0) {
+        const int slot = sslot[p];
+#pragma unroll
+        for (int q = 0; q < D; ++q) a.y[(size_t)slot * DP + q] = sy[p * D + q];
+        // sum w of this update, at the position before its step: the prune's
+        // density of a seed whose last update this is
+        a.wlast[slot] = W;
+        a.it[slot] = t;
+        if (st == kConverged) {
+          a.conv[slot] = t;
+          atomicAdd(a.hist + t, 1);
+        }
+        a.state[slot] = st;
+      }
+    }
+    if (cta == 0 && tid == 0) atomicAdd(a.evals, (unsigned long long)A * (unsigned long long)a.n);
+    __syncthreads();
+    next_list();
+    __syncthreads();
+  }
+}
+
+namespace {
+
+template <int D, int DP, int DA, int KF, bool RES>
+cudaError_t launch_grid_t(const GridRoundArgs& a, int G, int smem_bytes, cudaStream_t st) {
+  auto kern = ms_grid_round_kernel<D, DP, DA, KF, RES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kGridThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int D, int DP, int DA, int KF, bool RES>
+int occupancy_t(int smem_bytes) {
+  auto kern = ms_grid_round_kernel<D, DP, DA, KF, RES>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kGridThreads, smem_bytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
+}
+
+int accumulators_of(int d) { return d == 1 ? 2 : (d <= 3 ? 4 : 8); }
+
+}  // namespace
+
+GridPlan grid_round_plan(int64_t n, int d, int sms, int max_iter) {
+  GridPlan p{};
+  if (d < 1 || d > 7 || sms < 1 || n < 1 || n > INT32_MAX || max_iter >= kGridHist) return p;
+  const int DP = d <= 4 ? 4 : 8, DA = accumulators_of(d);
+  p.G = sms;
+  p.per_cta = (int)((n + sms - 1) / sms);
+  p.n_sub = (p.per_cta + kGridSubLen - 1) / kGridSubLen;
+  if (p.n_sub < 1) p.n_sub = 1;
+  p.sub_len = ((p.per_cta + p.n_sub - 1) / p.n_sub + 31) / 32 * 32;
+  int dev_max = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return GridPlan{};
+  const int with_pts = grid_smem(d, DA, DP, p.per_cta).total;
+  const int without = grid_smem(d, DA, DP, 0).total;
+  if (with_pts <= dev_max) {
+    p.resident = 1;
+    p.smem = with_pts;
+  } else if (without <= dev_max) {
+    p.resident = 0;
+    p.smem = without;
+  } else {
+    return GridPlan{};
+  }
+  int bits = 0;
+  while ((1LL << bits) <= n) ++bits;
+  p.fx_bits = 62 - bits;
+  // one CTA of this size must fit on every SM (the cooperative launch needs
+  // the whole grid resident)
+  int occ = 0;
+#define FMS_GRID_OCC(D_, DP_, DA_)                                                        \
+  occ = p.resident ? occupancy_t<D_, DP_, DA_, kKernelGaussian, true>(p.smem)            \
+                   : occupancy_t<D_, DP_, DA_, kKernelGaussian, false>(p.smem)
+  switch (d) {
+    case 1: FMS_GRID_OCC(1, 4, 2); break;
+    case 2: FMS_GRID_OCC(2, 4, 4); break;
+    case 3: FMS_GRID_OCC(3, 4, 4); break;
+    case 4: FMS_GRID_OCC(4, 4, 8); break;
+    case 5: FMS_GRID_OCC(5, 8, 8); break;
+    case 6: FMS_GRID_OCC(6, 8, 8); break;
+    case 7: FMS_GRID_OCC(7, 8, 8); break;
+  }
+#undef FMS_GRID_OCC
+  if (occ < 1) return GridPlan{};
+  p.ok = 1;
+  return p;
+}
+
+size_t grid_scratch_bytes(int d) {
+  // barrier counter (256 bytes) + three accumulators [kGridMaxSeeds][DA] u64
+  return 256 + (size_t)3 * kGridMaxSeeds * accumulators_of(d) * 8;
+}
+
+size_t grid_scratch_clear_bytes(int d) {
+  // the counter and the first update's accumulator must be zero at launch
+  return 256 + (size_t)kGridMaxSeeds * accumulators_of(d) * 8;
+}
+
+cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs a,
+                                 void* scratch, cudaStream_t st) {
+  if (!p.ok) return cudaErrorInvalidValue;
+  a.per_cta = p.per_cta;
+  a.n_sub = p.n_sub;
+  a.sub_len = p.sub_len;
+  a.gbar = reinterpret_cast<unsigned*>(scratch);
+  a.gacc = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 256);
+  a.fx_scale = ldexpf(1.0f, p.fx_bits);
+  a.inv_fx_scale = ldexpf(1.0f, -p.fx_bits);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, grid_scratch_clear_bytes(d), st);
+  if (e != cudaSuccess) return e;
+#define FMS_GRID(D_, DP_, DA_)                                                              \
+  if (kf == kKernelFlat)                                                                    \
+    return p.resident ? launch_grid_t<D_, DP_, DA_, kKernelFlat, true>(a, p.G, p.smem, st)  \
+                      : launch_grid_t<D_, DP_, DA_, kKernelFlat, false>(a, p.G, p.smem, st); \
+  return p.resident ? launch_grid_t<D_, DP_, DA_, kKernelGaussian, true>(a, p.G, p.smem, st) \
+                    : launch_grid_t<D_, DP_, DA_, kKernelGaussian, false>(a, p.G, p.smem, st)
+  switch (d) {
+    case 1: FMS_GRID(1, 4, 2);
+    case 2: FMS_GRID(2, 4, 4);
+    case 3: FMS_GRID(3, 4, 4);
+    case 4: FMS_GRID(4, 4, 8);
+    case 5: FMS_GRID(5, 8, 8);
+    case 6: FMS_GRID(6, 8, 8);
+    case 7: FMS_GRID(7, 8, 8);
+  }
+#undef FMS_GRID
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fms

@@ -2,8 +2,8 @@
 
 A call seen for the second time with the same arguments (pointers, sizes,
 scalars, options) runs as one cached CUDA graph: a conditional WHILE node
-repeats the cluster round (list, ms_round, stop bookkeeping, density scores,
-prune, seed-count decision) while the device asks for another round, and an
+repeats the round (the persistent grid round, stop bookkeeping with the
+density scores, prune, seed-count decision) while the device asks for another round, and an
 IF node runs the refinement, second prune, ordering and labels; the host
 synchronises once.  The graph launches the same kernels with the same
 arguments as the host-driven path, so results must be bit-identical to it;
@@ -59,8 +59,9 @@ def test_graph_matches_host_path_paper_3d():
     out = _three_calls(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
     _identical(out)
     st = out[1][3]
-    # the graph: packing, seed init, round start; 5 launches per round; 4 after
-    assert st["kernel_launches"] == 3 + 5 * st["rounds"] + 4
+    # the graph: packing, seed init, round start; 4 launches per round (grid
+    # round, stop bookkeeping, prune, seed-count decision); 4 after
+    assert st["kernel_launches"] == 3 + 4 * st["rounds"] + 4
     assert out[0][3]["graph"] == 0 and out[1][3]["graph"] == 1 and out[2][3]["graph"] == 1
     ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
     cmp = compare_clustering(out[2][0].cpu().numpy(), out[2][1].cpu().numpy(), ref, w.h)

@@ -559,7 +559,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     else if (o.seed_indices) N0 = o.n_seed_indices;
     else N0 = (int32_t)(o.n_initial < n ? o.n_initial : n);
     RoundCtl* rctl_round = at<RoundCtl>(ws, Lo.off_ctl + kCtlRoundOff);
-    const int cap_seeds = gp.ok ? kGridMaxSeeds : qmax * kSeedsPerCluster;
+    const int cap_seeds = gp.ok ? gp.seeds : qmax * kSeedsPerCluster;
     const int cap_modes = qmax * kModesPerCluster;
     // one grid round over the RUNNING seeds of [0, N) (N and target from rcp
     // when non-null)
@@ -785,7 +785,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       if (target < 1) target = 1;
       if (target > N) target = N;
       // --- mean-shift iterations under Early Stopping (Sec. II-C) ---
-      const bool use_grid = gp.ok && N <= kGridMaxSeeds;
+      const bool use_grid = gp.ok && N <= gp.seeds;
       const bool use_clusters =
           use_grid || (qmax > 0 && N <= qmax * kSeedsPerCluster && max_iter <= kHistCap);
       if (use_clusters) {

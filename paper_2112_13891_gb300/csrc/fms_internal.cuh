@@ -367,8 +367,9 @@ cudaError_t launch_round_finish(const int32_t* hist, int target, int max_iter,
                                 float* score = nullptr);        // densities from wlast
 
 // k_grid.cu: persistent grid rounds (one CTA per SM, cooperative launch).
-// Most seeds one round launch holds, and the convergence histogram entries
-// every CTA keeps (max_iter must be below kGridHist).
+// Most seeds one round launch holds (fewer for d >= 4, see GridPlan::seeds),
+// and the convergence histogram entries every CTA keeps (max_iter must be
+// below kGridHist).
 constexpr int kGridMaxSeeds = 1024;
 constexpr int kGridHist = 2048;
 
@@ -382,6 +383,7 @@ struct GridPlan {
   int resident;   // 1: the slice is staged in shared memory
   int smem;       // dynamic shared memory per CTA (bytes)
   int fx_bits;    // fixed-point scale of the cross-CTA sums: 2^fx_bits
+  int seeds;      // most seeds one launch holds
 };
 
 struct GridRoundArgs {

@@ -36,38 +36,52 @@ namespace fms {
 
 namespace {
 
-constexpr int kGridWarps = 16;
-constexpr int kGridThreads = kGridWarps * 32;
+constexpr int kGridCompWarps = 16;                  // warps that evaluate seeds
+constexpr int kCommWarp = kGridCompWarps;           // the exchange / update warp
+constexpr int kGridThreads = (kGridCompWarps + 1) * 32;
+constexpr int kGridBufs = 4;                        // accumulators in rotation
+constexpr int kGridMerge = 48;   // at most this many active seeds: one list per update
 constexpr int kGridSubLen = 2048;                // longest sub-slice (points)
 constexpr long long kGridSpinCycles = 4000000000LL;   // bound of one wait (~2 s)
 
 // Shared memory carving (bytes), identical on host and device.
 struct GridSmem {
-  int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_list, off_hist, off_pts;
+  int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_w, off_conv, off_list, off_hist, off_stage, off_pts;
   int total;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
+// Seeds one round launch holds: two staged publications of DA accumulators
+// per seed must fit in shared memory beside the seed state and the slice.
+__host__ __device__ constexpr int grid_seed_cap(int DA) { return DA == 8 ? 512 : kGridMaxSeeds; }
+
 __host__ __device__ inline GridSmem grid_smem(int D, int DA, int DP, int pts) {
+  const int SC = grid_seed_cap(DA);
   GridSmem s{};
   int o = 0;
   s.off_bar = o;
   o += 16;
   s.off_misc = o;
-  o += 128;
+  o += 256;
   s.off_y = o;
-  o = al16(o + kGridMaxSeeds * D * 4);
+  o = al16(o + SC * D * 4);
   s.off_it = o;
-  o += kGridMaxSeeds * 4;
+  o += SC * 4;
   s.off_slot = o;
-  o += kGridMaxSeeds * 4;
-  s.off_act = o;
-  o += kGridMaxSeeds * 4;
-  s.off_list = o;
-  o += kGridMaxSeeds * 4;
+  o += SC * 4;
+  s.off_act = o;   // state (kRunning, kConverged, ...)
+  o += SC * 4;
+  s.off_w = o;     // sum w of the latest update
+  o += SC * 4;
+  s.off_conv = o;  // convergence update
+  o += SC * 4;
+  s.off_list = o;  // two phase lists and the pool of deferred seeds
+  o += 3 * SC * 4;
   s.off_hist = o;
   o += kGridHist * 4;
+  s.off_stage = o; // the staged totals of the last publication of each parity
+  o += 2 * SC * DA * 8;
   s.off_pts = o;
   o += pts * DP * 4;
   s.total = o;
@@ -86,6 +100,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
@@ -199,7 +221,7 @@ __device__ __forceinline__ void grid_task_r(int R, const float* pts, int j0, int
 // Largest seed group a warp task takes (two reduce-scatters at most).
 template <int D, int DA>
 constexpr int grid_rmax() {
-  return DA == 2 ? 24 : (DA == 4 ? 12 : 6);
+  return DA == 2 ? 12 : (DA == 4 ? 6 : 3);
 }
 
 }  // namespace
@@ -207,17 +229,24 @@ constexpr int grid_rmax() {
 template <int D, int DP, int DA, int KF, bool RES>
 __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const GridRoundArgs a) {
   constexpr int RMAX = grid_rmax<D, DA>();
+  constexpr int SC = grid_seed_cap(DA);
+  constexpr int kComp = kGridCompWarps * 32;   // compute threads
   extern __shared__ __align__(16) unsigned char smem[];
   const GridSmem L = grid_smem(D, DA, DP, RES ? a.per_cta : 0);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  // misc: [0] A, [1] abort, [2] t_stop, [3] S, [4] converged seeds, [16..31] scan scratch
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar);   // [0] slice, [1] totals
+  // misc: [0], [1] sizes of the even / odd phase lists, [2] done, [3] S,
+  // [4] converged seeds (all rounds), [5] abort, [6] pool size, [32..63] scan
   int* misc = reinterpret_cast<int*>(smem + L.off_misc);
   float* sy = reinterpret_cast<float*>(smem + L.off_y);
   int* sit = reinterpret_cast<int*>(smem + L.off_it);
   int* sslot = reinterpret_cast<int*>(smem + L.off_slot);
-  int* sact = reinterpret_cast<int*>(smem + L.off_act);
-  int* alist = reinterpret_cast<int*>(smem + L.off_list);
+  int* sst = reinterpret_cast<int*>(smem + L.off_act);
+  float* sw = reinterpret_cast<float*>(smem + L.off_w);
+  int* sconv = reinterpret_cast<int*>(smem + L.off_conv);
+  int* lists = reinterpret_cast<int*>(smem + L.off_list);   // [2][SC], then pool[SC]
+  int* pool = lists + 2 * SC;
   int* hist_s = reinterpret_cast<int*>(smem + L.off_hist);
+  unsigned long long* stage = reinterpret_cast<unsigned long long*>(smem + L.off_stage);
   float* spts = reinterpret_cast<float*>(smem + L.off_pts);
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
@@ -228,28 +257,31 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
   const int nc = ce - cb;
   const float fx = a.fx_scale, inv_fx = a.inv_fx_scale;
 
-  // --- stage this CTA's point slice (TMA bulk copies into shared memory) ---
-  if (RES && tid == 0) {
+  // --- barriers; stage this CTA's point slice (TMA bulk copies) ---
+  if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const uint32_t bytes = (uint32_t)nc * DP * 4;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-                 "r"(bytes)
-                 : "memory");
-    const char* src = reinterpret_cast<const char*>(a.Xs + (size_t)cb * DP);
-    for (uint32_t off = 0; off < bytes; off += 32768u) {
-      const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              smem_u32(spts) + off),
-          "l"(src + off), "r"(len), "r"(smem_u32(mbar))
-          : "memory");
+    if (RES) {
+      const uint32_t bytes = (uint32_t)nc * DP * 4;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                   "r"(bytes)
+                   : "memory");
+      const char* src = reinterpret_cast<const char*>(a.Xs + (size_t)cb * DP);
+      for (uint32_t off = 0; off < bytes; off += 32768u) {
+        const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(spts) + off),
+            "l"(src + off), "r"(len), "r"(smem_u32(mbar))
+            : "memory");
+      }
     }
-  }
-  if (tid == 0) {
-    misc[1] = 0;
+    misc[2] = 0;
     misc[4] = 0;
+    misc[5] = 0;
+    misc[6] = 0;
   }
   // --- the round's seeds: RUNNING slots of [0, N) in slot order (the same
   // list in every CTA) ---
@@ -259,12 +291,14 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
       const int i = b + tid;
       const int take = (i < N) && a.state[i] == kRunning;
       int tot;
-      const int off = block_exclusive_scan(take, &tot, misc + 16);
-      if (take && base + off < kGridMaxSeeds) {
+      const int off = block_exclusive_scan(take, &tot, misc + 32);
+      if (take && base + off < SC) {
         const int p = base + off;
         sslot[p] = i;
         sit[p] = a.it[i];
-        sact[p] = 1;
+        sst[p] = kRunning;
+        sw[p] = a.wlast[i];
+        sconv[p] = a.conv[i];
 #pragma unroll
         for (int k = 0; k < D; ++k) sy[p * D + k] = a.y[(size_t)i * DP + k];
       }
@@ -283,31 +317,36 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
   }
   __syncthreads();
   const int S = misc[3];
-  if (S > kGridMaxSeeds) {
-    // the host keeps N within the capacity; a larger list is an error (all
-    // CTAs see the same S and return before the first barrier), once the
-    // slice copy has landed
-    if (cta == 0 && tid == 0) atomicOr(a.status, kStCapacity);
-    if (RES) {
-      for (long long it = 0; it < (1LL << 30); ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(ok)
-            : "r"(smem_u32(mbar)), "r"(0u)
-            : "memory");
-        if (ok) break;
+  if (RES) {
+    // every thread waits for the slice copy (bounded); a copy that did not
+    // land is flagged, and the first grid barrier sends every CTA home
+    bool ok = false;
+    const long long t0 = clock64();
+    for (;;) {
+      uint32_t r;
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(r)
+          : "r"(smem_u32(mbar)), "r"(0u)
+          : "memory");
+      if (r) {
+        ok = true;
+        break;
       }
+      if (clock64() - t0 > kGridSpinCycles) break;
     }
+    if (!ok && tid == 0) atomicOr(a.status, kStTimeout);
+  }
+  if (S > SC) {
+    // the host keeps N within the capacity; a larger list is an error (every
+    // CTA sees the same S and returns before the first grid barrier)
+    if (cta == 0 && tid == 0) atomicOr(a.status, kStCapacity);
     return;
   }
 
-  // Early Stopping and the next active list (warp 0): t_stop = the first
-  // update count whose cumulative convergence count reaches the target
-  // (none while fewer seeds than the target have converged); seeds that have
-  // made t_stop or more updates leave the active set
-  auto next_list = [&]() {
-    if (warp != 0) return;
+  // t_stop (one warp): the first update count whose cumulative convergence
+  // count reaches the target; INT32_MAX while fewer seeds have converged
+  auto t_stop = [&]() -> int {
     int ts = INT32_MAX;
     if (misc[4] >= target) {
       int carry = 0;
@@ -324,169 +363,302 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
         carry += __shfl_sync(kFull, v, 31);
       }
     }
-    int base = 0;
+    return ts;
+  };
+  // a seed stays in the lists while RUNNING and below t_stop (a seed that
+  // has made t_stop updates without converging cannot be kept)
+  auto live = [&](int p, int ts) { return sst[p] == kRunning && sit[p] < ts; };
+
+  // first two phase lists: the live seeds alternately (one list when few)
+  if (warp == kCommWarp) {
+    const int ts = t_stop();
+    int nl = 0;
     for (int b0 = 0; b0 < S; b0 += 32) {
       const int p = b0 + lane;
-      int take = 0;
-      if (p < S && sact[p]) {
-        if (sit[p] >= ts) sact[p] = 0;
-        else take = 1;
-      }
-      const unsigned m = __ballot_sync(kFull, take);
-      if (take) alist[base + __popc(m & ((1u << lane) - 1))] = p;
-      base += __popc(m);
+      const unsigned m = __ballot_sync(kFull, p < S && live(p, ts));
+      nl += __popc(m);
     }
-    if (lane == 0) misc[0] = base;
-  };
-
-  const float* pts = RES ? spts : a.Xs + (size_t)cb * DP;
-  if (RES) {
-    bool ok = false;
-    const long long t0 = clock64();
-    for (;;) {
-      uint32_t r;
-      asm volatile(
-          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-          : "=r"(r)
-          : "r"(smem_u32(mbar)), "r"(0u)
-          : "memory");
-      if (r) {
-        ok = true;
-        break;
+    const bool split = nl > kGridMerge;
+    int n0 = 0, n1 = 0;
+    for (int b0 = 0; b0 < S; b0 += 32) {
+      const int p = b0 + lane;
+      const bool t = p < S && live(p, ts);
+      const unsigned m = __ballot_sync(kFull, t);
+      if (t) {
+        const int r = n0 + n1 + __popc(m & ((1u << lane) - 1));
+        if (split && (r & 1)) lists[SC + (r >> 1)] = p;
+        else lists[split ? (r >> 1) : r] = p;
       }
-      if (clock64() - t0 > kGridSpinCycles) break;
+      const int c = __popc(m);
+      if (split) {
+        const int tot = n0 + n1 + c;
+        n0 = (tot + 1) >> 1;
+        n1 = tot >> 1;
+      } else {
+        n0 += c;
+      }
     }
-    // a copy that did not land is flagged; the first barrier sees the flag
-    // and every CTA leaves the round
-    if (!ok) atomicOr(a.status, kStTimeout);
+    if (lane == 0) {
+      misc[0] = n0;
+      misc[1] = n1;
+    }
   }
-  next_list();
   __syncthreads();
+  if (misc[0] + misc[1] == 0) return;
 
-  const int n_sub = a.n_sub, sub_len = a.sub_len;
-  const size_t stride = (size_t)kGridMaxSeeds * DA;
-  for (int k = 0; k <= a.max_iter + 1; ++k) {
-    const int A = misc[0];
-    if (A == 0) break;
-    unsigned long long* gcur = a.gacc + (size_t)(k % 3) * stride;
-    // CTA 0 clears the next update's accumulator (last read two barriers ago)
-    if (cta == 0) {
-      unsigned long long* gnext = a.gacc + (size_t)((k + 1) % 3) * stride;
-      for (int e = tid; e < A * DA; e += kGridThreads) gnext[e] = 0ull;
-    }
-    // this CTA's leaves of every active seed: tasks (seed group, sub-slice),
-    // groups of R <= RMAX seeds, a multiple of the warp count when possible
-    int m = (A + kGridWarps * RMAX - 1) / (kGridWarps * RMAX);
-    int R = (A + kGridWarps * m - 1) / (kGridWarps * m);
-    if (R < 1) R = 1;
-    const int groups = (A + R - 1) / R;
-    const int tasks = groups * n_sub;
-    for (int t = warp; t < tasks; t += kGridWarps) {
-      const int g = t / n_sub, sb = t - g * n_sub;
-      const int j0 = min(nc, sb * sub_len), j1 = min(nc, j0 + sub_len);
-      const int a0 = g * R;
-      const int cnt = min(R, A - a0);
-      grid_task_r<D, DP, DA, KF, RES, RMAX>(R, pts, j0, j1, lane, alist, a0, cnt, sy, gcur, fx);
-    }
-    __syncthreads();
-    // grid barrier: every CTA's leaves of this update are in gcur
-    if (tid == 0) {
-      __threadfence();
-      red_release_add(a.gbar, 1u);
-      const unsigned want = (unsigned)G * (unsigned)(k + 1);
-      const long long t0 = clock64();
-      for (int it = 0;; ++it) {
-        if (ld_acquire(a.gbar) >= want) break;
-        if ((it & 31) == 31) {
-          if (*(volatile uint32_t*)a.status & kStTimeout) {
-            misc[1] = 1;
-            break;
+  const int max_phase = 4 * (a.max_iter + 4);
+  const size_t stride = (size_t)SC * DA;
+  if (warp < kGridCompWarps) {
+    // ---- compute warps.  Phase j: apply the staged totals of phase j - 2
+    // (this parity) to its seeds, build list j from them, evaluate list j ----
+    const int n_sub = a.n_sub, sub_len = a.sub_len;
+    int q = 0;   // publications so far (non-empty phases)
+    for (int j = 0; j < max_phase; ++j) {
+      const int par = j & 1;
+      int* lst = lists + par * SC;
+      if (j >= 2) {
+        bar_sync(3 + par, kGridThreads);   // totals of phase j - 2 staged
+        if (*(volatile int*)(misc + 5)) break;
+        const int Aold = misc[par];
+        const unsigned long long* stg = stage + (size_t)par * stride;
+        // update of every seed of phase j - 2 from the exact totals (the
+        // same in every CTA): m(y) = y + S / W with S = sum w (x - y)
+        for (int e = tid; e < Aold; e += kComp) {
+          const int p = lst[e];
+          float tot[DA];
+#pragma unroll
+          for (int k = 0; k < DA; ++k) tot[k] = __ll2float_rn((long long)stg[(size_t)e * DA + k]) * inv_fx;
+          const float W = tot[0];
+          bool ok = W > 0.0f && isfinite(W);
+          const float rW = ok ? __frcp_rn(W) : 0.0f;
+          float dl[D], step2 = 0.0f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            dl[k] = tot[1 + k] * rW;
+            step2 = fmaf(dl[k], dl[k], step2);
           }
-          if (clock64() - t0 > kGridSpinCycles) {
-            atomicOr(a.status, kStTimeout);
-            misc[1] = 1;
-            break;
+          ok = ok && isfinite(step2);
+          if (ok && a.sphere_r > 0.0f) {
+            // cosine metric: the mean scaled back onto the sphere of radius
+            // sphere_r; the step is the projected one
+            float pp[D], nn = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              pp[k] = sy[p * D + k] + dl[k];
+              nn = fmaf(pp[k], pp[k], nn);
+            }
+            const float f = a.sphere_r / sqrtf(nn);
+            step2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              pp[k] *= f;
+              const float d2 = pp[k] - sy[p * D + k];
+              step2 = fmaf(d2, d2, step2);
+            }
+            ok = nn > 0.0f && isfinite(step2);
+            if (ok) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) sy[p * D + k] = pp[k];
+            }
+          } else if (ok) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) sy[p * D + k] += dl[k];
+          }
+          const int t = sit[p] + 1;
+          sit[p] = t;
+          int st = kRunning;
+          if (!ok) st = kFailed;
+          else if (step2 <= a.tol2_s) st = kConverged;
+          else if (t >= a.max_iter) st = kExhausted;
+          sst[p] = st;
+          // sum w of this update, at the position before its step: the
+          // prune's density of a seed whose last update this is
+          sw[p] = W;
+          if (st == kConverged) {
+            sconv[p] = t;
+            if (t < kGridHist) atomicAdd(hist_s + t, 1);
+            atomicAdd(misc + 4, 1);
           }
         }
+        bar_sync(5, kComp);
+        if (warp == 0) {
+          // list j: the live seeds of phase j - 2 and of the pool, or none
+          // (the candidates wait in the pool) when few seeds are left and
+          // phase j - 1 has some, so that the lists merge
+          const int ts = t_stop();
+          int nl = 0;
+          for (int b0 = 0; b0 < Aold; b0 += 32) {   // in place: writes never pass reads
+            const int e = b0 + lane;
+            const int p = e < Aold ? lst[e] : 0;
+            const bool t = e < Aold && live(p, ts);
+            const unsigned m = __ballot_sync(kFull, t);
+            if (t) lst[nl + __popc(m & ((1u << lane) - 1))] = p;
+            nl += __popc(m);
+          }
+          const int ps = misc[6];
+          int np = 0;
+          for (int b0 = 0; b0 < ps; b0 += 32) {
+            const int e = b0 + lane;
+            const int p = e < ps ? pool[e] : 0;
+            const bool t = e < ps && live(p, ts);
+            const unsigned m = __ballot_sync(kFull, t);
+            if (t) pool[np + __popc(m & ((1u << lane) - 1))] = p;
+            np += __popc(m);
+          }
+          __syncwarp();
+          const int B = misc[par ^ 1];   // phase j - 1: evaluated, not yet applied
+          const bool defer = B > 0 && B + nl + np <= kGridMerge;
+          int next = 0;
+          if (defer) {
+            for (int e = lane; e < nl; e += 32) pool[np + e] = lst[e];
+            np += nl;
+          } else {
+            for (int e = lane; e < np; e += 32) lst[nl + e] = pool[e];
+            next = nl + np;
+            np = 0;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            misc[par] = next;
+            misc[6] = np;
+            if (next == 0 && B == 0 && np == 0) misc[2] = 1;   // nothing left anywhere
+          }
+        }
+        bar_sync(5, kComp);
+        if (misc[2]) {
+          bar_arrive(1 + par, kGridThreads);   // releases the comm warp, which then leaves
+          break;
+        }
       }
-      if (*(volatile uint32_t*)a.status & kStTimeout) misc[1] = 1;
+      const int A = misc[par];
+      if (A > 0) {
+        unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
+        int m = (A + kGridCompWarps * RMAX - 1) / (kGridCompWarps * RMAX);
+        int R = (A + kGridCompWarps * m - 1) / (kGridCompWarps * m);
+        if (R < 1) R = 1;
+        const int groups = (A + R - 1) / R;
+        const int tasks = groups * n_sub;
+        for (int t = warp; t < tasks; t += kGridCompWarps) {
+          const int gi = t / n_sub, sb = t - gi * n_sub;
+          const int j0 = min(nc, sb * sub_len), j1 = min(nc, j0 + sub_len);
+          const int a0 = gi * R;
+          const int cnt = min(R, A - a0);
+          grid_task_r<D, DP, DA, KF, RES, RMAX>(R, RES ? spts : a.Xs + (size_t)cb * DP, j0, j1,
+                                                lane, lst, a0, cnt, sy, g, fx);
+        }
+        ++q;
+      }
+      bar_arrive(1 + par, kGridThreads);   // pass j done
     }
-    __syncthreads();
-    if (misc[1]) break;
-
-    // update of every active seed from the exact totals (identical in every
-    // CTA): m(y) = y + S / W with S = sum w (x - y)
-    for (int ap = tid; ap < A; ap += kGridThreads) {
-      const int p = alist[ap];
-      float tot[DA];
-#pragma unroll
-      for (int j = 0; j < DA; ++j)
-        tot[j] = __ll2float_rn((long long)__ldcg(gcur + (size_t)ap * DA + j)) * inv_fx;
-      const float W = tot[0];
-      bool ok = W > 0.0f && isfinite(W);
-      float dl[D], step2 = 0.0f;
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        dl[q] = ok ? tot[1 + q] / W : 0.0f;
-        step2 = fmaf(dl[q], dl[q], step2);
-      }
-      ok = ok && isfinite(step2);
-      if (ok && a.sphere_r > 0.0f) {
-        // cosine metric: the mean scaled back onto the sphere of radius
-        // sphere_r; the step is the projected one
-        float pp[D], nn = 0.0f;
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          pp[q] = sy[p * D + q] + dl[q];
-          nn = fmaf(pp[q], pp[q], nn);
+  } else {
+    // ---- comm warp: publishes phase j, waits for every CTA's leaves and
+    // stages the totals in shared memory, while the compute warps run
+    // phase j + 1 ----
+    int q = 0, prev_used = 0;
+    unsigned long long evals = 0;
+    for (int j = 0; j < max_phase; ++j) {
+      const int par = j & 1;
+      bar_sync(1 + par, kGridThreads);   // leaves of phase j issued (or done)
+      if (*(volatile int*)(misc + 2)) break;
+      const int A = misc[par];
+      bool bad = false;
+      if (A > 0) {
+        const unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
+        int b = 0;
+        if (lane == 0) {
+          __threadfence();
+          red_release_add(a.gbar, 1u);
+          const unsigned want = (unsigned)G * (unsigned)(q + 1);
+          const long long t0 = clock64();
+          for (int it = 0;; ++it) {
+            if (ld_acquire(a.gbar) >= want) break;
+            if ((it & 31) == 31) {
+              if (*(volatile uint32_t*)a.status & kStTimeout) {
+                b = 1;
+                break;
+              }
+              if (clock64() - t0 > kGridSpinCycles) {
+                atomicOr(a.status, kStTimeout);
+                b = 1;
+                break;
+              }
+            }
+          }
+          if (*(volatile uint32_t*)a.status & kStTimeout) b = 1;
+          if (!b) {
+            // the totals into shared memory: one bulk copy (async proxy)
+            // after the acquire, one round trip for any A
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            const uint32_t bytes = (uint32_t)A * DA * 8;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                             smem_u32(mbar + 1)),
+                         "r"(bytes)
+                         : "memory");
+            const char* src = reinterpret_cast<const char*>(g);
+            const uint32_t dst = smem_u32(stage + (size_t)par * stride);
+            for (uint32_t off = 0; off < bytes; off += 32768u) {
+              const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                      dst + off),
+                  "l"(src + off), "r"(len), "r"(smem_u32(mbar + 1))
+                  : "memory");
+            }
+          }
         }
-        const float f = a.sphere_r / sqrtf(nn);
-        step2 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          pp[q] *= f;
-          const float e = pp[q] - sy[p * D + q];
-          step2 = fmaf(e, e, step2);
+        __syncwarp();
+        bad = __shfl_sync(kFull, b, 0) != 0;
+        if (!bad) {
+          // every CTA has read the previous publication's totals: CTA 0
+          // clears that accumulator for the publication four ahead
+          if (cta == 0 && q >= 1) {
+            unsigned long long* gp = a.gacc + (size_t)((q - 1) % kGridBufs) * stride;
+            for (int e = lane; e < prev_used * DA; e += 32) gp[e] = 0ull;
+          }
+          bool landed = false;
+          const long long t0 = clock64();
+          for (;;) {
+            uint32_t r;
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                : "=r"(r)
+                : "r"(smem_u32(mbar + 1)), "r"((uint32_t)(q & 1))
+                : "memory");
+            if (r) {
+              landed = true;
+              break;
+            }
+            if (clock64() - t0 > kGridSpinCycles) break;
+          }
+          if (!__all_sync(kFull, landed)) {
+            if (lane == 0) atomicOr(a.status, kStTimeout);
+            bad = true;
+          }
         }
-        ok = nn > 0.0f && isfinite(step2);
-        if (ok) {
-#pragma unroll
-          for (int q = 0; q < D; ++q) sy[p * D + q] = pp[q];
-        }
-      } else if (ok) {
-#pragma unroll
-        for (int q = 0; q < D; ++q) sy[p * D + q] += dl[q];
+        evals += (unsigned long long)A * (unsigned long long)a.n;
+        prev_used = A;
+        ++q;
       }
-      const int t = sit[p] + 1;
-      sit[p] = t;
-      int st = kRunning;
-      if (!ok) st = kFailed;
-      else if (step2 <= a.tol2_s) st = kConverged;
-      else if (t >= a.max_iter) st = kExhausted;
-      if (st != kRunning) sact[p] = 0;
-      if (st == kConverged) {
-        if (t < kGridHist) atomicAdd(hist_s + t, 1);
-        atomicAdd(misc + 4, 1);
-      }
-      if (cta == 0) {
-        const int slot = sslot[p];
-#pragma unroll
-        for (int q = 0; q < D; ++q) a.y[(size_t)slot * DP + q] = sy[p * D + q];
-        // sum w of this update, at the position before its step: the prune's
-        // density of a seed whose last update this is
-        a.wlast[slot] = W;
-        a.it[slot] = t;
-        if (st == kConverged) {
-          a.conv[slot] = t;
-          atomicAdd(a.hist + t, 1);
-        }
-        a.state[slot] = st;
-      }
+      if (bad && lane == 0) misc[5] = 1;
+      __syncwarp();
+      bar_arrive(3 + par, kGridThreads);   // totals of phase j staged
+      if (bad) break;
     }
-    if (cta == 0 && tid == 0) atomicAdd(a.evals, (unsigned long long)A * (unsigned long long)a.n);
-    __syncthreads();
-    next_list();
-    __syncthreads();
+    if (cta == 0 && lane == 0 && evals) atomicAdd(a.evals, evals);
+  }
+  // the round's seed state and the convergence counts back to global memory
+  __syncthreads();
+  if (cta == 0) {
+    for (int p = tid; p < S; p += kGridThreads) {
+      const int slot = sslot[p];
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.y[(size_t)slot * DP + k] = sy[p * D + k];
+      a.it[slot] = sit[p];
+      a.state[slot] = sst[p];
+      a.wlast[slot] = sw[p];
+      a.conv[slot] = sconv[p];
+    }
+    for (int t = 1 + tid; t <= a.max_iter; t += kGridThreads) a.hist[t] = hist_s[t];
   }
 }
 
@@ -575,18 +747,20 @@ GridPlan grid_round_plan(int64_t n, int d, int sms, int max_iter) {
   }
 #undef FMS_GRID_OCC
   if (occ < 1) return GridPlan{};
+  p.seeds = grid_seed_cap(DA);
   p.ok = 1;
   return p;
 }
 
 size_t grid_scratch_bytes(int d) {
-  // barrier counter (256 bytes) + three accumulators [kGridMaxSeeds][DA] u64
-  return 256 + (size_t)3 * kGridMaxSeeds * accumulators_of(d) * 8;
+  // barrier counter (256 bytes) + kGridBufs accumulators [seed capacity][DA] u64
+  const int DA = accumulators_of(d);
+  return 256 + (size_t)kGridBufs * grid_seed_cap(DA) * DA * 8;
 }
 
 size_t grid_scratch_clear_bytes(int d) {
-  // the counter and the first update's accumulator must be zero at launch
-  return 256 + (size_t)kGridMaxSeeds * accumulators_of(d) * 8;
+  // everything starts at zero (each accumulator is cleared again after use)
+  return grid_scratch_bytes(d);
 }
 
 cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs a,

@@ -8,9 +8,18 @@ case).  Inputs are resident in HBM when the timed region starts; L2 is flushed
 (256 MB write) between timed steps, outside the per-step CUDA events.
 
 Extra measurements on the same line:
-  roofline      ms_step (the dominant kernel): seed-point evaluations per
-                second from CUDA events around each launch, against the FP32
-                pipe bound of the minimal formulation (2d+2 FP32 ops per eval).
+  roofline      the dominant kernel (the grid round): seed-point evaluations
+                per second from CUDA events around each launch, against the
+                FP32 pipe bound of the exact-difference evaluation the kernel
+                runs (3d+1 FP32 ops per eval; frac_2d2: the same against the
+                minimal 2d+2 count); frac_measured divides by the FFMA rate the
+                library measures on this GPU in this run (fms_probe_pipe_rates).
+  accuracy      the timed clustering against the FP64 oracle's: largest mode
+                error / h, labels that differ away from near-ties, points
+                whose oracle margin is below 1e-2 h, mode counts and order.
+  all_seeds     the plain all-seeds GPU path (Alg. 1) on the same points: its
+                time, the speedup of the faster path over it, and how its modes
+                and labels compare with the faster path's on the blobs.
   e2e           the same clustering through the C ABI with host buffers: the
                 pinned host -> device copy of the points and the device -> host
                 copy of labels and modes are inside the timed region.
@@ -152,8 +161,8 @@ def measured_peaks():
 # Source files whose contents fix each profiled kernel's code: a stored DRAM
 # traffic figure counts only while their digest matches the one it was taken at.
 KERNEL_SOURCES = {
-    "ms_round": ["paper_2112_13891_gb300/csrc/k_round.cu",
-                 "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
+    "ms_grid_round": ["paper_2112_13891_gb300/csrc/k_grid.cu",
+                      "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
     "ms_step": ["paper_2112_13891_gb300/csrc/k_step.cu",
                 "paper_2112_13891_gb300/csrc/fms_step_body.cuh",
                 "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
@@ -187,17 +196,50 @@ def stored_traffic(kname):
 
 
 def run_oracle_sample(w, seconds=12.0):
-    """Time the FP64 oracle's full clustering of the workload on the host cores."""
+    """Time the FP64 oracle's full clustering of the workload on the host cores;
+    also returns the oracle's result (for the accuracy record)."""
     import oracle as orc
     t0 = time.perf_counter()
     runs = 0
     while True:
-        orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
+        ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=0)
         runs += 1
         el = time.perf_counter() - t0
         if el >= seconds or runs >= 20:
             break
-    return el / runs * 1e3, runs
+    return el / runs * 1e3, runs, ref
+
+
+def accuracy_vs_oracle(modes, labels, ref, h, mode_tol=1e-3, margin_tol=1e-2, score_rtol=1e-4):
+    """GPU clustering against the FP64 oracle: modes matched one-to-one
+    (Hungarian assignment on distances), labels compared after that mapping
+    away from near-ties (oracle margin >= margin_tol h), the canonical order
+    checked up to near-equal oracle scores."""
+    from scipy.optimize import linear_sum_assignment
+    g = np.asarray(modes, dtype=np.float64)
+    r = np.asarray(ref.modes, dtype=np.float64)
+    out = {"n_modes": int(g.shape[0]), "n_modes_oracle": int(r.shape[0])}
+    if g.shape != r.shape:
+        out["mode_count_equal"] = False
+        return out
+    D = np.sqrt(((g[:, None, :] - r[None, :, :]) ** 2).sum(-1))
+    gi, ri = linear_sum_assignment(D)
+    perm = np.empty(g.shape[0], dtype=np.int64)
+    perm[gi] = ri
+    err = float(D[gi, ri].max()) if len(gi) else 0.0
+    lab = np.asarray(labels).astype(np.int64)
+    mapped = np.where(lab >= 0, perm[np.clip(lab, 0, None)], -1)
+    keep = ref.margins >= margin_tol * h
+    s = np.asarray(ref.scores, dtype=np.float64)[perm]
+    i, j = np.triu_indices(perm.shape[0], k=1)
+    viol = int(((perm[i] > perm[j]) &
+                (np.abs(s[i] - s[j]) > score_rtol * np.maximum(np.abs(s[i]), np.abs(s[j])))).sum())
+    out.update({"mode_count_equal": True, "max_mode_err_over_h": err / h,
+                "modes_within_1e-3h": bool(err <= mode_tol * h),
+                "label_mismatch": int((mapped[keep] != ref.labels[keep]).sum()),
+                "low_margin_points": int((~keep).sum()), "order_violations": viol,
+                "n_seeds_oracle": int(ref.n_seeds)})
+    return out
 
 
 def oracle_one_core_ms(seconds):
@@ -311,16 +353,26 @@ def bench_fms(args):
         prof["phase"] = [a + b for a, b in zip(prof["phase"], rp["phase_ms"])]
     barrier()
     if prof["round_ms"] >= prof["step_ms"] and prof["round_n"] > 0:
-        kname, kms, kev, kn = "ms_round", prof["round_ms"], prof["round_ev"], prof["round_n"]
+        kname, kms, kev, kn = "ms_grid_round", prof["round_ms"], prof["round_ev"], prof["round_n"]
     else:
         kname, kms, kev, kn = "ms_step", prof["step_ms"], prof["step_ev"], prof["step_n"]
     avg_launch_ms = kms / max(kn, 1)
     evals_per_launch = kev / max(kn, 1)
     achieved = evals_per_launch / (avg_launch_ms * 1e-3) / 1e9          # Geval/s
-    ops_per_eval = 2 * d + 2
+    ops_per_eval = 3 * d + 1          # the exact-difference evaluation the kernels run
+    ops_minimal = 2 * d + 2           # the minimal (expanded) formulation
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ops_per_eval / 1e9
+    peak_min = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ops_minimal / 1e9
+    try:
+        rates = fms.probe_pipe_rates()
+    except Exception:
+        rates = None
+    peak_meas = None
+    if rates and rates["ffma_ops_per_clk_sm"] > 0:
+        # the same bound from the FFMA rate measured here, at the maximum clock
+        peak_meas = SM_COUNT * rates["ffma_ops_per_clk_sm"] * sm_max * 1e6 / ops_per_eval / 1e9
     traffic = stored_traffic(kname)
     phases = {k: v / args.steps for k, v in zip(("rounds", "prunes", "refine", "labels"),
                                                prof["phase"])}
@@ -352,9 +404,47 @@ def bench_fms(args):
     d2h_bytes = n * 4 + cap_h * d * 4 + 1024
     e2e = reduce_max(float(np.mean(e2e_ms)), pg, dev) / world
 
+    # --- the plain all-seeds path (Alg. 1) on the same points: time and agreement ---
+    all_seeds = None
+    if rank == 0 and world == 1 and not args.no_all_seeds:
+        fast_modes = r.modes.cpu().numpy().astype(np.float64)
+        fast_labels = labels.cpu().numpy().astype(np.int64)
+        fast_margins = margins.cpu().numpy()
+        ws_a = fms.Workspace(fms.workspace_size(n, d), dev)
+        run_a = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, all_seeds=True, workspace=ws_a)
+        ra = run_a()
+        t_a, _ = _events_ms(run_a, 2, flush=flush)
+        A = ra.modes.cpu().numpy().astype(np.float64)
+        la = ra.labels.cpu().numpy().astype(np.int64)
+        # every faster-path mode against its nearest all-seeds mode
+        DA = np.sqrt(((fast_modes[:, None, :] - A[None, :, :]) ** 2).sum(-1))
+        near = DA.argmin(axis=1)
+        near_d = DA[np.arange(DA.shape[0]), near]
+        # labels: points the all-seeds path gives to a mode that matches a
+        # faster-path mode, compared away from the faster path's near-ties
+        a2f = np.full(A.shape[0], -1, dtype=np.int64)
+        ok_m = near_d <= 1e-3 * w.h
+        a2f[near[ok_m]] = np.nonzero(ok_m)[0]
+        mapped = a2f[la]
+        on_blobs = mapped >= 0
+        firm = fast_margins >= 1e-2 * w.h
+        cmp = on_blobs & firm
+        all_seeds = {"ms": t_a, "speedup_of_faster_path": t_a / value,
+                     "n_modes": int(A.shape[0]), "n_modes_faster_path": int(fast_modes.shape[0]),
+                     "max_dist_faster_mode_to_all_seeds_mode_over_h": float(near_d.max() / w.h),
+                     "faster_modes_matched_within_1e-3h": int(ok_m.sum()),
+                     "points_on_matched_modes": int(on_blobs.sum()),
+                     "label_agreement_on_matched_modes": float((mapped[cmp] == fast_labels[cmp]).mean())
+                     if cmp.any() else None,
+                     "label_mismatch_on_matched_modes": int((mapped[cmp] != fast_labels[cmp]).sum()),
+                     "evals": int(ra.stats["evals"])}
+        del ws_a
+
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_cpu, runs = run_oracle_sample(w, seconds=args.cpu_seconds)
+        ms_cpu, runs, ref = run_oracle_sample(w, seconds=args.cpu_seconds)
+        accuracy = accuracy_vs_oracle(r.modes.cpu().numpy(), labels.cpu().numpy(), ref, w.h)
         cpu = {"value": ms_cpu, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"full FP64 oracle clustering of the same 200K-point workload, "
                          f"{runs} run(s), OpenMP over seeds"}
@@ -371,7 +461,13 @@ def bench_fms(args):
                              "peak": peak, "unit": "Geval/s", "frac": achieved / peak,
                              "traffic": traffic,
                              "peak_basis": f"FP32 pipe {FP32_LANES_PER_SM} lanes/clk/SM x {SM_COUNT} SMs x "
-                                           f"{sm_max:.0f} MHz / {ops_per_eval} FP32 ops per eval (2d+2)",
+                                           f"{sm_max:.0f} MHz / {ops_per_eval} FP32 ops per eval (3d+1, "
+                                           f"the exact-difference form the kernel runs)",
+                             "frac_2d2": achieved / peak_min,
+                             "peak_2d2": peak_min,
+                             "frac_measured": achieved / peak_meas if peak_meas else None,
+                             "peak_measured": peak_meas,
+                             "pipe_rates_per_clk_sm": rates,
                              "avg_launch_us": avg_launch_ms * 1e3,
                              "evals_per_launch": evals_per_launch, "launches": kn,
                              "share_of_step": kms / max(sum(prof["phase"]), 1e-9)},
@@ -379,7 +475,8 @@ def bench_fms(args):
                 "evals_per_s": r.stats["evals"] / (ms_per_step * 1e-3),
                 "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": n * d * 4,
                         "d2h_bytes_per_step": d2h_bytes},
-                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "cpu_baseline": cpu, "accuracy": accuracy, "all_seeds": all_seeds,
+                "clocks": clk, "gpu_launches": launches,
                 "wall_s_timed": wall,
                 "stats": {k: r.stats[k] for k in ("iterations", "rounds", "n_seeds_final",
                                                    "n_modes", "refine_iterations", "evals",
@@ -647,6 +744,8 @@ def main():
     ap.add_argument("--impl", default="fms", choices=["fms", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-all-seeds", action="store_true",
+                    help="skip the all-seeds (Alg. 1) record of the headline line")
     ap.add_argument("--workload", default="paper_3d",
                     choices=["paper_3d", "all_seeds_3d", "batched_16d", "unrolled_16d",
                              "embedding_32d", "step_wide", "pixels_rgb", "flat_3d", "frames_3d",
@@ -660,7 +759,7 @@ def main():
                     help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample_only > 0:
-        ms, runs = run_oracle_sample(make_input(0), seconds=args.oracle_sample_only)
+        ms, runs, _ = run_oracle_sample(make_input(0), seconds=args.oracle_sample_only)
         print(json.dumps({"ms": ms, "runs": runs}))
         return
     if args.kernel_probe:

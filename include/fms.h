@@ -392,6 +392,18 @@ fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n, int32_t d
                                        float* out_wsum, void* stream);
 
 /*
+ * Measured pipe rates of the current device, per clock and per SM (median
+ * over SMs, SM cycle counter around a fixed instruction mix on every SM).
+ * The paper has no counterpart: these are the throughputs that the roofline
+ * of the evaluation kernels divides by, measured rather than taken from data
+ * sheets.  rates[0] FFMA FP32 ops, [1] packed FFMA2 (f32x2) FP32 ops,
+ * [2] MUFU ex2, [3] units of 10 FFMA + 1 ex2 (the exact-difference evaluation
+ * mix at d = 3); the first min(n_rates, 4) are written.  Synchronous; takes
+ * a few milliseconds and allocates (a diagnostic, not for hot paths).
+ */
+fms_status fms_probe_pipe_rates(double* rates, int32_t n_rates);
+
+/*
  * Nearest-mode labelling (Alg. 2 lines 11-13): labels[j] = argmin_k
  * ||x_j - modes_k|| (ties -> lowest k) and, if margins is non-NULL,
  * margins[j] = second-nearest minus nearest distance (+inf when M = 1).

@@ -549,3 +549,19 @@ def cluster_batched(points, h: float, tol: float = 0.0, max_iter: int = 300, *, 
     per = [modes[b, : min(counts[b], int(max_modes))] for b in range(B)]
     return BatchedResult(modes=per, n_modes=n_modes, labels=labels, margins=mar,
                          stats=st.as_dict(), status=code)
+
+
+# ---------------------------------------------------------------------------
+# Measured pipe rates (fms_probe_pipe_rates)
+# ---------------------------------------------------------------------------
+
+_lib.fms_probe_pipe_rates.restype = ctypes.c_int
+_lib.fms_probe_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
+
+
+def probe_pipe_rates() -> dict:
+    """FP32 / SFU throughputs of the current device per clock and per SM."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.fms_probe_pipe_rates(out, 4), "fms_probe_pipe_rates")
+    return {"ffma_ops_per_clk_sm": out[0], "ffma2_ops_per_clk_sm": out[1],
+            "ex2_per_clk_sm": out[2], "eval_mix_units_per_clk_sm": out[3]}

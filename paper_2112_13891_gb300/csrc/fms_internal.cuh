@@ -422,12 +422,17 @@ struct UGeom {
   int Cp, Lp;          // point chunks of the seed-major passes (Lp points each)
   int Cs, Ls;          // seed chunks of the point-major pass (Ls seeds each)
 };
+// One forward update; Wout (W_t) and Sh (the weight shift of seeds whose W
+// underflowed, 0 otherwise) may be null; rlist [B m] and rcount (zero on
+// entry, zero again on return) are scratch.
 cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                            float* Ynext, float* Wout, int grid, cudaStream_t st);
+                            float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
+                            int grid, cudaStream_t st);
 cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
-                            const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
-                            float* part_s, float* part_p, float* gmu, float* dh_part, float* Gprev,
-                            float* dX, double* dh, int grid, cudaStream_t st);
+                            const float* Wt, const float* Sh, const UGeom& g, float c,
+                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* gmu,
+                            float* dh_part, float* Gprev, float* dX, double* dh, int grid,
+                            cudaStream_t st);
 cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
                              cudaStream_t st);
 cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, float* dst,

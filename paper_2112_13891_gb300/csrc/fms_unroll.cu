@@ -58,7 +58,7 @@ int grid_blocks() {
 int n_ckpt(int32_t T, int32_t k) { return (T + k - 1) / k; }
 
 struct FwdLayout {
-  size_t Xp, Ya, Yb, part, total;
+  size_t Xp, Ya, Yb, part, rlist, total;
 };
 FwdLayout fwd_layout(const UGeom& g) {
   FwdLayout L{};
@@ -72,12 +72,13 @@ FwdLayout fwd_layout(const UGeom& g) {
   L.Ya = take((size_t)g.B * g.m * g.DP * 4);
   L.Yb = take((size_t)g.B * g.m * g.DP * 4);
   L.part = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * 4);
+  L.rlist = take(((size_t)g.B * g.m + 1) * 4);   // rescue list, then its count
   L.total = o;
   return L;
 }
 
 struct BwdLayout {
-  size_t Xp, seg, Wseg, Ga, Gb, part_s, part_p, gmu, dh_part, dXp, dh, total;
+  size_t Xp, seg, Wseg, Sseg, Ga, Gb, part_s, part_p, gmu, dh_part, dXp, dh, rlist, total;
 };
 BwdLayout bwd_layout(const UGeom& g, int32_t k) {
   BwdLayout L{};
@@ -91,6 +92,7 @@ BwdLayout bwd_layout(const UGeom& g, int32_t k) {
   L.Xp = take((size_t)g.B * g.n * g.DP * 4);
   L.seg = take((size_t)(k + 1) * rowsY * g.DP * 4);
   L.Wseg = take((size_t)k * rowsY * 4);
+  L.Sseg = take((size_t)k * rowsY * 4);   // weight shifts of the segment's updates
   L.Ga = take(rowsY * g.DP * 4);
   L.Gb = take(rowsY * g.DP * 4);
   L.part_s = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * 4);
@@ -99,6 +101,7 @@ BwdLayout bwd_layout(const UGeom& g, int32_t k) {
   L.dh_part = take(rowsY * 4);
   L.dXp = take((size_t)g.B * g.n * g.DP * 4);
   L.dh = take((size_t)g.B * 8);
+  L.rlist = take((rowsY + 1) * 4);
   L.total = o;
   return L;
 }
@@ -143,19 +146,23 @@ fms_status fms_unrolled_forward(const float* points, const float* seeds0, int32_
   float* Ya = at<float>(ws, L.Ya);
   float* Yb = at<float>(ws, L.Yb);
   float* part = at<float>(ws, L.part);
+  int32_t* rlist = at<int32_t>(ws, L.rlist);
+  int32_t* rcount = rlist + (size_t)B * m;
   float* C = static_cast<float*>(ckpt);
   const size_t rowsY = (size_t)B * m;
   const float c = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
   const int grid = grid_blocks();
   if (unroll_pack_rows(points, (int64_t)B * n, d, g.DP, Xp, st) != cudaSuccess ||
-      unroll_pack_rows(seeds0, (int64_t)rowsY, d, g.DP, Ya, st) != cudaSuccess)
+      unroll_pack_rows(seeds0, (int64_t)rowsY, d, g.DP, Ya, st) != cudaSuccess ||
+      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess)
     return FMS_ERR_CUDA;
   for (int t = 0; t < T; ++t) {
     if (t % k == 0 &&
         cudaMemcpyAsync(C + (size_t)(t / k) * rowsY * g.DP, Ya, rowsY * g.DP * 4,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return FMS_ERR_CUDA;
-    if (unroll_fwd_step(Xp, Ya, g, c, part, Yb, nullptr, grid, st) != cudaSuccess)
+    if (unroll_fwd_step(Xp, Ya, g, c, part, Yb, nullptr, nullptr, rlist, rcount, grid, st) !=
+        cudaSuccess)
       return FMS_ERR_CUDA;
     float* tmp = Ya;
     Ya = Yb;
@@ -184,6 +191,9 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
   float* Xp = at<float>(ws, L.Xp);
   float* seg = at<float>(ws, L.seg);
   float* Wseg = at<float>(ws, L.Wseg);
+  float* Sseg = at<float>(ws, L.Sseg);
+  int32_t* rlist = at<int32_t>(ws, L.rlist);
+  int32_t* rcount = rlist + (size_t)B * m;
   float* Ga = at<float>(ws, L.Ga);
   float* Gb = at<float>(ws, L.Gb);
   float* part_s = at<float>(ws, L.part_s);
@@ -202,7 +212,8 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
   if (unroll_pack_rows(points, (int64_t)B * n, d, g.DP, Xp, st) != cudaSuccess ||
       unroll_pack_rows(grad_out, (int64_t)rowsY, d, g.DP, Ga, st) != cudaSuccess ||
       cudaMemsetAsync(dXp, 0, (size_t)B * n * g.DP * 4, st) != cudaSuccess ||
-      cudaMemsetAsync(dh, 0, (size_t)B * 8, st) != cudaSuccess)
+      cudaMemsetAsync(dh, 0, (size_t)B * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess)
     return FMS_ERR_CUDA;
   float* G = Ga;
   float* Gp = Gb;
@@ -215,12 +226,14 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
       return FMS_ERR_CUDA;
     for (int u = 0; u < len; ++u)
       if (unroll_fwd_step(Xp, seg + (size_t)u * rowY, g, c, part_s, seg + (size_t)(u + 1) * rowY,
-                          Wseg + (size_t)u * rowsY, grid, st) != cudaSuccess)
+                          Wseg + (size_t)u * rowsY, Sseg + (size_t)u * rowsY, rlist, rcount, grid,
+                          st) != cudaSuccess)
         return FMS_ERR_CUDA;
     for (int u = len - 1; u >= 0; --u) {
       if (unroll_bwd_step(Xp, seg + (size_t)u * rowY, seg + (size_t)(u + 1) * rowY, G,
-                          Wseg + (size_t)u * rowsY, g, c, inv_h2, inv_h3, part_s, part_p, gmu,
-                          dh_part, Gp, dXp, dh, grid, st) != cudaSuccess)
+                          Wseg + (size_t)u * rowsY, Sseg + (size_t)u * rowsY, g, c, inv_h2,
+                          inv_h3, part_s, part_p, gmu, dh_part, Gp, dXp, dh, grid,
+                          st) != cudaSuccess)
         return FMS_ERR_CUDA;
       float* tmp = G;
       G = Gp;

@@ -12,6 +12,7 @@
 // list, prune, ordering); the last CTA to finish (atomic ticket, no waiting)
 // rebuilds the plan for the next launch.
 #include "fms_prune_body.cuh"
+#include "fms_seedperm.cuh"
 #include "fms_step_body.cuh"
 
 namespace fms {
@@ -133,32 +134,18 @@ __device__ __forceinline__ int find_set(const int64_t* __restrict__ off, int B, 
 // ---------------------------------------------------------------------------
 // seeds
 // ---------------------------------------------------------------------------
+// the seeds of every set: the keyed permutation of fms_seedperm.cuh over the
+// set's own points (its half width depends on the set's size)
 struct BFeistel {
   uint64_t k[6];
 };
 
-__device__ __forceinline__ uint64_t bmix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ int64_t bpermute(int64_t r, int64_t n, const BFeistel& f) {
-  int hb = 1;
-  while ((int64_t(1) << (2 * hb)) < n) ++hb;
-  const uint64_t mask = (uint64_t(1) << hb) - 1;
-  uint64_t x = (uint64_t)r;
-  do {
-    uint64_t L = x >> hb, R = x & mask;
+__device__ __forceinline__ int64_t bpermute(int64_t r, int64_t n, const BFeistel& b) {
+  FeistelKey f;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const uint64_t nl = R;
-      R = L ^ (bmix64(f.k[q] ^ R) & mask);
-      L = nl;
-    }
-    x = (L << hb) | R;
-  } while (x >= (uint64_t)n);
-  return (int64_t)x;
+  for (int q = 0; q < 6; ++q) f.k[q] = b.k[q];
+  f.hb = feistel_half_bits(n);
+  return permute(r, n, f);
 }
 
 // New seeds of every set: ranks [prevN, N) -> slots p0 + rank.
@@ -758,13 +745,9 @@ __global__ void __launch_bounds__(256)
 // launchers
 // ---------------------------------------------------------------------------
 static BFeistel bkey(uint64_t seed) {
+  const FeistelKey k = make_key(1, seed);   // the round keys do not depend on n
   BFeistel f;
-  for (int r = 0; r < 6; ++r) {
-    uint64_t z = seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    f.k[r] = z ^ (z >> 31);
-  }
+  for (int r = 0; r < 6; ++r) f.k[r] = k.k[r];
   return f;
 }
 

@@ -1,6 +1,7 @@
 // Point packing, Seed Selection, the per-update seed update and the
 // Early-Stopping bookkeeping that compacts the active set.
 #include "fms_internal.cuh"
+#include "fms_seedperm.cuh"
 
 namespace fms {
 
@@ -95,49 +96,9 @@ cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float s
 }
 
 // ---------------------------------------------------------------------------
-// Seed Selection (Alg. 2 line 2): entry r of a keyed permutation of [0, n).
-// A balanced Feistel network on 2*hb bits, cycle-walked into [0, n).
+// Seed Selection (Alg. 2 line 2): entries of the keyed permutation of
+// fms_seedperm.cuh.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-struct FeistelKey {
-  uint64_t k[6];
-  int hb;
-};
-
-static FeistelKey make_key(int64_t n, uint64_t rng_seed) {
-  FeistelKey f;
-  for (int r = 0; r < 6; ++r) f.k[r] = mix64(rng_seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
-  int hb = 1;
-  while ((int64_t(1) << (2 * hb)) < n) ++hb;
-  f.hb = hb;
-  return f;
-}
-
-__device__ __forceinline__ uint64_t feistel(uint64_t x, const FeistelKey& f) {
-  const uint64_t mask = (uint64_t(1) << f.hb) - 1;
-  uint64_t L = x >> f.hb, R = x & mask;
-#pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    const uint64_t nl = R;
-    R = L ^ (mix64(f.k[r] ^ R) & mask);
-    L = nl;
-  }
-  return (L << f.hb) | R;
-}
-
-__device__ __forceinline__ int64_t permute(int64_t r, int64_t n, const FeistelKey& f) {
-  uint64_t x = feistel((uint64_t)r, f);
-  // cycle walking: the walk stays on r's cycle of the bijection of [0, 4^hb)
-  // and that cycle contains r < n, so it ends within 4^hb steps
-  while (x >= (uint64_t)n) x = feistel(x, f);
-  return (int64_t)x;
-}
-
 __global__ void select_seeds_kernel(int64_t n, FeistelKey f, int64_t start, int64_t count,
                                     int32_t* __restrict__ out) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;

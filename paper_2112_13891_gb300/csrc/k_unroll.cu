@@ -16,7 +16,11 @@
 // Kernels (all FP32, exact differences, fixed-order reductions):
 //   fwd_partial   lanes own seeds, points streamed with warp-uniform loads,
 //                 partial (W, S = sum w (x - y)) per point chunk
-//   fwd_finish    y' = y + S/W, W_t kept for the backward
+//   fwd_finish    y' = y + S/W, W_t kept for the backward; a seed whose W
+//                 underflows (every point farther than ~13 h) is listed for
+//   fwd_rescue    which recomputes it with the weights taken relative to its
+//                 nearest point, w = exp2(-c (D2 - D2min)) (the shift cancels
+//                 in w / W), and records the shift c D2min for the backward
 //   bwd_seed      lanes own seeds: partial sum_j p a (x - mu) and
 //                 sum_j p a ||y - x||^2 per point chunk
 //   bwd_point     lanes own points, seeds streamed: partial
@@ -85,16 +89,28 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// Below this W the unshifted weights lose precision (terms under 2^-126
+// flush to zero) and the seed is recomputed with a shift.
+constexpr float kUnrollMinW = 1e-20f;
+
 // y_next = y + S/W (sums over chunks in chunk order), W kept for the backward.
+// Seeds with W < kUnrollMinW (or not finite) go to the rescue list instead.
 __global__ void unroll_fwd_finish(const float* __restrict__ part, const float* __restrict__ Y,
-                                  UGeom g, float* __restrict__ Ynext, float* __restrict__ Wout) {
+                                  UGeom g, float* __restrict__ Ynext, float* __restrict__ Wout,
+                                  float* __restrict__ Sh, int32_t* __restrict__ rlist,
+                                  int32_t* __restrict__ rcount) {
   const int64_t total = (int64_t)g.B * g.m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / g.m), i = (int)(e % g.m);
     float W = 0.f;
     for (int ch = 0; ch < g.Cp; ++ch) W += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1)];
+    if (!(W >= kUnrollMinW) || !isfinite(W)) {
+      rlist[atomicAdd(rcount, 1)] = (int32_t)e;
+      continue;
+    }
     if (Wout) Wout[e] = W;
+    if (Sh) Sh[e] = 0.f;
     for (int k = 0; k < g.DP; ++k) {
       float v = 0.f;
       if (k < g.d) {
@@ -108,13 +124,82 @@ __global__ void unroll_fwd_finish(const float* __restrict__ part, const float* _
   }
 }
 
+// Recomputes the listed seeds (one warp each, points over lanes): pass 1 the
+// nearest squared distance D2min, pass 2 the weights exp2(-c (D2 - D2min)),
+// their sums (fixed xor tree over lanes) and y' = y + S/W; the shift c D2min
+// goes to Sh for the backward.  One block; it clears the list count at the end.
+template <int DPAD>
+__global__ void __launch_bounds__(1024)
+    unroll_fwd_rescue(const float* __restrict__ X, const float* __restrict__ Y, UGeom g, float c,
+                      const int32_t* __restrict__ rlist, int32_t* rcount,
+                      float* __restrict__ Ynext, float* __restrict__ Wout,
+                      float* __restrict__ Sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = *(volatile int32_t*)rcount;
+  for (int q = warp; q < cnt; q += (int)(blockDim.x >> 5)) {
+    const int64_t e = rlist[q];
+    const int b = (int)(e / g.m);
+    const float* Xb = X + (int64_t)b * g.n * g.DP;
+    float y[DPAD];
+    load_row<DPAD>(Y + e * g.DP, g.DP, y);
+    float dmin = INFINITY;
+    for (int j = lane; j < g.n; j += 32) {
+      float x[DPAD];
+      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      float D2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) {
+        const float dx = x[k] - y[k];
+        D2 = fmaf(dx, dx, D2);
+      }
+      dmin = fminf(dmin, D2);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(kFull, dmin, o));
+    const float sh = c * dmin;
+    float W = 0.f, S[DPAD];
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) S[k] = 0.f;
+    for (int j = lane; j < g.n; j += 32) {
+      float x[DPAD];
+      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      float dx[DPAD], D2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) {
+        dx[k] = x[k] - y[k];
+        D2 = fmaf(dx[k], dx[k], D2);
+      }
+      const float w = ex2_ftz(fmaf(-c, D2, sh));
+      W += w;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) S[k] = fmaf(w, dx[k], S[k]);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      W += __shfl_xor_sync(kFull, W, o);
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) S[k] += __shfl_xor_sync(kFull, S[k], o);
+    }
+    if (lane == 0) {
+      if (Wout) Wout[e] = W;
+      if (Sh) Sh[e] = sh;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k)
+        if (k < g.DP) Ynext[e * g.DP + k] = k < g.d ? y[k] + S[k] / W : 0.f;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *rcount = 0;
+}
+
 // ---- backward, seed-major: partial sums over point chunks of
 //   DY_i = sum_j p_ij a_ij (x_j - mu_i),  DH_i = sum_j p_ij a_ij ||y_i - x_j||^2
 template <int DPAD>
 __global__ void __launch_bounds__(128)
     unroll_bwd_seed(const float* __restrict__ X, const float* __restrict__ Y,
                     const float* __restrict__ MU, const float* __restrict__ G,
-                    const float* __restrict__ Wt, UGeom g, float c, float* __restrict__ part) {
+                    const float* __restrict__ Wt, const float* __restrict__ Sh, UGeom g, float c,
+                    float* __restrict__ part) {
   const int lane = threadIdx.x & 31;
   const int Gs = (g.m + 31) / 32;
   const int64_t T = (int64_t)g.B * Gs * g.Cp;
@@ -133,6 +218,7 @@ __global__ void __launch_bounds__(128)
     load_row<DPAD>(MU + row * g.DP, g.DP, mu);
     load_row<DPAD>(G + row * g.DP, g.DP, gg);
     const float invW = 1.0f / Wt[row];
+    const float sh = Sh[row];   // the forward's weight shift (0 unless rescued)
 #pragma unroll
     for (int k = 0; k < DPAD; ++k) DY[k] = 0.f;
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
@@ -147,7 +233,7 @@ __global__ void __launch_bounds__(128)
         e[k] = x[k] - mu[k];
         a = fmaf(gg[k], e[k], a);
       }
-      const float pa = ex2_ftz(-c * D2) * invW * a;
+      const float pa = ex2_ftz(fmaf(-c, D2, sh)) * invW * a;
       DH = fmaf(pa, D2, DH);
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) DY[k] = fmaf(pa, e[k], DY[k]);
@@ -194,8 +280,8 @@ template <int DPAD>
 __global__ void __launch_bounds__(128)
     unroll_bwd_point(const float* __restrict__ X, const float* __restrict__ Y,
                      const float* __restrict__ G, const float* __restrict__ Wt,
-                     const float* __restrict__ gmu, UGeom g, float c, float inv_h2,
-                     float* __restrict__ part) {
+                     const float* __restrict__ Sh, const float* __restrict__ gmu, UGeom g,
+                     float c, float inv_h2, float* __restrict__ part) {
   const int lane = threadIdx.x & 31;
   const int Gp = (g.n + 31) / 32;
   const int64_t T = (int64_t)g.B * Gp * g.Cs;
@@ -218,6 +304,7 @@ __global__ void __launch_bounds__(128)
       load_row<DPAD>(Y + row * g.DP, g.DP, y);
       load_row<DPAD>(G + row * g.DP, g.DP, gg);
       const float invW = 1.0f / __ldg(Wt + row);
+      const float sh = __ldg(Sh + row);
       const float gm = __ldg(gmu + row);
       float dx[DPAD], D2 = 0.f, gx = 0.f;
 #pragma unroll
@@ -226,7 +313,7 @@ __global__ void __launch_bounds__(128)
         D2 = fmaf(dx[k], dx[k], D2);
         gx = fmaf(gg[k], x[k], gx);
       }
-      const float p = ex2_ftz(-c * D2) * invW;
+      const float p = ex2_ftz(fmaf(-c, D2, sh)) * invW;
       const float q = p * (gx - gm) * inv_h2;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) DX[k] = fmaf(p, gg[k], fmaf(-q, dx[k], DX[k]));
@@ -315,28 +402,33 @@ static int blocks_for(int64_t work, int per = 256) {
 
 template <int DPAD>
 static cudaError_t fwd_step_t(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                              float* Ynext, float* Wout, int grid, cudaStream_t st) {
+                              float* Ynext, float* Wout, float* Sh, int32_t* rlist,
+                              int32_t* rcount, int grid, cudaStream_t st) {
   unroll_fwd_partial<DPAD><<<grid, 128, 0, st>>>(X, Y, g, c, part);
-  unroll_fwd_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout);
+  unroll_fwd_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout, Sh,
+                                                                    rlist, rcount);
+  unroll_fwd_rescue<DPAD><<<1, 1024, 0, st>>>(X, Y, g, c, rlist, rcount, Ynext, Wout, Sh);
   return cudaGetLastError();
 }
 
 cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                            float* Ynext, float* Wout, int grid, cudaStream_t st) {
-  if (g.DP <= 4) return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, grid, st);
-  if (g.DP <= 8) return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, grid, st);
-  if (g.DP <= 16) return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, grid, st);
-  return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, grid, st);
+                            float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
+                            int grid, cudaStream_t st) {
+  if (g.DP <= 4) return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+  if (g.DP <= 8) return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+  if (g.DP <= 16) return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+  return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
 }
 
 template <int DPAD>
 static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, const float* G,
-                              const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
-                              float* part_s, float* part_p, float* gmu, float* dh_part,
-                              float* Gprev, float* dX, double* dh, int grid, cudaStream_t st) {
+                              const float* Wt, const float* Sh, const UGeom& g, float c,
+                              float inv_h2, float inv_h3, float* part_s, float* part_p,
+                              float* gmu, float* dh_part, float* Gprev, float* dX, double* dh,
+                              int grid, cudaStream_t st) {
   unroll_gmu<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(G, MU, g, gmu);
-  unroll_bwd_point<DPAD><<<grid, 128, 0, st>>>(X, Y, G, Wt, gmu, g, c, inv_h2, part_p);
-  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, Y, MU, G, Wt, g, c, part_s);
+  unroll_bwd_point<DPAD><<<grid, 128, 0, st>>>(X, Y, G, Wt, Sh, gmu, g, c, inv_h2, part_p);
+  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, Y, MU, G, Wt, Sh, g, c, part_s);
   unroll_bwd_point_finish<<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
   unroll_bwd_seed_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2, inv_h3,
                                                                          Gprev, dh_part);
@@ -345,13 +437,14 @@ static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, c
 }
 
 cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
-                            const float* Wt, const UGeom& g, float c, float inv_h2, float inv_h3,
-                            float* part_s, float* part_p, float* gmu, float* dh_part, float* Gprev,
-                            float* dX, double* dh, int grid, cudaStream_t st) {
-  if (g.DP <= 4) return bwd_step_t<4>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  if (g.DP <= 8) return bwd_step_t<8>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  if (g.DP <= 16) return bwd_step_t<16>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  return bwd_step_t<32>(X, Y, MU, G, Wt, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+                            const float* Wt, const float* Sh, const UGeom& g, float c,
+                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* gmu,
+                            float* dh_part, float* Gprev, float* dX, double* dh, int grid,
+                            cudaStream_t st) {
+  if (g.DP <= 4) return bwd_step_t<4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  if (g.DP <= 8) return bwd_step_t<8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  if (g.DP <= 16) return bwd_step_t<16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  return bwd_step_t<32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
 }
 
 cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,

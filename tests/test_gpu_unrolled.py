@@ -6,9 +6,12 @@ numpy code; FP32 budget: relative 2e-4 of each quantity's scale (weights carry
 ~1e-6 relative error, sums over <= 512 terms).  At the full configuration
 (8 sets x 16,384 points, d = 16, T = 20, k = 5) the forward is checked on
 sampled seeds (trajectories are independent of each other) and the backward
-for finiteness and for the identity dL/dh = -(1/h) [dL/dX . X + dL/dY0 . Y0]
-(the map is invariant to scaling X, Y0 and h together, so its derivative
-along (X, Y0, h) vanishes).
+for finiteness and for the scaling identity
+    h dL/dh = Y_T . G - X . dL/dX - Y0 . dL/dY0
+(Y_T(cX, cY0, ch) = c Y_T(X, Y0, h), so differentiating L = G . Y_T along
+(X, Y0, h) at c = 1 gives it).  A seed farther than 13 h from every point,
+whose Gaussian weights all underflow in FP32, must come out as the oracle's
+(which weighs relative to the nearest point), with finite gradients.
 """
 import numpy as np
 import pytest
@@ -91,3 +94,32 @@ def test_full_configuration_sampled():
     rhs = rhs.double().cpu().numpy()
     scale = ((Xt * dX).abs().sum(dim=(1, 2)) + (YT * G).abs().sum(dim=(1, 2))).double().cpu().numpy()
     assert np.all(np.abs(lhs - rhs) <= 1e-3 * scale), (lhs, rhs)
+
+
+def test_far_seed_matches_oracle():
+    # seed 0 starts 20 h away from every point: exp(-D^2 / 2h^2) < 1e-86, so
+    # every unshifted FP32 weight is 0; the library recomputes such seeds with
+    # weights relative to the nearest point, as the oracle does
+    B, n, d, h, T, k = 1, 180, 3, 1.0, 3, 2
+    X = _sets(44, B, n, d)
+    rng = np.random.default_rng(9)
+    Y0 = (X + 0.2 * rng.standard_normal(X.shape)).astype(np.float32)
+    far = X[0].max(axis=0) + 20.0 * h
+    Y0[0, 0] = far.astype(np.float32)
+    D = np.sqrt(((X[0].astype(np.float64) - Y0[0, 0]) ** 2).sum(-1))
+    assert D.min() > 15.0 * h
+    G = rng.standard_normal(Y0.shape).astype(np.float32)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y0).cuda()
+    YT, ck = fms.unrolled_forward(Xt, Yt, h, T, k)
+    dX, dY, dh = fms.unrolled_backward(Xt, ck, n, h, T, k, torch.from_numpy(G).cuda())
+    torch.cuda.synchronize()
+    ref = orc.unrolled_forward(X[0], Y0[0], h, T)[-1]
+    got = YT[0].cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 2e-4 * (1 + np.abs(ref).max())
+    rdX, rdY, rdh = orc.unrolled_backward(X[0], Y0[0], h, T, G[0])
+    for g_, want in ((dX[0], rdX), (dY[0], rdY)):
+        g_ = g_.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(g_))
+        assert np.abs(g_ - want).max() <= 2e-4 * (1 + np.abs(want).max())
+    assert abs(dh[0].item() - rdh) <= 2e-4 * (1 + abs(rdh))

@@ -556,13 +556,28 @@ def bench_extra(args):
         ms, _ = _events_ms(run, 5, flush)
         wss = fms.Workspace(max(fms.workspace_size(x.shape[0], 16) for x in X), Xc.device)
         loop = lambda: [fms.cluster(x, 2.5, 2.5e-3, 300, workspace=wss, max_modes=128) for x in X]
-        loop()
+        one = [(o.modes.clone(), o.labels.clone()) for o in loop()]
         ms_loop, _ = _events_ms(loop, 3, flush)
+        # equal accuracy: the batched result of every set against its own
+        # single-set call (same seeds, same rules)
+        same_count, max_diff, agree = 0, 0.0, 0
+        for b in range(len(X)):
+            mb, lb = r.modes[b], r.labels[int(offs[b]):int(offs[b + 1])]
+            if mb.shape == one[b][0].shape:
+                same_count += 1
+                if mb.numel():
+                    max_diff = max(max_diff, (mb - one[b][0]).abs().max().item() / 2.5)
+            agree += int((lb == one[b][1]).sum().item())
         line.update({"metric": "ms per batch of 256 point sets (3.2M points, d=16)",
                      "value": ms, "unit": "ms", "per_set_calls_ms": ms_loop,
                      "speedup_batched_over_per_set": ms_loop / ms,
                      "total_points": int(offs[-1]), "evals": r.stats["evals"],
-                     "kernel_launches": r.stats["kernel_launches"]})
+                     "kernel_launches": r.stats["kernel_launches"],
+                     "graph": r.stats["graph"], "rounds": r.stats["rounds"],
+                     "accuracy_vs_per_set_calls": {
+                         "sets_with_equal_mode_count": same_count, "sets": len(X),
+                         "max_mode_diff_over_h": max_diff,
+                         "label_agreement": agree / float(offs[-1])}})
     elif args.workload == "unrolled_16d":
         w = fi.unrolled_16d()
         X = torch.from_numpy(w.X).cuda()

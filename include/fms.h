@@ -7,13 +7,13 @@
  *   - the update of every seed y is the Gaussian-weighted mean over ALL n
  *     points, m(y) = sum_j w_j x_j / sum_j w_j, w_j = exp(-||y - x_j||^2/(2h^2))
  *     (Sec. II-A Eq. 6 and Eq. 9-10 read with the Gaussian profile; Sec. II-B,
- *     Alg. 2 line 6 and the prose after Eq. 11: no window search);
+ *     the update of Alg. 2 and the prose after Eq. 11: no window search);
  *   - Seed Selection: N = 128 seeds drawn from the points, doubled while
- *     N < L*M with L = 8 (Alg. 2 line 2, Sec. II-C Eq. 15, Sec. II-D);
+ *     N < L*M with L = 8 (Alg. 2, Sec. II-C Eq. 15, Sec. II-D);
  *   - Early Stopping: iteration ends once ceil(gamma*N) seeds have converged;
  *     seeds not converged by then are discarded (Sec. II-C);
- *   - modes are pruned (Alg. 2 line 10) and every point is labelled by its
- *     nearest mode (Alg. 2 lines 11-13);
+ *   - modes are pruned (the prune of Alg. 2) and every point is labelled by its
+ *     nearest mode (the labelling of Alg. 2);
  *   - options select the flat kernel of Eq. 12-15 instead of the Gaussian,
  *     and the cosine metric of the sibling method the paper cites.
  *
@@ -261,12 +261,25 @@ fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, 
  *   out_labels   [offsets[B]] int32, device: index of the nearest mode of the
  *                point's own set; out_margins as in fms_cluster (nullable).
  *   workspace    fms_batched_workspace_size(offsets, B, d, opt) bytes or NULL.
- * opt->seed_indices must be NULL.  A set whose seed count outgrows the
- * on-chip prune (about 1,400 seeds at d = 16) gives FMS_ERR_UNSUPPORTED.
- * The step kernel's tiling is chosen by a built-in autotuner the first time
- * a shape (d, size class of the total, size class of B) is seen on a device:
- * it times one update with each candidate tiling and keeps the fastest.
- * Synchronises `stream` a few times per seed round.
+ * opt->seed_indices must be NULL.  Any set size and seed count is accepted:
+ * a set's prune runs in shared memory while its candidates' sort keys fit
+ * there and in global memory beyond that (same result).
+ * The whole call is one CUDA graph launched on `stream`: its updates, seed
+ * rounds and refinement updates are conditional WHILE nodes whose conditions
+ * the kernels set, so no host decision interrupts it; the call synchronises
+ * `stream` once, at the end, to read the status and the statistics
+ * (stats->graph = 1; stats->kernel_launches counts the kernels the graph ran).
+ * The graph is built on the first call with a given (pointers, B, total,
+ * largest set, d, h, tol, max_iter, max_modes, options) and reused by later
+ * calls with the same values; the per-set sizes are copied in before every
+ * launch.  The step kernel's tiling is chosen by a built-in autotuner the
+ * first time a shape (d, size class of the total, size class of B) is seen
+ * on a device: it times one update with each candidate tiling (synchronising
+ * on each) and keeps the fastest.
+ * Errors: FMS_ERR_INVALID_ARG (bad sizes, offsets or options),
+ * FMS_ERR_WORKSPACE (workspace too small or not 256-byte aligned),
+ * FMS_ERR_NONFINITE (a non-finite point), FMS_ERR_CAPACITY (see out_n_modes),
+ * FMS_ERR_CUDA (a CUDA call failed, including the graph's construction).
  */
 size_t fms_batched_workspace_size(const int64_t* offsets, int32_t B, int32_t d,
                                   const fms_options* opt);
@@ -305,7 +318,7 @@ fms_status fms_cluster_frames(const float* frames, int32_t F, int64_t n, int32_t
                               void* stream);
 
 /*
- * Seed Selection (Alg. 2 line 2): writes entries [start, start+count) of a
+ * Seed Selection (Alg. 2): writes entries [start, start+count) of a
  * keyed pseudo-random permutation pi of [0, n) to out_indices (device int32).
  * pi(i) applies a balanced 6-round Feistel network on 2*hb bits (4^hb the
  * smallest power of four >= n, hb >= 1) whose round r XORs the left half with
@@ -320,7 +333,7 @@ fms_status fms_select_seeds(int64_t n, uint64_t rng_seed, int64_t start, int64_t
 
 /*
  * One Gaussian mean-shift update of m seeds against all n points (Eq. 6 with
- * the Gaussian weight; Alg. 2 line 6):
+ * the Gaussian weight; the update of Alg. 2):
  *   out_seeds[i] = sum_j w_ij x_j / sum_j w_ij,  w_ij = exp(-||seeds_i - x_j||^2/(2h^2)).
  *   seeds, out_seeds  [m x d] float32, device (may alias).
  *   out_wsum     [m] float32, device, nullable: sum_j w_ij.
@@ -404,7 +417,7 @@ fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n, int32_t d
 fms_status fms_probe_pipe_rates(double* rates, int32_t n_rates);
 
 /*
- * Nearest-mode labelling (Alg. 2 lines 11-13): labels[j] = argmin_k
+ * Nearest-mode labelling (the labelling of Alg. 2): labels[j] = argmin_k
  * ||x_j - modes_k|| (ties -> lowest k) and, if margins is non-NULL,
  * margins[j] = second-nearest minus nearest distance (+inf when M = 1).
  * points [n x d], modes [M x d] float32, device; M >= 1.  Asynchronous.

@@ -12,12 +12,12 @@ cores), the rest is numpy in the order the paper states the steps.
 Readings of the paper used here (where it is silent or garbled):
   * the kernel is the Gaussian exp(-||y-x||^2/(2h^2)); its shadow is itself,
     so the update is the Gaussian-weighted mean over all points (Sec. II-B,
-    Alg. 2 line 6, the prose after Eq. 11; Eq. 11 itself is garbled).  The
+    the update of Alg. 2, the prose after Eq. 11; Eq. 11 itself is garbled).  The
     flat (uniform) kernel of Eq. 12-15 is the alternative (kernel="flat"): the
     update is the mean of the window ||x_i - y|| <= h and the density is the
     window count;
-  * convergence: ||y_{t+1} - y_t|| <= tol (Alg. 1/2 say only "not converge");
-  * Seed Selection (Alg. 2 line 2, Sec. II-D): the seeds are the first N
+  * convergence: ||y_{t+1} - y_t|| <= tol (Alg. 1 and 2 name no test);
+  * Seed Selection (Alg. 2, Sec. II-D): the seeds are the first N
     entries of a keyed pseudo-random permutation of [0, n) (a 6-round Feistel
     network over SplitMix64 round functions with cycle walking); N starts at
     128 and doubles while N < L*M, L = 8 (Sec. II-D);
@@ -25,13 +25,13 @@ Readings of the paper used here (where it is silent or garbled):
     seeds have converged; seeds not converged by then are discarded.  With
     gamma = 1 (plain mean shift, Alg. 1) unconverged seeds are kept at their
     last position;
-  * "Prune modes" (Alg. 1 line 13, Alg. 2 line 10): greedy suppression in
+  * the prune of Alg. 1 and Alg. 2 is a greedy suppression in
     order of KDE score (descending, seed rank ascending): a seed is accepted
     unless an accepted mode lies closer than r_merge (default h);
   * each merged mode is then refined (more updates until the step is at most
     1e-5*h, at most 50 updates) and merged again with the same rule; modes are
     reported in canonical order (score descending, ties by coordinates);
-  * every point is labelled by its nearest mode (Alg. 2 lines 11-13), ties to
+  * every point is labelled by its nearest mode (the labelling of Alg. 2), ties to
     the lowest mode index; the margin is the gap to the second-nearest mode;
   * the cosine metric (the sibling method the paper cites, whose formulation
     it does not print; metric="cosine"): points are normalised to the unit
@@ -154,7 +154,7 @@ def step(X, Y, h, kernel="gaussian"):
 
 
 def trajectories(X, Y0, h, tol, max_iter, kernel="gaussian", sphere=False):
-    """Independent trajectories y <- m(y) until ||step|| <= tol (Alg. 1 / Alg. 2 lines 5-7).
+    """Independent trajectories y <- m(y) until ||step|| <= tol (the iteration loop of Alg. 1 and Alg. 2).
 
     Returns (Y_end, conv_iter, iters): conv_iter[i] is the 1-based update at
     which ||y_t - y_{t-1}|| <= tol first held, -1 if never within max_iter,
@@ -193,7 +193,7 @@ def normalize_rows(X):
 
 
 def label(X, modes, return_margins=True):
-    """Nearest-mode labels and margins (Alg. 2 lines 11-13); ties to the lowest index.
+    """Nearest-mode labels and margins (the labelling of Alg. 2); ties to the lowest index.
 
     Pinned by: exhaustive argmin in Python on small inputs.
     """
@@ -206,7 +206,7 @@ def label(X, modes, return_margins=True):
 
 
 # ----------------------------------------------------------------------------
-# Seed Selection (Alg. 2 line 2): keyed permutation of [0, n)
+# Seed Selection (Alg. 2): keyed permutation of [0, n)
 # ----------------------------------------------------------------------------
 
 def mix64(z: int) -> int:
@@ -329,7 +329,7 @@ def early_stop(conv_iter: np.ndarray, gamma: float, max_iter: int):
 
 
 def merge(X, Y, rank, h, r_merge, kernel="gaussian"):
-    """Prune modes (Alg. 1 line 13 / Alg. 2 line 10): greedy radius suppression.
+    """The prune of Alg. 1 and Alg. 2: greedy radius suppression.
 
     Candidates are visited in order of (density score descending, rank
     ascending); one is accepted unless an accepted mode lies at distance

@@ -126,7 +126,7 @@ void orc_step(const double* X, int64_t n, int d, double h, const double* Y, int6
 }
 
 /*
- * Independent trajectories (Alg. 1 inner loop / Alg. 2 lines 5-7): for each
+ * Independent trajectories (the iteration loop of Alg. 1 and Alg. 2): for each
  * start point Y_i, repeat y <- m(y) until ||m(y) - y|| <= tol or max_iter
  * updates were made.  On return Y_i holds the last iterate, iters[i] the
  * number of updates made and conv_iter[i] the update index t (1-based) at
@@ -202,7 +202,7 @@ void orc_trajectories(const double* X, int64_t n, int d, double h, double tol, i
 }
 
 /*
- * Nearest-mode labels (Alg. 2 lines 11-13): label_j = argmin_k ||x_j - mode_k||,
+ * Nearest-mode labels (the labelling of Alg. 2): label_j = argmin_k ||x_j - mode_k||,
  * ties to the lowest k; margin_j = (second-nearest distance) - (nearest
  * distance), +inf when there is a single mode.
  */

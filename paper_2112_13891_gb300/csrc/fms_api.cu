@@ -553,7 +553,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       return e;
     };
 
-    // --- Seed Selection (Alg. 2 line 2): initial seed count ---
+    // --- Seed Selection (Alg. 2): initial seed count ---
     int32_t N0;
     if (o.all_seeds) N0 = (int32_t)n;
     else if (o.seed_indices) N0 = o.n_seed_indices;
@@ -845,7 +845,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
           }
           if (hctl.done) break;
         }
-        // --- prune candidates (Alg. 2 line 10) and their densities: with
+        // --- prune candidates (the prune of Alg. 2) and their densities: with
         // gamma < 1 every candidate converged, and its density is sum w of its
         // last update (one step <= tol before it); kept seeds that did not
         // converge (gamma = 1) get a density pass at their positions ---
@@ -922,7 +922,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       FMS_LAUNCH(launch_canonical_order(ym, mscore, nullptr, &mctl->Mr, d, DP, 1.0 / scale,
                                       out_modes, max_modes, modes_full, nullptr, hm.M, st));
     }
-    // --- labels (Alg. 2 lines 11-13) ---
+    // --- labels (the labelling of Alg. 2) ---
     mark(3);
     FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st,
                             cosine ? 1 : 0));

@@ -137,6 +137,20 @@ struct SetCtl {
   int64_t evals;
 };
 
+// Batched call: a graph condition that a kernel sets when it finishes (on = 0:
+// the kernel runs outside the graph and sets nothing), and the slots of the
+// call's device counters.
+struct BatchCond {
+  cudaGraphConditionalHandle h;
+  int32_t on;
+};
+enum BatchCounter : int {
+  kCtrBlocksDone = 0,   // atomic ticket of the per-set kernels
+  kCtrRounds = 1,       // seed rounds run
+  kCtrUpdates = 2,      // seed updates run (all rounds)
+  kCtrRefine = 3,       // refinement updates run
+};
+
 // Tiling of a (seed-group x point-chunk) warp-task grid.
 struct Tiling {
   int32_t target_warps;   // warps the step grid runs (gridDim.x * warps per CTA)

@@ -48,6 +48,149 @@ __host__ __device__ inline size_t greedy_sorted_smem(int K, int d, int P, bool a
          (acc_in_smem ? (size_t)K * d * sizeof(PT) : 0);
 }
 
+// ---------------------------------------------------------------------------
+// The greedy visit for candidate sets too large for the sorted prune's shared
+// memory: repeatedly accept the remaining candidate of highest (score, lowest
+// index) and drop every candidate within r of it.  The remaining candidates
+// are kept as a compacted list (in `list`, K entries of global memory); one
+// pass per accepted mode drops the new mode's neighbours and finds the next
+// winner, each thread taking kGlobalRun list entries per step with their loads
+// issued together.  The winner and every suppression are decided exactly as
+// in the one-by-one visit, so the accepted set and order are the same.
+// Candidate q has rank q; its row is cand_row[q] (or q when cand_row is
+// null).  `sm` holds greedy_global_smem() bytes of shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kGlobalRun = 8;
+
+template <typename ST>
+__device__ __forceinline__ void argmax_merge(ST& best, int& bq, ST os, int oq) {
+  if (os > best || (os == best && oq < bq)) {
+    best = os;
+    bq = oq;
+  }
+}
+
+// Block-wide (score desc, index asc) winner; INT32_MAX when no candidate
+// has a comparable score.  Every thread returns the same value.
+template <typename ST>
+__device__ int block_argmax(ST best, int bq, ST* sh_s, int* sh_q, int* sh_best) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const ST os = __shfl_xor_sync(kFull, best, o);
+    const int oq = __shfl_xor_sync(kFull, bq, o);
+    argmax_merge<ST>(best, bq, os, oq);
+  }
+  if (lane == 0) {
+    sh_s[wid] = best;
+    sh_q[wid] = bq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ST b = sh_s[0];
+    int bb = sh_q[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge<ST>(b, bb, sh_s[w], sh_q[w]);
+    *sh_best = bb;
+  }
+  __syncthreads();
+  const int win = *sh_best;
+  __syncthreads();   // sh_best and sh_s / sh_q are reused by the next call
+  return win;
+}
+
+// shared memory of greedy_global_body: winner scores and indices per warp,
+// the winner's coordinates, the winner, the scan's warp sums
+template <typename PT, typename ST>
+__host__ __device__ constexpr size_t greedy_global_smem() {
+  return 32 * sizeof(ST) + 32 * 4 + kPruneMaxDim * sizeof(PT) + 16 + 64 * 4;
+}
+
+template <typename PT, typename ST>
+__device__ void greedy_global_body(const int32_t* __restrict__ cand_row, const int K,
+                                   const ST* __restrict__ score, const PT* __restrict__ pos,
+                                   int DP, int d, PT r2, int32_t* __restrict__ list,
+                                   int32_t* __restrict__ accepted, int32_t* __restrict__ M_out,
+                                   unsigned char* sm) {
+  ST* sh_s = reinterpret_cast<ST*>(sm);
+  int* sh_q = reinterpret_cast<int*>(sh_s + 32);
+  PT* sh_pos = reinterpret_cast<PT*>(sh_q + 32);
+  int* sh_best = reinterpret_cast<int*>(sh_pos + kPruneMaxDim);
+  int* scratch = sh_best + 4;
+  const int T = blockDim.x;
+  ST best = (ST)-INFINITY;
+  int bq = INT32_MAX;
+  for (int b = 0; b < K; b += T * kGlobalRun) {
+#pragma unroll
+    for (int v = 0; v < kGlobalRun; ++v) {
+      const int q = b + v * T + threadIdx.x;
+      if (q < K) {
+        list[q] = q;
+        argmax_merge<ST>(best, bq, score[q], q);
+      }
+    }
+  }
+  int win = block_argmax<ST>(best, bq, sh_s, sh_q, sh_best);
+  int len = K, M = 0;
+  while (win != INT32_MAX) {
+    if (threadIdx.x == 0) accepted[M] = win;
+    ++M;
+    const int64_t wrow = cand_row ? cand_row[win] : win;
+    for (int k = threadIdx.x; k < d; k += T) sh_pos[k] = pos[wrow * DP + k];
+    __syncthreads();
+    best = (ST)-INFINITY;
+    bq = INT32_MAX;
+    int newlen = 0;
+    for (int b = 0; b < len; b += T * kGlobalRun) {
+      int q[kGlobalRun];
+      int64_t row[kGlobalRun];
+      ST sc[kGlobalRun];
+      PT d2[kGlobalRun];
+#pragma unroll
+      for (int v = 0; v < kGlobalRun; ++v) {
+        const int idx = b + v * T + threadIdx.x;
+        q[v] = idx < len ? list[idx] : -1;
+      }
+#pragma unroll
+      for (int v = 0; v < kGlobalRun; ++v) {
+        sc[v] = q[v] >= 0 ? score[q[v]] : (ST)0;
+        row[v] = q[v] >= 0 ? (cand_row ? (int64_t)cand_row[q[v]] : (int64_t)q[v]) : 0;
+        d2[v] = 0;
+      }
+      for (int k = 0; k < d; ++k) {
+        const PT pk = sh_pos[k];
+#pragma unroll
+        for (int v = 0; v < kGlobalRun; ++v) {
+          if (q[v] >= 0) {
+            const PT e = pos[row[v] * DP + k] - pk;
+            d2[v] += e * e;
+          }
+        }
+      }
+      unsigned keep = 0;
+      int cnt = 0;
+#pragma unroll
+      for (int v = 0; v < kGlobalRun; ++v) {
+        if (q[v] >= 0 && q[v] != win && !(d2[v] < r2)) {
+          keep |= 1u << v;
+          ++cnt;
+          argmax_merge<ST>(best, bq, sc[v], q[v]);
+        }
+      }
+      // in-place compaction: this step writes only below the end of what it
+      // read, and every read precedes the scan's barriers
+      int tot;
+      int off = block_exclusive_scan(cnt, &tot, scratch);
+#pragma unroll
+      for (int v = 0; v < kGlobalRun; ++v)
+        if ((keep >> v) & 1u) list[newlen + off++] = q[v];
+      newlen += tot;
+    }
+    len = newlen;
+    win = block_argmax<ST>(best, bq, sh_s, sh_q, sh_best);
+  }
+  if (threadIdx.x == 0) *M_out = M;
+}
+
 template <typename PT, typename ST, int DT = 0>
 __device__ void greedy_sorted_body(const int32_t* __restrict__ cand_row, const int K,
                                    const ST* __restrict__ score, const PT* __restrict__ pos,

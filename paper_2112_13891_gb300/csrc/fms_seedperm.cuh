@@ -1,5 +1,5 @@
-// The keyed permutation behind Seed Selection (Alg. 2 line 2: "evenly random
-// select" N of the n points), shared by every kernel that draws seeds so that
+// The keyed permutation behind Seed Selection (Alg. 2: N of the n points
+// chosen evenly at random), shared by every kernel that draws seeds so that
 // the single-set and batched paths produce the same seeds bit for bit.
 //
 // Entry r of the permutation of [0, n): a balanced Feistel network on 2*hb

@@ -10,7 +10,10 @@
 // index to (set, local index) by binary search.  One CTA per set runs the
 // per-set bookkeeping (compaction under the Early Stopping clock rule, kept
 // list, prune, ordering); the last CTA to finish (atomic ticket, no waiting)
-// rebuilds the plan for the next launch.
+// rebuilds the plan for the next launch.  The whole call runs as one CUDA
+// graph: the compaction, advance and refinement kernels decide on the device,
+// through conditional-node handles, whether another update, another seed round
+// or another refinement update follows.
 #include "fms_prune_body.cuh"
 #include "fms_seedperm.cuh"
 #include "fms_step_body.cuh"
@@ -115,10 +118,21 @@ __device__ void build_plan(const SetCtl* __restrict__ sc, int B, int kind, int R
   }
 }
 
+// a kernel given cond.on sets cond.h to "more work follows" when it finishes
+__device__ __forceinline__ void set_cond(const BatchCond& cond, bool more,
+                                         const uint32_t* status) {
+  if (cond.on) {
+    const bool ok = !(__ldcg(status) & kStNonFinite);   // stop early on bad input
+    cudaGraphSetConditional(cond.h, (more && ok) ? 1u : 0u);
+  }
+}
+
 __global__ void __launch_bounds__(1024)
     plan_kernel(const SetCtl* sc, int B, int kind, int R, int DA, int64_t* task_off,
-                int64_t* part_off, int64_t* list_off, int64_t* totals) {
+                int64_t* part_off, int64_t* list_off, int64_t* totals, BatchCond cond,
+                const uint32_t* status) {
   build_plan(sc, B, kind, R, DA, task_off, part_off, list_off, totals);
+  if (threadIdx.x == 0) set_cond(cond, totals[1] > 0, status);
 }
 
 __device__ __forceinline__ int find_set(const int64_t* __restrict__ off, int B, int64_t x) {
@@ -148,12 +162,14 @@ __device__ __forceinline__ int64_t bpermute(int64_t r, int64_t n, const BFeistel
   return permute(r, n, f);
 }
 
-// New seeds of every set: ranks [prevN, N) -> slots p0 + rank.
+// New seeds of every set: ranks [prevN, N) -> slots p0 + rank.  A set whose
+// prune result is final keeps its seeds.
 __global__ void batched_seed_init(SetCtl* sc, int B, const float* __restrict__ Xs, int DP,
                                   BFeistel f, float* __restrict__ y, int32_t* __restrict__ it,
                                   int32_t* __restrict__ conv, int32_t* __restrict__ state) {
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     const SetCtl c = sc[b];
+    if (c.final_) continue;
     for (int r = c.prevN + threadIdx.x; r < c.N; r += blockDim.x) {
       const int64_t idx = c.p0 + bpermute(r, c.n, f);
       const int64_t slot = c.p0 + r;
@@ -174,9 +190,11 @@ __global__ void __launch_bounds__(1024)
                     const int32_t* __restrict__ it, const int32_t* __restrict__ conv,
                     int32_t* __restrict__ active, int begin, int max_iter, int R, int DA,
                     Tiling tl, int64_t* task_off, int64_t* part_off, int64_t* list_off,
-                    int64_t* totals, int32_t* blocks_done, int32_t* sets_running) {
+                    int64_t* totals, int32_t* counters, BatchCond cond,
+                    const uint32_t* status) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
+  int32_t* blocks_done = counters + kCtrBlocksDone;
   const int b = blockIdx.x;
   SetCtl* c = sc + b;
   if (begin && c->final_) {
@@ -236,7 +254,6 @@ __global__ void __launch_bounds__(1024)
       c->C = C;
       c->Lc = Lc;
       if (!done) c->evals += (int64_t)s * c->n;
-      if (!done) atomicAdd(sets_running, 1);
     }
   }
   __threadfence();
@@ -246,7 +263,11 @@ __global__ void __launch_bounds__(1024)
   if (!sh_last) return;
   __threadfence();
   build_plan(sc, B, kPlanActive, R, DA, task_off, part_off, list_off, totals);
-  if (threadIdx.x == 0) *blocks_done = 0;
+  if (threadIdx.x == 0) {
+    *blocks_done = 0;
+    if (!begin) counters[kCtrUpdates] += 1;
+    set_cond(cond, totals[1] > 0, status);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -421,9 +442,10 @@ __global__ void __launch_bounds__(1024)
     batched_kept(SetCtl* sc, int B, const int32_t* __restrict__ state,
                  const int32_t* __restrict__ conv, int keep_exhausted, int32_t* __restrict__ kept,
                  int R, int DA, Tiling tl, int64_t* task_off, int64_t* part_off,
-                 int64_t* list_off, int64_t* totals, int32_t* blocks_done) {
+                 int64_t* list_off, int64_t* totals, int32_t* counters) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
+  int32_t* blocks_done = counters + kCtrBlocksDone;
   const int b = blockIdx.x;
   SetCtl* c = sc + b;
   const int N = c->final_ ? 0 : c->N, p0 = c->p0, t_star = c->r;
@@ -483,12 +505,15 @@ __global__ void batched_score(const float* __restrict__ part, const SetCtl* __re
   }
 }
 
-// sorted prune of each set (one CTA per set)
+// Prune of each set (one CTA per set): the sorted visit while its sort keys
+// (and, when they fit too, the accepted modes' coordinates) fit in the launch's
+// smem_bytes of shared memory, else the one-block global greedy over the set's
+// own region of `list`; both give the one-by-one greedy visit's result.
 template <typename PT, typename ST>
 __global__ void __launch_bounds__(1024)
     batched_prune(SetCtl* sc, const int32_t* __restrict__ kept, const ST* __restrict__ score,
                   const PT* __restrict__ pos, int DP, int d, PT r2, int32_t* __restrict__ accepted,
-                  int P, int second, int pos_in_smem) {
+                  int32_t* __restrict__ list, int smem_bytes, int second) {
   extern __shared__ __align__(16) unsigned char smem[];
   SetCtl* c = sc + blockIdx.x;
   if (!second && c->final_) return;  // this set's prune result is already final
@@ -496,33 +521,51 @@ __global__ void __launch_bounds__(1024)
   const int K = second ? c->M : c->K;
   // candidates: first prune -> kept seeds (rows = seed slots); second prune ->
   // refined modes (rows = mode slots p0 + m)
-  greedy_sorted_body<PT, ST>(second ? nullptr : kept + p0, K, score + p0,
-                             second ? pos + (int64_t)p0 * DP : pos, DP, d, r2, accepted + p0,
-                             second ? &c->Mr : &c->M, P, smem, pos_in_smem != 0);
+  const int32_t* rows = second ? nullptr : kept + p0;
+  const PT* cpos = second ? pos + (int64_t)p0 * DP : pos;
+  int32_t* M_out = second ? &c->Mr : &c->M;
+  int P = 1;
+  while (P < K) P <<= 1;
+  if (greedy_sorted_smem<PT, ST>(K, d, P, false) <= (size_t)smem_bytes) {
+    const bool acc_in_smem = greedy_sorted_smem<PT, ST>(K, d, P, true) <= (size_t)smem_bytes;
+    greedy_sorted_body<PT, ST>(rows, K, score + p0, cpos, DP, d, r2, accepted + p0, M_out, P, smem,
+                               acc_in_smem);
+  } else {
+    greedy_global_body<PT, ST>(rows, K, score + p0, cpos, DP, d, r2, list + p0, accepted + p0,
+                               M_out, smem);
+  }
 }
 
-__global__ void batched_doubling(SetCtl* sc, int B, float L, int allow, int32_t* any) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+// Seed-count decision of every set after its prune (Sec. II-D: double N while
+// N < L*M and N < n) and the start of the next round for the sets that double
+// (prevN <- N, N <- next N, target from gamma).  One CTA; it also counts the
+// round and sets the round loop's condition: another round while any set doubles.
+__global__ void __launch_bounds__(1024)
+    batched_advance(SetCtl* sc, int B, float L, int allow, float gamma, int32_t* counters,
+                    BatchCond cond, const uint32_t* status) {
+  __shared__ int red[32];
+  int any = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
     SetCtl* c = sc + b;
     if (c->final_) continue;
     int next = c->N;
     if (allow && (float)c->N < L * (float)c->M && c->N < c->n) next = min(2 * c->N, c->n);
     c->next_N = next;
-    if (next > c->N) atomicAdd(any, 1);
-    else c->final_ = 1;
+    if (next > c->N) {
+      c->prevN = c->N;
+      c->N = next;
+      const int t = (int)ceil((double)gamma * (double)next);
+      c->target = max(1, min(t, next));
+      c->done = 0;
+      any = 1;
+    } else {
+      c->final_ = 1;
+    }
   }
-}
-
-// start of the next round: prevN <- N, N <- next_N, target from gamma
-__global__ void batched_next_round(SetCtl* sc, int B, float gamma) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-    SetCtl* c = sc + b;
-    if (c->final_) continue;
-    c->prevN = c->N;
-    c->N = c->next_N;
-    int t = (int)ceil((double)gamma * (double)c->N);
-    c->target = max(1, min(t, c->N));
-    c->done = 0;
+  any = block_sum(any, red);
+  if (threadIdx.x == 0) {
+    counters[kCtrRounds] += 1;
+    set_cond(cond, any > 0, status);
   }
 }
 
@@ -629,9 +672,11 @@ __global__ void __launch_bounds__(1024)
     batched_refine_compact(SetCtl* sc, int B, const int32_t* __restrict__ mdone,
                            int32_t* __restrict__ ract, int max_iter, int R, int DA, Tiling tl,
                            int64_t* task_off, int64_t* part_off, int64_t* list_off,
-                           int64_t* totals, int32_t* blocks_done, int32_t* sets_running) {
+                           int64_t* totals, int32_t* counters, BatchCond cond,
+                           const uint32_t* status) {
   __shared__ int scratch[64];
   __shared__ int sh_last;
+  int32_t* blocks_done = counters + kCtrBlocksDone;
   SetCtl* c = sc + blockIdx.x;
   if (!__ldcg(&c->rdone)) {
     const int M = c->M, p0 = c->p0;
@@ -654,10 +699,7 @@ __global__ void __launch_bounds__(1024)
       if (!done) choose_chunks(c->n, base, R, tl, &C, &Lc);
       c->rC = C;
       c->rLc = Lc;
-      if (!done) {
-        c->evals += (int64_t)base * c->n;
-        atomicAdd(sets_running, 1);
-      }
+      if (!done) c->evals += (int64_t)base * c->n;
     }
   }
   __threadfence();
@@ -667,7 +709,11 @@ __global__ void __launch_bounds__(1024)
   if (!sh_last) return;
   __threadfence();
   build_plan(sc, B, kPlanModes, R, DA, task_off, part_off, list_off, totals);
-  if (threadIdx.x == 0) *blocks_done = 0;
+  if (threadIdx.x == 0) {
+    *blocks_done = 0;
+    counters[kCtrRefine] += 1;
+    set_cond(cond, totals[1] > 0, status);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -762,11 +808,11 @@ cudaError_t launch_batched_seed_init(SetCtl* sc, int B, const float* Xs, int DP,
 cudaError_t launch_batched_compact(SetCtl* sc, int B, const int32_t* state, const int32_t* it,
                                    const int32_t* conv, int32_t* active, int begin, int max_iter,
                                    int R, int DA, Tiling tl, int64_t* task_off, int64_t* part_off,
-                                   int64_t* list_off, int64_t* totals, int32_t* blocks_done,
-                                   int32_t* sets_running, cudaStream_t st) {
+                                   int64_t* list_off, int64_t* totals, int32_t* counters,
+                                   BatchCond cond, const uint32_t* status, cudaStream_t st) {
   batched_compact<<<B, 1024, 0, st>>>(sc, B, state, it, conv, active, begin, max_iter, R, DA, tl,
-                                      task_off, part_off, list_off, totals, blocks_done,
-                                      sets_running);
+                                      task_off, part_off, list_off, totals, counters, cond,
+                                      status);
   return cudaGetLastError();
 }
 
@@ -783,9 +829,9 @@ cudaError_t launch_batched_update(const float* part, const int32_t* active, cons
 cudaError_t launch_batched_kept(SetCtl* sc, int B, const int32_t* state, const int32_t* conv,
                                 int keep_exhausted, int32_t* kept, int R, int DA, Tiling tl,
                                 int64_t* task_off, int64_t* part_off, int64_t* list_off,
-                                int64_t* totals, int32_t* blocks_done, cudaStream_t st) {
+                                int64_t* totals, int32_t* counters, cudaStream_t st) {
   batched_kept<<<B, 1024, 0, st>>>(sc, B, state, conv, keep_exhausted, kept, R, DA, tl, task_off,
-                                   part_off, list_off, totals, blocks_done);
+                                   part_off, list_off, totals, counters);
   return cudaGetLastError();
 }
 
@@ -797,64 +843,55 @@ cudaError_t launch_batched_score(const float* part, const SetCtl* sc, int B,
   return cudaGetLastError();
 }
 
-// Shared memory of the per-set sorted prune: sort keys and indices, plus the
-// coordinates when they fit in kBatchedPruneSmem (else they are read from
-// global memory; *with_pos tells which).
-size_t batched_prune_smem(int maxK, int d, int pos_bytes, int score_bytes, int* P,
-                          int* with_pos) {
-  int p = 1;
-  while (p < maxK) p <<= 1;
-  *P = p;
-  // keys and indices, scratch, the two batch tiles (as greedy_sorted_smem)
-  const size_t keys = (((size_t)p * (score_bytes + 4) + kPruneScratchInts * 4 + 15) / 16) * 16 +
-                      2 * (size_t)kPruneMaxDim * kPruneTileStride * pos_bytes;
-  const size_t full = keys + (size_t)maxK * d * pos_bytes;
-  if (with_pos) *with_pos = full <= kBatchedPruneSmem ? 1 : 0;
-  return full <= kBatchedPruneSmem ? full : keys;
+// Shared memory of the per-set prune launch for sets of up to maxK candidates:
+// the sorted visit's keys, indices, tiles and accepted coordinates when they
+// fit in kBatchedPruneSmem, else kBatchedPruneSmem (sets whose keys do not fit
+// take the global greedy).
+template <typename PT, typename ST>
+static size_t prune_launch_smem(int maxK, int d) {
+  int P = 1;
+  while (P < maxK) P <<= 1;
+  size_t sm = greedy_sorted_smem<PT, ST>(maxK, d, P, true);
+  if (sm > kBatchedPruneSmem) sm = kBatchedPruneSmem;
+  if (sm < greedy_global_smem<PT, ST>()) sm = greedy_global_smem<PT, ST>();
+  return sm;
+}
+
+template <typename PT, typename ST>
+static cudaError_t launch_prune_t(SetCtl* sc, int B, const int32_t* kept, const ST* score,
+                                  const PT* pos, int DP, int d, PT r2, int32_t* accepted,
+                                  int32_t* list, int maxK, int second, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        batched_prune<PT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchedPruneSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const size_t sm = prune_launch_smem<PT, ST>(maxK, d);
+  batched_prune<PT, ST><<<B, 1024, sm, st>>>(sc, kept, score, pos, DP, d, r2, accepted, list,
+                                             (int)sm, second);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batched_prune_f(SetCtl* sc, int B, const int32_t* kept, const float* score,
                                    const float* pos, int DP, int d, float r2, int32_t* accepted,
-                                   int maxK, cudaStream_t st) {
-  int P = 1, with_pos = 0;
-  const size_t sm = batched_prune_smem(maxK, d, 4, 4, &P, &with_pos);
-  if (sm > kBatchedPruneSmem) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(batched_prune<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kBatchedPruneSmem);
-    attr = true;
-  }
-  batched_prune<float, float><<<B, 1024, sm, st>>>(sc, kept, score, pos, DP, d, r2, accepted, P, 0,
-                                                   with_pos);
-  return cudaGetLastError();
+                                   int32_t* list, int maxK, cudaStream_t st) {
+  return launch_prune_t<float, float>(sc, B, kept, score, pos, DP, d, r2, accepted, list, maxK, 0,
+                                      st);
 }
 
 cudaError_t launch_batched_prune_d(SetCtl* sc, int B, const double* score, const double* pos,
-                                   int DP, int d, double r2, int32_t* accepted, int maxK,
+                                   int DP, int d, double r2, int32_t* accepted, int32_t* list,
+                                   int maxK, cudaStream_t st) {
+  return launch_prune_t<double, double>(sc, B, nullptr, score, pos, DP, d, r2, accepted, list,
+                                        maxK, 1, st);
+}
+
+cudaError_t launch_batched_advance(SetCtl* sc, int B, float L, int allow, float gamma,
+                                   int32_t* counters, BatchCond cond, const uint32_t* status,
                                    cudaStream_t st) {
-  int P = 1, with_pos = 0;
-  const size_t sm = batched_prune_smem(maxK, d, 8, 8, &P, &with_pos);
-  if (sm > kBatchedPruneSmem) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(batched_prune<double, double>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchedPruneSmem);
-    attr = true;
-  }
-  batched_prune<double, double><<<B, 1024, sm, st>>>(sc, nullptr, score, pos, DP, d, r2, accepted,
-                                                     P, 1, with_pos);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batched_doubling(SetCtl* sc, int B, float L, int allow, int32_t* any,
-                                    cudaStream_t st) {
-  batched_doubling<<<(B + 255) / 256, 256, 0, st>>>(sc, B, L, allow, any);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batched_next_round(SetCtl* sc, int B, float gamma, cudaStream_t st) {
-  batched_next_round<<<(B + 255) / 256, 256, 0, st>>>(sc, B, gamma);
+  batched_advance<<<1, 1024, 0, st>>>(sc, B, L, allow, gamma, counters, cond, status);
   return cudaGetLastError();
 }
 
@@ -868,8 +905,10 @@ cudaError_t launch_batched_refine_setup(SetCtl* sc, int B, const float* y, const
 }
 
 cudaError_t launch_plan(const SetCtl* sc, int B, int kind, int R, int DA, int64_t* task_off,
-                        int64_t* part_off, int64_t* list_off, int64_t* totals, cudaStream_t st) {
-  plan_kernel<<<1, 1024, 0, st>>>(sc, B, kind, R, DA, task_off, part_off, list_off, totals);
+                        int64_t* part_off, int64_t* list_off, int64_t* totals, BatchCond cond,
+                        const uint32_t* status, cudaStream_t st) {
+  plan_kernel<<<1, 1024, 0, st>>>(sc, B, kind, R, DA, task_off, part_off, list_off, totals, cond,
+                                  status);
   return cudaGetLastError();
 }
 
@@ -887,11 +926,10 @@ cudaError_t launch_batched_refine_update(const float* part, const int32_t* ract,
 cudaError_t launch_batched_refine_compact(SetCtl* sc, int B, const int32_t* mdone, int32_t* ract,
                                           int max_iter, int R, int DA, Tiling tl,
                                           int64_t* task_off, int64_t* part_off, int64_t* list_off,
-                                          int64_t* totals, int32_t* blocks_done,
-                                          int32_t* sets_running, cudaStream_t st) {
+                                          int64_t* totals, int32_t* counters, BatchCond cond,
+                                          const uint32_t* status, cudaStream_t st) {
   batched_refine_compact<<<B, 1024, 0, st>>>(sc, B, mdone, ract, max_iter, R, DA, tl, task_off,
-                                             part_off, list_off, totals, blocks_done,
-                                             sets_running);
+                                             part_off, list_off, totals, counters, cond, status);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 // ms_grid_round: one Seed-Selection round of Gaussian mean-shift updates
-// (Eq. 6 / Alg. 2 line 6 under the Early Stopping of Sec. II-C) on a
+// (Eq. 6, the update of Alg. 2 under the Early Stopping of Sec. II-C) on a
 // persistent grid of one CTA per SM.
 //
 // Decomposition.  CTA c owns a fixed, contiguous slice of the points (n / G

@@ -96,7 +96,7 @@ cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float s
 }
 
 // ---------------------------------------------------------------------------
-// Seed Selection (Alg. 2 line 2): entries of the keyed permutation of
+// Seed Selection (Alg. 2): entries of the keyed permutation of
 // fms_seedperm.cuh.
 // ---------------------------------------------------------------------------
 __global__ void select_seeds_kernel(int64_t n, FeistelKey f, int64_t start, int64_t count,

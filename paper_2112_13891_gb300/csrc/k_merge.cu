@@ -82,142 +82,19 @@ cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA,
 }
 
 // ---------------------------------------------------------------------------
-// Prune modes (Alg. 1 line 13, Alg. 2 line 10): greedy radius suppression in
-// order of (score descending, rank ascending).  Implemented as repeated
-// "take the best live candidate, accept it, kill every live candidate closer
-// than r" -- the same accepted set as visiting the sorted list once.
-// One CTA of 1024 threads; candidate q has rank q.
+// The prune of Alg. 1 and Alg. 2: greedy radius
+// suppression in order of (score descending, rank ascending).  Candidate q has
+// rank q.  The sorted visit (fms_prune_body.cuh) is used while its sort keys fit
+// in shared memory; larger candidate sets take the one-block global greedy.
 // ---------------------------------------------------------------------------
-template <typename ST>
-__device__ __forceinline__ void argmax_merge(ST& best, int& bq, ST os, int oq) {
-  if (os > best || (os == best && oq < bq)) {
-    best = os;
-    bq = oq;
-  }
-}
-
-// Block-wide (score desc, index asc) winner; INT32_MAX when no candidate
-// has a comparable score.  Every thread returns the same value.
-template <typename ST>
-__device__ int block_argmax(ST best, int bq, ST* sh_s, int* sh_q, int* sh_best) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const ST os = __shfl_xor_sync(kFull, best, o);
-    const int oq = __shfl_xor_sync(kFull, bq, o);
-    argmax_merge<ST>(best, bq, os, oq);
-  }
-  if (lane == 0) {
-    sh_s[wid] = best;
-    sh_q[wid] = bq;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ST b = sh_s[0];
-    int bb = sh_q[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge<ST>(b, bb, sh_s[w], sh_q[w]);
-    *sh_best = bb;
-  }
-  __syncthreads();
-  const int win = *sh_best;
-  __syncthreads();   // sh_best and sh_s / sh_q are reused by the next call
-  return win;
-}
-
-// The greedy visit for candidate sets too large for the sorted prune's
-// shared memory: repeatedly accept the remaining candidate of highest
-// (score, lowest index) and drop every candidate within r of it.  The
-// remaining candidates are kept as a compacted list (in `list`); one pass per
-// accepted mode drops the new mode's neighbours and finds the next winner,
-// each thread taking kRun list entries per step with their loads issued
-// together.  The winner and every suppression are decided exactly as in the
-// one-by-one visit, so the accepted set and order are the same.
 template <typename PT, typename ST>
 __global__ void __launch_bounds__(512)
     greedy_merge_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
                         const ST* __restrict__ score, const PT* __restrict__ pos, int DP, int d,
                         PT r2, int32_t* __restrict__ list, int32_t* __restrict__ accepted,
                         int32_t* __restrict__ M_out) {
-  constexpr int kRun = 8;
-  __shared__ ST sh_s[32];
-  __shared__ int sh_q[32];
-  __shared__ PT sh_pos[FMS_MAX_DIM_PAD];
-  __shared__ int sh_best;
-  __shared__ int scratch[64];
-  const int K = *K_ptr;
-  const int T = blockDim.x;
-  ST best = (ST)-INFINITY;
-  int bq = INT32_MAX;
-  for (int b = 0; b < K; b += T * kRun) {
-#pragma unroll
-    for (int v = 0; v < kRun; ++v) {
-      const int q = b + v * T + threadIdx.x;
-      if (q < K) {
-        list[q] = q;
-        argmax_merge<ST>(best, bq, score[q], q);
-      }
-    }
-  }
-  int win = block_argmax<ST>(best, bq, sh_s, sh_q, &sh_best);
-  int len = K, M = 0;
-  while (win != INT32_MAX) {
-    if (threadIdx.x == 0) accepted[M] = win;
-    ++M;
-    const int64_t wrow = cand_row ? cand_row[win] : win;
-    for (int k = threadIdx.x; k < d; k += T) sh_pos[k] = pos[wrow * DP + k];
-    __syncthreads();
-    best = (ST)-INFINITY;
-    bq = INT32_MAX;
-    int newlen = 0;
-    for (int b = 0; b < len; b += T * kRun) {
-      int q[kRun];
-      int64_t row[kRun];
-      ST sc[kRun];
-      PT d2[kRun];
-#pragma unroll
-      for (int v = 0; v < kRun; ++v) {
-        const int idx = b + v * T + threadIdx.x;
-        q[v] = idx < len ? list[idx] : -1;
-      }
-#pragma unroll
-      for (int v = 0; v < kRun; ++v) {
-        sc[v] = q[v] >= 0 ? score[q[v]] : (ST)0;
-        row[v] = q[v] >= 0 ? (cand_row ? (int64_t)cand_row[q[v]] : (int64_t)q[v]) : 0;
-        d2[v] = 0;
-      }
-      for (int k = 0; k < d; ++k) {
-        const PT pk = sh_pos[k];
-#pragma unroll
-        for (int v = 0; v < kRun; ++v) {
-          if (q[v] >= 0) {
-            const PT e = pos[row[v] * DP + k] - pk;
-            d2[v] += e * e;
-          }
-        }
-      }
-      unsigned keep = 0;
-      int cnt = 0;
-#pragma unroll
-      for (int v = 0; v < kRun; ++v) {
-        if (q[v] >= 0 && q[v] != win && !(d2[v] < r2)) {
-          keep |= 1u << v;
-          ++cnt;
-          argmax_merge<ST>(best, bq, sc[v], q[v]);
-        }
-      }
-      // in-place compaction: this step writes only below the end of what it
-      // read, and every read precedes the scan's barriers
-      int tot;
-      int off = block_exclusive_scan(cnt, &tot, scratch);
-#pragma unroll
-      for (int v = 0; v < kRun; ++v)
-        if ((keep >> v) & 1u) list[newlen + off++] = q[v];
-      newlen += tot;
-    }
-    len = newlen;
-    win = block_argmax<ST>(best, bq, sh_s, sh_q, &sh_best);
-  }
-  if (threadIdx.x == 0) *M_out = M;
+  __shared__ __align__(16) unsigned char sm[greedy_global_smem<PT, ST>()];
+  greedy_global_body<PT, ST>(cand_row, *K_ptr, score, pos, DP, d, r2, list, accepted, M_out, sm);
 }
 
 // DT > 0: d = DT at compile time (candidates in registers during the visit)
@@ -667,7 +544,7 @@ cudaError_t launch_unrefined_modes(const float* y, const int32_t* kept, const in
 }
 
 // ---------------------------------------------------------------------------
-// Nearest-mode labels (Alg. 2 lines 11-13).  One thread per point; modes are
+// Nearest-mode labels (the labelling of Alg. 2).  One thread per point; modes are
 // staged through shared memory in tiles.  Ties go to the lowest index.
 // ---------------------------------------------------------------------------
 constexpr int kLabelTileFloats = 8192;

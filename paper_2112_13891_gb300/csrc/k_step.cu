@@ -1,6 +1,6 @@
 // ms_step: partial sums of one Gaussian mean-shift update for the active seeds.
 //
-// For every active seed y and every point x_j (Sec. II-B, Alg. 2 line 6: all
+// For every active seed y and every point x_j (Sec. II-B, the update of Alg. 2: all
 // points, no window search) the update needs
 //   W = sum_j w_j,   S = sum_j w_j (x_j - y),   w_j = exp(-||y - x_j||^2 / (2h^2)),
 // after which m(y) = y + S / W (Eq. 6 with the Gaussian profile).  Points are

@@ -73,3 +73,91 @@ def test_batched_full_configuration_sampled():
     for b in sorted(pick):
         _check_set(sets[b], res.modes[b], res.labels[off[b]:off[b + 1]])
     assert res.stats["kernel_launches"] > 0
+
+
+def _check_set_all_seeds(w, modes, labels):
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, all_seeds=True)
+    cmp = compare_clustering(modes.cpu().numpy(), labels.cpu().numpy(), ref, w.h)
+    assert cmp["mode_ok"], cmp
+    assert cmp["label_mismatch"] == 0, cmp
+
+
+def test_batched_all_seeds_sets_above_the_on_chip_prune():
+    # every point a seed (Alg. 1 per set).  Set 0 (20,000 points, d = 3) has
+    # more prune candidates than the sorted visit's keys can hold in shared
+    # memory, so its prune takes the global-memory greedy; set 1 (2,500
+    # points) sorts on chip; set 2 is small.
+    h = 1.5
+    sets = [fi.separated_blobs(seed=41, k=5, d=3, per=4000, sigma=1.0, h=h),
+            fi.separated_blobs(seed=42, k=5, d=3, per=500, sigma=1.0, h=h),
+            fi.separated_blobs(seed=43, k=3, d=3, per=100, sigma=1.0, h=h)]
+    X = [torch.from_numpy(w.X).cuda() for w in sets]
+    res = fms.cluster_batched(X, h, 1e-3 * h, 300, all_seeds=True, max_modes=64)
+    assert res.status == fms.FMS_OK
+    assert res.stats["graph"] == 1
+    assert res.stats["n_kept"] > 16384 + 2000
+    off = np.concatenate([[0], np.cumsum([w.X.shape[0] for w in sets])])
+    for b, w in enumerate(sets):
+        _check_set_all_seeds(w, res.modes[b], res.labels[off[b]:off[b + 1]])
+
+
+def test_batched_all_seeds_wide_set_reads_modes_from_global_memory():
+    # d = 16, 2,500 candidates: the sort keys fit in shared memory but the
+    # accepted modes' coordinates do not, so the visit reads them back from
+    # global memory
+    h = 3.0
+    sets = [fi.separated_blobs(seed=44, k=5, d=16, per=500, sigma=1.0, h=h),
+            fi.separated_blobs(seed=45, k=4, d=16, per=150, sigma=1.0, h=h)]
+    X = [torch.from_numpy(w.X).cuda() for w in sets]
+    res = fms.cluster_batched(X, h, 1e-3 * h, 300, all_seeds=True, max_modes=64)
+    assert res.status == fms.FMS_OK
+    off = np.concatenate([[0], np.cumsum([w.X.shape[0] for w in sets])])
+    for b, w in enumerate(sets):
+        _check_set_all_seeds(w, res.modes[b], res.labels[off[b]:off[b + 1]])
+
+
+def test_batched_call_is_one_graph_with_counted_launches():
+    # the second call with the same arguments reuses the cached graph; both
+    # report the same work and a launch count that follows the loop counts
+    h = 1.5
+    sets = _mixed_sets(5, 8, 3, 400, 3000, h)
+    X = [torch.from_numpy(w.X).cuda() for w in sets]
+    Xc = torch.cat(X)
+    offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in X])]).astype(np.int64)
+    r1 = fms.cluster_batched(Xc, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
+    r2 = fms.cluster_batched(Xc, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
+    for r in (r1, r2):
+        assert r.status == fms.FMS_OK and r.stats["graph"] == 1
+    s1, s2 = r1.stats, r2.stats
+    for k in ("rounds", "evals", "n_modes", "n_seeds_final", "refine_iterations",
+              "kernel_launches"):
+        assert s1[k] == s2[k], k
+    assert s1["rounds"] >= 1
+    # launches: 2 before the rounds, 7 per round plus 3 per update, 2 + 3 per
+    # refinement update, 4 for the density pass and 3 after
+    upd = (s1["kernel_launches"] - 2 - 7 * s1["rounds"] - 2 - 3 * s1["refine_iterations"] - 7)
+    assert upd > 0 and upd % 3 == 0
+    for b in range(len(sets)):
+        assert torch.equal(r1.modes[b], r2.modes[b])
+    assert torch.equal(r1.labels, r2.labels)
+
+
+def test_batched_sets_of_other_sizes_reuse_nothing_stale():
+    # same B, total and largest size with a different split: the control
+    # blocks are copied in before every launch, so the cached graph gives
+    # the per-set results of the new split
+    h = 1.5
+    base = [fi.separated_blobs(seed=51, k=5, d=3, per=300, sigma=1.0, h=h),
+            fi.separated_blobs(seed=52, k=4, d=3, per=200, sigma=1.0, h=h),
+            fi.separated_blobs(seed=53, k=3, d=3, per=300, sigma=1.0, h=h),
+            fi.separated_blobs(seed=54, k=5, d=3, per=400, sigma=1.0, h=h)]
+    X = torch.cat([torch.from_numpy(w.X) for w in base]).cuda()
+    offs_a = np.array([0, 1500, 2300, 3200, 5200], dtype=np.int64)
+    offs_b = np.array([0, 1500, 2200, 3200, 5200], dtype=np.int64)   # 100 points move to set 2
+    for offs in (offs_a, offs_b, offs_a):
+        res = fms.cluster_batched(X, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
+        assert res.status == fms.FMS_OK
+        for b in range(4):
+            one = fms.cluster(X[offs[b]:offs[b + 1]].contiguous(), h, 1e-3 * h, 300)
+            assert one.modes.shape == res.modes[b].shape
+            assert torch.allclose(one.modes, res.modes[b], atol=1e-3 * h, rtol=0)

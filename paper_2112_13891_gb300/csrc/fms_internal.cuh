@@ -432,7 +432,7 @@ cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs
 
 // k_unroll.cu: unrolled steps and their adjoint
 struct UGeom {
-  int B, n, m, d, DP;  // DP: padded row length (multiple of 4) of the packed copies
+  int B, n, m, d, DP;  // DP: padded row length of the packed copies (4, 8, 16 or 32)
   int Cp, Lp;          // point chunks of the seed-major passes (Lp points each)
   int Cs, Ls;          // seed chunks of the point-major pass (Ls seeds each)
 };
@@ -442,9 +442,10 @@ struct UGeom {
 cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
                             float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
                             int grid, cudaStream_t st);
+// The adjoint of one update; SD is scratch of [B m] x (2 DP + 4) floats.
 cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
                             const float* Wt, const float* Sh, const UGeom& g, float c,
-                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* gmu,
+                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* SD,
                             float* dh_part, float* Gprev, float* dX, double* dh, int grid,
                             cudaStream_t st);
 cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,

@@ -37,16 +37,21 @@ void chunks(int64_t groups, int64_t len, int sms, int* C, int* L) {
   *L = (int)l;
 }
 
+// rows padded to 4, 8, 16 or 32 floats (the kernels know the width at compile time)
+int padded_width(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : 32)); }
+
 UGeom geom(int32_t B, int64_t n, int64_t m, int32_t d) {
   UGeom g{};
   g.B = B;
   g.n = (int)n;
   g.m = (int)m;
   g.d = d;
-  g.DP = (d + 3) / 4 * 4;
+  g.DP = padded_width(d);
   const int sms = sm_count();
+  // seed-major passes: groups of 32 seeds; point-major pass: 64 points (32 at DP = 32)
+  const int ppw = g.DP <= 16 ? 64 : 32;
   chunks((int64_t)B * ((m + 31) / 32), n, sms, &g.Cp, &g.Lp);
-  chunks((int64_t)B * ((n + 31) / 32), m, sms, &g.Cs, &g.Ls);
+  chunks((int64_t)B * ((n + ppw - 1) / ppw), m, sms, &g.Cs, &g.Ls);
   return g;
 }
 
@@ -78,7 +83,7 @@ FwdLayout fwd_layout(const UGeom& g) {
 }
 
 struct BwdLayout {
-  size_t Xp, seg, Wseg, Sseg, Ga, Gb, part_s, part_p, gmu, dh_part, dXp, dh, rlist, total;
+  size_t Xp, seg, Ga, Gb, part_s, part_p, SD, dh_part, dXp, dh, rlist, total;
 };
 BwdLayout bwd_layout(const UGeom& g, int32_t k) {
   BwdLayout L{};
@@ -90,20 +95,35 @@ BwdLayout bwd_layout(const UGeom& g, int32_t k) {
   };
   const size_t rowsY = (size_t)g.B * g.m;
   L.Xp = take((size_t)g.B * g.n * g.DP * 4);
-  L.seg = take((size_t)(k + 1) * rowsY * g.DP * 4);
-  L.Wseg = take((size_t)k * rowsY * 4);
-  L.Sseg = take((size_t)k * rowsY * 4);   // weight shifts of the segment's updates
+  L.seg = take((size_t)k * rowsY * g.DP * 4);   // recomputed positions inside a segment
   L.Ga = take(rowsY * g.DP * 4);
   L.Gb = take(rowsY * g.DP * 4);
   L.part_s = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * 4);
   L.part_p = take((size_t)g.B * g.Cs * g.n * g.DP * 4);
-  L.gmu = take(rowsY * 4);
+  L.SD = take(rowsY * (2 * g.DP + 4) * 4);
   L.dh_part = take(rowsY * 4);
   L.dXp = take((size_t)g.B * g.n * g.DP * 4);
   L.dh = take((size_t)g.B * 8);
   L.rlist = take((rowsY + 1) * 4);
   L.total = o;
   return L;
+}
+
+// The checkpoint buffer: positions Y_t for t = 0, k, 2k, .. and Y_T (rows of
+// DP floats), then W_t and the weight shift of every update t < T (one float
+// per seed each), so the backward recomputes only the positions between
+// checkpoints.
+struct CkptLayout {
+  size_t pos, W, Sh, total;
+};
+CkptLayout ckpt_layout(int32_t B, int64_t m, int32_t d, int32_t T, int32_t k) {
+  CkptLayout C{};
+  const size_t rowsY = (size_t)B * m;
+  C.pos = 0;
+  C.W = (size_t)(n_ckpt(T, k) + 1) * rowsY * padded_width(d) * 4;
+  C.Sh = C.W + (size_t)T * rowsY * 4;
+  C.total = C.Sh + (size_t)T * rowsY * 4;
+  return C;
 }
 
 template <typename T>
@@ -117,8 +137,7 @@ extern "C" {
 
 size_t fms_unrolled_ckpt_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T, int32_t k) {
   if (!valid(B, n, m, d, T, k)) return 0;
-  const int DP = (d + 3) / 4 * 4;
-  return (size_t)n_ckpt(T, k) * B * m * DP * 4;
+  return ckpt_layout(B, m, d, T, k).total;
 }
 
 size_t fms_unrolled_workspace_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
@@ -148,7 +167,10 @@ fms_status fms_unrolled_forward(const float* points, const float* seeds0, int32_
   float* part = at<float>(ws, L.part);
   int32_t* rlist = at<int32_t>(ws, L.rlist);
   int32_t* rcount = rlist + (size_t)B * m;
-  float* C = static_cast<float*>(ckpt);
+  const CkptLayout CL = ckpt_layout(B, m, d, T, k);
+  float* C = at<float>(ckpt, CL.pos);
+  float* Wh = at<float>(ckpt, CL.W);
+  float* Shh = at<float>(ckpt, CL.Sh);
   const size_t rowsY = (size_t)B * m;
   const float c = (float)(1.4426950408889634 / (2.0 * (double)h * (double)h));
   const int grid = grid_blocks();
@@ -161,14 +183,16 @@ fms_status fms_unrolled_forward(const float* points, const float* seeds0, int32_
         cudaMemcpyAsync(C + (size_t)(t / k) * rowsY * g.DP, Ya, rowsY * g.DP * 4,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return FMS_ERR_CUDA;
-    if (unroll_fwd_step(Xp, Ya, g, c, part, Yb, nullptr, nullptr, rlist, rcount, grid, st) !=
-        cudaSuccess)
+    if (unroll_fwd_step(Xp, Ya, g, c, part, Yb, Wh + (size_t)t * rowsY, Shh + (size_t)t * rowsY,
+                        rlist, rcount, grid, st) != cudaSuccess)
       return FMS_ERR_CUDA;
     float* tmp = Ya;
     Ya = Yb;
     Yb = tmp;
   }
-  if (unroll_unpack_rows(Ya, (int64_t)rowsY, d, g.DP, out_seeds, st) != cudaSuccess)
+  if (cudaMemcpyAsync(C + (size_t)n_ckpt(T, k) * rowsY * g.DP, Ya, rowsY * g.DP * 4,
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      unroll_unpack_rows(Ya, (int64_t)rowsY, d, g.DP, out_seeds, st) != cudaSuccess)
     return FMS_ERR_CUDA;
   return FMS_OK;
 }
@@ -190,19 +214,20 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
     return FMS_ERR_WORKSPACE;
   float* Xp = at<float>(ws, L.Xp);
   float* seg = at<float>(ws, L.seg);
-  float* Wseg = at<float>(ws, L.Wseg);
-  float* Sseg = at<float>(ws, L.Sseg);
   int32_t* rlist = at<int32_t>(ws, L.rlist);
   int32_t* rcount = rlist + (size_t)B * m;
   float* Ga = at<float>(ws, L.Ga);
   float* Gb = at<float>(ws, L.Gb);
   float* part_s = at<float>(ws, L.part_s);
   float* part_p = at<float>(ws, L.part_p);
-  float* gmu = at<float>(ws, L.gmu);
+  float* SD = at<float>(ws, L.SD);
   float* dh_part = at<float>(ws, L.dh_part);
   float* dXp = at<float>(ws, L.dXp);
   double* dh = at<double>(ws, L.dh);
+  const CkptLayout CL = ckpt_layout(B, m, d, T, k);
   const float* Ck = static_cast<const float*>(ckpt);
+  const float* Wh = Ck + CL.W / 4;
+  const float* Shh = Ck + CL.Sh / 4;
   const size_t rowsY = (size_t)B * m;
   const size_t rowY = rowsY * g.DP;
   const double hd = (double)h;
@@ -220,19 +245,22 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
   for (int s = n_ckpt(T, k) - 1; s >= 0; --s) {
     const int t0 = s * k;
     const int len = (t0 + k <= T) ? k : T - t0;
-    // recompute the segment: seg[0] = Y_t0, seg[u+1] = Y_{t0+u+1}, Wseg[u] = W_{t0+u}
-    if (cudaMemcpyAsync(seg, Ck + (size_t)s * rowY, rowY * 4, cudaMemcpyDeviceToDevice, st) !=
-        cudaSuccess)
-      return FMS_ERR_CUDA;
-    for (int u = 0; u < len; ++u)
-      if (unroll_fwd_step(Xp, seg + (size_t)u * rowY, g, c, part_s, seg + (size_t)(u + 1) * rowY,
-                          Wseg + (size_t)u * rowsY, Sseg + (size_t)u * rowsY, rlist, rcount, grid,
-                          st) != cudaSuccess)
+    // positions of the segment: Y_t0 and Y_{t0+len} are checkpoints (the last
+    // is Y_T for the final segment); Y_{t0+1} .. Y_{t0+len-1} are recomputed
+    // into seg (W and the shifts of every update were stored by the forward)
+    auto pos = [&](int u) -> const float* {
+      if (u == 0) return Ck + (size_t)s * rowY;
+      if (u == len) return Ck + (size_t)(s + 1) * rowY;
+      return seg + (size_t)(u - 1) * rowY;
+    };
+    for (int u = 0; u + 1 < len; ++u)
+      if (unroll_fwd_step(Xp, pos(u), g, c, part_s, seg + (size_t)u * rowY, nullptr, nullptr,
+                          rlist, rcount, grid, st) != cudaSuccess)
         return FMS_ERR_CUDA;
     for (int u = len - 1; u >= 0; --u) {
-      if (unroll_bwd_step(Xp, seg + (size_t)u * rowY, seg + (size_t)(u + 1) * rowY, G,
-                          Wseg + (size_t)u * rowsY, Sseg + (size_t)u * rowsY, g, c, inv_h2,
-                          inv_h3, part_s, part_p, gmu, dh_part, Gp, dXp, dh, grid,
+      const size_t t = (size_t)(t0 + u);
+      if (unroll_bwd_step(Xp, pos(u), pos(u + 1), G, Wh + t * rowsY, Shh + t * rowsY, g, c,
+                          inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gp, dXp, dh, grid,
                           st) != cudaSuccess)
         return FMS_ERR_CUDA;
       float* tmp = G;

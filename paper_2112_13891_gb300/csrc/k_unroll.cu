@@ -13,29 +13,34 @@
 // Positions Y_t are checkpointed every k updates; the backward recomputes one
 // segment of k updates from its checkpoint, then walks it in reverse.
 //
-// Kernels (all FP32, exact differences, fixed-order reductions):
-//   fwd_partial   lanes own seeds, points streamed with warp-uniform loads,
+// Kernels (all FP32, exact differences, fixed-order reductions; rows padded
+// to DPAD = 4, 8, 16 or 32 floats, the padding known at compile time):
+//   fwd_partial   lanes own R seeds, points streamed with warp-uniform loads
+//                 (the next point's row loaded while this one is evaluated),
 //                 partial (W, S = sum w (x - y)) per point chunk
 //   fwd_finish    y' = y + S/W, W_t kept for the backward; a seed whose W
 //                 underflows (every point farther than ~13 h) is listed for
 //   fwd_rescue    which recomputes it with the weights taken relative to its
 //                 nearest point, w = exp2(-c (D2 - D2min)) (the shift cancels
 //                 in w / W), and records the shift c D2min for the backward
-//   bwd_seed      lanes own seeds: partial sum_j p a (x - mu) and
+//   seed_data     one row per seed [y | g | 1/W, shift, g . (y - mu)] for
+//                 the adjoint passes (no division or scattered load per pair)
+//   bwd_seed      lanes own seeds: partial sum_j p a (x - y), sum_j p a and
 //                 sum_j p a ||y - x||^2 per point chunk
-//   bwd_point     lanes own points, seeds streamed: partial
-//                 sum_i p_ij [g_i - a_ij (x_j - y_i)/h^2] per seed chunk
+//   bwd_point     lanes own R points, seeds streamed: partial
+//                 sum_i p_ij [g_i - a_ij (x_j - y_i) / h^2] per seed chunk
+// Both adjoint passes take a_ij = g_i . (x_j - y_i) + g_i . (y_i - mu_i): every
+// term is a difference of nearby positions (no cancellation of coordinates).
 //   finish kernels sum the chunk partials in chunk order.
 #include "fms_internal.cuh"
 
 namespace fms {
 
 template <int DPAD>
-__device__ __forceinline__ void load_row(const float* __restrict__ p, int DP, float (&v)[DPAD]) {
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[DPAD]) {
 #pragma unroll
   for (int q = 0; q < DPAD / 4; ++q) {
-    const float4 t = (4 * q < DP) ? __ldg(reinterpret_cast<const float4*>(p) + q)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
     v[4 * q] = t.x;
     v[4 * q + 1] = t.y;
     v[4 * q + 2] = t.z;
@@ -43,13 +48,24 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, int DP, fl
   }
 }
 
-// ---- forward partials: grid-stride over (set, seed group of 32, point chunk)
+// seeds (forward, seed-major adjoint) or points (point-major adjoint) per lane
 template <int DPAD>
+constexpr int unroll_fwd_r() {
+  return DPAD <= 4 ? 4 : (DPAD <= 8 ? 2 : 1);
+}
+template <int DPAD>
+constexpr int unroll_point_r() {
+  return DPAD <= 16 ? 2 : 1;
+}
+
+// ---- forward partials: grid-stride over (set, seed group of 32 R, point chunk)
+template <int DPAD, int R>
 __global__ void __launch_bounds__(128)
     unroll_fwd_partial(const float* __restrict__ X, const float* __restrict__ Y, UGeom g,
                        float c, float* __restrict__ part) {
+  constexpr int SPW = 32 * R;
   const int lane = threadIdx.x & 31;
-  const int Gs = (g.m + 31) / 32;
+  const int Gs = (g.m + SPW - 1) / SPW;
   const int64_t T = (int64_t)g.B * Gs * g.Cp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
@@ -58,33 +74,48 @@ __global__ void __launch_bounds__(128)
     const int64_t rest = task / g.Cp;
     const int gs = (int)(rest % Gs);
     const int b = (int)(rest / Gs);
-    const int i = min(gs * 32 + lane, g.m - 1);
-    const float* Xb = X + (int64_t)b * g.n * g.DP;
-    float y[DPAD], S[DPAD], W = 0.f;
-    load_row<DPAD>(Y + ((int64_t)b * g.m + i) * g.DP, g.DP, y);
+    const float* Xb = X + (int64_t)b * g.n * DPAD;
+    float y[R][DPAD], S[R][DPAD], W[R];
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) S[k] = 0.f;
+    for (int r = 0; r < R; ++r) {
+      const int i = min(gs * SPW + r * 32 + lane, g.m - 1);
+      load_row<DPAD>(Y + ((int64_t)b * g.m + i) * DPAD, y[r]);
+      W[r] = 0.f;
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) S[r][k] = 0.f;
+    }
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
+    float xn[DPAD];   // the next point's row, loaded while this one is evaluated
+    if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
     for (int j = j0; j < j1; ++j) {
       float x[DPAD];
-      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
-      float dx[DPAD], D2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) {
-        dx[k] = x[k] - y[k];
-        D2 = fmaf(dx[k], dx[k], D2);
+      for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
+      if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float dx[DPAD], D2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) {
+          dx[k] = x[k] - y[r][k];
+          D2 = fmaf(dx[k], dx[k], D2);
+        }
+        const float w = ex2_ftz(-c * D2);
+        W[r] += w;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) S[r][k] = fmaf(w, dx[k], S[r][k]);
       }
-      const float w = ex2_ftz(-c * D2);
-      W += w;
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) S[k] = fmaf(w, dx[k], S[k]);
     }
-    if (gs * 32 + lane < g.m) {
-      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1);
-      o[0] = W;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k)
-        if (k < g.d) o[1 + k] = S[k];
+    for (int r = 0; r < R; ++r) {
+      const int i = gs * SPW + r * 32 + lane;
+      if (i < g.m) {
+        float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
+        o[0] = W[r];
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k)
+          if (k < g.d) o[1 + k] = S[r][k];
+      }
     }
   }
 }
@@ -139,18 +170,18 @@ __global__ void __launch_bounds__(1024)
   for (int q = warp; q < cnt; q += (int)(blockDim.x >> 5)) {
     const int64_t e = rlist[q];
     const int b = (int)(e / g.m);
-    const float* Xb = X + (int64_t)b * g.n * g.DP;
+    const float* Xb = X + (int64_t)b * g.n * DPAD;
     float y[DPAD];
-    load_row<DPAD>(Y + e * g.DP, g.DP, y);
+    load_row<DPAD>(Y + e * DPAD, y);
     float dmin = INFINITY;
     for (int j = lane; j < g.n; j += 32) {
       float x[DPAD];
-      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      load_row<DPAD>(Xb + (int64_t)j * DPAD, x);
       float D2 = 0.f;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
-        const float dx = x[k] - y[k];
-        D2 = fmaf(dx, dx, D2);
+        const float e = x[k] - y[k];
+        D2 = fmaf(e, e, D2);
       }
       dmin = fminf(dmin, D2);
     }
@@ -162,7 +193,7 @@ __global__ void __launch_bounds__(1024)
     for (int k = 0; k < DPAD; ++k) S[k] = 0.f;
     for (int j = lane; j < g.n; j += 32) {
       float x[DPAD];
-      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
+      load_row<DPAD>(Xb + (int64_t)j * DPAD, x);
       float dx[DPAD], D2 = 0.f;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
@@ -192,14 +223,45 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) *rcount = 0;
 }
 
+// ---- adjoint inputs per seed: SD row = [y | g | 1/W, shift, g . (y - mu), 0]
+template <int DPAD>
+__global__ void unroll_seed_data(const float* __restrict__ Y, const float* __restrict__ MU,
+                                 const float* __restrict__ G, const float* __restrict__ Wt,
+                                 const float* __restrict__ Sh, UGeom g, float* __restrict__ SD) {
+  constexpr int SDW = 2 * DPAD + 4;
+  const int64_t total = (int64_t)g.B * g.m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float* o = SD + e * SDW;
+    float gm = 0.f;
+#pragma unroll
+    for (int k = 0; k < DPAD; ++k) {
+      const float gk = G[e * DPAD + k];
+      o[k] = Y[e * DPAD + k];
+      o[DPAD + k] = gk;
+      gm = fmaf(gk, Y[e * DPAD + k] - MU[e * DPAD + k], gm);
+    }
+    o[2 * DPAD] = 1.0f / Wt[e];
+    o[2 * DPAD + 1] = Sh[e];
+    o[2 * DPAD + 2] = gm;
+    o[2 * DPAD + 3] = 0.f;
+  }
+}
+
 // ---- backward, seed-major: partial sums over point chunks of
-//   DY_i = sum_j p_ij a_ij (x_j - mu_i),  DH_i = sum_j p_ij a_ij ||y_i - x_j||^2
+//   DY_i = sum_j p_ij a_ij (x_j - mu_i) = sum_j p a (x_j - y_i) + (y_i - mu_i) sum_j p a,
+//   DH_i = sum_j p_ij a_ij ||y_i - x_j||^2 = sum_j p a (||y_i - x_j||^2 - s_i).
+// The last form holds for any s_i because sum_j p_ij a_ij = g_i . sum_j p_ij
+// (x_j - mu_i) = 0; s_i = the seed's weight shift in squared-distance units
+// (0 unless the seed was rescued).  For a seed far from every point (D2 of
+// hundreds) the FP32 rounding of D2 perturbs its weights by ~1e-5, which
+// leaves sum p a at ~1e-5 instead of 0; subtracting s_i keeps that residual
+// from being multiplied by D2.
 template <int DPAD>
 __global__ void __launch_bounds__(128)
-    unroll_bwd_seed(const float* __restrict__ X, const float* __restrict__ Y,
-                    const float* __restrict__ MU, const float* __restrict__ G,
-                    const float* __restrict__ Wt, const float* __restrict__ Sh, UGeom g, float c,
-                    float* __restrict__ part) {
+    unroll_bwd_seed(const float* __restrict__ X, const float* __restrict__ MU,
+                    const float* __restrict__ SD, UGeom g, float c, float* __restrict__ part) {
+  constexpr int SDW = 2 * DPAD + 4;
   const int lane = threadIdx.x & 31;
   const int Gs = (g.m + 31) / 32;
   const int64_t T = (int64_t)g.B * Gs * g.Cp;
@@ -212,38 +274,45 @@ __global__ void __launch_bounds__(128)
     const int b = (int)(rest / Gs);
     const int i = min(gs * 32 + lane, g.m - 1);
     const int64_t row = (int64_t)b * g.m + i;
-    const float* Xb = X + (int64_t)b * g.n * g.DP;
-    float y[DPAD], mu[DPAD], gg[DPAD], DY[DPAD], DH = 0.f;
-    load_row<DPAD>(Y + row * g.DP, g.DP, y);
-    load_row<DPAD>(MU + row * g.DP, g.DP, mu);
-    load_row<DPAD>(G + row * g.DP, g.DP, gg);
-    const float invW = 1.0f / Wt[row];
-    const float sh = Sh[row];   // the forward's weight shift (0 unless rescued)
+    const float* Xb = X + (int64_t)b * g.n * DPAD;
+    const float* sd = SD + row * SDW;
+    float y[DPAD], gg[DPAD], DY[DPAD], DH = 0.f, SA = 0.f;
+    load_row<DPAD>(sd, y);
+    load_row<DPAD>(sd + DPAD, gg);
+    const float4 tail = __ldg(reinterpret_cast<const float4*>(sd + 2 * DPAD));
+    const float invW = tail.x, sh = tail.y, gd = tail.z;
+    const float s0 = sh / c;
 #pragma unroll
     for (int k = 0; k < DPAD; ++k) DY[k] = 0.f;
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
+    float xn[DPAD];
+    if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
     for (int j = j0; j < j1; ++j) {
       float x[DPAD];
-      load_row<DPAD>(Xb + (int64_t)j * g.DP, g.DP, x);
-      float D2 = 0.f, a = 0.f, e[DPAD];
+#pragma unroll
+      for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
+      if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
+      float dx[DPAD], D2 = 0.f, a = gd;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
-        const float dx = x[k] - y[k];
-        D2 = fmaf(dx, dx, D2);
-        e[k] = x[k] - mu[k];
-        a = fmaf(gg[k], e[k], a);
+        dx[k] = x[k] - y[k];
+        D2 = fmaf(dx[k], dx[k], D2);
+        a = fmaf(gg[k], dx[k], a);
       }
       const float pa = ex2_ftz(fmaf(-c, D2, sh)) * invW * a;
-      DH = fmaf(pa, D2, DH);
+      DH = fmaf(pa, D2 - s0, DH);
+      SA += pa;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) DY[k] = fmaf(pa, e[k], DY[k]);
+      for (int k = 0; k < DPAD; ++k) DY[k] = fmaf(pa, dx[k], DY[k]);
     }
     if (gs * 32 + lane < g.m) {
-      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1);
+      float mu[DPAD];
+      load_row<DPAD>(MU + row * DPAD, mu);
+      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
       o[0] = DH;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k)
-        if (k < g.d) o[1 + k] = DY[k];
+        if (k < g.d) o[1 + k] = fmaf(y[k] - mu[k], SA, DY[k]);
     }
   }
 }
@@ -273,17 +342,16 @@ __global__ void unroll_bwd_seed_finish(const float* __restrict__ part, UGeom g, 
 }
 
 // ---- backward, point-major: partial over seed chunks of
-//   DX_j = sum_i p_ij g_i - (1/h^2) sum_i p_ij a_ij (x_j - y_i)
-// with a_ij = g_i . x_j - (g_i . mu_i).  Per-seed data (y_i, g_i, 1/W_i,
-// g_i . mu_i) are read with warp-uniform loads.
-template <int DPAD>
+//   DX_j = sum_i p_ij g_i - (1/h^2) sum_i p_ij a_ij (x_j - y_i).
+// Lanes own R points; the seed rows (SD) are read with warp-uniform loads.
+template <int DPAD, int R>
 __global__ void __launch_bounds__(128)
-    unroll_bwd_point(const float* __restrict__ X, const float* __restrict__ Y,
-                     const float* __restrict__ G, const float* __restrict__ Wt,
-                     const float* __restrict__ Sh, const float* __restrict__ gmu, UGeom g,
-                     float c, float inv_h2, float* __restrict__ part) {
+    unroll_bwd_point(const float* __restrict__ X, const float* __restrict__ SD, UGeom g, float c,
+                     float inv_h2, float* __restrict__ part) {
+  constexpr int SDW = 2 * DPAD + 4;
+  constexpr int PPW = 32 * R;
   const int lane = threadIdx.x & 31;
-  const int Gp = (g.n + 31) / 32;
+  const int Gp = (g.n + PPW - 1) / PPW;
   const int64_t T = (int64_t)g.B * Gp * g.Cs;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
@@ -292,37 +360,46 @@ __global__ void __launch_bounds__(128)
     const int64_t rest = task / g.Cs;
     const int gp = (int)(rest % Gp);
     const int b = (int)(rest / Gp);
-    const int j = min(gp * 32 + lane, g.n - 1);
-    float x[DPAD], DX[DPAD];
-    load_row<DPAD>(X + ((int64_t)b * g.n + j) * g.DP, g.DP, x);
+    float x[R][DPAD], DX[R][DPAD];
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) DX[k] = 0.f;
-    const int i0 = ch * g.Ls, i1 = min(g.m, i0 + g.Ls);
-    for (int i = i0; i < i1; ++i) {
-      const int64_t row = (int64_t)b * g.m + i;
-      float y[DPAD], gg[DPAD];
-      load_row<DPAD>(Y + row * g.DP, g.DP, y);
-      load_row<DPAD>(G + row * g.DP, g.DP, gg);
-      const float invW = 1.0f / __ldg(Wt + row);
-      const float sh = __ldg(Sh + row);
-      const float gm = __ldg(gmu + row);
-      float dx[DPAD], D2 = 0.f, gx = 0.f;
+    for (int r = 0; r < R; ++r) {
+      const int j = min(gp * PPW + r * 32 + lane, g.n - 1);
+      load_row<DPAD>(X + ((int64_t)b * g.n + j) * DPAD, x[r]);
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) {
-        dx[k] = x[k] - y[k];
-        D2 = fmaf(dx[k], dx[k], D2);
-        gx = fmaf(gg[k], x[k], gx);
-      }
-      const float p = ex2_ftz(fmaf(-c, D2, sh)) * invW;
-      const float q = p * (gx - gm) * inv_h2;
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) DX[k] = fmaf(p, gg[k], fmaf(-q, dx[k], DX[k]));
+      for (int k = 0; k < DPAD; ++k) DX[r][k] = 0.f;
     }
-    if (gp * 32 + lane < g.n) {
-      float* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * g.DP;
+    const int i0 = ch * g.Ls, i1 = min(g.m, i0 + g.Ls);
+    const float* sdb = SD + (int64_t)b * g.m * SDW;
+    for (int i = i0; i < i1; ++i) {
+      const float* sd = sdb + (int64_t)i * SDW;
+      float y[DPAD], gg[DPAD];
+      load_row<DPAD>(sd, y);
+      load_row<DPAD>(sd + DPAD, gg);
+      const float4 tail = __ldg(reinterpret_cast<const float4*>(sd + 2 * DPAD));
+      const float invW = tail.x, sh = tail.y, gd = tail.z;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k)
-        if (k < g.DP) o[k] = k < g.d ? DX[k] : 0.f;
+      for (int r = 0; r < R; ++r) {
+        float dx[DPAD], D2 = 0.f, a = gd;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) {
+          dx[k] = x[r][k] - y[k];
+          D2 = fmaf(dx[k], dx[k], D2);
+          a = fmaf(gg[k], dx[k], a);
+        }
+        const float p = ex2_ftz(fmaf(-c, D2, sh)) * invW;
+        const float q = p * a * inv_h2;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) DX[r][k] = fmaf(p, gg[k], fmaf(-q, dx[k], DX[r][k]));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int j = gp * PPW + r * 32 + lane;
+      if (j < g.n) {
+        float* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * DPAD;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) o[k] = k < g.d ? DX[r][k] : 0.f;
+      }
     }
   }
 }
@@ -339,18 +416,6 @@ __global__ void unroll_bwd_point_finish(const float* __restrict__ part, UGeom g,
     float v = 0.f;
     for (int ch = 0; ch < g.Cs; ++ch) v += part[(((int64_t)b * g.Cs + ch) * g.n + j) * g.DP + k];
     dX[e] += v;
-  }
-}
-
-// g_i . mu_i for every seed (for the point-major pass).
-__global__ void unroll_gmu(const float* __restrict__ G, const float* __restrict__ MU, UGeom g,
-                           float* __restrict__ gmu) {
-  const int64_t total = (int64_t)g.B * g.m;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < g.d; ++k) s = fmaf(G[e * g.DP + k], MU[e * g.DP + k], s);
-    gmu[e] = s;
   }
 }
 
@@ -404,7 +469,7 @@ template <int DPAD>
 static cudaError_t fwd_step_t(const float* X, const float* Y, const UGeom& g, float c, float* part,
                               float* Ynext, float* Wout, float* Sh, int32_t* rlist,
                               int32_t* rcount, int grid, cudaStream_t st) {
-  unroll_fwd_partial<DPAD><<<grid, 128, 0, st>>>(X, Y, g, c, part);
+  unroll_fwd_partial<DPAD, unroll_fwd_r<DPAD>()><<<grid, 128, 0, st>>>(X, Y, g, c, part);
   unroll_fwd_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout, Sh,
                                                                     rlist, rcount);
   unroll_fwd_rescue<DPAD><<<1, 1024, 0, st>>>(X, Y, g, c, rlist, rcount, Ynext, Wout, Sh);
@@ -414,21 +479,25 @@ static cudaError_t fwd_step_t(const float* X, const float* Y, const UGeom& g, fl
 cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
                             float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
                             int grid, cudaStream_t st) {
-  if (g.DP <= 4) return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-  if (g.DP <= 8) return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-  if (g.DP <= 16) return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-  return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+  switch (g.DP) {
+    case 4: return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 8: return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 16: return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 32: return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int DPAD>
 static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, const float* G,
                               const float* Wt, const float* Sh, const UGeom& g, float c,
                               float inv_h2, float inv_h3, float* part_s, float* part_p,
-                              float* gmu, float* dh_part, float* Gprev, float* dX, double* dh,
+                              float* SD, float* dh_part, float* Gprev, float* dX, double* dh,
                               int grid, cudaStream_t st) {
-  unroll_gmu<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(G, MU, g, gmu);
-  unroll_bwd_point<DPAD><<<grid, 128, 0, st>>>(X, Y, G, Wt, Sh, gmu, g, c, inv_h2, part_p);
-  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, Y, MU, G, Wt, Sh, g, c, part_s);
+  unroll_seed_data<DPAD><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(Y, MU, G, Wt, Sh, g, SD);
+  unroll_bwd_point<DPAD, unroll_point_r<DPAD>()><<<grid, 128, 0, st>>>(X, SD, g, c, inv_h2,
+                                                                        part_p);
+  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, MU, SD, g, c, part_s);
   unroll_bwd_point_finish<<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
   unroll_bwd_seed_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2, inv_h3,
                                                                          Gprev, dh_part);
@@ -438,13 +507,16 @@ static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, c
 
 cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
                             const float* Wt, const float* Sh, const UGeom& g, float c,
-                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* gmu,
+                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* SD,
                             float* dh_part, float* Gprev, float* dX, double* dh, int grid,
                             cudaStream_t st) {
-  if (g.DP <= 4) return bwd_step_t<4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  if (g.DP <= 8) return bwd_step_t<8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  if (g.DP <= 16) return bwd_step_t<16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
-  return bwd_step_t<32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, gmu, dh_part, Gprev, dX, dh, grid, st);
+  switch (g.DP) {
+    case 4: return bwd_step_t<4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 8: return bwd_step_t<8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 16: return bwd_step_t<16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 32: return bwd_step_t<32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,

@@ -436,8 +436,11 @@ fms_status fms_label_points(const float* points, int64_t n, int32_t d, const flo
  *   dL/dx_j += p_ij [g_i - a_ij (x_j - y_i)/h^2]
  *   dL/dh   += (1/h^3) sum_ij p_ij ||y_i - x_j||^2 a_ij.
  * Weights are recomputed tile by tile (nothing of size m x n is stored); the
- * forward stores the positions every k updates in `ckpt` and the backward
- * recomputes one segment of k updates at a time.
+ * forward stores the positions every k updates and at the end (Y_T), and each
+ * update's W_i and weight shift (one value per seed), in `ckpt`; the backward
+ * recomputes the positions between two checkpoints one segment at a time.
+ * A seed whose sum of weights underflows (every point farther than ~13 h in
+ * FP32) is recomputed with its weights taken relative to its nearest point.
  *
  *   points  [B x n x d], seeds0 [B x m x d], out_seeds [B x m x d]: float32,
  *           device, row-major; 1 <= d <= 32.  h > 0, T >= 1, k >= 1.
@@ -448,7 +451,14 @@ fms_status fms_label_points(const float* points, int64_t n, int32_t d, const flo
  *   grad_out [B x m x d] = dL/dY_T; grad_points [B x n x d] and grad_seeds0
  *           [B x m x d] are overwritten; grad_h [B] (float64, device) receives
  *           dL/dh of each set.
- * Both calls are asynchronous on `stream`.
+ * Both calls are asynchronous on `stream`.  Errors: FMS_ERR_INVALID_ARG (null
+ * pointer, sizes out of range, h not finite and positive), FMS_ERR_WORKSPACE
+ * (buffers too small or misaligned), FMS_ERR_CUDA (a launch failed).
+ *
+ * The *_f64 entry points are the same computation in FP64 (double pointers,
+ * h as double; `ckpt` and `ws` sized by the *_f64 size functions), for
+ * checking gradients by finite differences on the GPU; the FP32 entry points
+ * are the fast path.
  */
 size_t fms_unrolled_ckpt_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T, int32_t k);
 size_t fms_unrolled_workspace_size(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
@@ -462,6 +472,19 @@ fms_status fms_unrolled_backward(const float* points, int32_t B, int64_t n, int6
                                  size_t ckpt_bytes, const float* grad_out, float* grad_points,
                                  float* grad_seeds0, double* grad_h, void* ws, size_t ws_bytes,
                                  void* stream);
+size_t fms_unrolled_ckpt_size_f64(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
+                                  int32_t k);
+size_t fms_unrolled_workspace_size_f64(int32_t B, int64_t n, int64_t m, int32_t d, int32_t T,
+                                       int32_t k);
+fms_status fms_unrolled_forward_f64(const double* points, const double* seeds0, int32_t B,
+                                    int64_t n, int64_t m, int32_t d, double h, int32_t T,
+                                    int32_t k, double* out_seeds, void* ckpt, size_t ckpt_bytes,
+                                    void* ws, size_t ws_bytes, void* stream);
+fms_status fms_unrolled_backward_f64(const double* points, int32_t B, int64_t n, int64_t m,
+                                     int32_t d, double h, int32_t T, int32_t k, const void* ckpt,
+                                     size_t ckpt_bytes, const double* grad_out,
+                                     double* grad_points, double* grad_seeds0, double* grad_h,
+                                     void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -407,55 +407,70 @@ def label_points(points: torch.Tensor, modes: torch.Tensor, with_margins=True):
 # Differentiable unrolled steps (fms_unrolled_forward / fms_unrolled_backward)
 # ---------------------------------------------------------------------------
 
-_lib.fms_unrolled_ckpt_size.restype = _SZ
-_lib.fms_unrolled_ckpt_size.argtypes = [_I32, _I64, _I64, _I32, _I32, _I32]
-_lib.fms_unrolled_workspace_size.restype = _SZ
-_lib.fms_unrolled_workspace_size.argtypes = [_I32, _I64, _I64, _I32, _I32, _I32]
-_lib.fms_unrolled_forward.restype = ctypes.c_int
-_lib.fms_unrolled_forward.argtypes = [_P, _P, _I32, _I64, _I64, _I32, _F32, _I32, _I32, _P, _P,
-                                      _SZ, _P, _SZ, _P]
-_lib.fms_unrolled_backward.restype = ctypes.c_int
-_lib.fms_unrolled_backward.argtypes = [_P, _I32, _I64, _I64, _I32, _F32, _I32, _I32, _P, _SZ, _P,
-                                       _P, _P, _P, _P, _SZ, _P]
+_F64 = ctypes.c_double
+for _sfx, _fh in (("", _F32), ("_f64", _F64)):
+    getattr(_lib, "fms_unrolled_ckpt_size" + _sfx).restype = _SZ
+    getattr(_lib, "fms_unrolled_ckpt_size" + _sfx).argtypes = [_I32, _I64, _I64, _I32, _I32, _I32]
+    getattr(_lib, "fms_unrolled_workspace_size" + _sfx).restype = _SZ
+    getattr(_lib, "fms_unrolled_workspace_size" + _sfx).argtypes = [_I32, _I64, _I64, _I32, _I32,
+                                                                    _I32]
+    getattr(_lib, "fms_unrolled_forward" + _sfx).restype = ctypes.c_int
+    getattr(_lib, "fms_unrolled_forward" + _sfx).argtypes = [_P, _P, _I32, _I64, _I64, _I32, _fh,
+                                                             _I32, _I32, _P, _P, _SZ, _P, _SZ, _P]
+    getattr(_lib, "fms_unrolled_backward" + _sfx).restype = ctypes.c_int
+    getattr(_lib, "fms_unrolled_backward" + _sfx).argtypes = [_P, _I32, _I64, _I64, _I32, _fh,
+                                                              _I32, _I32, _P, _SZ, _P, _P, _P, _P,
+                                                              _P, _SZ, _P]
 
 
-def _batched(x: torch.Tensor, name: str) -> torch.Tensor:
+def _batched(x: torch.Tensor, name: str, dtype=torch.float32) -> torch.Tensor:
     if not x.is_cuda or x.dim() != 3:
         raise ValueError(f"{name} must be a CUDA tensor [B, rows, d]")
-    return x.to(torch.float32).contiguous()
+    return x.to(dtype).contiguous()
+
+
+def _unrolled_sfx(dtype) -> str:
+    """FP64 tensors take the *_f64 entry points (gradient checks), others FP32."""
+    return "_f64" if dtype == torch.float64 else ""
 
 
 def unrolled_forward(X: torch.Tensor, Y0: torch.Tensor, h: float, T: int, k: int):
-    """T Gaussian updates of every row of Y0 (per set) against X; returns (Y_T, ckpt)."""
-    X, Y0 = _batched(X, "X"), _batched(Y0, "Y0")
+    """T Gaussian updates of every row of Y0 (per set) against X; returns (Y_T, ckpt).
+    FP64 inputs run the FP64 kernels, anything else FP32."""
+    dt = torch.float64 if X.dtype == torch.float64 else torch.float32
+    sfx = _unrolled_sfx(dt)
+    X, Y0 = _batched(X, "X", dt), _batched(Y0, "Y0", dt)
     B, n, d = X.shape
     m = Y0.shape[1]
-    cb = int(_lib.fms_unrolled_ckpt_size(B, n, m, d, T, k))
-    wb = int(_lib.fms_unrolled_workspace_size(B, n, m, d, T, k))
+    cb = int(getattr(_lib, "fms_unrolled_ckpt_size" + sfx)(B, n, m, d, T, k))
+    wb = int(getattr(_lib, "fms_unrolled_workspace_size" + sfx)(B, n, m, d, T, k))
     if cb == 0 or wb == 0:
-        raise FmsError(FMS_ERR_INVALID_ARG, "fms_unrolled_forward")
+        raise FmsError(FMS_ERR_INVALID_ARG, "fms_unrolled_forward" + sfx)
     ckpt = torch.empty(cb, dtype=torch.uint8, device=X.device)
     ws = torch.empty(wb, dtype=torch.uint8, device=X.device)
     out = torch.empty_like(Y0)
-    _check(_lib.fms_unrolled_forward(_ptr(X), _ptr(Y0), B, n, m, d, float(h), int(T), int(k),
-                                     _ptr(out), _ptr(ckpt), cb, _ptr(ws), wb, _stream()),
-           "fms_unrolled_forward")
+    _check(getattr(_lib, "fms_unrolled_forward" + sfx)(
+        _ptr(X), _ptr(Y0), B, n, m, d, float(h), int(T), int(k), _ptr(out), _ptr(ckpt), cb,
+        _ptr(ws), wb, _stream()), "fms_unrolled_forward" + sfx)
     return out, ckpt
 
 
 def unrolled_backward(X: torch.Tensor, ckpt: torch.Tensor, m: int, h: float, T: int, k: int,
                       grad_out: torch.Tensor):
-    """Adjoint of unrolled_forward: returns (dL/dX, dL/dY0, dL/dh per set as float64)."""
-    X, G = _batched(X, "X"), _batched(grad_out, "grad_out")
+    """Adjoint of unrolled_forward: returns (dL/dX, dL/dY0, dL/dh per set as float64),
+    in X's precision (FP64 or FP32)."""
+    dt = torch.float64 if X.dtype == torch.float64 else torch.float32
+    sfx = _unrolled_sfx(dt)
+    X, G = _batched(X, "X", dt), _batched(grad_out, "grad_out", dt)
     B, n, d = X.shape
-    wb = int(_lib.fms_unrolled_workspace_size(B, n, m, d, T, k))
+    wb = int(getattr(_lib, "fms_unrolled_workspace_size" + sfx)(B, n, m, d, T, k))
     ws = torch.empty(wb, dtype=torch.uint8, device=X.device)
     dX = torch.empty_like(X)
-    dY = torch.empty((B, m, d), dtype=torch.float32, device=X.device)
+    dY = torch.empty((B, m, d), dtype=dt, device=X.device)
     dh = torch.empty(B, dtype=torch.float64, device=X.device)
-    _check(_lib.fms_unrolled_backward(_ptr(X), B, n, m, d, float(h), int(T), int(k), _ptr(ckpt),
-                                      ckpt.numel(), _ptr(G), _ptr(dX), _ptr(dY), _ptr(dh),
-                                      _ptr(ws), wb, _stream()), "fms_unrolled_backward")
+    _check(getattr(_lib, "fms_unrolled_backward" + sfx)(
+        _ptr(X), B, n, m, d, float(h), int(T), int(k), _ptr(ckpt), ckpt.numel(), _ptr(G),
+        _ptr(dX), _ptr(dY), _ptr(dh), _ptr(ws), wb, _stream()), "fms_unrolled_backward" + sfx)
     return dX, dY, dh
 
 
@@ -477,7 +492,7 @@ class UnrolledMeanShift(torch.autograd.Function):
         X, ckpt = ctx.saved_tensors
         hv, T, k, m, h_is_tensor = ctx.cfg
         dX, dY, dh = unrolled_backward(X, ckpt, m, hv, T, k, grad_out)
-        gh = dh.sum().to(torch.float32).reshape(()) if h_is_tensor else None
+        gh = dh.sum().to(X.dtype).reshape(()) if h_is_tensor else None
         return dX, dY, gh, None, None
 
 

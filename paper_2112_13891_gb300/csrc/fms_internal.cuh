@@ -436,21 +436,23 @@ struct UGeom {
   int Cp, Lp;          // point chunks of the seed-major passes (Lp points each)
   int Cs, Ls;          // seed chunks of the point-major pass (Ls seeds each)
 };
-// One forward update; Wout (W_t) and Sh (the weight shift of seeds whose W
-// underflowed, 0 otherwise) may be null; rlist [B m] and rcount (zero on
-// entry, zero again on return) are scratch.
-cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                            float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
-                            int grid, cudaStream_t st);
-// The adjoint of one update; SD is scratch of [B m] x (2 DP + 4) floats.
-cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
-                            const float* Wt, const float* Sh, const UGeom& g, float c,
-                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* SD,
-                            float* dh_part, float* Gprev, float* dX, double* dh, int grid,
+// One forward update (T = float, or double for checking gradients); Wout (W_t)
+// and Sh (the weight shift of seeds whose W underflowed, 0 otherwise) may be
+// null; rlist [B m] and rcount (zero on entry, zero again on return) are scratch.
+template <typename T>
+cudaError_t unroll_fwd_step(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
+                            T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
                             cudaStream_t st);
-cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
-                             cudaStream_t st);
-cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
+// The adjoint of one update; SD is scratch of [B m] x (2 DP + 4) values.
+template <typename T>
+cudaError_t unroll_bwd_step(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
+                            const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
+                            T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t unroll_pack_rows(const T* src, int64_t rows, int d, int DP, T* dst, cudaStream_t st);
+template <typename T>
+cudaError_t unroll_unpack_rows(const T* src, int64_t rows, int d, int DP, T* dst,
                                cudaStream_t st);
 
 // k_step.cu: one update's partial sums for the active seeds

@@ -13,8 +13,9 @@
 // Positions Y_t are checkpointed every k updates; the backward recomputes one
 // segment of k updates from its checkpoint, then walks it in reverse.
 //
-// Kernels (all FP32, exact differences, fixed-order reductions; rows padded
-// to DPAD = 4, 8, 16 or 32 floats, the padding known at compile time):
+// Kernels (FP32, or FP64 for checking gradients; exact differences,
+// fixed-order reductions; rows padded to DPAD = 4, 8, 16 or 32 values, the
+// padding known at compile time):
 //   fwd_partial   lanes own R seeds, points streamed with warp-uniform loads
 //                 (the next point's row loaded while this one is evaluated),
 //                 partial (W, S = sum w (x - y)) per point chunk
@@ -48,69 +49,94 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)
   }
 }
 
-// seeds (forward, seed-major adjoint) or points (point-major adjoint) per lane
 template <int DPAD>
-constexpr int unroll_fwd_r() {
-  return DPAD <= 4 ? 4 : (DPAD <= 8 ? 2 : 1);
+__device__ __forceinline__ void load_row(const double* __restrict__ p, double (&v)[DPAD]) {
+#pragma unroll
+  for (int q = 0; q < DPAD / 2; ++q) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + q);
+    v[2 * q] = t.x;
+    v[2 * q + 1] = t.y;
+  }
 }
-template <int DPAD>
+
+// the element type's exp2, fma and min (FP32: the MUFU exp2 with flush to zero)
+__device__ __forceinline__ float uex2(float x) { return ex2_ftz(x); }
+__device__ __forceinline__ double uex2(double x) { return exp2(x); }
+__device__ __forceinline__ float ufma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double ufma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float umin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double umin(double a, double b) { return fmin(a, b); }
+
+// Below this W the unshifted weights lose precision (FP32 terms under 2^-126
+// flush to zero) and the seed is recomputed with a shift.
+template <typename T>
+__device__ __forceinline__ T unroll_min_w() {
+  return sizeof(T) == 4 ? (T)1e-20f : (T)1e-280;
+}
+
+// seeds (forward, seed-major adjoint) or points (point-major adjoint) per lane
+template <typename T, int DPAD>
+constexpr int unroll_fwd_r() {
+  return sizeof(T) != 4 ? 1 : (DPAD <= 4 ? 4 : (DPAD <= 8 ? 2 : 1));
+}
+template <typename T, int DPAD>
 constexpr int unroll_point_r() {
-  return DPAD <= 16 ? 2 : 1;
+  return sizeof(T) != 4 ? 1 : (DPAD <= 16 ? 2 : 1);
 }
 
 // ---- forward partials: grid-stride over (set, seed group of 32 R, point chunk)
-template <int DPAD, int R>
+template <typename T, int DPAD, int R>
 __global__ void __launch_bounds__(128)
-    unroll_fwd_partial(const float* __restrict__ X, const float* __restrict__ Y, UGeom g,
-                       float c, float* __restrict__ part) {
+    unroll_fwd_partial(const T* __restrict__ X, const T* __restrict__ Y, UGeom g,
+                       T c, T* __restrict__ part) {
   constexpr int SPW = 32 * R;
   const int lane = threadIdx.x & 31;
   const int Gs = (g.m + SPW - 1) / SPW;
-  const int64_t T = (int64_t)g.B * Gs * g.Cp;
+  const int64_t NT = (int64_t)g.B * Gs * g.Cp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < NT;
        task += nw) {
     const int ch = (int)(task % g.Cp);
     const int64_t rest = task / g.Cp;
     const int gs = (int)(rest % Gs);
     const int b = (int)(rest / Gs);
-    const float* Xb = X + (int64_t)b * g.n * DPAD;
-    float y[R][DPAD], S[R][DPAD], W[R];
+    const T* Xb = X + (int64_t)b * g.n * DPAD;
+    T y[R][DPAD], S[R][DPAD], W[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = min(gs * SPW + r * 32 + lane, g.m - 1);
       load_row<DPAD>(Y + ((int64_t)b * g.m + i) * DPAD, y[r]);
-      W[r] = 0.f;
+      W[r] = T(0);
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) S[r][k] = 0.f;
+      for (int k = 0; k < DPAD; ++k) S[r][k] = T(0);
     }
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
-    float xn[DPAD];   // the next point's row, loaded while this one is evaluated
+    T xn[DPAD];   // the next point's row, loaded while this one is evaluated
     if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
     for (int j = j0; j < j1; ++j) {
-      float x[DPAD];
+      T x[DPAD];
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
       if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float dx[DPAD], D2 = 0.f;
+        T dx[DPAD], D2 = T(0);
 #pragma unroll
         for (int k = 0; k < DPAD; ++k) {
           dx[k] = x[k] - y[r][k];
-          D2 = fmaf(dx[k], dx[k], D2);
+          D2 = ufma(dx[k], dx[k], D2);
         }
-        const float w = ex2_ftz(-c * D2);
+        const T w = uex2(-c * D2);
         W[r] += w;
 #pragma unroll
-        for (int k = 0; k < DPAD; ++k) S[r][k] = fmaf(w, dx[k], S[r][k]);
+        for (int k = 0; k < DPAD; ++k) S[r][k] = ufma(w, dx[k], S[r][k]);
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = gs * SPW + r * 32 + lane;
       if (i < g.m) {
-        float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
+        T* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
         o[0] = W[r];
 #pragma unroll
         for (int k = 0; k < DPAD; ++k)
@@ -120,32 +146,29 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// Below this W the unshifted weights lose precision (terms under 2^-126
-// flush to zero) and the seed is recomputed with a shift.
-constexpr float kUnrollMinW = 1e-20f;
-
 // y_next = y + S/W (sums over chunks in chunk order), W kept for the backward.
-// Seeds with W < kUnrollMinW (or not finite) go to the rescue list instead.
-__global__ void unroll_fwd_finish(const float* __restrict__ part, const float* __restrict__ Y,
-                                  UGeom g, float* __restrict__ Ynext, float* __restrict__ Wout,
-                                  float* __restrict__ Sh, int32_t* __restrict__ rlist,
+// Seeds with W < unroll_min_w<T>() (or not finite) go to the rescue list instead.
+template <typename T>
+__global__ void unroll_fwd_finish(const T* __restrict__ part, const T* __restrict__ Y,
+                                  UGeom g, T* __restrict__ Ynext, T* __restrict__ Wout,
+                                  T* __restrict__ Sh, int32_t* __restrict__ rlist,
                                   int32_t* __restrict__ rcount) {
   const int64_t total = (int64_t)g.B * g.m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / g.m), i = (int)(e % g.m);
-    float W = 0.f;
+    T W = T(0);
     for (int ch = 0; ch < g.Cp; ++ch) W += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1)];
-    if (!(W >= kUnrollMinW) || !isfinite(W)) {
+    if (!(W >= unroll_min_w<T>()) || !isfinite(W)) {
       rlist[atomicAdd(rcount, 1)] = (int32_t)e;
       continue;
     }
     if (Wout) Wout[e] = W;
-    if (Sh) Sh[e] = 0.f;
+    if (Sh) Sh[e] = T(0);
     for (int k = 0; k < g.DP; ++k) {
-      float v = 0.f;
+      T v = T(0);
       if (k < g.d) {
-        float S = 0.f;
+        T S = T(0);
         for (int ch = 0; ch < g.Cp; ++ch)
           S += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1) + 1 + k];
         v = Y[e * g.DP + k] + S / W;
@@ -159,51 +182,51 @@ __global__ void unroll_fwd_finish(const float* __restrict__ part, const float* _
 // nearest squared distance D2min, pass 2 the weights exp2(-c (D2 - D2min)),
 // their sums (fixed xor tree over lanes) and y' = y + S/W; the shift c D2min
 // goes to Sh for the backward.  One block; it clears the list count at the end.
-template <int DPAD>
+template <typename T, int DPAD>
 __global__ void __launch_bounds__(1024)
-    unroll_fwd_rescue(const float* __restrict__ X, const float* __restrict__ Y, UGeom g, float c,
+    unroll_fwd_rescue(const T* __restrict__ X, const T* __restrict__ Y, UGeom g, T c,
                       const int32_t* __restrict__ rlist, int32_t* rcount,
-                      float* __restrict__ Ynext, float* __restrict__ Wout,
-                      float* __restrict__ Sh) {
+                      T* __restrict__ Ynext, T* __restrict__ Wout,
+                      T* __restrict__ Sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cnt = *(volatile int32_t*)rcount;
   for (int q = warp; q < cnt; q += (int)(blockDim.x >> 5)) {
     const int64_t e = rlist[q];
     const int b = (int)(e / g.m);
-    const float* Xb = X + (int64_t)b * g.n * DPAD;
-    float y[DPAD];
+    const T* Xb = X + (int64_t)b * g.n * DPAD;
+    T y[DPAD];
     load_row<DPAD>(Y + e * DPAD, y);
-    float dmin = INFINITY;
+    T dmin = T(INFINITY);
     for (int j = lane; j < g.n; j += 32) {
-      float x[DPAD];
+      T x[DPAD];
       load_row<DPAD>(Xb + (int64_t)j * DPAD, x);
-      float D2 = 0.f;
+      T D2 = T(0);
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
-        const float e = x[k] - y[k];
-        D2 = fmaf(e, e, D2);
+        const T e = x[k] - y[k];
+        D2 = ufma(e, e, D2);
       }
-      dmin = fminf(dmin, D2);
+      dmin = umin(dmin, D2);
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(kFull, dmin, o));
-    const float sh = c * dmin;
-    float W = 0.f, S[DPAD];
+    for (int o = 16; o >= 1; o >>= 1) dmin = umin(dmin, __shfl_xor_sync(kFull, dmin, o));
+    const T sh = c * dmin;
+    T W = T(0), S[DPAD];
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) S[k] = 0.f;
+    for (int k = 0; k < DPAD; ++k) S[k] = T(0);
     for (int j = lane; j < g.n; j += 32) {
-      float x[DPAD];
+      T x[DPAD];
       load_row<DPAD>(Xb + (int64_t)j * DPAD, x);
-      float dx[DPAD], D2 = 0.f;
+      T dx[DPAD], D2 = T(0);
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
         dx[k] = x[k] - y[k];
-        D2 = fmaf(dx[k], dx[k], D2);
+        D2 = ufma(dx[k], dx[k], D2);
       }
-      const float w = ex2_ftz(fmaf(-c, D2, sh));
+      const T w = uex2(ufma(-c, D2, sh));
       W += w;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) S[k] = fmaf(w, dx[k], S[k]);
+      for (int k = 0; k < DPAD; ++k) S[k] = ufma(w, dx[k], S[k]);
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -216,7 +239,7 @@ __global__ void __launch_bounds__(1024)
       if (Sh) Sh[e] = sh;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k)
-        if (k < g.DP) Ynext[e * g.DP + k] = k < g.d ? y[k] + S[k] / W : 0.f;
+        if (k < g.DP) Ynext[e * g.DP + k] = k < g.d ? y[k] + S[k] / W : T(0);
     }
   }
   __syncthreads();
@@ -224,27 +247,27 @@ __global__ void __launch_bounds__(1024)
 }
 
 // ---- adjoint inputs per seed: SD row = [y | g | 1/W, shift, g . (y - mu), 0]
-template <int DPAD>
-__global__ void unroll_seed_data(const float* __restrict__ Y, const float* __restrict__ MU,
-                                 const float* __restrict__ G, const float* __restrict__ Wt,
-                                 const float* __restrict__ Sh, UGeom g, float* __restrict__ SD) {
+template <typename T, int DPAD>
+__global__ void unroll_seed_data(const T* __restrict__ Y, const T* __restrict__ MU,
+                                 const T* __restrict__ G, const T* __restrict__ Wt,
+                                 const T* __restrict__ Sh, UGeom g, T* __restrict__ SD) {
   constexpr int SDW = 2 * DPAD + 4;
   const int64_t total = (int64_t)g.B * g.m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    float* o = SD + e * SDW;
-    float gm = 0.f;
+    T* o = SD + e * SDW;
+    T gm = T(0);
 #pragma unroll
     for (int k = 0; k < DPAD; ++k) {
-      const float gk = G[e * DPAD + k];
+      const T gk = G[e * DPAD + k];
       o[k] = Y[e * DPAD + k];
       o[DPAD + k] = gk;
-      gm = fmaf(gk, Y[e * DPAD + k] - MU[e * DPAD + k], gm);
+      gm = ufma(gk, Y[e * DPAD + k] - MU[e * DPAD + k], gm);
     }
-    o[2 * DPAD] = 1.0f / Wt[e];
+    o[2 * DPAD] = T(1) / Wt[e];
     o[2 * DPAD + 1] = Sh[e];
     o[2 * DPAD + 2] = gm;
-    o[2 * DPAD + 3] = 0.f;
+    o[2 * DPAD + 3] = T(0);
   }
 }
 
@@ -257,16 +280,16 @@ __global__ void unroll_seed_data(const float* __restrict__ Y, const float* __res
 // hundreds) the FP32 rounding of D2 perturbs its weights by ~1e-5, which
 // leaves sum p a at ~1e-5 instead of 0; subtracting s_i keeps that residual
 // from being multiplied by D2.
-template <int DPAD>
+template <typename T, int DPAD>
 __global__ void __launch_bounds__(128)
-    unroll_bwd_seed(const float* __restrict__ X, const float* __restrict__ MU,
-                    const float* __restrict__ SD, UGeom g, float c, float* __restrict__ part) {
+    unroll_bwd_seed(const T* __restrict__ X, const T* __restrict__ MU,
+                    const T* __restrict__ SD, UGeom g, T c, T* __restrict__ part) {
   constexpr int SDW = 2 * DPAD + 4;
   const int lane = threadIdx.x & 31;
   const int Gs = (g.m + 31) / 32;
-  const int64_t T = (int64_t)g.B * Gs * g.Cp;
+  const int64_t NT = (int64_t)g.B * Gs * g.Cp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < NT;
        task += nw) {
     const int ch = (int)(task % g.Cp);
     const int64_t rest = task / g.Cp;
@@ -274,63 +297,65 @@ __global__ void __launch_bounds__(128)
     const int b = (int)(rest / Gs);
     const int i = min(gs * 32 + lane, g.m - 1);
     const int64_t row = (int64_t)b * g.m + i;
-    const float* Xb = X + (int64_t)b * g.n * DPAD;
-    const float* sd = SD + row * SDW;
-    float y[DPAD], gg[DPAD], DY[DPAD], DH = 0.f, SA = 0.f;
+    const T* Xb = X + (int64_t)b * g.n * DPAD;
+    const T* sd = SD + row * SDW;
+    T y[DPAD], gg[DPAD], DY[DPAD], DH = T(0), SA = T(0);
     load_row<DPAD>(sd, y);
     load_row<DPAD>(sd + DPAD, gg);
-    const float4 tail = __ldg(reinterpret_cast<const float4*>(sd + 2 * DPAD));
-    const float invW = tail.x, sh = tail.y, gd = tail.z;
-    const float s0 = sh / c;
+    T tail[4];
+    load_row<4>(sd + 2 * DPAD, tail);
+    const T invW = tail[0], sh = tail[1], gd = tail[2];
+    const T s0 = sh / c;
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) DY[k] = 0.f;
+    for (int k = 0; k < DPAD; ++k) DY[k] = T(0);
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
-    float xn[DPAD];
+    T xn[DPAD];
     if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
     for (int j = j0; j < j1; ++j) {
-      float x[DPAD];
+      T x[DPAD];
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
       if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
-      float dx[DPAD], D2 = 0.f, a = gd;
+      T dx[DPAD], D2 = T(0), a = gd;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
         dx[k] = x[k] - y[k];
-        D2 = fmaf(dx[k], dx[k], D2);
-        a = fmaf(gg[k], dx[k], a);
+        D2 = ufma(dx[k], dx[k], D2);
+        a = ufma(gg[k], dx[k], a);
       }
-      const float pa = ex2_ftz(fmaf(-c, D2, sh)) * invW * a;
-      DH = fmaf(pa, D2 - s0, DH);
+      const T pa = uex2(ufma(-c, D2, sh)) * invW * a;
+      DH = ufma(pa, D2 - s0, DH);
       SA += pa;
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) DY[k] = fmaf(pa, dx[k], DY[k]);
+      for (int k = 0; k < DPAD; ++k) DY[k] = ufma(pa, dx[k], DY[k]);
     }
     if (gs * 32 + lane < g.m) {
-      float mu[DPAD];
+      T mu[DPAD];
       load_row<DPAD>(MU + row * DPAD, mu);
-      float* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
+      T* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
       o[0] = DH;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k)
-        if (k < g.d) o[1 + k] = fmaf(y[k] - mu[k], SA, DY[k]);
+        if (k < g.d) o[1 + k] = ufma(y[k] - mu[k], SA, DY[k]);
     }
   }
 }
 
 // G_prev = DY / h^2 (the gradient w.r.t. the positions before this update);
 // dh_part[b*m + i] = DH_i / h^3.
-__global__ void unroll_bwd_seed_finish(const float* __restrict__ part, UGeom g, float inv_h2,
-                                       float inv_h3, float* __restrict__ Gprev,
-                                       float* __restrict__ dh_part) {
+template <typename T>
+__global__ void unroll_bwd_seed_finish(const T* __restrict__ part, UGeom g, T inv_h2,
+                                       T inv_h3, T* __restrict__ Gprev,
+                                       T* __restrict__ dh_part) {
   const int64_t total = (int64_t)g.B * g.m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / g.m), i = (int)(e % g.m);
-    float DH = 0.f;
+    T DH = T(0);
     for (int ch = 0; ch < g.Cp; ++ch) DH += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1)];
     dh_part[e] = DH * inv_h3;
     for (int k = 0; k < g.DP; ++k) {
-      float v = 0.f;
+      T v = T(0);
       if (k < g.d) {
         for (int ch = 0; ch < g.Cp; ++ch)
           v += part[(((int64_t)b * g.Cp + ch) * g.m + i) * (g.DP + 1) + 1 + k];
@@ -344,83 +369,86 @@ __global__ void unroll_bwd_seed_finish(const float* __restrict__ part, UGeom g, 
 // ---- backward, point-major: partial over seed chunks of
 //   DX_j = sum_i p_ij g_i - (1/h^2) sum_i p_ij a_ij (x_j - y_i).
 // Lanes own R points; the seed rows (SD) are read with warp-uniform loads.
-template <int DPAD, int R>
+template <typename T, int DPAD, int R>
 __global__ void __launch_bounds__(128)
-    unroll_bwd_point(const float* __restrict__ X, const float* __restrict__ SD, UGeom g, float c,
-                     float inv_h2, float* __restrict__ part) {
+    unroll_bwd_point(const T* __restrict__ X, const T* __restrict__ SD, UGeom g, T c,
+                     T inv_h2, T* __restrict__ part) {
   constexpr int SDW = 2 * DPAD + 4;
   constexpr int PPW = 32 * R;
   const int lane = threadIdx.x & 31;
   const int Gp = (g.n + PPW - 1) / PPW;
-  const int64_t T = (int64_t)g.B * Gp * g.Cs;
+  const int64_t NT = (int64_t)g.B * Gp * g.Cs;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < NT;
        task += nw) {
     const int ch = (int)(task % g.Cs);
     const int64_t rest = task / g.Cs;
     const int gp = (int)(rest % Gp);
     const int b = (int)(rest / Gp);
-    float x[R][DPAD], DX[R][DPAD];
+    T x[R][DPAD], DX[R][DPAD];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int j = min(gp * PPW + r * 32 + lane, g.n - 1);
       load_row<DPAD>(X + ((int64_t)b * g.n + j) * DPAD, x[r]);
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) DX[r][k] = 0.f;
+      for (int k = 0; k < DPAD; ++k) DX[r][k] = T(0);
     }
     const int i0 = ch * g.Ls, i1 = min(g.m, i0 + g.Ls);
-    const float* sdb = SD + (int64_t)b * g.m * SDW;
+    const T* sdb = SD + (int64_t)b * g.m * SDW;
     for (int i = i0; i < i1; ++i) {
-      const float* sd = sdb + (int64_t)i * SDW;
-      float y[DPAD], gg[DPAD];
+      const T* sd = sdb + (int64_t)i * SDW;
+      T y[DPAD], gg[DPAD];
       load_row<DPAD>(sd, y);
       load_row<DPAD>(sd + DPAD, gg);
-      const float4 tail = __ldg(reinterpret_cast<const float4*>(sd + 2 * DPAD));
-      const float invW = tail.x, sh = tail.y, gd = tail.z;
+      T tail[4];
+    load_row<4>(sd + 2 * DPAD, tail);
+      const T invW = tail[0], sh = tail[1], gd = tail[2];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float dx[DPAD], D2 = 0.f, a = gd;
+        T dx[DPAD], D2 = T(0), a = gd;
 #pragma unroll
         for (int k = 0; k < DPAD; ++k) {
           dx[k] = x[r][k] - y[k];
-          D2 = fmaf(dx[k], dx[k], D2);
-          a = fmaf(gg[k], dx[k], a);
+          D2 = ufma(dx[k], dx[k], D2);
+          a = ufma(gg[k], dx[k], a);
         }
-        const float p = ex2_ftz(fmaf(-c, D2, sh)) * invW;
-        const float q = p * a * inv_h2;
+        const T p = uex2(ufma(-c, D2, sh)) * invW;
+        const T q = p * a * inv_h2;
 #pragma unroll
-        for (int k = 0; k < DPAD; ++k) DX[r][k] = fmaf(p, gg[k], fmaf(-q, dx[k], DX[r][k]));
+        for (int k = 0; k < DPAD; ++k) DX[r][k] = ufma(p, gg[k], ufma(-q, dx[k], DX[r][k]));
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int j = gp * PPW + r * 32 + lane;
       if (j < g.n) {
-        float* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * DPAD;
+        T* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * DPAD;
 #pragma unroll
-        for (int k = 0; k < DPAD; ++k) o[k] = k < g.d ? DX[r][k] : 0.f;
+        for (int k = 0; k < DPAD; ++k) o[k] = k < g.d ? DX[r][k] : T(0);
       }
     }
   }
 }
 
 // dX += sum over seed chunks (chunk order).
-__global__ void unroll_bwd_point_finish(const float* __restrict__ part, UGeom g,
-                                        float* __restrict__ dX) {
+template <typename T>
+__global__ void unroll_bwd_point_finish(const T* __restrict__ part, UGeom g,
+                                        T* __restrict__ dX) {
   const int64_t total = (int64_t)g.B * g.n * g.DP;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t bj = e / g.DP;
     const int k = (int)(e % g.DP);
     const int b = (int)(bj / g.n), j = (int)(bj % g.n);
-    float v = 0.f;
+    T v = T(0);
     for (int ch = 0; ch < g.Cs; ++ch) v += part[(((int64_t)b * g.Cs + ch) * g.n + j) * g.DP + k];
     dX[e] += v;
   }
 }
 
 // dh[b] += sum_i dh_part[b, i] in FP64, seeds in order (one block per set).
-__global__ void unroll_dh_reduce(const float* __restrict__ dh_part, UGeom g,
+template <typename T>
+__global__ void unroll_dh_reduce(const T* __restrict__ dh_part, UGeom g,
                                  double* __restrict__ dh) {
   __shared__ double red[32];
   const int b = blockIdx.x;
@@ -438,18 +466,20 @@ __global__ void unroll_dh_reduce(const float* __restrict__ dh_part, UGeom g,
 }
 
 // Row repacking between the caller's [rows x d] and the padded [rows x DP].
-__global__ void unroll_pack(const float* __restrict__ src, int64_t rows, int d, int DP,
-                            float* __restrict__ dst) {
+template <typename T>
+__global__ void unroll_pack(const T* __restrict__ src, int64_t rows, int d, int DP,
+                            T* __restrict__ dst) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * DP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / DP;
     const int k = (int)(e % DP);
-    dst[e] = k < d ? src[r * d + k] : 0.f;
+    dst[e] = k < d ? src[r * d + k] : T(0);
   }
 }
 
-__global__ void unroll_unpack(const float* __restrict__ src, int64_t rows, int d, int DP,
-                              float* __restrict__ dst) {
+template <typename T>
+__global__ void unroll_unpack(const T* __restrict__ src, int64_t rows, int d, int DP,
+                              T* __restrict__ dst) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * d;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / d;
@@ -465,70 +495,85 @@ static int blocks_for(int64_t work, int per = 256) {
   return (int)b;
 }
 
-template <int DPAD>
-static cudaError_t fwd_step_t(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                              float* Ynext, float* Wout, float* Sh, int32_t* rlist,
-                              int32_t* rcount, int grid, cudaStream_t st) {
-  unroll_fwd_partial<DPAD, unroll_fwd_r<DPAD>()><<<grid, 128, 0, st>>>(X, Y, g, c, part);
-  unroll_fwd_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout, Sh,
-                                                                    rlist, rcount);
-  unroll_fwd_rescue<DPAD><<<1, 1024, 0, st>>>(X, Y, g, c, rlist, rcount, Ynext, Wout, Sh);
+template <typename T, int DPAD>
+static cudaError_t fwd_step_t(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
+                              T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
+                              cudaStream_t st) {
+  unroll_fwd_partial<T, DPAD, unroll_fwd_r<T, DPAD>()><<<grid, 128, 0, st>>>(X, Y, g, c, part);
+  unroll_fwd_finish<T><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout,
+                                                                       Sh, rlist, rcount);
+  unroll_fwd_rescue<T, DPAD><<<1, 1024, 0, st>>>(X, Y, g, c, rlist, rcount, Ynext, Wout, Sh);
   return cudaGetLastError();
 }
 
-cudaError_t unroll_fwd_step(const float* X, const float* Y, const UGeom& g, float c, float* part,
-                            float* Ynext, float* Wout, float* Sh, int32_t* rlist, int32_t* rcount,
-                            int grid, cudaStream_t st) {
-  switch (g.DP) {
-    case 4: return fwd_step_t<4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 8: return fwd_step_t<8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 16: return fwd_step_t<16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 32: return fwd_step_t<32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int DPAD>
-static cudaError_t bwd_step_t(const float* X, const float* Y, const float* MU, const float* G,
-                              const float* Wt, const float* Sh, const UGeom& g, float c,
-                              float inv_h2, float inv_h3, float* part_s, float* part_p,
-                              float* SD, float* dh_part, float* Gprev, float* dX, double* dh,
-                              int grid, cudaStream_t st) {
-  unroll_seed_data<DPAD><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(Y, MU, G, Wt, Sh, g, SD);
-  unroll_bwd_point<DPAD, unroll_point_r<DPAD>()><<<grid, 128, 0, st>>>(X, SD, g, c, inv_h2,
-                                                                        part_p);
-  unroll_bwd_seed<DPAD><<<grid, 128, 0, st>>>(X, MU, SD, g, c, part_s);
-  unroll_bwd_point_finish<<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
-  unroll_bwd_seed_finish<<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2, inv_h3,
-                                                                         Gprev, dh_part);
-  unroll_dh_reduce<<<g.B, 256, 0, st>>>(dh_part, g, dh);
-  return cudaGetLastError();
-}
-
-cudaError_t unroll_bwd_step(const float* X, const float* Y, const float* MU, const float* G,
-                            const float* Wt, const float* Sh, const UGeom& g, float c,
-                            float inv_h2, float inv_h3, float* part_s, float* part_p, float* SD,
-                            float* dh_part, float* Gprev, float* dX, double* dh, int grid,
+template <typename T>
+cudaError_t unroll_fwd_step(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
+                            T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
                             cudaStream_t st) {
   switch (g.DP) {
-    case 4: return bwd_step_t<4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 8: return bwd_step_t<8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 16: return bwd_step_t<16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 32: return bwd_step_t<32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 4: return fwd_step_t<T, 4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 8: return fwd_step_t<T, 8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 16: return fwd_step_t<T, 16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 32: return fwd_step_t<T, 32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t unroll_pack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
-                             cudaStream_t st) {
-  unroll_pack<<<blocks_for(rows * DP), 256, 0, st>>>(src, rows, d, DP, dst);
+template <typename T, int DPAD>
+static cudaError_t bwd_step_t(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
+                              const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
+                              T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
+                              cudaStream_t st) {
+  unroll_seed_data<T, DPAD><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(Y, MU, G, Wt, Sh, g,
+                                                                           SD);
+  unroll_bwd_point<T, DPAD, unroll_point_r<T, DPAD>()><<<grid, 128, 0, st>>>(X, SD, g, c, inv_h2,
+                                                                              part_p);
+  unroll_bwd_seed<T, DPAD><<<grid, 128, 0, st>>>(X, MU, SD, g, c, part_s);
+  unroll_bwd_point_finish<T><<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
+  unroll_bwd_seed_finish<T><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2,
+                                                                            inv_h3, Gprev,
+                                                                            dh_part);
+  unroll_dh_reduce<T><<<g.B, 256, 0, st>>>(dh_part, g, dh);
   return cudaGetLastError();
 }
 
-cudaError_t unroll_unpack_rows(const float* src, int64_t rows, int d, int DP, float* dst,
-                               cudaStream_t st) {
-  unroll_unpack<<<blocks_for(rows * d), 256, 0, st>>>(src, rows, d, DP, dst);
+template <typename T>
+cudaError_t unroll_bwd_step(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
+                            const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
+                            T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
+                            cudaStream_t st) {
+  switch (g.DP) {
+    case 4: return bwd_step_t<T, 4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 8: return bwd_step_t<T, 8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 16: return bwd_step_t<T, 16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 32: return bwd_step_t<T, 32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t unroll_pack_rows(const T* src, int64_t rows, int d, int DP, T* dst, cudaStream_t st) {
+  unroll_pack<T><<<blocks_for(rows * DP), 256, 0, st>>>(src, rows, d, DP, dst);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t unroll_unpack_rows(const T* src, int64_t rows, int d, int DP, T* dst,
+                               cudaStream_t st) {
+  unroll_unpack<T><<<blocks_for(rows * d), 256, 0, st>>>(src, rows, d, DP, dst);
+  return cudaGetLastError();
+}
+
+#define FMS_UNROLL_INST(T)                                                                      \
+  template cudaError_t unroll_fwd_step<T>(const T*, const T*, const UGeom&, T, T*, T*, T*, T*,  \
+                                          int32_t*, int32_t*, int, cudaStream_t);              \
+  template cudaError_t unroll_bwd_step<T>(const T*, const T*, const T*, const T*, const T*,     \
+                                          const T*, const UGeom&, T, T, T, T*, T*, T*, T*, T*, \
+                                          T*, double*, int, cudaStream_t);                     \
+  template cudaError_t unroll_pack_rows<T>(const T*, int64_t, int, int, T*, cudaStream_t);      \
+  template cudaError_t unroll_unpack_rows<T>(const T*, int64_t, int, int, T*, cudaStream_t);
+FMS_UNROLL_INST(float)
+FMS_UNROLL_INST(double)
+#undef FMS_UNROLL_INST
 
 }  // namespace fms

@@ -123,3 +123,39 @@ def test_far_seed_matches_oracle():
         assert np.all(np.isfinite(g_))
         assert np.abs(g_ - want).max() <= 2e-4 * (1 + np.abs(want).max())
     assert abs(dh[0].item() - rdh) <= 2e-4 * (1 + abs(rdh))
+
+
+def test_fp64_kernels_match_oracle_tightly():
+    # the FP64 entry points run the same kernels in double precision: forward
+    # and adjoint agree with the FP64 oracle to ~1e-10 (rounding order only)
+    B, n, d, h, T, k = 2, 120, 4, 1.5, 4, 3
+    X = _sets(61, B, n, d).astype(np.float64)
+    rng = np.random.default_rng(3)
+    Y0 = X + 0.25 * rng.standard_normal(X.shape)
+    G = rng.standard_normal(X.shape)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y0).cuda()
+    YT, ck = fms.unrolled_forward(Xt, Yt, h, T, k)
+    assert YT.dtype == torch.float64
+    dX, dY, dh = fms.unrolled_backward(Xt, ck, n, h, T, k, torch.from_numpy(G).cuda())
+    torch.cuda.synchronize()
+    for b in range(B):
+        ref = orc.unrolled_forward(X[b], Y0[b], h, T)[-1]
+        assert np.abs(YT[b].cpu().numpy() - ref).max() <= 1e-10 * (1 + np.abs(ref).max())
+        rdX, rdY, rdh = orc.unrolled_backward(X[b], Y0[b], h, T, G[b])
+        for got, want in ((dX[b], rdX), (dY[b], rdY)):
+            got = got.cpu().numpy()
+            assert np.abs(got - want).max() <= 1e-9 * (1 + np.abs(want).max())
+        assert abs(dh[b].item() - rdh) <= 1e-9 * (1 + abs(rdh))
+
+
+def test_gradcheck_fp64_on_gpu():
+    # torch.autograd.gradcheck of the library's adjoint (FP64 kernels on the
+    # GPU) against central finite differences of its own forward, n = 64, d = 4
+    B, n, d, T, k = 1, 64, 4, 3, 2
+    X = torch.from_numpy(_sets(62, B, n, d).astype(np.float64)).cuda().requires_grad_(True)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    Y0 = (X.detach() + 0.2 * torch.randn(X.shape, generator=g, device="cuda",
+                                          dtype=torch.float64)).requires_grad_(True)
+    h = torch.tensor(1.7, dtype=torch.float64, device="cuda", requires_grad=True)
+    fn = lambda X_, Y_, h_: fms.unrolled_mean_shift(X_, Y_, h_, T, k)
+    assert torch.autograd.gradcheck(fn, (X, Y0, h), eps=1e-6, atol=1e-7, rtol=1e-5)

@@ -167,6 +167,7 @@ KERNEL_SOURCES = {
                 "paper_2112_13891_gb300/csrc/fms_step_body.cuh",
                 "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
     "ms_step_tc": ["paper_2112_13891_gb300/csrc/k_step_tc.cu",
+                   "paper_2112_13891_gb300/csrc/fms_tc.cuh",
                    "paper_2112_13891_gb300/csrc/fms_internal.cuh"],
 }
 
@@ -721,6 +722,14 @@ def bench_extra(args):
     elif args.workload == "step_wide":
         # one update of every point as a seed: the coarse tensor-core step vs the FP32 step
         peaks = measured_peaks()
+        # the tcgen05 rate measured on this device (completed MMAs, N = 128, one
+        # issuing thread per SM) at the maximum SM clock, as the tensor roofline
+        tcr = fms.probe_tensor_rates()
+        smx = peaks.get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        tc_peak = tcr["n128"]["one_issuer"] * sms * smx * 1e6 / 1e12
+        line["tcgen05_flop_per_clk_sm"] = {k: v["one_issuer"] for k, v in tcr.items()}
+        line["tcgen05_peak_tflops"] = tc_peak
         for d in (16, 32):
             w = fi.embedding_32d(d=d)
             X = torch.from_numpy(w.X).cuda()
@@ -744,6 +753,8 @@ def bench_extra(args):
             rec["coarse"]["algorithmic_tflops"] = alg_flops / (rec["coarse"]["ms"] * 1e-3) / 1e12
             if tf:
                 rec["coarse"]["mma_frac_of_measured_bf16"] = rec["coarse"]["mma_tflops"] / tf
+            if tc_peak:
+                rec["coarse"]["mma_frac_of_measured_tcgen05"] = rec["coarse"]["mma_tflops"] / tc_peak
             rec["speedup_coarse_over_fp32"] = rec["fp32"]["ms"] / rec["coarse"]["ms"]
             line[f"d{d}"] = rec
         line["metric"] = "ms per update of 65,536 seeds against 65,536 points"

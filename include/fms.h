@@ -417,6 +417,20 @@ fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n, int32_t d
 fms_status fms_probe_pipe_rates(double* rates, int32_t n_rates);
 
 /*
+ * Measured BF16 tensor-core rate of the current device (tcgen05.mma.kind::f16,
+ * M = 128, K = 16, FP32 accumulation in tensor memory), from one bounded
+ * launch per configuration with one CTA per SM (bounded mbarrier waits; the
+ * tensor memory is freed before the CTA exits).  rates[2 i] (one issuing
+ * thread per SM) and rates[2 i + 1] (two issuing threads in different warps)
+ * are FLOP per clock per SM of completed MMAs for N = 16, 32, 64, 128, 256
+ * (i = 0 .. 4), the median over SMs; multiply by the SM clock and the SM
+ * count for FLOP/s.  Writes min(n_rates, 10) entries; a negative entry means
+ * a wait gave up.  Synchronises the device.  FMS_ERR_INVALID_ARG (null or
+ * n_rates < 1), FMS_ERR_CUDA.
+ */
+fms_status fms_probe_tensor_rates(double* rates, int32_t n_rates);
+
+/*
  * Nearest-mode labelling (the labelling of Alg. 2): labels[j] = argmin_k
  * ||x_j - modes_k|| (ties -> lowest k) and, if margins is non-NULL,
  * margins[j] = second-nearest minus nearest distance (+inf when M = 1).

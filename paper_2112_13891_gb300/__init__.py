@@ -574,6 +574,19 @@ _lib.fms_probe_pipe_rates.restype = ctypes.c_int
 _lib.fms_probe_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
 
 
+_lib.fms_probe_tensor_rates.restype = ctypes.c_int
+_lib.fms_probe_tensor_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
+
+
+def probe_tensor_rates() -> dict:
+    """BF16 tcgen05 FLOP per clock per SM (completed MMAs, M = 128, K = 16) for
+    N = 16 .. 256, with one and with two issuing threads per SM."""
+    out = (ctypes.c_double * 10)()
+    _check(_lib.fms_probe_tensor_rates(out, 10), "fms_probe_tensor_rates")
+    return {f"n{n}": {"one_issuer": out[2 * i], "two_issuers": out[2 * i + 1]}
+            for i, n in enumerate((16, 32, 64, 128, 256))}
+
+
 def probe_pipe_rates() -> dict:
     """FP32 / SFU throughputs of the current device per clock and per SM."""
     out = (ctypes.c_double * 4)()

@@ -87,11 +87,7 @@ enum : int { kPlanActive = 0, kPlanKept = 1, kPlanModes = 2 };
 
 size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
-int padded(int d) {
-  if (d <= 4) return 4;
-  if (d <= 8) return 8;
-  return (d + 3) / 4 * 4;
-}
+int padded(int d) { return padded_dim(d); }
 
 int sms_now() {
   int dev = 0, s = 0;

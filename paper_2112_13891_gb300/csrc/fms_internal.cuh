@@ -479,10 +479,15 @@ struct StepLayout {
   int DP, DA, R, grid_ctas, C, Lc;
 };
 
+// Row width of the packed copies: the padded dimension the step kernels are
+// compiled for (4, 8, 16, 32 or 64), so their row loads need no bounds test;
+// the padding coordinates are zero for points and seeds alike.
 inline int padded_dim(int d) {
   if (d <= 4) return 4;
   if (d <= 8) return 8;
-  return (d + 3) / 4 * 4;
+  if (d <= 16) return 16;
+  if (d <= 32) return 32;
+  return 64;
 }
 
 inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }

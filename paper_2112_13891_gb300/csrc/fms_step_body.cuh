@@ -152,16 +152,16 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
     p = p < s ? p : s - 1;
     const int64_t slot = __ldg(active + p);
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) ys[r][k] = k < DP ? __ldg(y + slot * DP + k) : 0.0f;
+    for (int k = 0; k < DPAD; ++k) ys[r][k] = __ldg(y + slot * DPAD + k);
 #pragma unroll
     for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
   }
   for (int j = j0; j < j1; ++j) {
     float x[DPAD];
-    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DP);
+    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DPAD);
 #pragma unroll
     for (int q = 0; q < DPAD / 4; ++q) {
-      float4 v = (4 * q < DP) ? __ldg(xp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = __ldg(xp + q);
       x[4 * q] = v.x;
       x[4 * q + 1] = v.y;
       x[4 * q + 2] = v.z;
@@ -216,15 +216,15 @@ __device__ __forceinline__ void quad_task(const float* __restrict__ Xs, int DP, 
     p = p < s ? p : s - 1;
     const int64_t slot = __ldg(active + p);
 #pragma unroll
-    for (int k = 0; k < DPAD; ++k) ys[r][k] = k < DP ? __ldg(y + slot * DP + k) : 0.0f;
+    for (int k = 0; k < DPAD; ++k) ys[r][k] = __ldg(y + slot * DPAD + k);
 #pragma unroll
     for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
   }
   auto load_point = [&](int j, float (&x)[DPAD]) {
-    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DP);
+    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DPAD);
 #pragma unroll
     for (int u = 0; u < DPAD / 4; ++u) {
-      const float4 v = (4 * u < DP) ? __ldg(xp + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = __ldg(xp + u);
       x[4 * u] = v.x;
       x[4 * u + 1] = v.y;
       x[4 * u + 2] = v.z;

@@ -329,6 +329,7 @@ cudaError_t launch_batched_step(const float* Xs, int d, int DP, const float* y,
                                 const int64_t* totals, float* part, int target_warps,
                                 cudaStream_t st) {
   const int g = (target_warps + 7) / 8;
+  if (d > 7 && DP != padded_dim(d)) return cudaErrorInvalidValue;   // rows of the compiled width
   switch (d) {
     case 1: batched_step_lowd<1, 4, 2><<<g, 256, 0, st>>>(Xs, y, list, sc, B, kind, task_off, part_off, totals, part); break;
     case 2: batched_step_lowd<2, 4, 4><<<g, 256, 0, st>>>(Xs, y, list, sc, B, kind, task_off, part_off, totals, part); break;

@@ -189,6 +189,8 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
                                    const int32_t* p_lo_ptr) {
   const dim3 g((target_warps + 7) / 8);
   const int grid_ctas = (int)g.x;
+  // the quad and wide kernels read rows of exactly their compiled width
+  if (d > 7 && DP != padded_dim(d)) return cudaErrorInvalidValue;
   switch (d) {
     case 1: ms_step_lowd<1, 4, 2, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;
     case 2: ms_step_lowd<2, 4, 4, KF><<<g, 256, 0, st>>>(Xs, n, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log); break;

@@ -615,6 +615,45 @@ def bench_extra(args):
                    "phase_ms": st["phase_ms"]}
             line[prec] = rec
         line["value"] = line["tensor"]["ms"]
+        # the same data with every point a seed (Alg. 1): 65,536 seeds keep the
+        # tensor-core step at full load; the two precisions are compared with
+        # each other (modes matched within 1e-3 h, labels of matched modes)
+        if not args.no_all_seeds:
+            allr = {}
+            for prec in ("tensor", "fp32"):
+                ws = fms.Workspace(fms.workspace_size(X.shape[0], 32, precision=prec,
+                                                      all_seeds=True), X.device)
+                run = lambda: fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, precision=prec,
+                                          all_seeds=True, max_modes=X.shape[0])
+                r = run()
+                ms, _ = _events_ms(run, 1, flush)
+                st = fms.cluster(X, w.h, w.tol, w.max_iter, workspace=ws, precision=prec,
+                                 all_seeds=True, max_modes=X.shape[0], profile=True).stats
+                allr[prec] = {"ms": ms, "n_modes": r.stats["n_modes"],
+                              "iterations": r.stats["iterations"], "evals": r.stats["evals"],
+                              "fp32_step_ms": st["step_kernel_ms"],
+                              "coarse_step_ms": st["coarse_kernel_ms"],
+                              "coarse_evals": st["coarse_evals"], "fp32_evals": st["step_evals"],
+                              "_r": r}
+            rt, rf = allr["tensor"].pop("_r"), allr["fp32"].pop("_r")
+            mt, mf = rt.modes.double(), rf.modes.double()
+            dmat = torch.cdist(mt, mf)
+            near = dmat.min(dim=1)
+            matched = int((near.values <= 1e-3 * w.h).sum().item())
+            # labels: a point whose tensor-path mode is matched must carry the
+            # fp32-path label of that mode
+            lt, lf = rt.labels.long(), rf.labels.long()
+            ok_mode = near.values <= 1e-3 * w.h
+            have = ok_mode[lt]
+            same = int((near.indices[lt][have] == lf[have]).sum().item())
+            allr["accuracy_tensor_vs_fp32"] = {
+                "modes_tensor": int(mt.shape[0]), "modes_fp32": int(mf.shape[0]),
+                "tensor_modes_matched_within_1e-3h": matched,
+                "max_mode_diff_over_h": float(near.values.max().item() / w.h),
+                "points_of_matched_modes": int(have.sum().item()),
+                "same_label_among_them": same}
+            allr["speedup_tensor_over_fp32"] = allr["fp32"]["ms"] / allr["tensor"]["ms"]
+            line["all_seeds"] = allr
     elif args.workload == "pixels_rgb":
         # N1: RGB image segmentation, 512^2 and 1024^2 pixels (the paper's image workload)
         line.update({"metric": "ms per RGB image segmentation (labels for every pixel)",

@@ -522,7 +522,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
         cudaEventRecord(a, st);
         lg = slog + n_slog;
         cudaError_t e = launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                                       Lo.tl.target_warps, st, lg, p_lo, kf);
+                                       Lo.tl.target_warps, st, lg, p_lo, kf, status);
         cudaEventRecord(b, st);
         evs.push_back(a);
         evs.push_back(b);
@@ -530,7 +530,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
         return e;
       }
       return launch_ms_step(Xs, n, d, DP, pos, list, s_ptr, C_ptr, Lc_ptr, part,
-                            Lo.tl.target_warps, st, nullptr, p_lo, kf);
+                            Lo.tl.target_warps, st, nullptr, p_lo, kf, status);
     };
     // the coarse step for active positions [0, ctl->s_tc)
     auto tc_launch = [&]() -> cudaError_t {
@@ -1258,13 +1258,14 @@ fms_status fms_mean_shift_step(const float* points, int64_t n, int32_t d, float 
     FMS_CUDA(launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st));
     FMS_CUDA(launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st));
     FMS_CUDA(launch_ms_step(Xs, n, d, L.DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
-                            L.grid_ctas * 8, st, nullptr));
+                            L.grid_ctas * 8, st, nullptr, nullptr, kKernelGaussian, status));
     FMS_CUDA(launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum,
                                 (int)m, st));
     if (owns) {
       FMS_CUDA(cudaMemcpyAsync(&hstatus, status, 4, cudaMemcpyDeviceToHost, st));
       FMS_CUDA(cudaStreamSynchronize(st));
       if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+      else if (hstatus & kStTimeout) rc = FMS_ERR_TIMEOUT;
     }
   }
 done:

@@ -27,7 +27,7 @@ cudaError_t launch_batched_step(const float* Xs, int d, int DP, const float* y,
                                 const int32_t* list, const SetCtl* sc, int B, int kind,
                                 const int64_t* task_off, const int64_t* part_off,
                                 const int64_t* totals, float* part, int target_warps,
-                                cudaStream_t st);
+                                uint32_t* status, cudaStream_t st);
 cudaError_t launch_batched_update(const float* part, const int32_t* active, const SetCtl* sc,
                                   int B, const int64_t* list_off, const int64_t* part_off,
                                   const int64_t* totals, float* y, int32_t* it, int32_t* conv,
@@ -417,7 +417,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
                                     status, st));
           BC(cudaEventRecord(e0, st));
           BC(launch_batched_step(Xs, d, DP, y, active, sc, B, kPlanActive, task_off, part_off,
-                                 totals, part, Lc.TW, st));
+                                 totals, part, Lc.TW, status, st));
           BC(cudaEventRecord(e1, st));
           BC(cudaEventSynchronize(e1));
           float ms = 0.f;
@@ -500,7 +500,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
         if (e2 == cudaSuccess) e2 = begin_while(cs1, h_upd, cs2, &upd_body);
         if (e2 == cudaSuccess) {
           cudaError_t e3 = launch_batched_step(Xs, d, DP, y, active, sc, B, kPlanActive, task_off,
-                                               part_off, totals, part, Lo.TW, cs2);
+                                               part_off, totals, part, Lo.TW, status, cs2);
           if (e3 == cudaSuccess)
             e3 = launch_batched_update(part, active, sc, B, list_off, part_off, totals, y, it,
                                        conv, state, d, DP, DA, tol2_s, max_iter, grid_upd, cs2);
@@ -516,7 +516,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
                                    task_off, part_off, list_off, totals, counters, cs1);
         if (e2 == cudaSuccess)
           e2 = launch_batched_step(Xs, d, DP, y, kept, sc, B, kPlanKept, task_off, part_off,
-                                   totals, part, Lo.TW, cs1);
+                                   totals, part, Lo.TW, status, cs1);
         if (e2 == cudaSuccess)
           e2 = launch_batched_score(part, sc, B, list_off, part_off, totals, DA, score, grid_upd,
                                     cs1);
@@ -543,7 +543,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
         if (e == cudaSuccess) e = begin_while(cs0, h_ref, cs1, &ref_body);
         if (e == cudaSuccess) {
           cudaError_t e2 = launch_batched_step(Xs, d, DP, yf, ract, sc, B, kPlanModes, task_off,
-                                               part_off, totals, part, Lo.TW, cs1);
+                                               part_off, totals, part, Lo.TW, status, cs1);
           if (e2 == cudaSuccess)
             e2 = launch_batched_refine_update(part, ract, sc, B, list_off, part_off, totals, ym,
                                               yf, mdone, mscore, d, DP, DA, rtol_s * rtol_s, 0,
@@ -564,7 +564,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
                         status, cs0);
       if (e == cudaSuccess)
         e = launch_batched_step(Xs, d, DP, yf, ract, sc, B, kPlanModes, task_off, part_off,
-                                totals, part, Lo.TW, cs0);
+                                totals, part, Lo.TW, status, cs0);
       if (e == cudaSuccess)
         e = launch_batched_refine_update(part, ract, sc, B, list_off, part_off, totals, ym, yf,
                                          mdone, mscore, d, DP, DA, 0.0, 1, grid_upd, cs0);
@@ -604,6 +604,7 @@ fms_status fms_cluster_batched(const float* points, const int64_t* offsets, int3
     BC(cudaMemcpyAsync(hcnt, counters, 16, cudaMemcpyDeviceToHost, st));
     BC(cudaStreamSynchronize(st));
     if (hstatus & kStNonFinite) rc = FMS_ERR_NONFINITE;
+    else if (hstatus & kStTimeout) rc = FMS_ERR_TIMEOUT;
     int64_t ev = 0;
     int maxMr = 0, iters = 0, conv_n = 0, kept_n = 0, seeds = 0, modes = 0;
     for (int b = 0; b < B; ++b) {

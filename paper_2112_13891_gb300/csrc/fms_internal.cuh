@@ -456,11 +456,14 @@ cudaError_t unroll_unpack_rows(const T* src, int64_t rows, int d, int DP, T* dst
                                cudaStream_t st);
 
 // k_step.cu: one update's partial sums for the active seeds
+// status: the call's status word (kStTimeout when a staged-tile wait gives up;
+// required for d > 16)
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps,
                            cudaStream_t st, int32_t* s_log = nullptr,
-                           const int32_t* p_lo_ptr = nullptr, int kf = kKernelGaussian);
+                           const int32_t* p_lo_ptr = nullptr, int kf = kKernelGaussian,
+                           uint32_t* status = nullptr);
 int step_seeds_per_warp(int d);
 int batched_seeds_per_warp(int d);   // the batched step's wide tasks (32 lanes x RG seeds)
 int step_resident_warps_per_sm(int d);

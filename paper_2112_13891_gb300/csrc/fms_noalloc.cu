@@ -74,7 +74,7 @@ extern "C" fms_status fms_mean_shift_step_noalloc(const float* points, int64_t n
       launch_pack_points(seeds, m, d, L.DP, (float)scale, Ys, status, st) != cudaSuccess ||
       launch_step_setup(active, (int32_t)m, ctl, L.C, L.Lc, st) != cudaSuccess ||
       launch_ms_step(Xs, n, d, L.DP, Ys, active, &ctl->s, &ctl->C, &ctl->Lc, part,
-                     L.grid_ctas * 8, st, nullptr) != cudaSuccess ||
+                     L.grid_ctas * 8, st, nullptr, nullptr, kKernelGaussian, status) != cudaSuccess ||
       launch_step_finish(part, ctl, seeds, d, L.DA, 1.0 / scale, out_seeds, out_wsum, (int)m,
                          st) != cudaSuccess)
     return FMS_ERR_CUDA;

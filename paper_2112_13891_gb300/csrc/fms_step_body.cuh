@@ -3,6 +3,7 @@
 #pragma once
 
 #include "fms_internal.cuh"
+#include "fms_tc.cuh"
 
 namespace fms {
 
@@ -134,16 +135,42 @@ __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, 
 }
 
 // One wide warp task: lanes own seeds (RG per lane, 32*RG seeds per task),
-// points [j0, j1) read with warp-uniform loads; DA = DPAD + 4.  Group g covers
-// active positions p_lo + g*32*RG ... (positions below p_lo belong to the
-// tensor-core step).
+// points [j0, j1) staged into shared memory 32 rows at a time by bulk copies
+// (TMA) into a two-tile ring of the warp's own (tiles: 2 x 32 x DPAD floats,
+// bars: two mbarriers of count 1, use0 / use1: completed phases of each,
+// carried across the warp's tasks), read back with broadcast loads; DA = DPAD + 4.
+// Group g covers active positions p_lo + g*32*RG ... (positions below p_lo
+// belong to the tensor-core step).  Every wait is bounded: one that gives up
+// sets kStTimeout in *status, waits once more for the warp's copies in flight
+// and makes the task return false (the caller stops).
+constexpr int kWideTile = 32;   // rows per staged tile
+
+// dynamic shared memory of a 128-thread CTA of wide tasks: 4 warps x 2 tiles
+template <int DPAD>
+constexpr int wide_smem_bytes() {
+  return 4 * 2 * kWideTile * DPAD * 4;
+}
+
+// per-warp setup of the tile ring (lane 0 initialises the two mbarriers)
+__device__ __forceinline__ void wide_ring_init(uint64_t* bars, int lane) {
+  if (lane == 0) {
+    tc::init_bar(&bars[0], 1);
+    tc::init_bar(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+}
+
 template <int DPAD, int RG, int KF = kKernelGaussian>
-__device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, int j0, int j1,
+__device__ __forceinline__ bool wide_task(const float* __restrict__ Xs, int j0, int j1,
                                           const float* __restrict__ y,
                                           const int32_t* __restrict__ active, int s, int g, int c,
-                                          float* __restrict__ part, int lane, int p_lo = 0) {
+                                          float* __restrict__ part, int lane, int p_lo,
+                                          float* tiles, uint64_t* bars, uint32_t& use0,
+                                          uint32_t& use1, uint32_t* status) {
   constexpr int DA = DPAD + 4;
   constexpr int SPW = 32 * RG;
+  constexpr int TF = kWideTile * DPAD;   // floats per tile
   float ys[RG][DPAD];
   float acc[RG][DPAD + 1];
 #pragma unroll
@@ -156,30 +183,71 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
 #pragma unroll
     for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
   }
-  for (int j = j0; j < j1; ++j) {
-    float x[DPAD];
-    const float4* xp = reinterpret_cast<const float4*>(Xs + (int64_t)j * DPAD);
-#pragma unroll
-    for (int q = 0; q < DPAD / 4; ++q) {
-      const float4 v = __ldg(xp + q);
-      x[4 * q] = v.x;
-      x[4 * q + 1] = v.y;
-      x[4 * q + 2] = v.z;
-      x[4 * q + 3] = v.w;
+  const int ntile = j1 > j0 ? (j1 - j0 + kWideTile - 1) / kWideTile : 0;
+  auto issue = [&](int t) {   // lane 0: tile t into stage t & 1
+    const int r0 = j0 + t * kWideTile;
+    const int rows = min(kWideTile, j1 - r0);
+    tc::fence_proxy_async();   // the warp's reads of this stage came before (syncwarp)
+    tc::bulk_g2s(tiles + (t & 1) * TF, Xs + (int64_t)r0 * DPAD, (uint32_t)(rows * DPAD * 4),
+                 &bars[t & 1]);
+  };
+  if (lane == 0) {
+    if (ntile > 0) issue(0);
+    if (ntile > 1) issue(1);
+  }
+  bool ok = true;
+  int t = 0;
+  for (; t < ntile; ++t) {
+    const int st = t & 1;
+    if (!tc::wait_bar(&bars[st], (st ? use1 : use0) & 1u)) {
+      ok = false;
+      break;
     }
+    if (st) ++use1;
+    else ++use0;
+    const float* tl = tiles + st * TF;
+    const int rows = min(kWideTile, j1 - (j0 + t * kWideTile));
+    for (int q = 0; q < rows; ++q) {
+      float x[DPAD];
+      const float4* xp = reinterpret_cast<const float4*>(tl + q * DPAD);
 #pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      float dx[DPAD];
+      for (int u = 0; u < DPAD / 4; ++u) {
+        const float4 v = xp[u];
+        x[4 * u] = v.x;
+        x[4 * u + 1] = v.y;
+        x[4 * u + 2] = v.z;
+        x[4 * u + 3] = v.w;
+      }
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
-      float t = -dx[0] * dx[0];
+      for (int r = 0; r < RG; ++r) {
+        float dx[DPAD];
 #pragma unroll
-      for (int k = 1; k < DPAD; ++k) t = fmaf(-dx[k], dx[k], t);
-      const float w = kweight<KF>(t);
-      acc[r][0] += w;
+        for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
+        float tt = -dx[0] * dx[0];
 #pragma unroll
-      for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
+        for (int k = 1; k < DPAD; ++k) tt = fmaf(-dx[k], dx[k], tt);
+        const float w = kweight<KF>(tt);
+        acc[r][0] += w;
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
+      }
     }
+    __syncwarp();
+    if (lane == 0 && t + 2 < ntile) issue(t + 2);
+  }
+  if (!ok) {
+    // the copies this task issued and did not consume: tiles t .. min(t + 1, ntile - 1)
+    if (lane == 0) atomicOr(status, kStTimeout);
+    for (int u = t; u < ntile && u < t + 2; ++u) {
+      if (u & 1) {
+        tc::wait_bar(&bars[1], use1 & 1u);
+        ++use1;
+      } else {
+        tc::wait_bar(&bars[0], use0 & 1u);
+        ++use0;
+      }
+    }
+    return false;
   }
 #pragma unroll
   for (int r = 0; r < RG; ++r) {
@@ -190,6 +258,7 @@ __device__ __forceinline__ void wide_task(const float* __restrict__ Xs, int DP, 
       for (int k = 0; k <= DPAD; ++k) o[k] = acc[r][k];
     }
   }
+  return true;
 }
 
 // One quad warp task (8 <= d <= 16): the warp's lanes are 8 seed slots x 4

@@ -300,16 +300,22 @@ __global__ void __launch_bounds__(256)
 
 template <int DPAD, int RG>
 __global__ void __launch_bounds__(128)
-    batched_step_wide(const float* __restrict__ Xs, int DP, const float* __restrict__ y,
+    batched_step_wide(const float* __restrict__ Xs, const float* __restrict__ y,
                       const int32_t* __restrict__ list, const SetCtl* __restrict__ sc, int B,
                       int kind, const int64_t* __restrict__ task_off,
                       const int64_t* __restrict__ part_off, const int64_t* __restrict__ totals,
-                      float* __restrict__ part) {
+                      float* __restrict__ part, uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) float wide_tiles[];
+  __shared__ __align__(8) uint64_t wide_bars[4][2];
   constexpr int SPW = 32 * RG;
   const int64_t T = totals[0];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* bars = wide_bars[warp];
+  float* tiles = wide_tiles + warp * 2 * kWideTile * DPAD;
+  wide_ring_init(bars, lane);
+  uint32_t use0 = 0u, use1 = 0u;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < T; t += nw) {
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; t < T; t += nw) {
     const int b = find_set(task_off, B, t);
     const SetCtl& c = sc[b];
     int cnt, C, Lc;
@@ -318,16 +324,32 @@ __global__ void __launch_bounds__(128)
     const int G = (cnt + SPW - 1) / SPW;
     const int g = (int)(local % G), ch = (int)(local / G);
     const int j0 = ch * Lc, j1 = min(c.n, j0 + Lc);
-    wide_task<DPAD, RG>(Xs + (int64_t)c.p0 * DP, DP, j0, j1, y, list + c.p0, cnt, g, ch,
-                        part + part_off[b], lane);
+    if (!wide_task<DPAD, RG>(Xs + (int64_t)c.p0 * DPAD, j0, j1, y, list + c.p0, cnt, g, ch,
+                             part + part_off[b], lane, 0, tiles, bars, use0, use1, status))
+      break;
   }
+}
+
+template <int DPAD, int RG>
+static void launch_bwide(int grid, const float* Xs, const float* y, const int32_t* list,
+                         const SetCtl* sc, int B, int kind, const int64_t* task_off,
+                         const int64_t* part_off, const int64_t* totals, float* part,
+                         uint32_t* status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr && wide_smem_bytes<DPAD>() > 48 * 1024) {
+    cudaFuncSetAttribute(batched_step_wide<DPAD, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         wide_smem_bytes<DPAD>());
+    attr = true;
+  }
+  batched_step_wide<DPAD, RG><<<grid, 128, wide_smem_bytes<DPAD>(), st>>>(
+      Xs, y, list, sc, B, kind, task_off, part_off, totals, part, status);
 }
 
 cudaError_t launch_batched_step(const float* Xs, int d, int DP, const float* y,
                                 const int32_t* list, const SetCtl* sc, int B, int kind,
                                 const int64_t* task_off, const int64_t* part_off,
                                 const int64_t* totals, float* part, int target_warps,
-                                cudaStream_t st) {
+                                uint32_t* status, cudaStream_t st) {
   const int g = (target_warps + 7) / 8;
   if (d > 7 && DP != padded_dim(d)) return cudaErrorInvalidValue;   // rows of the compiled width
   switch (d) {
@@ -339,10 +361,10 @@ cudaError_t launch_batched_step(const float* Xs, int d, int DP, const float* y,
     case 6: batched_step_lowd<6, 8, 8><<<g, 256, 0, st>>>(Xs, y, list, sc, B, kind, task_off, part_off, totals, part); break;
     case 7: batched_step_lowd<7, 8, 8><<<g, 256, 0, st>>>(Xs, y, list, sc, B, kind, task_off, part_off, totals, part); break;
     default:
-      if (d <= 8) batched_step_wide<8, 4><<<2 * g, 128, 0, st>>>(Xs, DP, y, list, sc, B, kind, task_off, part_off, totals, part);
-      else if (d <= 16) batched_step_wide<16, 2><<<2 * g, 128, 0, st>>>(Xs, DP, y, list, sc, B, kind, task_off, part_off, totals, part);
-      else if (d <= 32) batched_step_wide<32, 1><<<2 * g, 128, 0, st>>>(Xs, DP, y, list, sc, B, kind, task_off, part_off, totals, part);
-      else batched_step_wide<64, 1><<<2 * g, 128, 0, st>>>(Xs, DP, y, list, sc, B, kind, task_off, part_off, totals, part);
+      if (d <= 8) launch_bwide<8, 4>(2 * g, Xs, y, list, sc, B, kind, task_off, part_off, totals, part, status, st);
+      else if (d <= 16) launch_bwide<16, 2>(2 * g, Xs, y, list, sc, B, kind, task_off, part_off, totals, part, status, st);
+      else if (d <= 32) launch_bwide<32, 1>(2 * g, Xs, y, list, sc, B, kind, task_off, part_off, totals, part, status, st);
+      else launch_bwide<64, 1>(2 * g, Xs, y, list, sc, B, kind, task_off, part_off, totals, part, status, st);
       break;
   }
   return cudaGetLastError();

@@ -54,10 +54,12 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
   }
 }
 
-// Generic FP32 path for 8 <= d <= 64: lanes own seeds (RG per lane), points
-// are read with warp-uniform (broadcast) loads, so no cross-lane reduction is
-// needed.  DPAD is the padded dimension (pad coordinates are zero on both
-// sides and contribute nothing); DA = DPAD + 4 accumulators per seed in part.
+// Generic FP32 path for d > 16: lanes own seeds (RG per lane), every warp
+// stages its chunk's points into shared memory 32 rows at a time with bulk
+// copies (a two-tile ring per warp) and reads them with broadcast loads, so no
+// cross-lane reduction is needed.  DPAD is the padded dimension (pad
+// coordinates are zero on both sides and contribute nothing); DA = DPAD + 4
+// accumulators per seed in part.
 template <int DPAD, int RG, int KF>
 __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs, int64_t n,
                                                     int DP, const float* __restrict__ y,
@@ -67,7 +69,10 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
                                                     const int32_t* __restrict__ Lc_ptr,
                                                     float* __restrict__ part,
                                                     int32_t* __restrict__ s_log,
-                                                    const int32_t* __restrict__ p_lo_ptr) {
+                                                    const int32_t* __restrict__ p_lo_ptr,
+                                                    uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) float wide_tiles[];
+  __shared__ __align__(8) uint64_t wide_bars[4][2];
   constexpr int DA = DPAD + 4;
   constexpr int SPW = 32 * RG;  // seeds per warp task
   const int s = *s_ptr;
@@ -78,15 +83,20 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
   const int Lc = *Lc_ptr;
   const int G = (s - p_lo + SPW - 1) / SPW;
   const int64_t T = (int64_t)G * C;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* bars = wide_bars[warp];
+  float* tiles = wide_tiles + warp * 2 * kWideTile * DPAD;
+  wide_ring_init(bars, lane);
+  uint32_t use0 = 0u, use1 = 0u;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < T;
-       task += nw) {
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; task < T; task += nw) {
     const int g = (int)(task % G);
     const int c = (int)(task / G);
     const int j0 = c * Lc;
     const int j1 = (int)(j0 + Lc < n ? j0 + Lc : n);
-    wide_task<DPAD, RG, KF>(Xs, DP, j0, j1, y, active, s, g, c, part, lane, p_lo);
+    if (!wide_task<DPAD, RG, KF>(Xs, j0, j1, y, active, s, g, c, part, lane, p_lo, tiles, bars,
+                                 use0, use1, status))
+      break;
   }
 }
 
@@ -172,8 +182,12 @@ int step_resident_warps_per_sm(int d) {
       threads = 128;
       if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<8, 4, 0>, 128, 0);
       else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<16, 2, 0>, 128, 0);
-      else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1, 0>, 128, 0);
-      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1, 0>, 128, 0);
+      else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1, 0>, 128, wide_smem_bytes<32>());
+      else {
+        e = cudaFuncSetAttribute(ms_step_wide<64, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes<64>());
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<64, 1, 0>, 128, wide_smem_bytes<64>());
+      }
       break;
   }
   if (e != cudaSuccess || blocks < 1) blocks = 1;
@@ -186,7 +200,7 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
                                    const int32_t* active, const int32_t* s_ptr,
                                    const int32_t* C_ptr, const int32_t* Lc_ptr, float* part,
                                    int target_warps, cudaStream_t st, int32_t* s_log,
-                                   const int32_t* p_lo_ptr) {
+                                   const int32_t* p_lo_ptr, uint32_t* status) {
   const dim3 g((target_warps + 7) / 8);
   const int grid_ctas = (int)g.x;
   // the quad and wide kernels read rows of exactly their compiled width
@@ -205,9 +219,16 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
       else if (d <= 16)
         ms_step_quad<16, 2, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 32)
-        ms_step_wide<32, 1, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
-      else
-        ms_step_wide<64, 1, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<32, 1, KF><<<grid_ctas * 2, 128, wide_smem_bytes<32>(), st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr, status);
+      else {
+        static bool attr = false;
+        if (!attr) {
+          const cudaError_t e = cudaFuncSetAttribute(ms_step_wide<64, 1, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes<64>());
+          if (e != cudaSuccess) return e;
+          attr = true;
+        }
+        ms_step_wide<64, 1, KF><<<grid_ctas * 2, 128, wide_smem_bytes<64>(), st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr, status);
+      }
       break;
   }
   return cudaGetLastError();
@@ -216,12 +237,13 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
-                           int32_t* s_log, const int32_t* p_lo_ptr, int kf) {
+                           int32_t* s_log, const int32_t* p_lo_ptr, int kf, uint32_t* status) {
+  if (d > 16 && !status) return cudaErrorInvalidValue;   // the staged kernel reports timeouts
   if (kf == kKernelFlat)
     return launch_ms_step_t<kKernelFlat>(Xs, n, d, DP, y, active, s_ptr, C_ptr, Lc_ptr, part,
-                                         target_warps, st, s_log, p_lo_ptr);
+                                         target_warps, st, s_log, p_lo_ptr, status);
   return launch_ms_step_t<kKernelGaussian>(Xs, n, d, DP, y, active, s_ptr, C_ptr, Lc_ptr, part,
-                                           target_warps, st, s_log, p_lo_ptr);
+                                           target_warps, st, s_log, p_lo_ptr, status);
 }
 
 }  // namespace fms

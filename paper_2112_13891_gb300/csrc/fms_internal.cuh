@@ -457,7 +457,7 @@ cudaError_t unroll_unpack_rows(const T* src, int64_t rows, int d, int DP, T* dst
 
 // k_step.cu: one update's partial sums for the active seeds
 // status: the call's status word (kStTimeout when a staged-tile wait gives up;
-// required for d > 16)
+// required for d > 8)
 cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const float* y,
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps,
@@ -468,9 +468,9 @@ int step_seeds_per_warp(int d);
 int batched_seeds_per_warp(int d);   // the batched step's wide tasks (32 lanes x RG seeds)
 int step_resident_warps_per_sm(int d);
 // smallest chunk (points) of a warp task: the low-d kernel splits a chunk over
-// 32 lanes, the quad kernel (8 <= d <= 16) over 4 point lanes, the wide kernel
-// (d > 16) gives every point to all 32 lanes
-inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : (d <= 16 ? 256 : 64); }
+// 32 lanes, the quad kernel (d = 8) over 4 point lanes, the wide kernel
+// (d > 8) gives every point to all 32 lanes
+inline int step_min_chunk(int d) { return d <= 7 ? kStepMinChunk : (d <= 8 ? 256 : 64); }
 int step_accumulators(int d);
 
 // Scratch layout of one stand-alone update (fms_mean_shift_step and its

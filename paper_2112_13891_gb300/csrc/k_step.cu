@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
   }
 }
 
-// Generic FP32 path for d > 16: lanes own seeds (RG per lane), every warp
+// Generic FP32 path for d > 8: lanes own seeds (RG per lane), every warp
 // stages its chunk's points into shared memory 32 rows at a time with bulk
 // copies (a two-tile ring per warp) and reads them with broadcast loads, so no
 // cross-lane reduction is needed.  DPAD is the padded dimension (pad
@@ -100,10 +100,12 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
   }
 }
 
-// 8 <= d <= 16: the quad kernel (8 seed slots x 4 point lanes per warp).  At
-// d = 32 (one seed per slot) its four distinct point rows per load cost more
-// L1 wavefronts per evaluation than the arithmetic can cover (measured: 73 vs
-// 170 Geval/s with 65,536 seeds), so d > 16 keeps the wide kernel.
+// d = 8: the quad kernel (8 seed slots x 4 point lanes per warp).  At d = 32
+// (one seed per slot) its four distinct point rows per load cost more L1
+// wavefronts per evaluation than the arithmetic can cover (measured: 73 vs 170
+// Geval/s with 65,536 seeds); at 9 <= d <= 16 the staged wide kernel measured
+// 8.1 against 10.7 ms for one update of 65,536 x 65,536, so quad tasks serve
+// d = 8 only.
 template <int DPAD, int RG, int KF>
 __global__ void __launch_bounds__(128) ms_step_quad(const float* __restrict__ Xs, int64_t n,
                                                     int DP, const float* __restrict__ y,
@@ -140,7 +142,6 @@ int step_seeds_per_warp(int d) {
   if (d <= 3) return 8;
   if (d <= 7) return 4;
   if (d <= 8) return 8 * 4;    // quad kernel: 8 slots x RG seeds
-  if (d <= 16) return 8 * 2;
   return 32;                   // wide kernel: 32 lanes x 1 seed
 }
 
@@ -181,7 +182,7 @@ int step_resident_warps_per_sm(int d) {
     default:
       threads = 128;
       if (d <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<8, 4, 0>, 128, 0);
-      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_quad<16, 2, 0>, 128, 0);
+      else if (d <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<16, 1, 0>, 128, wide_smem_bytes<16>());
       else if (d <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ms_step_wide<32, 1, 0>, 128, wide_smem_bytes<32>());
       else {
         e = cudaFuncSetAttribute(ms_step_wide<64, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes<64>());
@@ -217,7 +218,7 @@ static cudaError_t launch_ms_step_t(const float* Xs, int64_t n, int d, int DP, c
       if (d <= 8)
         ms_step_quad<8, 4, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
       else if (d <= 16)
-        ms_step_quad<16, 2, KF><<<grid_ctas * 2, 128, 0, st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr);
+        ms_step_wide<16, 1, KF><<<grid_ctas * 2, 128, wide_smem_bytes<16>(), st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr, status);
       else if (d <= 32)
         ms_step_wide<32, 1, KF><<<grid_ctas * 2, 128, wide_smem_bytes<32>(), st>>>(Xs, n, DP, y, active, s_ptr, C_ptr, Lc_ptr, part, s_log, p_lo_ptr, status);
       else {
@@ -238,7 +239,7 @@ cudaError_t launch_ms_step(const float* Xs, int64_t n, int d, int DP, const floa
                            const int32_t* active, const int32_t* s_ptr, const int32_t* C_ptr,
                            const int32_t* Lc_ptr, float* part, int target_warps, cudaStream_t st,
                            int32_t* s_log, const int32_t* p_lo_ptr, int kf, uint32_t* status) {
-  if (d > 16 && !status) return cudaErrorInvalidValue;   // the staged kernel reports timeouts
+  if (d > 8 && !status) return cudaErrorInvalidValue;   // the staged kernel reports timeouts
   if (kf == kKernelFlat)
     return launch_ms_step_t<kKernelFlat>(Xs, n, d, DP, y, active, s_ptr, C_ptr, Lc_ptr, part,
                                          target_warps, st, s_log, p_lo_ptr, status);

@@ -467,7 +467,10 @@ fms_status fms_label_points(const float* points, int64_t n, int32_t d, const flo
  *           dL/dh of each set.
  * Both calls are asynchronous on `stream`.  Errors: FMS_ERR_INVALID_ARG (null
  * pointer, sizes out of range, h not finite and positive), FMS_ERR_WORKSPACE
- * (buffers too small or misaligned), FMS_ERR_CUDA (a launch failed).
+ * (buffers too small or misaligned), FMS_ERR_CUDA (a launch failed).  The
+ * pair kernels stage rows in shared memory with bulk copies whose waits are
+ * bounded; a wait that gives up turns the affected outputs into NaN (the
+ * calls do not synchronise, so it is reported through the results).
  *
  * The *_f64 entry points are the same computation in FP64 (double pointers,
  * h as double; `ckpt` and `ws` sized by the *_f64 size functions), for

@@ -438,17 +438,19 @@ struct UGeom {
 };
 // One forward update (T = float, or double for checking gradients); Wout (W_t)
 // and Sh (the weight shift of seeds whose W underflowed, 0 otherwise) may be
-// null; rlist [B m] and rcount (zero on entry, zero again on return) are scratch.
+// null; rlist [B m] and rcount (zero on entry, zero again on return) are
+// scratch; status receives kStTimeout if a staged-row wait gives up (the
+// affected outputs are then NaN).
 template <typename T>
 cudaError_t unroll_fwd_step(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
                             T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
-                            cudaStream_t st);
+                            uint32_t* status, cudaStream_t st);
 // The adjoint of one update; SD is scratch of [B m] x (2 DP + 4) values.
 template <typename T>
 cudaError_t unroll_bwd_step(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
                             const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
                             T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
-                            cudaStream_t st);
+                            uint32_t* status, cudaStream_t st);
 template <typename T>
 cudaError_t unroll_pack_rows(const T* src, int64_t rows, int d, int DP, T* dst, cudaStream_t st);
 template <typename T>

@@ -114,6 +114,69 @@ __device__ __forceinline__ void init_bar(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
 
+// A warp walks rows [r0, r1) of a row-major global array (ROW elements of T
+// per row, rows 16-byte aligned, ROW * sizeof(T) a multiple of 16) through a
+// two-tile ring of its own in shared memory: lane 0 keeps up to two bulk
+// copies of kRingRows rows in flight, every lane calls row_fn(row pointer) for
+// each row in order.  tiles: 2 x kRingRows x ROW elements; bars: two
+// mbarriers of count 1 (ring_init); use0 / use1: completed phases of each,
+// carried across calls.  A wait that gives up sets kStTimeout in *status,
+// waits once more for the copies in flight and returns false.
+constexpr int kRingRows = 32;
+
+__device__ __forceinline__ void ring_init(uint64_t* bars, int lane) {
+  if (lane == 0) {
+    init_bar(&bars[0], 1);
+    init_bar(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+}
+
+template <int ROW, typename T, typename F>
+__device__ __forceinline__ bool ring_rows(const T* __restrict__ src, int r0, int r1, T* tiles,
+                                          uint64_t* bars, uint32_t& use0, uint32_t& use1,
+                                          int lane, uint32_t* status, F&& row_fn) {
+  static_assert((ROW * sizeof(T)) % 16 == 0, "bulk copies move multiples of 16 bytes");
+  constexpr int TE = kRingRows * ROW;   // elements per tile
+  const int ntile = r1 > r0 ? (r1 - r0 + kRingRows - 1) / kRingRows : 0;
+  auto issue = [&](int t) {
+    const int a = r0 + t * kRingRows;
+    const int rows = min(kRingRows, r1 - a);
+    fence_proxy_async();   // the warp's reads of this stage came before (syncwarp)
+    bulk_g2s(tiles + (t & 1) * TE, src + (int64_t)a * ROW, (uint32_t)(rows * ROW * sizeof(T)),
+             &bars[t & 1]);
+  };
+  if (lane == 0) {
+    if (ntile > 0) issue(0);
+    if (ntile > 1) issue(1);
+  }
+  int t = 0;
+  for (; t < ntile; ++t) {
+    const int st = t & 1;
+    if (!wait_bar(&bars[st], (st ? use1 : use0) & 1u)) break;
+    if (st) ++use1;
+    else ++use0;
+    const T* tl = tiles + st * TE;
+    const int rows = min(kRingRows, r1 - (r0 + t * kRingRows));
+    for (int q = 0; q < rows; ++q) row_fn(tl + q * ROW);
+    __syncwarp();
+    if (lane == 0 && t + 2 < ntile) issue(t + 2);
+  }
+  if (t == ntile) return true;
+  if (lane == 0) atomicOr(status, kStTimeout);
+  for (int u = t; u < ntile && u < t + 2; ++u) {   // the copies issued and not consumed
+    if (u & 1) {
+      wait_bar(&bars[1], use1 & 1u);
+      ++use1;
+    } else {
+      wait_bar(&bars[0], use0 & 1u);
+      ++use0;
+    }
+  }
+  return false;
+}
+
 __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }

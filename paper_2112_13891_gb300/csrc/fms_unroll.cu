@@ -64,7 +64,7 @@ int grid_blocks() {
 int n_ckpt(int32_t T, int32_t k) { return (T + k - 1) / k; }
 
 struct FwdLayout {
-  size_t Xp, Ya, Yb, part, rlist, total;
+  size_t Xp, Ya, Yb, part, rlist, status, total;
 };
 FwdLayout fwd_layout(const UGeom& g, size_t es) {
   FwdLayout L{};
@@ -79,12 +79,13 @@ FwdLayout fwd_layout(const UGeom& g, size_t es) {
   L.Yb = take((size_t)g.B * g.m * g.DP * es);
   L.part = take((size_t)g.B * g.Cp * g.m * (g.DP + 1) * es);
   L.rlist = take(((size_t)g.B * g.m + 1) * 4);   // rescue list, then its count
+  L.status = take(64);   // kStTimeout if a staged-row wait gave up
   L.total = o;
   return L;
 }
 
 struct BwdLayout {
-  size_t Xp, seg, Ga, Gb, part_s, part_p, SD, dh_part, dXp, dh, rlist, total;
+  size_t Xp, seg, Ga, Gb, part_s, part_p, SD, dh_part, dXp, dh, rlist, status, total;
 };
 BwdLayout bwd_layout(const UGeom& g, int32_t k, size_t es) {
   BwdLayout L{};
@@ -106,6 +107,7 @@ BwdLayout bwd_layout(const UGeom& g, int32_t k, size_t es) {
   L.dXp = take((size_t)g.B * g.n * g.DP * es);
   L.dh = take((size_t)g.B * 8);
   L.rlist = take((rowsY + 1) * 4);
+  L.status = take(64);
   L.total = o;
   return L;
 }
@@ -156,6 +158,7 @@ fms_status forward_impl(const E* points, const E* seeds0, int32_t B, int64_t n,
   E* part = at<E>(ws, L.part);
   int32_t* rlist = at<int32_t>(ws, L.rlist);
   int32_t* rcount = rlist + (size_t)B * m;
+  uint32_t* status = at<uint32_t>(ws, L.status);
   const CkptLayout CL = ckpt_layout(B, m, d, T, k, sizeof(E));
   E* C = at<E>(ckpt, CL.pos);
   E* Wh = at<E>(ckpt, CL.W);
@@ -165,7 +168,8 @@ fms_status forward_impl(const E* points, const E* seeds0, int32_t B, int64_t n,
   const int grid = grid_blocks();
   if (unroll_pack_rows<E>(points, (int64_t)B * n, d, g.DP, Xp, st) != cudaSuccess ||
       unroll_pack_rows<E>(seeds0, (int64_t)rowsY, d, g.DP, Ya, st) != cudaSuccess ||
-      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess)
+      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, 64, st) != cudaSuccess)
     return FMS_ERR_CUDA;
   for (int t = 0; t < T; ++t) {
     if (t % k == 0 &&
@@ -173,7 +177,7 @@ fms_status forward_impl(const E* points, const E* seeds0, int32_t B, int64_t n,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return FMS_ERR_CUDA;
     if (unroll_fwd_step<E>(Xp, Ya, g, c, part, Yb, Wh + (size_t)t * rowsY, Shh + (size_t)t * rowsY,
-                        rlist, rcount, grid, st) != cudaSuccess)
+                           rlist, rcount, grid, status, st) != cudaSuccess)
       return FMS_ERR_CUDA;
     E* tmp = Ya;
     Ya = Yb;
@@ -211,6 +215,7 @@ fms_status backward_impl(const E* points, int32_t B, int64_t n, int64_t m, int32
   E* part_s = at<E>(ws, L.part_s);
   E* part_p = at<E>(ws, L.part_p);
   E* SD = at<E>(ws, L.SD);
+  uint32_t* status = at<uint32_t>(ws, L.status);
   E* dh_part = at<E>(ws, L.dh_part);
   E* dXp = at<E>(ws, L.dXp);
   double* dh = at<double>(ws, L.dh);
@@ -228,7 +233,8 @@ fms_status backward_impl(const E* points, int32_t B, int64_t n, int64_t m, int32
       unroll_pack_rows<E>(grad_out, (int64_t)rowsY, d, g.DP, Ga, st) != cudaSuccess ||
       cudaMemsetAsync(dXp, 0, (size_t)B * n * g.DP * sizeof(E), st) != cudaSuccess ||
       cudaMemsetAsync(dh, 0, (size_t)B * 8, st) != cudaSuccess ||
-      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess)
+      cudaMemsetAsync(rcount, 0, 4, st) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, 64, st) != cudaSuccess)
     return FMS_ERR_CUDA;
   E* G = Ga;
   E* Gp = Gb;
@@ -245,13 +251,13 @@ fms_status backward_impl(const E* points, int32_t B, int64_t n, int64_t m, int32
     };
     for (int u = 0; u + 1 < len; ++u)
       if (unroll_fwd_step<E>(Xp, pos(u), g, c, part_s, seg + (size_t)u * rowY, nullptr, nullptr,
-                          rlist, rcount, grid, st) != cudaSuccess)
+                             rlist, rcount, grid, status, st) != cudaSuccess)
         return FMS_ERR_CUDA;
     for (int u = len - 1; u >= 0; --u) {
       const size_t t = (size_t)(t0 + u);
       if (unroll_bwd_step<E>(Xp, pos(u), pos(u + 1), G, Wh + t * rowsY, Shh + t * rowsY, g, c,
-                          inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gp, dXp, dh, grid,
-                          st) != cudaSuccess)
+                             inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gp, dXp, dh, grid,
+                             status, st) != cudaSuccess)
         return FMS_ERR_CUDA;
       E* tmp = G;
       G = Gp;

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) ms_step_lowd(const float* __restrict__ Xs
 // coordinates are zero on both sides and contribute nothing); DA = DPAD + 4
 // accumulators per seed in part.
 template <int DPAD, int RG, int KF>
-__global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs, int64_t n,
+__global__ void __launch_bounds__(128, DPAD <= 16 ? 6 : (DPAD <= 32 ? 3 : 2)) ms_step_wide(const float* __restrict__ Xs, int64_t n,
                                                     int DP, const float* __restrict__ y,
                                                     const int32_t* __restrict__ active,
                                                     const int32_t* __restrict__ s_ptr,
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) ms_step_wide(const float* __restrict__ Xs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* bars = wide_bars[warp];
   float* tiles = wide_tiles + warp * 2 * kWideTile * DPAD;
-  wide_ring_init(bars, lane);
+  tc::ring_init(bars, lane);
   uint32_t use0 = 0u, use1 = 0u;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; task < T; task += nw) {

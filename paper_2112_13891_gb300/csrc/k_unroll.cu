@@ -34,6 +34,7 @@
 // term is a difference of nearby positions (no cancellation of coordinates).
 //   finish kernels sum the chunk partials in chunk order.
 #include "fms_internal.cuh"
+#include "fms_tc.cuh"
 
 namespace fms {
 
@@ -57,6 +58,36 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, double (&
     v[2 * q] = t.x;
     v[2 * q + 1] = t.y;
   }
+}
+
+// a row already in shared memory (staged by the ring): plain vector loads
+template <int DPAD>
+__device__ __forceinline__ void smem_row(const float* p, float (&v)[DPAD]) {
+#pragma unroll
+  for (int q = 0; q < DPAD / 4; ++q) {
+    const float4 t = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+template <int DPAD>
+__device__ __forceinline__ void smem_row(const double* p, double (&v)[DPAD]) {
+#pragma unroll
+  for (int q = 0; q < DPAD / 2; ++q) {
+    const double2 t = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = t.x;
+    v[2 * q + 1] = t.y;
+  }
+}
+
+// Per-warp staging rings of the three pair kernels (tc::ring_rows): the
+// forward and seed-major passes stream point rows (DPAD values), the
+// point-major pass streams seed rows (2 DPAD + 4 values); 4 warps per CTA.
+template <typename T, int ROW>
+constexpr int unroll_ring_smem() {
+  return 4 * 2 * tc::kRingRows * ROW * (int)sizeof(T);
 }
 
 // the element type's exp2, fma and min (FP32: the MUFU exp2 with flush to zero)
@@ -88,9 +119,14 @@ constexpr int unroll_point_r() {
 template <typename T, int DPAD, int R>
 __global__ void __launch_bounds__(128)
     unroll_fwd_partial(const T* __restrict__ X, const T* __restrict__ Y, UGeom g,
-                       T c, T* __restrict__ part) {
+                       T c, T* __restrict__ part, uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  __shared__ __align__(8) uint64_t ring_bars[4][2];
   constexpr int SPW = 32 * R;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* tiles = reinterpret_cast<T*>(ring_smem) + warp * 2 * tc::kRingRows * DPAD;
+  tc::ring_init(ring_bars[warp], lane);
+  uint32_t use0 = 0u, use1 = 0u;
   const int Gs = (g.m + SPW - 1) / SPW;
   const int64_t NT = (int64_t)g.B * Gs * g.Cp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -111,13 +147,10 @@ __global__ void __launch_bounds__(128)
       for (int k = 0; k < DPAD; ++k) S[r][k] = T(0);
     }
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
-    T xn[DPAD];   // the next point's row, loaded while this one is evaluated
-    if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
-    for (int j = j0; j < j1; ++j) {
+    const bool ok = tc::ring_rows<DPAD>(Xb, j0, j1, tiles, ring_bars[warp], use0, use1, lane,
+                                        status, [&](const T* row) {
       T x[DPAD];
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
-      if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
+      smem_row<DPAD>(row, x);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         T dx[DPAD], D2 = T(0);
@@ -131,10 +164,11 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int k = 0; k < DPAD; ++k) S[r][k] = ufma(w, dx[k], S[r][k]);
       }
-    }
+    });
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = gs * SPW + r * 32 + lane;
+      if (!ok) W[r] = T(NAN);   // a wait gave up: the seed's update comes out NaN
       if (i < g.m) {
         T* o = part + (((int64_t)b * g.Cp + ch) * g.m + i) * (DPAD + 1);
         o[0] = W[r];
@@ -143,6 +177,7 @@ __global__ void __launch_bounds__(128)
           if (k < g.d) o[1 + k] = S[r][k];
       }
     }
+    if (!ok) break;
   }
 }
 
@@ -283,9 +318,15 @@ __global__ void unroll_seed_data(const T* __restrict__ Y, const T* __restrict__ 
 template <typename T, int DPAD>
 __global__ void __launch_bounds__(128)
     unroll_bwd_seed(const T* __restrict__ X, const T* __restrict__ MU,
-                    const T* __restrict__ SD, UGeom g, T c, T* __restrict__ part) {
+                    const T* __restrict__ SD, UGeom g, T c, T* __restrict__ part,
+                    uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  __shared__ __align__(8) uint64_t ring_bars[4][2];
   constexpr int SDW = 2 * DPAD + 4;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* tiles = reinterpret_cast<T*>(ring_smem) + warp * 2 * tc::kRingRows * DPAD;
+  tc::ring_init(ring_bars[warp], lane);
+  uint32_t use0 = 0u, use1 = 0u;
   const int Gs = (g.m + 31) / 32;
   const int64_t NT = (int64_t)g.B * Gs * g.Cp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -309,13 +350,10 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int k = 0; k < DPAD; ++k) DY[k] = T(0);
     const int j0 = ch * g.Lp, j1 = min(g.n, j0 + g.Lp);
-    T xn[DPAD];
-    if (j0 < j1) load_row<DPAD>(Xb + (int64_t)j0 * DPAD, xn);
-    for (int j = j0; j < j1; ++j) {
+    const bool ok = tc::ring_rows<DPAD>(Xb, j0, j1, tiles, ring_bars[warp], use0, use1, lane,
+                                        status, [&](const T* row) {
       T x[DPAD];
-#pragma unroll
-      for (int k = 0; k < DPAD; ++k) x[k] = xn[k];
-      if (j + 1 < j1) load_row<DPAD>(Xb + (int64_t)(j + 1) * DPAD, xn);
+      smem_row<DPAD>(row, x);
       T dx[DPAD], D2 = T(0), a = gd;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) {
@@ -328,7 +366,8 @@ __global__ void __launch_bounds__(128)
       SA += pa;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k) DY[k] = ufma(pa, dx[k], DY[k]);
-    }
+    });
+    if (!ok) DH = T(NAN);   // a wait gave up: the gradient comes out NaN
     if (gs * 32 + lane < g.m) {
       T mu[DPAD];
       load_row<DPAD>(MU + row * DPAD, mu);
@@ -336,8 +375,9 @@ __global__ void __launch_bounds__(128)
       o[0] = DH;
 #pragma unroll
       for (int k = 0; k < DPAD; ++k)
-        if (k < g.d) o[1 + k] = ufma(y[k] - mu[k], SA, DY[k]);
+        if (k < g.d) o[1 + k] = ok ? ufma(y[k] - mu[k], SA, DY[k]) : T(NAN);
     }
+    if (!ok) break;
   }
 }
 
@@ -372,10 +412,15 @@ __global__ void unroll_bwd_seed_finish(const T* __restrict__ part, UGeom g, T in
 template <typename T, int DPAD, int R>
 __global__ void __launch_bounds__(128)
     unroll_bwd_point(const T* __restrict__ X, const T* __restrict__ SD, UGeom g, T c,
-                     T inv_h2, T* __restrict__ part) {
+                     T inv_h2, T* __restrict__ part, uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  __shared__ __align__(8) uint64_t ring_bars[4][2];
   constexpr int SDW = 2 * DPAD + 4;
   constexpr int PPW = 32 * R;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* tiles = reinterpret_cast<T*>(ring_smem) + warp * 2 * tc::kRingRows * SDW;
+  tc::ring_init(ring_bars[warp], lane);
+  uint32_t use0 = 0u, use1 = 0u;
   const int Gp = (g.n + PPW - 1) / PPW;
   const int64_t NT = (int64_t)g.B * Gp * g.Cs;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -395,13 +440,13 @@ __global__ void __launch_bounds__(128)
     }
     const int i0 = ch * g.Ls, i1 = min(g.m, i0 + g.Ls);
     const T* sdb = SD + (int64_t)b * g.m * SDW;
-    for (int i = i0; i < i1; ++i) {
-      const T* sd = sdb + (int64_t)i * SDW;
+    const bool ok = tc::ring_rows<SDW>(sdb, i0, i1, tiles, ring_bars[warp], use0, use1, lane,
+                                       status, [&](const T* sd) {
       T y[DPAD], gg[DPAD];
-      load_row<DPAD>(sd, y);
-      load_row<DPAD>(sd + DPAD, gg);
+      smem_row<DPAD>(sd, y);
+      smem_row<DPAD>(sd + DPAD, gg);
       T tail[4];
-    load_row<4>(sd + 2 * DPAD, tail);
+      smem_row<4>(sd + 2 * DPAD, tail);
       const T invW = tail[0], sh = tail[1], gd = tail[2];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -417,16 +462,20 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int k = 0; k < DPAD; ++k) DX[r][k] = ufma(p, gg[k], ufma(-q, dx[k], DX[r][k]));
       }
-    }
+    });
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int j = gp * PPW + r * 32 + lane;
+      if (!ok)
+#pragma unroll
+        for (int k = 0; k < DPAD; ++k) DX[r][k] = T(NAN);   // a wait gave up
       if (j < g.n) {
         T* o = part + (((int64_t)b * g.Cs + ch) * g.n + j) * DPAD;
 #pragma unroll
         for (int k = 0; k < DPAD; ++k) o[k] = k < g.d ? DX[r][k] : T(0);
       }
     }
+    if (!ok) break;
   }
 }
 
@@ -495,11 +544,27 @@ static int blocks_for(int64_t work, int per = 256) {
   return (int)b;
 }
 
+// dynamic shared memory above the default 48 KB needs the kernel's attribute
+// (set once per kernel)
+template <typename K>
+static cudaError_t ring_attr(K kernel, int bytes, bool& done) {
+  if (done || bytes <= 48 * 1024) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 template <typename T, int DPAD>
 static cudaError_t fwd_step_t(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
                               T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
-                              cudaStream_t st) {
-  unroll_fwd_partial<T, DPAD, unroll_fwd_r<T, DPAD>()><<<grid, 128, 0, st>>>(X, Y, g, c, part);
+                              uint32_t* status, cudaStream_t st) {
+  constexpr int sm = unroll_ring_smem<T, DPAD>();
+  static bool attr = false;
+  const cudaError_t ea = ring_attr(unroll_fwd_partial<T, DPAD, unroll_fwd_r<T, DPAD>()>, sm, attr);
+  if (ea != cudaSuccess) return ea;
+  unroll_fwd_partial<T, DPAD, unroll_fwd_r<T, DPAD>()><<<grid, 128, sm, st>>>(X, Y, g, c, part,
+                                                                               status);
   unroll_fwd_finish<T><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part, Y, g, Ynext, Wout,
                                                                        Sh, rlist, rcount);
   unroll_fwd_rescue<T, DPAD><<<1, 1024, 0, st>>>(X, Y, g, c, rlist, rcount, Ynext, Wout, Sh);
@@ -509,12 +574,12 @@ static cudaError_t fwd_step_t(const T* X, const T* Y, const UGeom& g, T c, T* pa
 template <typename T>
 cudaError_t unroll_fwd_step(const T* X, const T* Y, const UGeom& g, T c, T* part, T* Ynext,
                             T* Wout, T* Sh, int32_t* rlist, int32_t* rcount, int grid,
-                            cudaStream_t st) {
+                            uint32_t* status, cudaStream_t st) {
   switch (g.DP) {
-    case 4: return fwd_step_t<T, 4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 8: return fwd_step_t<T, 8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 16: return fwd_step_t<T, 16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
-    case 32: return fwd_step_t<T, 32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, st);
+    case 4: return fwd_step_t<T, 4>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, status, st);
+    case 8: return fwd_step_t<T, 8>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, status, st);
+    case 16: return fwd_step_t<T, 16>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, status, st);
+    case 32: return fwd_step_t<T, 32>(X, Y, g, c, part, Ynext, Wout, Sh, rlist, rcount, grid, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -523,12 +588,17 @@ template <typename T, int DPAD>
 static cudaError_t bwd_step_t(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
                               const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
                               T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
-                              cudaStream_t st) {
+                              uint32_t* status, cudaStream_t st) {
+  constexpr int sm_p = unroll_ring_smem<T, 2 * DPAD + 4>(), sm_s = unroll_ring_smem<T, DPAD>();
+  static bool attr_p = false, attr_s = false;
+  cudaError_t ea = ring_attr(unroll_bwd_point<T, DPAD, unroll_point_r<T, DPAD>()>, sm_p, attr_p);
+  if (ea == cudaSuccess) ea = ring_attr(unroll_bwd_seed<T, DPAD>, sm_s, attr_s);
+  if (ea != cudaSuccess) return ea;
   unroll_seed_data<T, DPAD><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(Y, MU, G, Wt, Sh, g,
                                                                            SD);
-  unroll_bwd_point<T, DPAD, unroll_point_r<T, DPAD>()><<<grid, 128, 0, st>>>(X, SD, g, c, inv_h2,
-                                                                              part_p);
-  unroll_bwd_seed<T, DPAD><<<grid, 128, 0, st>>>(X, MU, SD, g, c, part_s);
+  unroll_bwd_point<T, DPAD, unroll_point_r<T, DPAD>()><<<grid, 128, sm_p, st>>>(
+      X, SD, g, c, inv_h2, part_p, status);
+  unroll_bwd_seed<T, DPAD><<<grid, 128, sm_s, st>>>(X, MU, SD, g, c, part_s, status);
   unroll_bwd_point_finish<T><<<blocks_for((int64_t)g.B * g.n * g.DP), 256, 0, st>>>(part_p, g, dX);
   unroll_bwd_seed_finish<T><<<blocks_for((int64_t)g.B * g.m), 256, 0, st>>>(part_s, g, inv_h2,
                                                                             inv_h3, Gprev,
@@ -541,12 +611,12 @@ template <typename T>
 cudaError_t unroll_bwd_step(const T* X, const T* Y, const T* MU, const T* G, const T* Wt,
                             const T* Sh, const UGeom& g, T c, T inv_h2, T inv_h3, T* part_s,
                             T* part_p, T* SD, T* dh_part, T* Gprev, T* dX, double* dh, int grid,
-                            cudaStream_t st) {
+                            uint32_t* status, cudaStream_t st) {
   switch (g.DP) {
-    case 4: return bwd_step_t<T, 4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 8: return bwd_step_t<T, 8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 16: return bwd_step_t<T, 16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
-    case 32: return bwd_step_t<T, 32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, st);
+    case 4: return bwd_step_t<T, 4>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, status, st);
+    case 8: return bwd_step_t<T, 8>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, status, st);
+    case 16: return bwd_step_t<T, 16>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, status, st);
+    case 32: return bwd_step_t<T, 32>(X, Y, MU, G, Wt, Sh, g, c, inv_h2, inv_h3, part_s, part_p, SD, dh_part, Gprev, dX, dh, grid, status, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -566,10 +636,10 @@ cudaError_t unroll_unpack_rows(const T* src, int64_t rows, int d, int DP, T* dst
 
 #define FMS_UNROLL_INST(T)                                                                      \
   template cudaError_t unroll_fwd_step<T>(const T*, const T*, const UGeom&, T, T*, T*, T*, T*,  \
-                                          int32_t*, int32_t*, int, cudaStream_t);              \
+                                          int32_t*, int32_t*, int, uint32_t*, cudaStream_t);   \
   template cudaError_t unroll_bwd_step<T>(const T*, const T*, const T*, const T*, const T*,     \
                                           const T*, const UGeom&, T, T, T, T*, T*, T*, T*, T*, \
-                                          T*, double*, int, cudaStream_t);                     \
+                                          T*, double*, int, uint32_t*, cudaStream_t);          \
   template cudaError_t unroll_pack_rows<T>(const T*, int64_t, int, int, T*, cudaStream_t);      \
   template cudaError_t unroll_unpack_rows<T>(const T*, int64_t, int, int, T*, cudaStream_t);
 FMS_UNROLL_INST(float)

@@ -695,10 +695,16 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
           e = cudaStreamBeginCaptureToGraph(cs2, post, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cudaError_t e2 = launch_ms_refine(
-              Xs, n, d, y, kept, acc1, &mctl->M, qmax, ym, yf, mscore, rtol_s * rtol_s,
-              kRefineMaxIter, &rctl->steps, reinterpret_cast<unsigned long long*>(&rctl->evals),
-              cs2, kf, sphere_rd);
+          cudaError_t e2 =
+              gp.ok ? launch_ms_grid_refine(
+                          gp, Xs, n, d, y, kept, acc1, &mctl->M, ym, yf, mscore, rtol_s * rtol_s,
+                          kRefineMaxIter, &rctl->steps,
+                          reinterpret_cast<unsigned long long*>(&rctl->evals), status,
+                          grid_scratch, cs2, kf, sphere_rd)
+                    : launch_ms_refine(
+                          Xs, n, d, y, kept, acc1, &mctl->M, qmax, ym, yf, mscore, rtol_s * rtol_s,
+                          kRefineMaxIter, &rctl->steps,
+                          reinterpret_cast<unsigned long long*>(&rctl->evals), cs2, kf, sphere_rd);
           if (e2 == cudaSuccess)
             e2 = launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        cap_modes, cs2);
@@ -887,10 +893,16 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       // cluster-persistent refinement (all updates, and each mode's density, in one launch)
       const double rtol_s = kRefineTolFactor * (double)h * scale;
       const int clusters = hm.M < qmax ? hm.M : qmax;
-      FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
-                                  rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
-                                  reinterpret_cast<unsigned long long*>(&rctl->evals), st, kf,
-                                  sphere_rd));
+      if (gp.ok && hm.M <= grid_refine_capacity())
+        FMS_LAUNCH(launch_ms_grid_refine(gp, Xs, n, d, y, kept, acc1, &mctl->M, ym, yf, mscore,
+                                         rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
+                                         reinterpret_cast<unsigned long long*>(&rctl->evals),
+                                         status, grid_scratch, st, kf, sphere_rd));
+      else
+        FMS_LAUNCH(launch_ms_refine(Xs, n, d, y, kept, acc1, &mctl->M, clusters, ym, yf, mscore,
+                                    rtol_s * rtol_s, kRefineMaxIter, &rctl->steps,
+                                    reinterpret_cast<unsigned long long*>(&rctl->evals), st, kf,
+                                    sphere_rd));
       FMS_LAUNCH(launch_greedy_merge_d(&mctl->M, mscore, ym, DP, d, r2_s, alive, acc2, &mctl->Mr,
                                        hm.M, st));
       FMS_LAUNCH(launch_canonical_order(ym, mscore, acc2, &mctl->Mr, d, DP, 1.0 / scale,

@@ -429,6 +429,15 @@ size_t grid_scratch_clear_bytes(int d);
 // Clears the scratch's counter and first accumulator, then launches the round.
 cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs a,
                                  void* scratch, cudaStream_t st);
+// The refinement (FP64 positions, up to grid_refine_capacity() merged modes)
+// on the same persistent grid; the accumulators reuse the round's scratch.
+int grid_refine_capacity();
+cudaError_t launch_ms_grid_refine(const GridPlan& p, const float* Xs, int64_t n, int d,
+                                  const float* y, const int32_t* kept, const int32_t* accepted,
+                                  const int32_t* M_ptr, double* ym, float* yf, double* mscore,
+                                  double tol2_s, int max_iter, int32_t* iters_out,
+                                  unsigned long long* evals, uint32_t* status, void* scratch,
+                                  cudaStream_t st, int kf, double sphere_r);
 
 // k_unroll.cu: unrolled steps and their adjoint
 struct UGeom {

@@ -664,6 +664,284 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// ms_grid_refine: the merged modes take more updates with FP64 positions (the
+// refinement before the second prune), on the same decomposition as the
+// round: CTA c owns a point slice (staged into shared memory by TMA bulk
+// copies when it fits), every CTA evaluates every active mode against its
+// slice with the round's warp tasks at the FP32 positions yf = fl32(ym), and
+// the leaves are added exactly in 64-bit fixed point into one of three
+// rotating accumulators.  One grid barrier per update (bounded; a timeout
+// sets kStTimeout and every CTA leaves); after it every CTA reads the same
+// totals and applies the same FP64 update to its copy of the modes:
+//   ym <- ym + S/W - (ym - yf)   (= m(yf)),
+// a mode stops once ||step|| <= tol (FP64) or after max_iter updates.  The
+// density that orders the second prune is W of the mode's last update.  CTA
+// 0 clears the accumulator of update u - 1 after barrier u (every CTA has
+// read it) and writes the modes back at the end.
+// ---------------------------------------------------------------------------
+constexpr int kGridRefineModes = 512;   // modes one refinement launch holds
+constexpr int kGridRefineWarps = 16;
+constexpr int kGridRefineBufs = 3;
+
+struct GridRefineArgs {
+  const float* Xs;
+  int n, per_cta, n_sub, sub_len;
+  const float* y;
+  const int32_t* kept;
+  const int32_t* accepted;
+  const int32_t* M_ptr;
+  double* ym;
+  float* yf;
+  double* mscore;
+  double tol2_s;
+  int max_iter;
+  int32_t* iters_out;
+  unsigned long long* evals;
+  unsigned long long* gacc;
+  unsigned* gbar;
+  uint32_t* status;
+  float fx_scale;
+  double inv_fx;
+  double sphere_r;
+};
+
+struct RefineSmem {
+  int off_bar, off_misc, off_y, off_ym, off_act, off_list, off_pts, total;
+};
+
+__host__ __device__ inline RefineSmem refine_smem(int D, int DP, int pts) {
+  RefineSmem r{};
+  int o = 0;
+  r.off_bar = o;
+  o += 16;
+  r.off_misc = o;
+  o += 256;
+  r.off_y = o;
+  o = al16(o + kGridRefineModes * D * 4);
+  r.off_ym = o;
+  o = al16(o + kGridRefineModes * D * 8);
+  r.off_act = o;
+  o += kGridRefineModes * 4;
+  r.off_list = o;
+  o += kGridRefineModes * 4;
+  r.off_pts = o;
+  o += pts * DP * 4;
+  r.total = o;
+  return r;
+}
+
+}  // namespace
+
+template <int D, int DP, int DA, int KF, bool RES>
+__global__ void __launch_bounds__(kGridRefineWarps * 32, 1)
+    ms_grid_refine_kernel(const GridRefineArgs a) {
+  constexpr int RMAX = grid_rmax<D, DA>();
+  constexpr int kT = kGridRefineWarps * 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const RefineSmem L = refine_smem(D, DP, RES ? a.per_cta : 0);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  int* misc = reinterpret_cast<int*>(smem + L.off_misc);   // [0] active count, [1] abort
+  float* sy = reinterpret_cast<float*>(smem + L.off_y);
+  double* sym = reinterpret_cast<double*>(smem + L.off_ym);
+  int* sact = reinterpret_cast<int*>(smem + L.off_act);
+  int* alist = reinterpret_cast<int*>(smem + L.off_list);
+  float* spts = reinterpret_cast<float*>(smem + L.off_pts);
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int M = *a.M_ptr;
+  if (M <= 0) return;
+  if (M > kGridRefineModes) {   // the host keeps M within the capacity
+    if (cta == 0 && tid == 0) atomicOr(a.status, kStCapacity);
+    return;
+  }
+  const int cb = min(a.n, cta * a.per_cta), ce = min(a.n, cb + a.per_cta);
+  const int nc = ce - cb;
+  const float fx = a.fx_scale;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (RES) {
+      const uint32_t bytes = (uint32_t)nc * DP * 4;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                   "r"(bytes)
+                   : "memory");
+      const char* src = reinterpret_cast<const char*>(a.Xs + (size_t)cb * DP);
+      for (uint32_t off = 0; off < bytes; off += 32768u) {
+        const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(spts) + off),
+            "l"(src + off), "r"(len), "r"(smem_u32(mbar))
+            : "memory");
+      }
+    }
+    misc[1] = 0;
+  }
+  for (int i = tid; i < M; i += kT) {
+    const int64_t src = a.kept[a.accepted[i]];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float v = a.y[src * DP + k];
+      sy[i * D + k] = v;
+      sym[i * D + k] = (double)v;
+    }
+    sact[i] = 1;
+  }
+  __syncthreads();
+  if (RES) {
+    bool ok = false;
+    const long long t0 = clock64();
+    for (;;) {
+      uint32_t r;
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(r)
+          : "r"(smem_u32(mbar)), "r"(0u)
+          : "memory");
+      if (r) {
+        ok = true;
+        break;
+      }
+      if (clock64() - t0 > kGridSpinCycles) break;
+    }
+    if (!ok) atomicOr(a.status, kStTimeout);   // the first barrier sends every CTA home
+  }
+  const size_t stride = (size_t)kGridRefineModes * DA;
+  const float* pts = RES ? spts : a.Xs + (size_t)cb * DP;
+  int iters = 0, prev_used = 0;
+  unsigned long long evals = 0;
+  for (int pass = 0; pass < a.max_iter; ++pass) {
+    if (warp == 0) {
+      int base = 0;
+      for (int b0 = 0; b0 < M; b0 += 32) {
+        const int i = b0 + lane;
+        const bool t = i < M && sact[i];
+        const unsigned m = __ballot_sync(kFull, t);
+        if (t) alist[base + __popc(m & ((1u << lane) - 1))] = i;
+        base += __popc(m);
+      }
+      if (lane == 0) misc[0] = base;
+    }
+    __syncthreads();
+    const int A = misc[0];
+    if (A == 0) break;   // every mode has stopped (the same in every CTA)
+    unsigned long long* g = a.gacc + (size_t)(pass % kGridRefineBufs) * stride;
+    {
+      const int m = (A + kGridRefineWarps * RMAX - 1) / (kGridRefineWarps * RMAX);
+      int R = (A + kGridRefineWarps * m - 1) / (kGridRefineWarps * m);
+      if (R < 1) R = 1;
+      const int groups = (A + R - 1) / R;
+      const int tasks = groups * a.n_sub;
+      for (int t = warp; t < tasks; t += kGridRefineWarps) {
+        const int gi = t / a.n_sub, sb = t - gi * a.n_sub;
+        const int j0 = min(nc, sb * a.sub_len), j1 = min(nc, j0 + a.sub_len);
+        const int a0 = gi * R;
+        grid_task_r<D, DP, DA, KF, RES, RMAX>(R, pts, j0, j1, lane, alist, a0, min(R, A - a0),
+                                              sy, g, fx);
+      }
+    }
+    __syncthreads();   // this CTA's leaves are issued
+    if (tid == 0) {
+      int b = 0;
+      __threadfence();
+      red_release_add(a.gbar, 1u);
+      const unsigned want = (unsigned)G * (unsigned)(pass + 1);
+      const long long t0 = clock64();
+      for (int it = 0;; ++it) {
+        if (ld_acquire(a.gbar) >= want) break;
+        if ((it & 31) == 31) {
+          if (*(volatile uint32_t*)a.status & kStTimeout) {
+            b = 1;
+            break;
+          }
+          if (clock64() - t0 > kGridSpinCycles) {
+            atomicOr(a.status, kStTimeout);
+            b = 1;
+            break;
+          }
+        }
+      }
+      if (*(volatile uint32_t*)a.status & kStTimeout) b = 1;
+      misc[1] = b;
+    }
+    __syncthreads();
+    if (misc[1]) break;
+    // every CTA has read the previous update's totals: CTA 0 clears them
+    // for the update three ahead
+    if (cta == 0 && pass >= 1) {
+      unsigned long long* gp = a.gacc + (size_t)((pass - 1) % kGridRefineBufs) * stride;
+      for (int e = tid; e < prev_used * DA; e += kT) gp[e] = 0ull;
+    }
+    prev_used = A;
+    evals += (unsigned long long)A * (unsigned long long)a.n;
+    ++iters;
+    for (int e = tid; e < A; e += kT) {
+      const int i = alist[e];
+      double tot[DA];
+#pragma unroll
+      for (int k = 0; k < DA; ++k) tot[k] = (double)(long long)__ldcg(g + (size_t)e * DA + k) * a.inv_fx;
+      const double W = tot[0];
+      if (cta == 0) a.mscore[i] = W;
+      bool ok = W > 0.0 && isfinite(W);
+      const double rW = ok ? 1.0 / W : 0.0;   // one FP64 division per mode
+      double step2 = 0.0, dl[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dl[k] = ok ? tot[1 + k] * rW - (sym[i * D + k] - (double)sy[i * D + k]) : 0.0;
+        step2 += dl[k] * dl[k];
+      }
+      if (ok && a.sphere_r > 0.0) {
+        // cosine metric: the FP64 position projected back onto the sphere
+        double pp[D], nn = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          pp[k] = sym[i * D + k] + dl[k];
+          nn += pp[k] * pp[k];
+        }
+        const double f = a.sphere_r / sqrt(nn);
+        step2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          pp[k] *= f;
+          dl[k] = pp[k] - sym[i * D + k];
+          step2 += dl[k] * dl[k];
+        }
+        ok = nn > 0.0 && isfinite(step2);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            sym[i * D + k] = pp[k];
+            sy[i * D + k] = (float)pp[k];
+          }
+        }
+      } else if (ok) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          sym[i * D + k] += dl[k];
+          sy[i * D + k] = (float)sym[i * D + k];
+        }
+      }
+      if (!ok || step2 <= a.tol2_s) sact[i] = 0;
+    }
+    __syncthreads();
+  }
+  if (cta == 0) {
+    for (int e = tid; e < M * D; e += kT) {
+      const int i = e / D, k = e - i * D;
+      a.ym[(int64_t)i * DP + k] = sym[i * D + k];
+      a.yf[(int64_t)i * DP + k] = sy[i * D + k];
+    }
+    if (tid == 0) {
+      atomicMax(a.iters_out, iters);
+      if (evals) atomicAdd(a.evals, evals);
+    }
+  }
+}
+
+namespace {
+
 template <int D, int DP, int DA, int KF, bool RES>
 cudaError_t launch_grid_t(const GridRoundArgs& a, int G, int smem_bytes, cudaStream_t st) {
   auto kern = ms_grid_round_kernel<D, DP, DA, KF, RES>;
@@ -761,6 +1039,97 @@ size_t grid_scratch_bytes(int d) {
 size_t grid_scratch_clear_bytes(int d) {
   // everything starts at zero (each accumulator is cleared again after use)
   return grid_scratch_bytes(d);
+}
+
+namespace {
+
+template <int D, int DP, int DA, int KF, bool RES>
+cudaError_t launch_refine_grid_t(const GridRefineArgs& a, int G, int smem_bytes, cudaStream_t st) {
+  auto kern = ms_grid_refine_kernel<D, DP, DA, KF, RES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGridRefineWarps * 32, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kGridRefineWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace
+
+int grid_refine_capacity() { return kGridRefineModes; }
+
+cudaError_t launch_ms_grid_refine(const GridPlan& p, const float* Xs, int64_t n, int d,
+                                  const float* y, const int32_t* kept, const int32_t* accepted,
+                                  const int32_t* M_ptr, double* ym, float* yf, double* mscore,
+                                  double tol2_s, int max_iter, int32_t* iters_out,
+                                  unsigned long long* evals, uint32_t* status, void* scratch,
+                                  cudaStream_t st, int kf, double sphere_r) {
+  if (!p.ok) return cudaErrorInvalidValue;
+  const int DP = d <= 4 ? 4 : 8, DA = accumulators_of(d);
+  // the accumulators reuse the round's scratch (256-byte counter + buffers)
+  if ((size_t)kGridRefineBufs * kGridRefineModes * DA * 8 + 256 > grid_scratch_bytes(d))
+    return cudaErrorInvalidValue;
+  int dev_max = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return cudaErrorInvalidValue;
+  const int with_pts = refine_smem(d, DP, p.per_cta).total;
+  const bool resident = with_pts <= dev_max;
+  const int smem = resident ? with_pts : refine_smem(d, DP, 0).total;
+  GridRefineArgs a{};
+  a.Xs = Xs;
+  a.n = (int)n;
+  a.per_cta = p.per_cta;
+  a.n_sub = p.n_sub;
+  a.sub_len = p.sub_len;
+  a.y = y;
+  a.kept = kept;
+  a.accepted = accepted;
+  a.M_ptr = M_ptr;
+  a.ym = ym;
+  a.yf = yf;
+  a.mscore = mscore;
+  a.tol2_s = tol2_s;
+  a.max_iter = max_iter;
+  a.iters_out = iters_out;
+  a.evals = evals;
+  a.gbar = reinterpret_cast<unsigned*>(scratch);
+  a.gacc = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 256);
+  a.status = status;
+  a.fx_scale = ldexpf(1.0f, p.fx_bits);
+  a.inv_fx = ldexp(1.0, -p.fx_bits);
+  a.sphere_r = sphere_r;
+  cudaError_t e = cudaMemsetAsync(
+      scratch, 0, 256 + (size_t)kGridRefineBufs * kGridRefineModes * DA * 8, st);
+  if (e != cudaSuccess) return e;
+#define FMS_GRID_REF(D_, DP_, DA_)                                                                      \
+  if (kf == kKernelFlat)                                                                                \
+    return resident ? launch_refine_grid_t<D_, DP_, DA_, kKernelFlat, true>(a, p.G, smem, st)           \
+                    : launch_refine_grid_t<D_, DP_, DA_, kKernelFlat, false>(a, p.G, smem, st);         \
+  return resident ? launch_refine_grid_t<D_, DP_, DA_, kKernelGaussian, true>(a, p.G, smem, st)         \
+                  : launch_refine_grid_t<D_, DP_, DA_, kKernelGaussian, false>(a, p.G, smem, st)
+  switch (d) {
+    case 1: FMS_GRID_REF(1, 4, 2);
+    case 2: FMS_GRID_REF(2, 4, 4);
+    case 3: FMS_GRID_REF(3, 4, 4);
+    case 4: FMS_GRID_REF(4, 4, 8);
+    case 5: FMS_GRID_REF(5, 8, 8);
+    case 6: FMS_GRID_REF(6, 8, 8);
+    case 7: FMS_GRID_REF(7, 8, 8);
+  }
+#undef FMS_GRID_REF
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_ms_grid_round(const GridPlan& p, int d, int kf, GridRoundArgs a,

@@ -161,3 +161,21 @@ def test_batched_sets_of_other_sizes_reuse_nothing_stale():
             one = fms.cluster(X[offs[b]:offs[b + 1]].contiguous(), h, 1e-3 * h, 300)
             assert one.modes.shape == res.modes[b].shape
             assert torch.allclose(one.modes, res.modes[b], atol=1e-3 * h, rtol=0)
+
+
+def test_batched_nonfinite_point_ends_the_graph_with_an_error():
+    # a NaN point: the packing kernel flags it, every conditional node's
+    # condition goes false, the graph runs to its end and the call reports
+    # FMS_ERR_NONFINITE (it neither hangs nor returns OK); a clean call with
+    # the same shapes afterwards still succeeds
+    h = 1.5
+    sets = _mixed_sets(21, 3, 3, 300, 900, h)
+    X = torch.cat([torch.from_numpy(w.X) for w in sets]).cuda()
+    offs = np.concatenate([[0], np.cumsum([w.X.shape[0] for w in sets])]).astype(np.int64)
+    bad = X.clone()
+    bad[int(offs[1]) + 5, 1] = float("nan")
+    with pytest.raises(fms.FmsError) as e:
+        fms.cluster_batched(bad, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
+    assert e.value.code == fms.FMS_ERR_NONFINITE
+    ok = fms.cluster_batched(X, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
+    assert ok.status == fms.FMS_OK

@@ -143,22 +143,12 @@ __device__ __forceinline__ void lowd_task(const float* __restrict__ Xs, int j0, 
 // belong to the tensor-core step).  Every wait is bounded: one that gives up
 // sets kStTimeout in *status, waits once more for the warp's copies in flight
 // and makes the task return false (the caller stops).
-constexpr int kWideTile = 32;   // rows per staged tile
+constexpr int kWideTile = tc::kRingRows;   // rows per staged tile (tc::ring_init sets up the ring)
 
 // dynamic shared memory of a 128-thread CTA of wide tasks: 4 warps x 2 tiles
 template <int DPAD>
 constexpr int wide_smem_bytes() {
   return 4 * 2 * kWideTile * DPAD * 4;
-}
-
-// per-warp setup of the tile ring (lane 0 initialises the two mbarriers)
-__device__ __forceinline__ void wide_ring_init(uint64_t* bars, int lane) {
-  if (lane == 0) {
-    tc::init_bar(&bars[0], 1);
-    tc::init_bar(&bars[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
 }
 
 template <int DPAD, int RG, int KF = kKernelGaussian>

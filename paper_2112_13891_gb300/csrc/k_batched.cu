@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* bars = wide_bars[warp];
   float* tiles = wide_tiles + warp * 2 * kWideTile * DPAD;
-  wide_ring_init(bars, lane);
+  tc::ring_init(bars, lane);
   uint32_t use0 = 0u, use1 = 0u;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; t < T; t += nw) {

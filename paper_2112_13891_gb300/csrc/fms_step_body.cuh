@@ -160,7 +160,6 @@ __device__ __forceinline__ bool wide_task(const float* __restrict__ Xs, int j0, 
                                           uint32_t& use1, uint32_t* status) {
   constexpr int DA = DPAD + 4;
   constexpr int SPW = 32 * RG;
-  constexpr int TF = kWideTile * DPAD;   // floats per tile
   float ys[RG][DPAD];
   float acc[RG][DPAD + 1];
 #pragma unroll
@@ -173,72 +172,33 @@ __device__ __forceinline__ bool wide_task(const float* __restrict__ Xs, int j0, 
 #pragma unroll
     for (int k = 0; k <= DPAD; ++k) acc[r][k] = 0.0f;
   }
-  const int ntile = j1 > j0 ? (j1 - j0 + kWideTile - 1) / kWideTile : 0;
-  auto issue = [&](int t) {   // lane 0: tile t into stage t & 1
-    const int r0 = j0 + t * kWideTile;
-    const int rows = min(kWideTile, j1 - r0);
-    tc::fence_proxy_async();   // the warp's reads of this stage came before (syncwarp)
-    tc::bulk_g2s(tiles + (t & 1) * TF, Xs + (int64_t)r0 * DPAD, (uint32_t)(rows * DPAD * 4),
-                 &bars[t & 1]);
-  };
-  if (lane == 0) {
-    if (ntile > 0) issue(0);
-    if (ntile > 1) issue(1);
-  }
-  bool ok = true;
-  int t = 0;
-  for (; t < ntile; ++t) {
-    const int st = t & 1;
-    if (!tc::wait_bar(&bars[st], (st ? use1 : use0) & 1u)) {
-      ok = false;
-      break;
+  const bool ok = tc::ring_rows<DPAD>(Xs, j0, j1, tiles, bars, use0, use1, lane, status,
+                                      [&](const float* row) {
+    float x[DPAD];
+    const float4* xp = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int u = 0; u < DPAD / 4; ++u) {
+      const float4 v = xp[u];
+      x[4 * u] = v.x;
+      x[4 * u + 1] = v.y;
+      x[4 * u + 2] = v.z;
+      x[4 * u + 3] = v.w;
     }
-    if (st) ++use1;
-    else ++use0;
-    const float* tl = tiles + st * TF;
-    const int rows = min(kWideTile, j1 - (j0 + t * kWideTile));
-    for (int q = 0; q < rows; ++q) {
-      float x[DPAD];
-      const float4* xp = reinterpret_cast<const float4*>(tl + q * DPAD);
 #pragma unroll
-      for (int u = 0; u < DPAD / 4; ++u) {
-        const float4 v = xp[u];
-        x[4 * u] = v.x;
-        x[4 * u + 1] = v.y;
-        x[4 * u + 2] = v.z;
-        x[4 * u + 3] = v.w;
-      }
+    for (int r = 0; r < RG; ++r) {
+      float dx[DPAD];
 #pragma unroll
-      for (int r = 0; r < RG; ++r) {
-        float dx[DPAD];
+      for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
+      float tt = -dx[0] * dx[0];
 #pragma unroll
-        for (int k = 0; k < DPAD; ++k) dx[k] = x[k] - ys[r][k];
-        float tt = -dx[0] * dx[0];
+      for (int k = 1; k < DPAD; ++k) tt = fmaf(-dx[k], dx[k], tt);
+      const float w = kweight<KF>(tt);
+      acc[r][0] += w;
 #pragma unroll
-        for (int k = 1; k < DPAD; ++k) tt = fmaf(-dx[k], dx[k], tt);
-        const float w = kweight<KF>(tt);
-        acc[r][0] += w;
-#pragma unroll
-        for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
-      }
+      for (int k = 0; k < DPAD; ++k) acc[r][1 + k] = fmaf(w, dx[k], acc[r][1 + k]);
     }
-    __syncwarp();
-    if (lane == 0 && t + 2 < ntile) issue(t + 2);
-  }
-  if (!ok) {
-    // the copies this task issued and did not consume: tiles t .. min(t + 1, ntile - 1)
-    if (lane == 0) atomicOr(status, kStTimeout);
-    for (int u = t; u < ntile && u < t + 2; ++u) {
-      if (u & 1) {
-        tc::wait_bar(&bars[1], use1 & 1u);
-        ++use1;
-      } else {
-        tc::wait_bar(&bars[0], use0 & 1u);
-        ++use0;
-      }
-    }
-    return false;
-  }
+  });
+  if (!ok) return false;
 #pragma unroll
   for (int r = 0; r < RG; ++r) {
     const int p = p_lo + g * SPW + r * 32 + lane;

@@ -179,3 +179,33 @@ def test_batched_nonfinite_point_ends_the_graph_with_an_error():
     assert e.value.code == fms.FMS_ERR_NONFINITE
     ok = fms.cluster_batched(X, h, 1e-3 * h, 300, offsets=offs, max_modes=64)
     assert ok.status == fms.FMS_OK
+
+
+@pytest.mark.parametrize("d", [2, 64])
+def test_batched_degenerate_and_wide_sets(d):
+    # one-point and two-point sets next to ordinary ones (d = 2), and d = 64
+    # (the widest staged step); every set against the oracle run alone
+    h = 2.0 if d == 2 else 6.0
+    rng = np.random.default_rng(70 + d)
+    sets = [rng.normal(0, 1, (1, d)).astype(np.float32),
+            (rng.normal(0, 1, (2, d)) * 0.1).astype(np.float32),
+            fi.separated_blobs(seed=71 + d, k=3, d=d, per=80, sigma=1.0, h=h).X]
+    X = [torch.from_numpy(x).cuda() for x in sets]
+    res = fms.cluster_batched(X, h, 1e-3 * h, 300, max_modes=32)
+    assert res.status == fms.FMS_OK
+    off = np.concatenate([[0], np.cumsum([x.shape[0] for x in sets])])
+    for b, x in enumerate(sets):
+        ref = orc.cluster(x, h, 1e-3 * h, 300, gamma=0.95, rng_seed=0)
+        cmp = compare_clustering(res.modes[b].cpu().numpy(), res.labels[off[b]:off[b + 1]].cpu().numpy(), ref, h)
+        assert cmp["mode_ok"] and cmp["label_mismatch"] == 0, (b, cmp)
+
+
+def test_batched_single_set_equals_single_call():
+    h = 1.5
+    w = fi.separated_blobs(seed=80, k=4, d=3, per=300, sigma=1.0, h=h)
+    X = torch.from_numpy(w.X).cuda()
+    res = fms.cluster_batched([X], h, 1e-3 * h, 300, max_modes=32)
+    one = fms.cluster(X, h, 1e-3 * h, 300)
+    assert one.modes.shape == res.modes[0].shape
+    assert torch.allclose(one.modes, res.modes[0], atol=1e-3 * h, rtol=0)
+    assert torch.equal(one.labels, res.labels)

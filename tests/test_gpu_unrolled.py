@@ -35,7 +35,8 @@ def _sets(seed, B, n, d, k=4):
     return np.stack(out).astype(np.float32)
 
 
-@pytest.mark.parametrize("d,n,T,k", [(2, 200, 3, 2), (4, 257, 4, 3), (16, 300, 5, 2), (7, 130, 2, 5)])
+@pytest.mark.parametrize("d,n,T,k", [(2, 200, 3, 2), (4, 257, 4, 3), (16, 300, 5, 2), (7, 130, 2, 5),
+                                     (1, 150, 3, 2), (32, 140, 3, 2)])
 def test_forward_and_adjoint_match_oracle(d, n, T, k):
     B, h = 2, 2.0
     X = _sets(d * 100 + n, B, n, d)

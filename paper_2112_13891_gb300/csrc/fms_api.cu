@@ -678,7 +678,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
                                      mctl, ctl, n, R, Lo.tl, cs2, rctl_round, wlast, score);
           if (e2 == cudaSuccess)
             e2 = launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
-                                       &mctl->M, cap_seeds, cs2);
+                                       &mctl->M, cap_seeds, cs2, status);
           if (e2 == cudaSuccess)
             e2 = launch_round_advance(rctl_round, mctl, n, o.L, allow_doubling ? 1 : 0, o.gamma,
                                       cap_seeds, cap_modes, o.rng_seed, Xs, DP, seed_idx, y, it,
@@ -867,7 +867,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
         }
       }
       FMS_LAUNCH(launch_greedy_merge_f(kept, &mctl->K, score, y, DP, d, (float)r2_s, alive, acc1,
-                                       &mctl->M, N, st));
+                                       &mctl->M, N, st, status));
       // --- seed-count control (Sec. II-D) ---
       FMS_LAUNCH(launch_doubling_decision(mctl, N, n, o.L, allow_doubling ? 1 : 0, st));
       mark(2);

@@ -553,10 +553,12 @@ cudaError_t launch_kept_list(const IterCtl* ctl, const int32_t* state, const int
                              float* score = nullptr);        // each kept seed's last update
 cudaError_t launch_score_reduce(const float* part, const MergeCtl* mctl, int DA, float* score,
                                 int max_K, cudaStream_t st);
+// status: the call's status word; with it, candidate sets too large for one
+// CTA's sorted visit take the grid visit (kStTimeout if a barrier gives up)
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
                                   const float* score, const float* pos, int DP, int d, float r2,
                                   int32_t* alive, int32_t* accepted, int32_t* M_out, int max_K,
-                                  cudaStream_t st);
+                                  cudaStream_t st, uint32_t* status = nullptr);
 cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,
                                   int DP, int d, double r2, int32_t* alive, int32_t* accepted,
                                   int32_t* M_out, int max_K, cudaStream_t st);

@@ -97,6 +97,206 @@ __global__ void __launch_bounds__(512)
   greedy_global_body<PT, ST>(cand_row, *K_ptr, score, pos, DP, d, r2, list, accepted, M_out, sm);
 }
 
+// ---------------------------------------------------------------------------
+// The greedy visit on the whole GPU, for candidate sets whose sort keys do not
+// fit one CTA (FP32 scores): one cooperative CTA per SM holds a contiguous
+// share of the candidates in shared memory (coordinates, a 64-bit key whose
+// unsigned order is the visit order -- score bits mapped to an unsigned order,
+// the complemented candidate index below them -- and an alive flag).  Per
+// accepted mode: every CTA posts its best alive key with one atomicMax into a
+// winner slot; after one grid barrier (bounded) every CTA reads the winner,
+// drops its candidates closer than r to it (the same FP32 distance as the
+// one-block visit), and posts its next best into the next slot.  Three slots
+// rotate; CTA 0 clears the one every CTA has finished reading.  The winners,
+// in order, are the one-by-one greedy visit's accepted modes.
+// ---------------------------------------------------------------------------
+constexpr int kGridGreedyThreads = 512;
+constexpr long long kGridGreedySpin = 4000000000LL;   // bound of one barrier wait (~2 s)
+
+__device__ __forceinline__ unsigned long long greedy_key(float f, int q) {
+  if (!(f == f)) f = -INFINITY;   // a NaN score counts as -inf (as in the sorted visit)
+  if (f == 0.0f) f = 0.0f;        // -0 and +0 are equal scores
+  unsigned u = __float_as_uint(f);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)q);
+}
+
+// bytes of shared memory for `per` candidates of DPC staged coordinates
+__host__ __device__ inline size_t grid_greedy_smem(int per, int DPC) {
+  return (((size_t)per * DPC * 4 + 15) / 16) * 16 + (size_t)per * 8 + (((size_t)per + 15) / 16) * 16;
+}
+
+template <int DPC>
+__global__ void __launch_bounds__(kGridGreedyThreads, 1)
+    greedy_grid_kernel(const int32_t* __restrict__ cand_row, const int32_t* __restrict__ K_ptr,
+                       const float* __restrict__ score, const float* __restrict__ pos, int DP,
+                       int d, float r2, int per, unsigned* gbar, unsigned long long* slots,
+                       int32_t* __restrict__ accepted, int32_t* __restrict__ M_out,
+                       uint32_t* status) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  __shared__ unsigned long long red[32];
+  __shared__ float wpos[DPC];
+  __shared__ int s_stop;
+  float* spos = reinterpret_cast<float*>(gsm);
+  unsigned long long* skey =
+      reinterpret_cast<unsigned long long*>(gsm + (((size_t)per * DPC * 4 + 15) / 16) * 16);
+  unsigned char* salive = reinterpret_cast<unsigned char*>(skey + per);
+  const int K = *K_ptr;
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int q0 = min(K, cta * per), nq = max(0, min(K, q0 + per) - q0);
+  unsigned long long best = 0ull;
+  for (int e = tid; e < nq; e += kGridGreedyThreads) {
+    const int q = q0 + e;
+    const int64_t row = cand_row ? (int64_t)cand_row[q] : (int64_t)q;
+#pragma unroll
+    for (int k = 0; k < DPC; ++k) spos[(size_t)e * DPC + k] = k < d ? pos[row * DP + k] : 0.0f;
+    const unsigned long long key = greedy_key(score[q], q);
+    skey[e] = key;
+    salive[e] = 1;
+    best = key > best ? key : best;
+  }
+  auto block_max = [&](unsigned long long v) -> unsigned long long {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(kFull, v, o);
+      v = u > v ? u : v;
+    }
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    unsigned long long m = 0ull;
+    for (int w = 0; w < kGridGreedyThreads / 32; ++w) m = red[w] > m ? red[w] : m;
+    __syncthreads();
+    return m;
+  };
+  // grid barrier number b (1, 2, ...): all CTAs have posted into the slot
+  // that follows; false when the bounded wait gave up
+  auto grid_barrier = [&](unsigned b) -> bool {
+    if (tid == 0) {
+      int stop = 0;
+      __threadfence();
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(gbar), "r"(1u) : "memory");
+      const unsigned want = (unsigned)G * b;
+      const long long t0 = clock64();
+      for (int it = 0;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gbar) : "memory");
+        if (v >= want) break;
+        if ((it & 31) == 31) {
+          if (*(volatile uint32_t*)status & kStTimeout) {
+            stop = 1;
+            break;
+          }
+          if (clock64() - t0 > kGridGreedySpin) {
+            atomicOr(status, kStTimeout);
+            stop = 1;
+            break;
+          }
+        }
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    return s_stop == 0;
+  };
+  best = block_max(best);
+  if (tid == 0 && best) atomicMax(&slots[0], best);
+  int it = 0;
+  bool ok = grid_barrier(1u);
+  while (ok) {
+    unsigned long long W;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(W) : "l"(&slots[it % 3]) : "memory");
+    if (W == 0ull) break;   // no alive candidate anywhere
+    const int win = (int)(0xFFFFFFFFu - (unsigned)(W & 0xFFFFFFFFull));
+    if (cta == 0 && tid == 0) accepted[it] = win;
+    const int64_t wrow = cand_row ? (int64_t)cand_row[win] : (int64_t)win;
+    if (tid < d) wpos[tid] = pos[wrow * DP + tid];
+    __syncthreads();
+    unsigned long long b = 0ull;
+    for (int e = tid; e < nq; e += kGridGreedyThreads) {
+      if (!salive[e]) continue;
+      bool keep = q0 + e != win;
+      if (keep) {
+        float d2 = 0.0f;
+        for (int k = 0; k < d; ++k) {
+          const float dd = spos[(size_t)e * DPC + k] - wpos[k];
+          d2 += dd * dd;
+        }
+        keep = !(d2 < r2);
+      }
+      if (keep) b = skey[e] > b ? skey[e] : b;
+      else salive[e] = 0;
+    }
+    b = block_max(b);
+    if (tid == 0) {
+      if (b) atomicMax(&slots[(it + 1) % 3], b);
+      if (cta == 0) slots[(it + 2) % 3] = 0ull;   // read by every CTA before the last barrier
+    }
+    ++it;
+    ok = grid_barrier((unsigned)it + 1u);
+  }
+  if (cta == 0 && tid == 0) *M_out = it;
+}
+
+template <int DPC>
+static cudaError_t launch_grid_greedy_t(const int32_t* cand_row, const int32_t* K_ptr,
+                                        const float* score, const float* pos, int DP, int d,
+                                        float r2, int per, int G, size_t sm, unsigned* gbar,
+                                        unsigned long long* slots, int32_t* accepted,
+                                        int32_t* M_out, uint32_t* status, cudaStream_t st) {
+  auto kern = greedy_grid_kernel<DPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGridGreedyThreads, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kGridGreedyThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, cand_row, K_ptr, score, pos, DP, d, r2, per, gbar, slots,
+                            accepted, M_out, status);
+}
+
+// The grid visit for up to max_K FP32-scored candidates; its barrier counter
+// and winner slots live in the first 64 bytes of `scratch` (cleared here).
+// Returns cudaErrorInvalidValue when the candidates do not fit.
+static cudaError_t launch_greedy_grid(const int32_t* cand_row, const int32_t* K_ptr,
+                                      const float* score, const float* pos, int DP, int d,
+                                      float r2, int32_t* scratch, int32_t* accepted,
+                                      int32_t* M_out, int max_K, uint32_t* status,
+                                      cudaStream_t st) {
+  int dev = 0, sms = 0, dev_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess || sms < 1)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(scratch) & 15u) != 0) return cudaErrorInvalidValue;
+  const int DPC = d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : (d <= 32 ? 32 : 64)));
+  const int per = (max_K + sms - 1) / sms;
+  const size_t sm = grid_greedy_smem(per > 0 ? per : 1, DPC);
+  if (sm > (size_t)dev_max - 2048) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 64, st);
+  if (e != cudaSuccess) return e;
+  unsigned* gbar = reinterpret_cast<unsigned*>(scratch);
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(scratch + 4);   // 16-byte offset
+  switch (DPC) {
+    case 4: return launch_grid_greedy_t<4>(cand_row, K_ptr, score, pos, DP, d, r2, per, sms, sm, gbar, slots, accepted, M_out, status, st);
+    case 8: return launch_grid_greedy_t<8>(cand_row, K_ptr, score, pos, DP, d, r2, per, sms, sm, gbar, slots, accepted, M_out, status, st);
+    case 16: return launch_grid_greedy_t<16>(cand_row, K_ptr, score, pos, DP, d, r2, per, sms, sm, gbar, slots, accepted, M_out, status, st);
+    case 32: return launch_grid_greedy_t<32>(cand_row, K_ptr, score, pos, DP, d, r2, per, sms, sm, gbar, slots, accepted, M_out, status, st);
+    default: return launch_grid_greedy_t<64>(cand_row, K_ptr, score, pos, DP, d, r2, per, sms, sm, gbar, slots, accepted, M_out, status, st);
+  }
+}
+
 // DT > 0: d = DT at compile time (candidates in registers during the visit)
 template <typename PT, typename ST, int DT>
 __global__ void __launch_bounds__(1024)
@@ -144,7 +344,8 @@ constexpr size_t kGreedySmemMax = 200 * 1024;
 template <typename PT, typename ST>
 cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const ST* score,
                           const PT* pos, int DP, int d, PT r2, int32_t* alive,
-                          int32_t* accepted, int32_t* M_out, int max_K, cudaStream_t st) {
+                          int32_t* accepted, int32_t* M_out, int max_K, cudaStream_t st,
+                          uint32_t* status = nullptr) {
   // largest layout that fits: preloaded candidates and accepted modes in
   // shared memory, then accepted modes only, then neither
   int P = 1;
@@ -176,6 +377,13 @@ cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const S
     FMS_SORTED(0);
 #undef FMS_SORTED
   }
+  if constexpr (sizeof(ST) == 4 && sizeof(PT) == 4) {
+    // FP32 scores: the visit on the whole GPU when its shares fit
+    if (status && launch_greedy_grid(cand_row, K_ptr, score, pos, DP, d, r2, alive, accepted,
+                                     M_out, max_K, status, st) == cudaSuccess)
+      return cudaSuccess;
+    cudaGetLastError();   // (a refused grid launch leaves no error behind)
+  }
   greedy_merge_kernel<PT, ST><<<1, 512, 0, st>>>(cand_row, K_ptr, score, pos, DP, d, r2, alive,
                                                   accepted, M_out);
   return cudaGetLastError();
@@ -184,9 +392,9 @@ cudaError_t launch_greedy(const int32_t* cand_row, const int32_t* K_ptr, const S
 cudaError_t launch_greedy_merge_f(const int32_t* cand_row, const int32_t* K_ptr,
                                   const float* score, const float* pos, int DP, int d, float r2,
                                   int32_t* alive, int32_t* accepted, int32_t* M_out, int max_K,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, uint32_t* status) {
   return launch_greedy<float, float>(cand_row, K_ptr, score, pos, DP, d, r2, alive, accepted,
-                                     M_out, max_K, st);
+                                     M_out, max_K, st, status);
 }
 
 cudaError_t launch_greedy_merge_d(const int32_t* K_ptr, const double* score, const double* pos,

@@ -4,24 +4,34 @@
 //
 // Decomposition.  CTA c owns a fixed, contiguous slice of the points (n / G
 // points for G CTAs), staged once into shared memory by TMA bulk copies when
-// it fits (else read from L2).  The slice is cut into fixed sub-slices.  In
-// every update each CTA evaluates every active seed of the round against its
-// slice: a warp task is (a group of R seeds, one sub-slice); lane l takes the
-// sub-slice points l, l + 32, ...; the 32 lane sums are combined by a fixed
-// xor tree.  That FP32 value -- the partial of one seed over one sub-slice --
-// is a leaf.  Leaves are converted to 64-bit fixed point (2^F units, F chosen
-// so that no sum over all n points can overflow) and added exactly: first in
-// shared memory, then across CTAs with red.global.add.u64 into a triple-
-// buffered accumulator.  Integer addition is associative, so the totals (and
-// every seed's trajectory) do not depend on which warp took which task, on the
-// group size R, on the order of the atomics or on which other seeds are
-// active; the only rounding is that of the leaves and of one conversion to
-// FP64 per total.
+// it fits (else read from L2), and cut into sub-slices.  In every update each
+// CTA evaluates every active seed of the round against its slice.  A warp task
+// is (a group of seeds, a range of the slice); lane l takes the range's points
+// l, l + 32, ...; the 32 lane sums are combined by a fixed xor tree.  That
+// FP32 value -- the partial of one seed over one range -- is a leaf.  A list of
+// A >= 16 seeds is cut into 16 contiguous shares of A / 16 or A / 16 + 1
+// seeds, one per compute warp, each over whole sub-slices; the extra seeds go
+// to consecutive warps, which sit on different SM sub-partitions, so that the
+// issue load of every sub-partition is even.  A shorter list (the last,
+// latency-bound updates) is evaluated by every warp over its chunk of each
+// sub-slice.  Leaves are converted to 64-bit fixed point (2^F units, F chosen
+// so that no sum over all n points can overflow) and added exactly: directly
+// into the update's global accumulator (red.global.add.u64), or for a chunked
+// list first per warp in shared memory.  Integer addition is associative, so
+// the totals do
+// not depend on which warp or CTA took which task or on the order of the
+// atomics; the only rounding is that of the leaves and of one conversion to
+// FP32 per total.  Four accumulators rotate.
 //
-// One grid barrier per update (a release-add on a counter, an acquire poll,
-// both bounded): after it every CTA reads the same totals and applies the same
-// update to its replicated copy of the round's seed state, so no second
-// exchange is needed.  CTA 0 writes the seed state back to global memory.
+// Roles and pipeline.  Phases alternate between two seed lists.  While 16
+// compute warps evaluate list j, the comm warp publishes phase j - 1 (one grid
+// barrier: a release-add on a counter, an acquire poll, both bounded) and
+// stages its totals in shared memory with one bulk copy; two service warps
+// then apply them to list j - 1's seeds (the same update in every CTA's
+// replicated copy of the round's seed state) and build list j + 1.  Named
+// barriers pass each phase from role to role, so the compute warps wait only
+// for a list whose update is complete.  CTA 0 writes
+// the seed state back to global memory.
 //
 // Early Stopping.  Every CTA keeps the convergence histogram of all seeds of
 // all rounds; after each update it finds t_stop, the first update count whose
@@ -37,8 +47,16 @@ namespace fms {
 namespace {
 
 constexpr int kGridCompWarps = 16;                  // warps that evaluate seeds
-constexpr int kCommWarp = kGridCompWarps;           // the exchange / update warp
+constexpr int kCommWarp = kGridCompWarps;           // the exchange warp
 constexpr int kGridThreads = (kGridCompWarps + 1) * 32;
+constexpr int kComp = kGridCompWarps * 32;          // compute threads
+// Largest list that is evaluated in chunks (its sums pass through shared memory)
+constexpr int kGridRem = kGridCompWarps - 1;
+// Named barriers (0 is __syncthreads), one per parity where a phase passes
+// from the compute warps to the comm warp and back.
+constexpr int kBarPass = 1;     // compute -> comm: leaves of phase j issued
+constexpr int kBarStaged = 3;   // comm -> compute: totals of phase j staged
+constexpr int kBarComp = 5;     // among the compute warps
 constexpr int kGridBufs = 4;                        // accumulators in rotation
 constexpr int kGridMerge = 48;   // at most this many active seeds: one list per update
 constexpr int kGridSubLen = 2048;                // longest sub-slice (points)
@@ -46,7 +64,8 @@ constexpr long long kGridSpinCycles = 4000000000LL;   // bound of one wait (~2 s
 
 // Shared memory carving (bytes), identical on host and device.
 struct GridSmem {
-  int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_w, off_conv, off_list, off_hist, off_stage, off_pts;
+  int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_w, off_conv, off_list, off_ws, off_hist,
+      off_stage, off_rem, off_pts;
   int total;
 };
 
@@ -55,6 +74,9 @@ __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 // Seeds one round launch holds: two staged publications of DA accumulators
 // per seed must fit in shared memory beside the seed state and the slice.
 __host__ __device__ constexpr int grid_seed_cap(int DA) { return DA == 8 ? 512 : kGridMaxSeeds; }
+
+// Seeds one compute warp takes in a phase, at most: a share of a full list.
+__host__ __device__ constexpr int grid_ws(int SC) { return SC / kGridCompWarps + 4; }
 
 __host__ __device__ inline GridSmem grid_smem(int D, int DA, int DP, int pts) {
   const int SC = grid_seed_cap(DA);
@@ -76,12 +98,16 @@ __host__ __device__ inline GridSmem grid_smem(int D, int DA, int DP, int pts) {
   o += SC * 4;
   s.off_conv = o;  // convergence update
   o += SC * 4;
-  s.off_list = o;  // two phase lists and the pool of deferred seeds
-  o += 3 * SC * 4;
+  s.off_list = o;  // two buffers of each phase list, the pool of deferred seeds
+  o += 5 * SC * 4;
+  s.off_ws = o;    // each compute warp's seeds of the current phase
+  o += kGridCompWarps * grid_ws(SC) * 4;
   s.off_hist = o;
   o += kGridHist * 4;
   s.off_stage = o; // the staged totals of the last publication of each parity
   o += 2 * SC * DA * 8;
+  s.off_rem = o;   // a chunked phase's sums per compute warp, per parity
+  o += 2 * kGridCompWarps * kGridRem * DA * 8;
   s.off_pts = o;
   o += pts * DP * 4;
   s.total = o;
@@ -135,12 +161,14 @@ __device__ __forceinline__ float grid_rs32(float (&v)[32], int lane) {
 // per point): exact-difference form, acc[r][0] = sum w, acc[r][1 + k] =
 // sum w (x - y)_k.  The RR x DA sums are reduce-scattered over the warp in
 // blocks of 32 (lane l of block q holds accumulator 32 q + l), converted to
-// fixed point and added into the update's global accumulator gacc.
+// fixed point and added into dst[r * DA + k]: the update's global accumulator
+// (mode 0: red.global), or this warp's own sums in shared memory (mode 1:
+// store, the warp's first leaf of these seeds; mode 2: add).
 template <int D, int DP, int DA, int RR, int KF, bool RES>
 __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0, int j1, int lane,
                                           const int* __restrict__ alist, int a0, int cnt,
                                           const float* __restrict__ sy,
-                                          unsigned long long* gacc, float fx) {
+                                          unsigned long long* dst, int mode, float fx) {
   constexpr int NV = (RR * DA + 31) / 32;
   float ys[RR][D];
 #pragma unroll
@@ -200,7 +228,9 @@ __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0,
     const int f = 32 * q + lane;
     if (f < cnt * DA) {
       const long long qv = __float2ll_rn(s * fx);
-      red_add_u64(gacc + (size_t)a0 * DA + f, (unsigned long long)qv);
+      if (mode == 0) red_add_u64(dst + f, (unsigned long long)qv);
+      else if (mode == 1) dst[f] = (unsigned long long)qv;
+      else dst[f] += (unsigned long long)qv;
     }
   }
 }
@@ -208,13 +238,13 @@ __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0,
 template <int D, int DP, int DA, int KF, bool RES, int RR>
 __device__ __forceinline__ void grid_task_r(int R, const float* pts, int j0, int j1, int lane,
                                             const int* alist, int a0, int cnt, const float* sy,
-                                            unsigned long long* gacc, float fx) {
+                                            unsigned long long* dst, int mode, float fx) {
   if constexpr (RR >= 1) {
     if (R == RR) {
-      grid_task<D, DP, DA, RR, KF, RES>(pts, j0, j1, lane, alist, a0, cnt, sy, gacc, fx);
+      grid_task<D, DP, DA, RR, KF, RES>(pts, j0, j1, lane, alist, a0, cnt, sy, dst, mode, fx);
       return;
     }
-    grid_task_r<D, DP, DA, KF, RES, RR - 1>(R, pts, j0, j1, lane, alist, a0, cnt, sy, gacc, fx);
+    grid_task_r<D, DP, DA, KF, RES, RR - 1>(R, pts, j0, j1, lane, alist, a0, cnt, sy, dst, mode, fx);
   }
 }
 
@@ -230,11 +260,13 @@ template <int D, int DP, int DA, int KF, bool RES>
 __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const GridRoundArgs a) {
   constexpr int RMAX = grid_rmax<D, DA>();
   constexpr int SC = grid_seed_cap(DA);
-  constexpr int kComp = kGridCompWarps * 32;   // compute threads
   extern __shared__ __align__(16) unsigned char smem[];
   const GridSmem L = grid_smem(D, DA, DP, RES ? a.per_cta : 0);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar);   // [0] slice, [1] totals
-  // misc: [0], [1] sizes of the even / odd phase lists, [2] done, [3] S,
+  // misc: [0], [1] sizes of the even / odd phase lists, [2] the phase at
+  // which the compute warps stop (0: not known yet), [3] S, [12], [13] the
+  // buffer holding each parity's list, [14] the t_stop it was built with,
+  // [16 .. 31] the compute warps' ballots of live entries,
   // [4] converged seeds (all rounds), [5] abort, [6] pool size, [32..63] scan
   int* misc = reinterpret_cast<int*>(smem + L.off_misc);
   float* sy = reinterpret_cast<float*>(smem + L.off_y);
@@ -243,10 +275,12 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
   int* sst = reinterpret_cast<int*>(smem + L.off_act);
   float* sw = reinterpret_cast<float*>(smem + L.off_w);
   int* sconv = reinterpret_cast<int*>(smem + L.off_conv);
-  int* lists = reinterpret_cast<int*>(smem + L.off_list);   // [2][SC], then pool[SC]
-  int* pool = lists + 2 * SC;
+  int* lists = reinterpret_cast<int*>(smem + L.off_list);   // [parity][buffer][SC], pool[SC]
+  int* pool = lists + 4 * SC;
+  int* wseeds = reinterpret_cast<int*>(smem + L.off_ws);
   int* hist_s = reinterpret_cast<int*>(smem + L.off_hist);
   unsigned long long* stage = reinterpret_cast<unsigned long long*>(smem + L.off_stage);
+  unsigned long long* remacc = reinterpret_cast<unsigned long long*>(smem + L.off_rem);
   float* spts = reinterpret_cast<float*>(smem + L.off_pts);
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
@@ -386,7 +420,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
       const unsigned m = __ballot_sync(kFull, t);
       if (t) {
         const int r = n0 + n1 + __popc(m & ((1u << lane) - 1));
-        if (split && (r & 1)) lists[SC + (r >> 1)] = p;
+        if (split && (r & 1)) lists[2 * SC + (r >> 1)] = p;
         else lists[split ? (r >> 1) : r] = p;
       }
       const int c = __popc(m);
@@ -401,6 +435,9 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
     if (lane == 0) {
       misc[0] = n0;
       misc[1] = n1;
+      misc[12] = 0;   // buffer of each parity's list
+      misc[13] = 0;
+      misc[14] = ts;  // the t_stop the lists were built with
     }
   }
   __syncthreads();
@@ -409,32 +446,64 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
   const int max_phase = 4 * (a.max_iter + 4);
   const size_t stride = (size_t)SC * DA;
   if (warp < kGridCompWarps) {
-    // ---- compute warps.  Phase j: apply the staged totals of phase j - 2
-    // (this parity) to its seeds, build list j from them, evaluate list j ----
+    // ---- compute warps.  Phase j: apply the staged updates of phase j - 2
+    // (this parity) to its seeds, find which stay live, evaluate list j ----
     const int n_sub = a.n_sub, sub_len = a.sub_len;
+    const float* pts = RES ? spts : a.Xs + (size_t)cb * DP;
+    int* ws = wseeds + warp * grid_ws(SC);
     int q = 0;   // publications so far (non-empty phases)
     for (int j = 0; j < max_phase; ++j) {
       const int par = j & 1;
-      int* lst = lists + par * SC;
-      if (j >= 2) {
-        bar_sync(3 + par, kGridThreads);   // totals of phase j - 2 staged
-        if (*(volatile int*)(misc + 5)) break;
-        const int Aold = misc[par];
-        const unsigned long long* stg = stage + (size_t)par * stride;
-        // update of every seed of phase j - 2 from the exact totals (the
-        // same in every CTA): m(y) = y + S / W with S = sum w (x - y)
+      // Work split of a list of A seeds.  A >= 16: warp w takes a contiguous
+      // share of A / 16 seeds, one more for w < A mod 16 (consecutive warps
+      // sit on different SM sub-partitions, so the extra seeds spread over
+      // them), in groups of at most RMAX, each over every sub-slice.  A < 16
+      // (the last, latency-bound updates of a round): every warp takes all A
+      // seeds over its chunk of each sub-slice, and the CTA's sums go through
+      // shared memory.
+      int A, cw, aw;
+      auto split = [&](int A_) {
+        A = A_;
+        const int per = A / kGridCompWarps, ex = A - per * kGridCompWarps;
+        cw = A < kGridCompWarps ? A : per + (warp < ex ? 1 : 0);
+        aw = A < kGridCompWarps ? 0 : warp * per + min(warp, ex);
+      };
+      if (j < 2) {
+        const int* l0 = lists + 2 * par * SC;
+        split(misc[par]);
+        for (int r = lane; r < cw; r += 32) ws[r] = l0[aw + r];
+        __syncwarp();
+      } else {
+        bar_sync(kBarStaged + par, kGridThreads);   // updates of phase j - 2 staged
+        if (*(volatile int*)(misc + 5)) break;     // the exchange failed
+        const int Aold = misc[par], ps = misc[6], B = misc[par ^ 1];
+        const int cur = misc[12 + par], ts_old = misc[14];
+        const int* lold = lists + (2 * par + cur) * SC;
+        int* lnew = lists + (2 * par + (cur ^ 1)) * SC;
+        const float* stg = reinterpret_cast<const float*>(stage + (size_t)par * stride);
+        const bool fast = Aold <= kComp && ps <= 32;
+        // the update of every seed of phase j - 2 (the same in every CTA):
+        // y + S / W, staged by the comm warp as [W, S_0 / W, S_1 / W, ...]
+        int pe = 0;
+        bool lv = false;
         for (int e = tid; e < Aold; e += kComp) {
-          const int p = lst[e];
-          float tot[DA];
+          const int p = lold[e];
+          float f[DA];
+          const float4* f4 = reinterpret_cast<const float4*>(stg + (size_t)e * 2 * DA);
 #pragma unroll
-          for (int k = 0; k < DA; ++k) tot[k] = __ll2float_rn((long long)stg[(size_t)e * DA + k]) * inv_fx;
-          const float W = tot[0];
+          for (int k = 0; k < (DA + 3) / 4; ++k) {
+            const float4 v = f4[k];
+            f[4 * k] = v.x;
+            if (4 * k + 1 < DA) f[4 * k + 1] = v.y;
+            if (4 * k + 2 < DA) f[4 * k + 2] = v.z;
+            if (4 * k + 3 < DA) f[4 * k + 3] = v.w;
+          }
+          const float W = f[0];
           bool ok = W > 0.0f && isfinite(W);
-          const float rW = ok ? __frcp_rn(W) : 0.0f;
           float dl[D], step2 = 0.0f;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            dl[k] = tot[1 + k] * rW;
+            dl[k] = f[1 + k];
             step2 = fmaf(dl[k], dl[k], step2);
           }
           ok = ok && isfinite(step2);
@@ -447,11 +516,11 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
               pp[k] = sy[p * D + k] + dl[k];
               nn = fmaf(pp[k], pp[k], nn);
             }
-            const float f = a.sphere_r / sqrtf(nn);
+            const float fs = a.sphere_r / sqrtf(nn);
             step2 = 0.0f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-              pp[k] *= f;
+              pp[k] *= fs;
               const float d2 = pp[k] - sy[p * D + k];
               step2 = fmaf(d2, d2, step2);
             }
@@ -479,41 +548,77 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
             if (t < kGridHist) atomicAdd(hist_s + t, 1);
             atomicAdd(misc + 4, 1);
           }
+          pe = p;
+          lv = st == kRunning && t < ts_old;   // live under the last t_stop
         }
-        bar_sync(5, kComp);
-        if (warp == 0) {
-          // list j: the live seeds of phase j - 2 and of the pool, or none
-          // (the candidates wait in the pool) when few seeds are left and
-          // phase j - 1 has some, so that the lists merge
-          const int ts = t_stop();
-          int nl = 0;
-          for (int b0 = 0; b0 < Aold; b0 += 32) {   // in place: writes never pass reads
-            const int e = b0 + lane;
-            const int p = e < Aold ? lst[e] : 0;
-            const bool t = e < Aold && live(p, ts);
-            const unsigned m = __ballot_sync(kFull, t);
-            if (t) lst[nl + __popc(m & ((1u << lane) - 1))] = p;
-            nl += __popc(m);
+        // list j: the live seeds of phase j - 2 and of the pool, or none (the
+        // candidates wait in the pool) when few seeds are left and phase
+        // j - 1 (evaluated, not yet applied) has some, so that the lists merge
+        const unsigned m = __ballot_sync(kFull, lv);
+        if (lane == 0) misc[16 + warp] = (int)m;
+        const int pp = lane < ps ? pool[lane] : 0;
+        const bool plv = lane < ps && live(pp, ts_old);
+        const unsigned pm = __ballot_sync(kFull, plv);
+        bar_sync(kBarComp, kComp);   // every update applied, every entry read, every ballot posted
+        const int ts = t_stop();
+        if (fast && ts == ts_old) {
+          // ranks from the ballots; the owners write the new list (or the
+          // pool) while the old list and the pool are no longer read
+          int c = lane < kGridCompWarps ? __popc((unsigned)misc[16 + lane]) : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(kFull, c, o);
+            if (lane >= o) c += u;
           }
-          const int ps = misc[6];
+          const int nl = __shfl_sync(kFull, c, kGridCompWarps - 1);
+          const int before = warp ? __shfl_sync(kFull, c, warp - 1) : 0;
+          const int np = __popc(pm);
+          const bool defer = B > 0 && B + nl + np <= kGridMerge;
+          const int rank = before + __popc(m & ((1u << lane) - 1));
+          const int prank = __popc(pm & ((1u << lane) - 1));
+          if (defer) {
+            if (lv) pool[np + rank] = pe;
+            if (warp == 0 && plv) pool[prank] = pp;
+          } else {
+            if (lv) lnew[rank] = pe;
+            if (warp == 0 && plv) lnew[nl + prank] = pp;
+          }
+          if (tid == 0) {
+            misc[par] = defer ? 0 : nl + np;
+            misc[6] = defer ? nl + np : 0;
+            misc[12 + par] = cur ^ 1;
+            // nothing left anywhere: the compute warps stop here
+            if (!defer && nl + np == 0 && B == 0) misc[2] = j;
+          }
+        } else if (warp == 0) {
+          // a list longer than one entry per thread, a long pool, or a new
+          // t_stop: one warp compacts
+          int nl = 0;
+          for (int b0 = 0; b0 < Aold; b0 += 32) {
+            const int e = b0 + lane;
+            const int p = e < Aold ? lold[e] : 0;
+            const bool t = e < Aold && live(p, ts);
+            const unsigned mm = __ballot_sync(kFull, t);
+            if (t) lnew[nl + __popc(mm & ((1u << lane) - 1))] = p;
+            nl += __popc(mm);
+          }
           int np = 0;
-          for (int b0 = 0; b0 < ps; b0 += 32) {
+          for (int b0 = 0; b0 < ps; b0 += 32) {   // in place: writes never pass reads
             const int e = b0 + lane;
             const int p = e < ps ? pool[e] : 0;
             const bool t = e < ps && live(p, ts);
-            const unsigned m = __ballot_sync(kFull, t);
-            if (t) pool[np + __popc(m & ((1u << lane) - 1))] = p;
-            np += __popc(m);
+            const unsigned mm = __ballot_sync(kFull, t);
+            if (t) pool[np + __popc(mm & ((1u << lane) - 1))] = p;
+            np += __popc(mm);
           }
           __syncwarp();
-          const int B = misc[par ^ 1];   // phase j - 1: evaluated, not yet applied
           const bool defer = B > 0 && B + nl + np <= kGridMerge;
           int next = 0;
           if (defer) {
-            for (int e = lane; e < nl; e += 32) pool[np + e] = lst[e];
+            for (int e = lane; e < nl; e += 32) pool[np + e] = lnew[e];
             np += nl;
           } else {
-            for (int e = lane; e < np; e += 32) lst[nl + e] = pool[e];
+            for (int e = lane; e < np; e += 32) lnew[nl + e] = pool[e];
             next = nl + np;
             np = 0;
           }
@@ -521,52 +626,82 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
           if (lane == 0) {
             misc[par] = next;
             misc[6] = np;
-            if (next == 0 && B == 0 && np == 0) misc[2] = 1;   // nothing left anywhere
+            misc[12 + par] = cur ^ 1;
+            misc[14] = ts;
+            if (next == 0 && B == 0 && np == 0) misc[2] = j;
           }
         }
-        bar_sync(5, kComp);
-        if (misc[2]) {
-          bar_arrive(1 + par, kGridThreads);   // releases the comm warp, which then leaves
+        bar_sync(kBarComp, kComp);   // list j written
+        split(misc[par]);
+        for (int r = lane; r < cw; r += 32) ws[r] = lnew[aw + r];
+        __syncwarp();
+        const bool done = misc[2] != 0;
+        if (done) {
+          bar_arrive(kBarPass + par, kGridThreads);   // releases the comm warp, which then leaves
           break;
         }
       }
-      const int A = misc[par];
       if (A > 0) {
         unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
-        int m = (A + kGridCompWarps * RMAX - 1) / (kGridCompWarps * RMAX);
-        int R = (A + kGridCompWarps * m - 1) / (kGridCompWarps * m);
-        if (R < 1) R = 1;
-        const int groups = (A + R - 1) / R;
-        const int tasks = groups * n_sub;
-        for (int t = warp; t < tasks; t += kGridCompWarps) {
+        const bool chunked = A < kGridCompWarps;
+        const int mg = (cw + RMAX - 1) / RMAX;
+        const int R = mg > 0 ? (cw + mg - 1) / mg : 0;
+        const int nch = kGridCompWarps * n_sub;
+        unsigned long long* rem = remacc + (size_t)(par * kGridCompWarps + warp) * kGridRem * DA;
+        // one call site, so that the kernel holds one copy of each group
+        // size's code
+        for (int t = 0; t < mg * n_sub; ++t) {
           const int gi = t / n_sub, sb = t - gi * n_sub;
-          const int j0 = min(nc, sb * sub_len), j1 = min(nc, j0 + sub_len);
-          const int a0 = gi * R;
-          const int cnt = min(R, A - a0);
-          grid_task_r<D, DP, DA, KF, RES, RMAX>(R, RES ? spts : a.Xs + (size_t)cb * DP, j0, j1,
-                                                lane, lst, a0, cnt, sy, g, fx);
+          const int a0 = gi * R, cnt = min(R, cw - gi * R);
+          int j0, j1;
+          if (chunked) {
+            const int c = warp + kGridCompWarps * sb;
+            j0 = (int)((long long)c * nc / nch);
+            j1 = (int)((long long)(c + 1) * nc / nch);
+          } else {
+            j0 = min(nc, sb * sub_len);
+            j1 = min(nc, j0 + sub_len);
+          }
+          grid_task_r<D, DP, DA, KF, RES, RMAX>(
+              cnt, pts, j0, j1, lane, ws, a0, cnt, sy,
+              chunked ? rem + (size_t)a0 * DA : g + (size_t)(aw + a0) * DA,
+              chunked ? (sb == 0 ? 1 : 2) : 0, fx);
         }
         ++q;
       }
-      bar_arrive(1 + par, kGridThreads);   // pass j done
+      bar_arrive(kBarPass + par, kGridThreads);   // pass j done
     }
-  } else {
-    // ---- comm warp: publishes phase j, waits for every CTA's leaves and
-    // stages the totals in shared memory, while the compute warps run
-    // phase j + 1 ----
+  } else if (warp == kCommWarp) {
+    // ---- comm warp: publishes phase j (for a chunked list it first adds the
+    // compute warps' sums up; then the grid barrier), waits for every CTA's
+    // leaves and stages the
+    // totals in shared memory, while the compute warps run phase j + 1 ----
     int q = 0, prev_used = 0;
     unsigned long long evals = 0;
     for (int j = 0; j < max_phase; ++j) {
       const int par = j & 1;
-      bar_sync(1 + par, kGridThreads);   // leaves of phase j issued (or done)
-      if (*(volatile int*)(misc + 2)) break;
+      bar_sync(kBarPass + par, kGridThreads);   // leaves of phase j issued (or done)
+      const int stop = *(volatile int*)(misc + 2);
+      if (stop && j >= stop) break;
       const int A = misc[par];
       bool bad = false;
       if (A > 0) {
         const unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
+        if (A < kGridCompWarps) {
+          // a chunked phase: every compute warp stored its sums of the A seeds
+          const unsigned long long* rem = remacc + (size_t)par * kGridCompWarps * kGridRem * DA;
+          unsigned long long* gr = a.gacc + (size_t)(q % kGridBufs) * stride;
+          for (int e = lane; e < A * DA; e += 32) {
+            unsigned long long v = 0ull;
+#pragma unroll
+            for (int w = 0; w < kGridCompWarps; ++w) v += rem[(size_t)w * kGridRem * DA + e];
+            red_add_u64(gr + e, v);
+          }
+        }
+        __syncwarp();
+        __threadfence();
         int b = 0;
         if (lane == 0) {
-          __threadfence();
           red_release_add(a.gbar, 1u);
           const unsigned want = (unsigned)G * (unsigned)(q + 1);
           const long long t0 = clock64();
@@ -635,13 +770,34 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
             bad = true;
           }
         }
+        if (!bad) {
+          // each seed's update from its exact totals, in place: the entry's
+          // DA integers become the floats [W, S_0 / W, S_1 / W, ...]
+          unsigned long long* stg = stage + (size_t)par * stride;
+          for (int e = lane; e < A; e += 32) {
+            unsigned long long v[DA];
+#pragma unroll
+            for (int k = 0; k < DA; ++k) v[k] = stg[(size_t)e * DA + k];
+            asm volatile("" ::: "memory");   // every integer read before the floats overwrite them
+            float tot[DA];
+#pragma unroll
+            for (int k = 0; k < DA; ++k) tot[k] = __ll2float_rn((long long)v[k]) * inv_fx;
+            const float W = tot[0];
+            const float rW = W > 0.0f && isfinite(W) ? __frcp_rn(W) : 0.0f;
+            float* fo = reinterpret_cast<float*>(stg + (size_t)e * DA);
+            fo[0] = W;
+#pragma unroll
+            for (int k = 0; k < D; ++k) fo[1 + k] = tot[1 + k] * rW;
+          }
+          __syncwarp();
+        }
         evals += (unsigned long long)A * (unsigned long long)a.n;
         prev_used = A;
         ++q;
       }
       if (bad && lane == 0) misc[5] = 1;
       __syncwarp();
-      bar_arrive(3 + par, kGridThreads);   // totals of phase j staged
+      bar_arrive(kBarStaged + par, kGridThreads);   // totals of phase j staged
       if (bad) break;
     }
     if (cta == 0 && lane == 0 && evals) atomicAdd(a.evals, evals);
@@ -839,7 +995,7 @@ __global__ void __launch_bounds__(kGridRefineWarps * 32, 1)
         const int j0 = min(nc, sb * a.sub_len), j1 = min(nc, j0 + a.sub_len);
         const int a0 = gi * R;
         grid_task_r<D, DP, DA, KF, RES, RMAX>(R, pts, j0, j1, lane, alist, a0, min(R, A - a0),
-                                              sy, g, fx);
+                                              sy, g + (size_t)a0 * DA, 0, fx);
       }
     }
     __syncthreads();   // this CTA's leaves are issued

@@ -9,16 +9,13 @@
 // is (a group of seeds, a range of the slice); lane l takes the range's points
 // l, l + 32, ...; the 32 lane sums are combined by a fixed xor tree.  That
 // FP32 value -- the partial of one seed over one range -- is a leaf.  A list of
-// A >= 16 seeds is cut into 16 contiguous shares of A / 16 or A / 16 + 1
-// seeds, one per compute warp, each over whole sub-slices; the extra seeds go
-// to consecutive warps, which sit on different SM sub-partitions, so that the
-// issue load of every sub-partition is even.  A shorter list (the last,
-// latency-bound updates) is evaluated by every warp over its chunk of each
-// sub-slice.  Leaves are converted to 64-bit fixed point (2^F units, F chosen
-// so that no sum over all n points can overflow) and added exactly: directly
-// into the update's global accumulator (red.global.add.u64), or for a chunked
-// list first per warp in shared memory.  Integer addition is associative, so
-// the totals do
+// A seeds is cut into 16 contiguous shares of A / 16 or A / 16 + 1 seeds, one
+// per compute warp, each over whole sub-slices; the extra seeds go to
+// consecutive warps, which sit on different SM sub-partitions, so that the
+// issue load of every sub-partition is even.  Leaves are converted to 64-bit
+// fixed point (2^F units, F chosen so that no sum over all n points can
+// overflow) and added exactly into the update's global accumulator
+// (red.global.add.u64).  Integer addition is associative, so the totals do
 // not depend on which warp or CTA took which task or on the order of the
 // atomics; the only rounding is that of the leaves and of one conversion to
 // FP32 per total.  Four accumulators rotate.
@@ -50,8 +47,6 @@ constexpr int kGridCompWarps = 16;                  // warps that evaluate seeds
 constexpr int kCommWarp = kGridCompWarps;           // the exchange warp
 constexpr int kGridThreads = (kGridCompWarps + 1) * 32;
 constexpr int kComp = kGridCompWarps * 32;          // compute threads
-// Largest list that is evaluated in chunks (its sums pass through shared memory)
-constexpr int kGridRem = kGridCompWarps - 1;
 // Named barriers (0 is __syncthreads), one per parity where a phase passes
 // from the compute warps to the comm warp and back.
 constexpr int kBarPass = 1;     // compute -> comm: leaves of phase j issued
@@ -65,7 +60,7 @@ constexpr long long kGridSpinCycles = 4000000000LL;   // bound of one wait (~2 s
 // Shared memory carving (bytes), identical on host and device.
 struct GridSmem {
   int off_bar, off_misc, off_y, off_it, off_slot, off_act, off_w, off_conv, off_list, off_ws, off_hist,
-      off_stage, off_rem, off_pts;
+      off_stage, off_pts;
   int total;
 };
 
@@ -106,8 +101,6 @@ __host__ __device__ inline GridSmem grid_smem(int D, int DA, int DP, int pts) {
   o += kGridHist * 4;
   s.off_stage = o; // the staged totals of the last publication of each parity
   o += 2 * SC * DA * 8;
-  s.off_rem = o;   // a chunked phase's sums per compute warp, per parity
-  o += 2 * kGridCompWarps * kGridRem * DA * 8;
   s.off_pts = o;
   o += pts * DP * 4;
   s.total = o;
@@ -161,14 +154,13 @@ __device__ __forceinline__ float grid_rs32(float (&v)[32], int lane) {
 // per point): exact-difference form, acc[r][0] = sum w, acc[r][1 + k] =
 // sum w (x - y)_k.  The RR x DA sums are reduce-scattered over the warp in
 // blocks of 32 (lane l of block q holds accumulator 32 q + l), converted to
-// fixed point and added into dst[r * DA + k]: the update's global accumulator
-// (mode 0: red.global), or this warp's own sums in shared memory (mode 1:
-// store, the warp's first leaf of these seeds; mode 2: add).
+// fixed point and added into the update's global accumulator dst[r * DA + k]
+// (red.global).
 template <int D, int DP, int DA, int RR, int KF, bool RES>
 __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0, int j1, int lane,
                                           const int* __restrict__ alist, int a0, int cnt,
                                           const float* __restrict__ sy,
-                                          unsigned long long* dst, int mode, float fx) {
+                                          unsigned long long* dst, float fx) {
   constexpr int NV = (RR * DA + 31) / 32;
   float ys[RR][D];
 #pragma unroll
@@ -228,9 +220,7 @@ __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0,
     const int f = 32 * q + lane;
     if (f < cnt * DA) {
       const long long qv = __float2ll_rn(s * fx);
-      if (mode == 0) red_add_u64(dst + f, (unsigned long long)qv);
-      else if (mode == 1) dst[f] = (unsigned long long)qv;
-      else dst[f] += (unsigned long long)qv;
+      red_add_u64(dst + f, (unsigned long long)qv);
     }
   }
 }
@@ -238,13 +228,13 @@ __device__ __forceinline__ void grid_task(const float* __restrict__ pts, int j0,
 template <int D, int DP, int DA, int KF, bool RES, int RR>
 __device__ __forceinline__ void grid_task_r(int R, const float* pts, int j0, int j1, int lane,
                                             const int* alist, int a0, int cnt, const float* sy,
-                                            unsigned long long* dst, int mode, float fx) {
+                                            unsigned long long* dst, float fx) {
   if constexpr (RR >= 1) {
     if (R == RR) {
-      grid_task<D, DP, DA, RR, KF, RES>(pts, j0, j1, lane, alist, a0, cnt, sy, dst, mode, fx);
+      grid_task<D, DP, DA, RR, KF, RES>(pts, j0, j1, lane, alist, a0, cnt, sy, dst, fx);
       return;
     }
-    grid_task_r<D, DP, DA, KF, RES, RR - 1>(R, pts, j0, j1, lane, alist, a0, cnt, sy, dst, mode, fx);
+    grid_task_r<D, DP, DA, KF, RES, RR - 1>(R, pts, j0, j1, lane, alist, a0, cnt, sy, dst, fx);
   }
 }
 
@@ -280,7 +270,6 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
   int* wseeds = reinterpret_cast<int*>(smem + L.off_ws);
   int* hist_s = reinterpret_cast<int*>(smem + L.off_hist);
   unsigned long long* stage = reinterpret_cast<unsigned long long*>(smem + L.off_stage);
-  unsigned long long* remacc = reinterpret_cast<unsigned long long*>(smem + L.off_rem);
   float* spts = reinterpret_cast<float*>(smem + L.off_pts);
 
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
@@ -454,19 +443,16 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
     int q = 0;   // publications so far (non-empty phases)
     for (int j = 0; j < max_phase; ++j) {
       const int par = j & 1;
-      // Work split of a list of A seeds.  A >= 16: warp w takes a contiguous
-      // share of A / 16 seeds, one more for w < A mod 16 (consecutive warps
-      // sit on different SM sub-partitions, so the extra seeds spread over
-      // them), in groups of at most RMAX, each over every sub-slice.  A < 16
-      // (the last, latency-bound updates of a round): every warp takes all A
-      // seeds over its chunk of each sub-slice, and the CTA's sums go through
-      // shared memory.
+      // Work split of a list of A seeds: warp w takes a contiguous share of
+      // A / 16 seeds, one more for w < A mod 16 (consecutive warps sit on
+      // different SM sub-partitions, so the extra seeds spread over them), in
+      // groups of at most RMAX, each over every sub-slice.
       int A, cw, aw;
       auto split = [&](int A_) {
         A = A_;
         const int per = A / kGridCompWarps, ex = A - per * kGridCompWarps;
-        cw = A < kGridCompWarps ? A : per + (warp < ex ? 1 : 0);
-        aw = A < kGridCompWarps ? 0 : warp * per + min(warp, ex);
+        cw = per + (warp < ex ? 1 : 0);
+        aw = warp * per + min(warp, ex);
       };
       if (j < 2) {
         const int* l0 = lists + 2 * par * SC;
@@ -643,39 +629,25 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
       }
       if (A > 0) {
         unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
-        const bool chunked = A < kGridCompWarps;
         const int mg = (cw + RMAX - 1) / RMAX;
         const int R = mg > 0 ? (cw + mg - 1) / mg : 0;
-        const int nch = kGridCompWarps * n_sub;
-        unsigned long long* rem = remacc + (size_t)(par * kGridCompWarps + warp) * kGridRem * DA;
         // one call site, so that the kernel holds one copy of each group
         // size's code
         for (int t = 0; t < mg * n_sub; ++t) {
           const int gi = t / n_sub, sb = t - gi * n_sub;
           const int a0 = gi * R, cnt = min(R, cw - gi * R);
-          int j0, j1;
-          if (chunked) {
-            const int c = warp + kGridCompWarps * sb;
-            j0 = (int)((long long)c * nc / nch);
-            j1 = (int)((long long)(c + 1) * nc / nch);
-          } else {
-            j0 = min(nc, sb * sub_len);
-            j1 = min(nc, j0 + sub_len);
-          }
-          grid_task_r<D, DP, DA, KF, RES, RMAX>(
-              cnt, pts, j0, j1, lane, ws, a0, cnt, sy,
-              chunked ? rem + (size_t)a0 * DA : g + (size_t)(aw + a0) * DA,
-              chunked ? (sb == 0 ? 1 : 2) : 0, fx);
+          const int j0 = min(nc, sb * sub_len), j1 = min(nc, j0 + sub_len);
+          grid_task_r<D, DP, DA, KF, RES, RMAX>(cnt, pts, j0, j1, lane, ws, a0, cnt, sy,
+                                                g + (size_t)(aw + a0) * DA, fx);
         }
         ++q;
       }
       bar_arrive(kBarPass + par, kGridThreads);   // pass j done
     }
   } else if (warp == kCommWarp) {
-    // ---- comm warp: publishes phase j (for a chunked list it first adds the
-    // compute warps' sums up; then the grid barrier), waits for every CTA's
-    // leaves and stages the
-    // totals in shared memory, while the compute warps run phase j + 1 ----
+    // ---- comm warp: publishes phase j (the grid barrier), waits for every
+    // CTA's leaves, stages the totals in shared memory and turns them into
+    // updates, while the compute warps run phase j + 1 ----
     int q = 0, prev_used = 0;
     unsigned long long evals = 0;
     for (int j = 0; j < max_phase; ++j) {
@@ -687,18 +659,6 @@ __global__ void __launch_bounds__(kGridThreads, 1) ms_grid_round_kernel(const Gr
       bool bad = false;
       if (A > 0) {
         const unsigned long long* g = a.gacc + (size_t)(q % kGridBufs) * stride;
-        if (A < kGridCompWarps) {
-          // a chunked phase: every compute warp stored its sums of the A seeds
-          const unsigned long long* rem = remacc + (size_t)par * kGridCompWarps * kGridRem * DA;
-          unsigned long long* gr = a.gacc + (size_t)(q % kGridBufs) * stride;
-          for (int e = lane; e < A * DA; e += 32) {
-            unsigned long long v = 0ull;
-#pragma unroll
-            for (int w = 0; w < kGridCompWarps; ++w) v += rem[(size_t)w * kGridRem * DA + e];
-            red_add_u64(gr + e, v);
-          }
-        }
-        __syncwarp();
         __threadfence();
         int b = 0;
         if (lane == 0) {
@@ -995,7 +955,7 @@ __global__ void __launch_bounds__(kGridRefineWarps * 32, 1)
         const int j0 = min(nc, sb * a.sub_len), j1 = min(nc, j0 + a.sub_len);
         const int a0 = gi * R;
         grid_task_r<D, DP, DA, KF, RES, RMAX>(R, pts, j0, j1, lane, alist, a0, min(R, A - a0),
-                                              sy, g + (size_t)a0 * DA, 0, fx);
+                                              sy, g + (size_t)a0 * DA, fx);
       }
     }
     __syncthreads();   // this CTA's leaves are issued

@@ -407,7 +407,6 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
   std::vector<int> tc_slot;
   cudaEvent_t phase_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double phase_acc[4] = {0, 0, 0, 0};
-  int64_t round_evals_total = 0;
   IterCtl hctl{}, hrctl{};
   MergeCtl hm{};
   uint32_t hstatus = 0;

@@ -22,13 +22,14 @@
 //
 // Roles and pipeline.  Phases alternate between two seed lists.  While 16
 // compute warps evaluate list j, the comm warp publishes phase j - 1 (one grid
-// barrier: a release-add on a counter, an acquire poll, both bounded) and
-// stages its totals in shared memory with one bulk copy; two service warps
-// then apply them to list j - 1's seeds (the same update in every CTA's
-// replicated copy of the round's seed state) and build list j + 1.  Named
-// barriers pass each phase from role to role, so the compute warps wait only
-// for a list whose update is complete.  CTA 0 writes
-// the seed state back to global memory.
+// barrier: a release-add on a counter, an acquire poll, both bounded), stages
+// its totals in shared memory with one bulk copy and turns each seed's
+// integer totals into the float update [W, S / W].  At the start of phase j + 1
+// the compute warps apply those updates to list j - 1's seeds (the same update
+// in every CTA's replicated copy of the round's seed state), ballot which stay
+// live and, behind two barriers, write and read list j + 1.  Named barriers
+// pass each phase between the roles.  CTA 0 writes the seed state back to
+// global memory.
 //
 // Early Stopping.  Every CTA keeps the convergence histogram of all seeds of
 // all rounds; after each update it finds t_stop, the first update count whose

@@ -245,3 +245,21 @@ def test_errors():
     res = fms.cluster(torch.from_numpy(w.X).cuda(), w.h, max_modes=2)
     assert res.status == fms.FMS_ERR_CAPACITY and res.stats["n_modes"] == 4
     assert res.modes.shape[0] == 2
+
+
+# The grid round's list handling at other list sizes than the default 128
+# seeds: single short lists from the start (8 seeds: one seed per warp on the
+# first warps), lists that merge into one (24, 40), several seed groups per
+# warp (600 seeds: lists of 300, 18-19 seeds per warp), and other stop
+# fractions (a t_stop that changes mid-round takes the serial compaction).
+@pytest.mark.parametrize("n_initial,gamma", [(8, 0.95), (24, 0.9), (40, 0.99), (600, 0.95),
+                                             (600, 0.8)])
+def test_grid_round_list_sizes(n_initial, gamma):
+    w = fi.paper_3d(n=40_000)
+    res = _run(w, gamma=gamma, rng_seed=11, n_initial=n_initial)
+    ref = orc.cluster(w.X, w.h, w.tol, w.max_iter, gamma=gamma, rng_seed=11, n_initial=n_initial)
+    _check(w, res, ref)
+    assert res.stats["n_seeds_final"] == ref.n_seeds
+    assert res.stats["rounds"] == len(ref.n_history)
+    assert res.stats["t_star_last"] == ref.t_star[-1]
+    assert res.stats["n_kept"] == int(ref.kept.sum())

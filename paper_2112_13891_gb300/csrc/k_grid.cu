@@ -54,7 +54,7 @@ constexpr int kBarPass = 1;     // compute -> comm: leaves of phase j issued
 constexpr int kBarStaged = 3;   // comm -> compute: totals of phase j staged
 constexpr int kBarComp = 5;     // among the compute warps
 constexpr int kGridBufs = 4;                        // accumulators in rotation
-constexpr int kGridMerge = 48;   // at most this many active seeds: one list per update
+constexpr int kGridMerge = 32;   // at most this many active seeds: one list per update
 constexpr int kGridSubLen = 2048;                // longest sub-slice (points)
 constexpr long long kGridSpinCycles = 4000000000LL;   // bound of one wait (~2 s)
 

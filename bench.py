@@ -379,7 +379,9 @@ def bench_fms(args):
                                                prof["phase"])}
 
     # --- end to end through the C ABI with host buffers (fms_cluster_host:
-    # the points uploaded, the labels and modes copied back, in one call) ---
+    # the points uploaded, the labels and modes copied back, in one call; the
+    # buffers are page-locked, so the call's kernels read the points and write
+    # the labels over the CPU-GPU link themselves, inside the timed region) ---
     cap_h = 256
     Xh = torch.from_numpy(w.X).pin_memory()
     lab_h = torch.empty(n, dtype=torch.int32).pin_memory()

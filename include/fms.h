@@ -235,7 +235,10 @@ fms_status fms_cluster(const float* points, int64_t n, int32_t d, float h, float
  *                clustering workspace and device copies of the inputs and
  *                outputs); NULL -> allocated with cudaMallocAsync and freed.
  * The host output buffers are written when the call returns FMS_OK or
- * FMS_ERR_CAPACITY.
+ * FMS_ERR_CAPACITY.  Page-locked (pinned) host buffers are used in place: the
+ * packing and label kernels read the points and write the labels and margins
+ * through their mapped addresses instead of staging copies (after an error
+ * such buffers may hold partial results); pageable buffers are copied.
  */
 size_t fms_cluster_host_workspace_size(int64_t n, int32_t d, int32_t max_modes,
                                        const fms_options* opt);

@@ -1087,20 +1087,36 @@ fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, 
     if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) return FMS_ERR_CUDA;
     owns = true;
   }
+  // Page-locked host buffers are addressable by the kernels (over the CPU-GPU
+  // link): the packing and label kernels then read the points and write the
+  // labels and margins there directly instead of through staging copies.
+  auto mapped = [](const void* p) -> void* {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  };
+  const float* mpoints = static_cast<const float*>(mapped(points));
+  int32_t* mlabels = static_cast<int32_t*>(mapped(out_labels));
+  float* mmargins = out_margins ? static_cast<float*>(mapped(out_margins)) : nullptr;
   float* dpoints = at<float>(ws, L.off_points);
-  int32_t* dlabels = at<int32_t>(ws, L.off_labels);
-  float* dmargins = out_margins ? at<float>(ws, L.off_margins) : nullptr;
+  int32_t* dlabels = mlabels ? mlabels : at<int32_t>(ws, L.off_labels);
+  float* dmargins = out_margins ? (mmargins ? mmargins : at<float>(ws, L.off_margins)) : nullptr;
   float* dmodes = at<float>(ws, L.off_modes);
   fms_status rc = FMS_OK;
-  if (cudaMemcpyAsync(dpoints, points, (size_t)n * d * 4, cudaMemcpyHostToDevice, st) !=
-      cudaSuccess) {
+  if (!mpoints && cudaMemcpyAsync(dpoints, points, (size_t)n * d * 4, cudaMemcpyHostToDevice,
+                                  st) != cudaSuccess) {
     rc = FMS_ERR_CUDA;
   } else {
     HostCopies hc{};
-    hc.dst[hc.count] = out_labels;
-    hc.src[hc.count] = dlabels;
-    hc.bytes[hc.count++] = (size_t)n * 4;
-    if (out_margins) {
+    if (!mlabels) {
+      hc.dst[hc.count] = out_labels;
+      hc.src[hc.count] = dlabels;
+      hc.bytes[hc.count++] = (size_t)n * 4;
+    }
+    if (out_margins && !mmargins) {
       hc.dst[hc.count] = out_margins;
       hc.src[hc.count] = dmargins;
       hc.bytes[hc.count++] = (size_t)n * 4;
@@ -1110,7 +1126,8 @@ fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, 
       hc.src[hc.count] = dmodes;
       hc.bytes[hc.count++] = (size_t)max_modes * d * 4;
     }
-    rc = cluster_impl(dpoints, n, d, h, tol, max_iter, opt, max_modes > 0 ? dmodes : nullptr,
+    rc = cluster_impl(mpoints ? mpoints : dpoints, n, d, h, tol, max_iter, opt,
+                      max_modes > 0 ? dmodes : nullptr,
                       max_modes, out_n_modes, dlabels, dmargins, ws, L.cluster, stats, stream_,
                       &hc);
   }

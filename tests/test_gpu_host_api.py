@@ -1,10 +1,12 @@
 """fms_cluster_host: the clustering with host input and output buffers.
 
-The call uploads the points into its workspace, runs fms_cluster's path and
-queues the copy-backs before its final synchronisation.  It must give the
-same bits as fms_cluster on device buffers (same kernels, same arguments),
-take the CUDA-graph form on repeated calls, honour max_modes and work with
-pageable as well as page-locked host memory.
+The call uploads pageable points into its workspace (page-locked ones are
+read in place by the kernels), runs fms_cluster's path and queues the
+copy-backs of pageable outputs before its final synchronisation (page-locked
+ones are written in place).  It must give the same bits as fms_cluster on
+device buffers (same kernels, same arguments), take the CUDA-graph form on
+repeated calls, honour max_modes and give the same bits with pageable and
+page-locked host memory.
 """
 import ctypes
 
@@ -69,6 +71,27 @@ def test_capacity_and_pageable_buffers():
     assert cut.stats["n_modes"] == 5
     assert torch.equal(cut.modes, full.modes[:2])
     assert torch.equal(labels, full.labels)
+
+
+def test_pageable_and_page_locked_buffers_give_the_same_bits():
+    w = fi.paper_3d(n=30_000)
+    Xp = torch.from_numpy(w.X)                       # pageable: copied in and out
+    Xl = Xp.pin_memory()                             # page-locked: used in place
+    n, d = Xp.shape
+    outs = []
+    for X, pin in ((Xp, False), (Xl, True)):
+        modes = torch.empty((64, d))
+        labels = torch.full((n,), -5, dtype=torch.int32)
+        margins = torch.full((n,), float("nan"))
+        if pin:
+            modes, labels, margins = modes.pin_memory(), labels.pin_memory(), margins.pin_memory()
+        r = fms.cluster_host(X, w.h, w.tol, w.max_iter, gamma=0.95, rng_seed=4,
+                             out=(modes, labels, margins))
+        assert r.status == fms.FMS_OK
+        outs.append((r.modes.clone(), labels.clone(), margins.clone()))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    assert (outs[1][1] >= 0).all()
 
 
 def test_host_call_argument_errors():

@@ -86,6 +86,7 @@ static_assert(kCtlRoundOff + sizeof(RoundCtl) <= kCtlBlockBytes, "control region
 // ---------------------------------------------------------------------------
 struct GraphKey {
   const void* points;
+  const void* points_copy;
   const void* modes;
   const void* labels;
   const void* margins;
@@ -347,6 +348,9 @@ struct HostCopies {
   void* dst[3];
   const void* src[3];
   size_t bytes[3];
+  // non-null: the points are read from host memory; the packing kernel also
+  // copies them here and the label kernel reads this copy
+  float* points_copy;
 };
 
 static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float h, float tol,
@@ -372,6 +376,10 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
                                fms_stats* stats, void* stream_, const HostCopies* hc) {
   fms_status rc = FMS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  // points in host memory: the packing kernel also copies them to pcopy, and
+  // the label kernel reads that copy
+  float* pcopy = hc ? hc->points_copy : nullptr;
+  const float* lpoints = pcopy ? pcopy : points;
   fms_options o;
   fill_defaults(opt_in, &o);
   if (stats) memset(stats, 0, sizeof(*stats));
@@ -597,6 +605,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
       GraphKey key;
       memset(&key, 0, sizeof(key));
       key.points = points;
+      key.points_copy = hc ? hc->points_copy : nullptr;
       key.modes = out_modes;
       key.labels = out_labels;
       key.margins = out_margins;
@@ -648,7 +657,8 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
         if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, kCtlBlockBytes, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)(kHistCap + 2) * 4, cs);
         if (e == cudaSuccess)
-          e = launch_pack_points(points, n, d, DP, (float)scale, Xs, status, cs, cosine ? 1 : 0);
+          e = launch_pack_points(points, n, d, DP, (float)scale, Xs, status, cs, cosine ? 1 : 0,
+                                 pcopy);
         if (e == cudaSuccess)
           e = launch_seed_init(Xs, n, DP, o.rng_seed, nullptr, 0, 0, N0, seed_idx, y, it, conv,
                                state, status, cs, init_state);
@@ -712,7 +722,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
                                         out_modes, max_modes, modes_full, nullptr, cap_modes,
                                         cs2);
           if (e2 == cudaSuccess)
-            e2 = launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins,
+            e2 = launch_label(lpoints, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins,
                               cs2, cosine ? 1 : 0);
           cudaGraph_t gp = post;
           const cudaError_t e3 = cudaStreamEndCapture(cs2, &gp);
@@ -777,7 +787,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     if (resume == 0) {
       mark(0);
       FMS_LAUNCH(launch_pack_points(points, n, d, DP, (float)scale, Xs, status, st,
-                                    cosine ? 1 : 0));
+                                    cosine ? 1 : 0, pcopy));
       if (tensor) FMS_LAUNCH(launch_tc_pack(Xs, n, d, DP, img, st));
       N = N0;
       FMS_LAUNCH(launch_seed_init(Xs, n, DP, o.rng_seed, o.seed_indices, 0, 0, N, seed_idx, y,
@@ -935,7 +945,7 @@ static fms_status cluster_impl(const float* points, int64_t n, int32_t d, float 
     }
     // --- labels (the labelling of Alg. 2) ---
     mark(3);
-    FMS_LAUNCH(launch_label(points, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st,
+    FMS_LAUNCH(launch_label(lpoints, n, d, modes_full, &mctl->Mr, 0, out_labels, out_margins, st,
                             cosine ? 1 : 0));
     mark(4);
     hslog.assign(n_slog, 0);
@@ -1111,6 +1121,7 @@ fms_status fms_cluster_host(const float* points, int64_t n, int32_t d, float h, 
     rc = FMS_ERR_CUDA;
   } else {
     HostCopies hc{};
+    hc.points_copy = mpoints ? dpoints : nullptr;
     if (!mlabels) {
       hc.dst[hc.count] = out_labels;
       hc.src[hc.count] = dlabels;

@@ -324,7 +324,8 @@ __device__ inline int block_min(int v, int* red) {
 // k_iter.cu
 // unit != 0 (cosine metric): each row normalised to unit length first
 cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
-                               uint32_t* status, cudaStream_t st, int unit = 0);
+                               uint32_t* status, cudaStream_t st, int unit = 0,
+                               float* Xcopy = nullptr);
 cudaError_t launch_seed_init(const float* Xs, int64_t n, int DP, uint64_t rng_seed,
                              const int32_t* explicit_idx, int64_t rank0, int32_t slot0,
                              int32_t count, int32_t* seed_idx, float* y, int32_t* it,

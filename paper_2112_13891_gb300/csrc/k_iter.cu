@@ -7,9 +7,12 @@ namespace fms {
 
 // ---------------------------------------------------------------------------
 // Packing: Xs = s * X, padded to DP floats per row; flags non-finite input.
+// Xcopy (nullable) receives the rows unchanged, for later passes over the
+// original points (X may be host memory read over the CPU-GPU link).
 // ---------------------------------------------------------------------------
 __global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d, int DP,
-                                   float scale, float* __restrict__ Xs, uint32_t* status) {
+                                   float scale, float* __restrict__ Xs, uint32_t* status,
+                                   float* __restrict__ Xcopy) {
   const int64_t total = n * DP;
   bool bad = false;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -19,6 +22,7 @@ __global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d
     float v = 0.0f;
     if (k < d) {
       v = X[j * d + k];
+      if (Xcopy) Xcopy[j * d + k] = v;
       if (!isfinite(v)) bad = true;
       v *= scale;
     }
@@ -30,7 +34,8 @@ __global__ void pack_points_kernel(const float* __restrict__ X, int64_t n, int d
 // DP = 4 or 8: one thread per point, the padded row written with vector stores
 template <int DP>
 __global__ void pack_rows_kernel(const float* __restrict__ X, int n, int d, float scale,
-                                 float* __restrict__ Xs, uint32_t* status) {
+                                 float* __restrict__ Xs, uint32_t* status,
+                                 float* __restrict__ Xcopy) {
   bool bad = false;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     float v[DP];
@@ -39,6 +44,7 @@ __global__ void pack_rows_kernel(const float* __restrict__ X, int n, int d, floa
       v[k] = 0.0f;
       if (k < d) {
         const float x = X[(int64_t)j * d + k];
+        if (Xcopy) Xcopy[(int64_t)j * d + k] = x;
         if (!isfinite(x)) bad = true;
         v[k] = x * scale;
       }
@@ -53,13 +59,15 @@ __global__ void pack_rows_kernel(const float* __restrict__ X, int n, int d, floa
 // Cosine metric: row j scaled to unit length, then by s; a zero row flags
 // kStBadArg (it has no direction), a non-finite one kStNonFinite.
 __global__ void pack_unit_rows_kernel(const float* __restrict__ X, int64_t n, int d, int DP,
-                                      float scale, float* __restrict__ Xs, uint32_t* status) {
+                                      float scale, float* __restrict__ Xs, uint32_t* status,
+                                      float* __restrict__ Xcopy) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     double nn = 0.0;
     bool bad = false;
     for (int k = 0; k < d; ++k) {
       const float v = X[j * d + k];
+      if (Xcopy) Xcopy[j * d + k] = v;
       if (!isfinite(v)) bad = true;
       nn += (double)v * (double)v;
     }
@@ -71,27 +79,27 @@ __global__ void pack_unit_rows_kernel(const float* __restrict__ X, int64_t n, in
 }
 
 cudaError_t launch_pack_points(const float* X, int64_t n, int d, int DP, float scale, float* Xs,
-                               uint32_t* status, cudaStream_t st, int unit) {
+                               uint32_t* status, cudaStream_t st, int unit, float* Xcopy) {
   if (unit) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    pack_unit_rows_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status);
+    pack_unit_rows_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status, Xcopy);
     return cudaGetLastError();
   }
   if ((DP == 4 || DP == 8) && n <= INT32_MAX && (reinterpret_cast<uintptr_t>(Xs) & 15) == 0) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (DP == 4)
-      pack_rows_kernel<4><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status);
+      pack_rows_kernel<4><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status, Xcopy);
     else
-      pack_rows_kernel<8><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status);
+      pack_rows_kernel<8><<<(int)blocks, 256, 0, st>>>(X, (int)n, d, scale, Xs, status, Xcopy);
     return cudaGetLastError();
   }
   int64_t total = n * DP;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  pack_points_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status);
+  pack_points_kernel<<<(int)blocks, 256, 0, st>>>(X, n, d, DP, scale, Xs, status, Xcopy);
   return cudaGetLastError();
 }
 
